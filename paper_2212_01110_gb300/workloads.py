@@ -1,0 +1,275 @@
+"""Seeded synthetic RAOCP instances (inputs only, no solver arithmetic).
+
+Every generator returns a plain dict of numpy arrays in *user* node order
+(which here is already stage-major breadth-first order):
+
+    anc     int32[n]        ancestor of each node, anc[0] = -1
+    prob    float64[n]      conditional probability of reaching node i from
+                            anc(i); prob[0] = 1
+    nx, nu  int
+    A       float64[n,nx,nx]  dynamics of the edge into node i (A[0] unused)
+    B       float64[n,nx,nu]
+    Q       float64[n,nx]   diagonal of Q^i, cost weight on the edge into i
+    R       float64[n,nu]   diagonal of R^i
+    QN      float64[n,nx]   diagonal of the terminal weight (read at leaves)
+    a       float64[n]      AV@R parameter of each nonleaf node, in [0, 1]
+    xmin, xmax float64[n,nx]; umin, umax float64[n,nu]   box constraints
+    x0      float64[nx]     initial state
+
+The tree shapes, distributions and sizes follow the workloads described for
+SPOCK (scenario trees with stage-wise branching, Sec. "Scenario trees"; the
+data-center system of Eq. (dynamics-example)).  Random draws use
+``numpy.random.default_rng(seed)``.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+# ----------------------------------------------------------------------------
+# tree shapes
+# ----------------------------------------------------------------------------
+
+def tree_from_branching(branching):
+    """Stage-wise branching factors -> (anc, stage).
+
+    ``branching[t]`` is the number of children of every node at stage t, so
+    the horizon is N = len(branching) and leaves sit at stage N.  Nodes are
+    numbered breadth first, children of a node contiguous.
+    """
+    anc = [-1]
+    stage = [0]
+    frontier = [0]
+    for t, b in enumerate(branching):
+        nxt = []
+        for parent in frontier:
+            for _ in range(int(b)):
+                anc.append(parent)
+                stage.append(t + 1)
+                nxt.append(len(anc) - 1)
+        frontier = nxt
+    return np.asarray(anc, np.int32), np.asarray(stage, np.int32)
+
+
+def _children_counts(anc):
+    n = len(anc)
+    cnt = np.zeros(n, np.int64)
+    np.add.at(cnt, anc[1:], 1)
+    return cnt
+
+
+def _conditional_probs(rng, anc, kind):
+    """Conditional child probabilities; kind in {'uniform', 'dirichlet'} or a
+    fixed tuple used for every parent with that many children."""
+    n = len(anc)
+    prob = np.zeros(n)
+    prob[0] = 1.0
+    cnt = _children_counts(anc)
+    start = 1
+    # children are contiguous in breadth-first numbering
+    for parent in range(n):
+        m = int(cnt[parent])
+        if m == 0:
+            continue
+        idx = np.arange(start, start + m)
+        assert np.all(anc[idx] == parent)
+        if m == 1:
+            p = np.ones(1)
+        elif isinstance(kind, tuple):
+            p = np.asarray(kind, float)
+            assert len(p) == m
+        elif kind == "uniform":
+            p = np.full(m, 1.0 / m)
+        elif kind == "dirichlet":
+            p = rng.dirichlet(np.ones(m))
+            p = np.maximum(p, 1e-3)
+            p = p / p.sum()
+        else:
+            raise ValueError(kind)
+        prob[idx] = p
+        start += m
+    return prob
+
+
+def _haar_orthogonal(rng, count, n):
+    g = rng.standard_normal((count, n, n))
+    q, r = np.linalg.qr(g)
+    d = np.sign(np.diagonal(r, axis1=1, axis2=2))
+    d[d == 0] = 1.0
+    return q * d[:, None, :]
+
+
+def _box(n, dim, lim):
+    lo = np.full((n, dim), -float(lim))
+    return lo, -lo
+
+
+def _draw_x0(rng, nx, xlim):
+    while True:
+        x0 = rng.standard_normal(nx)
+        if np.max(np.abs(x0)) <= xlim:
+            return x0
+
+
+# ----------------------------------------------------------------------------
+# workloads
+# ----------------------------------------------------------------------------
+
+def small_binary(seed=0, N=3, nx=3, nu=2, a=0.5):
+    """Binary tree of horizon N (N=3: 15 nodes, 8 leaves), uniform child
+    probabilities, A = I + 0.1 N(0,1), B ~ N(0,1), Q = I, R = 0.1 I, Q_N = I,
+    AV@R parameter ``a`` at every nonleaf node, |x| <= 5, |u| <= 1,
+    x0 ~ N(0,1) redrawn until inside the box."""
+    rng = np.random.default_rng(seed)
+    anc, _ = tree_from_branching([2] * N)
+    n = len(anc)
+    prob = _conditional_probs(rng, anc, "uniform")
+    A = np.eye(nx)[None] + 0.1 * rng.standard_normal((n, nx, nx))
+    B = rng.standard_normal((n, nx, nu))
+    A[0] = 0.0
+    B[0] = 0.0
+    Q = np.ones((n, nx))
+    R = np.full((n, nu), 0.1)
+    QN = np.ones((n, nx))
+    av = np.full(n, float(a))
+    xmin, xmax = _box(n, nx, 5.0)
+    umin, umax = _box(n, nu, 1.0)
+    x0 = _draw_x0(rng, nx, 5.0)
+    return dict(anc=anc, prob=prob, nx=nx, nu=nu, A=A, B=B, Q=Q, R=R, QN=QN,
+                a=av, xmin=xmin, xmax=xmax, umin=umin, umax=umax, x0=x0)
+
+
+def large_tree(seed=0, branching_stages=6, branch=4, N=20, nx=50, nu=20,
+               xlim=5.0, ulim=1.0):
+    """Branching ``branch`` for the first ``branching_stages`` stages, then one
+    child per node, horizon N (defaults: 62,805 nodes, 58,709 nonleaf, 4,096
+    scenarios, about 4.3 M state/input variables).  A = 0.95 U with U
+    Haar-orthogonal (spectral radius 0.95), B ~ N(0, 1/nx), Q = diag U(0.5, 2),
+    R = 0.1 I, Q_N = I, AV@R parameter U(0.1, 0.9) per nonleaf node,
+    Dirichlet(1) child probabilities, |x| <= xlim, |u| <= ulim, x0 ~ N(0,1)."""
+    rng = np.random.default_rng(seed)
+    branching = [branch] * branching_stages + [1] * (N - branching_stages)
+    anc, _ = tree_from_branching(branching)
+    n = len(anc)
+    prob = _conditional_probs(rng, anc, "dirichlet")
+    A = 0.95 * _haar_orthogonal(rng, n, nx)
+    B = rng.standard_normal((n, nx, nu)) / np.sqrt(nx)
+    A[0] = 0.0
+    B[0] = 0.0
+    Q = rng.uniform(0.5, 2.0, size=(n, nx))
+    R = np.full((n, nu), 0.1)
+    QN = np.ones((n, nx))
+    av = rng.uniform(0.1, 0.9, size=n)
+    xmin, xmax = _box(n, nx, xlim)
+    umin, umax = _box(n, nu, ulim)
+    x0 = _draw_x0(rng, nx, xlim)
+    return dict(anc=anc, prob=prob, nx=nx, nu=nu, A=A, B=B, Q=Q, R=R, QN=QN,
+                a=av, xmin=xmin, xmax=xmax, umin=umin, umax=umax, x0=x0)
+
+
+def random_tree(seed=0, N=3, max_branch=3, nx=4, nu=2, chain_after=None,
+                a_range=(0.0, 1.0), box=(5.0, 1.0), stable=False):
+    """Ragged random tree: every nonleaf node draws its own number of
+    children in 1..max_branch (optionally one child from stage
+    ``chain_after`` on); Dirichlet child probabilities; Gaussian data."""
+    rng = np.random.default_rng(seed)
+    anc = [-1]
+    frontier = [0]
+    for t in range(N):
+        nxt = []
+        for parent in frontier:
+            m = 1 if (chain_after is not None and t >= chain_after) else int(rng.integers(1, max_branch + 1))
+            for _ in range(m):
+                anc.append(parent)
+                nxt.append(len(anc) - 1)
+        frontier = nxt
+    anc = np.asarray(anc, np.int32)
+    n = len(anc)
+    prob = _conditional_probs(rng, anc, "dirichlet")
+    if stable:
+        A = 0.95 * _haar_orthogonal(rng, n, nx)
+    else:
+        A = np.eye(nx)[None] + 0.1 * rng.standard_normal((n, nx, nx))
+    B = rng.standard_normal((n, nx, nu)) / np.sqrt(nx)
+    A[0] = 0.0
+    B[0] = 0.0
+    Q = rng.uniform(0.5, 2.0, size=(n, nx))
+    R = rng.uniform(0.05, 0.5, size=(n, nu))
+    QN = rng.uniform(0.5, 2.0, size=(n, nx))
+    av = rng.uniform(a_range[0], a_range[1], size=n)
+    xmin, xmax = _box(n, nx, box[0])
+    umin, umax = _box(n, nu, box[1])
+    x0 = _draw_x0(rng, nx, box[0])
+    return dict(anc=anc, prob=prob, nx=nx, nu=nu, A=A, B=B, Q=Q, R=R, QN=QN,
+                a=av, xmin=xmin, xmax=xmax, umin=umin, umax=umax, x0=x0)
+
+
+def datacenter(N=7, nx=5, nu=None, d=2, probs=(0.3, 0.7), a=0.95):
+    """The data-center thermal system of Eq. (dynamics-example): tridiagonal
+    A(w) with diagonal 1 + (w-1)/d (1 + (j-1)/nx) and off-diagonals 0.01,
+    B = I, d disturbance values with conditional probabilities ``probs``,
+    Q = Q_N = I, R = 10 I, |x| <= 1, |u| <= 1.5, AV@R_a at every node,
+    x0 = 0.1 * 1."""
+    nu = nx if nu is None else nu
+    anc, _ = tree_from_branching([d] * N)
+    n = len(anc)
+    prob = _conditional_probs(None, anc, tuple(probs))
+    A = np.zeros((n, nx, nx))
+    B = np.zeros((n, nx, nu))
+    cnt = _children_counts(anc)
+    # child index w (1-based) within its sibling group
+    w_of = np.zeros(n, np.int64)
+    start = 1
+    for parent in range(n):
+        for w in range(int(cnt[parent])):
+            w_of[start + w] = w + 1
+        start += int(cnt[parent])
+    j = np.arange(1, nx + 1)
+    for i in range(1, n):
+        w = w_of[i]
+        Ai = np.diag(1.0 + (w - 1) / d * (1.0 + (j - 1) / nx))
+        Ai += np.diag(np.full(nx - 1, 0.01), 1) + np.diag(np.full(nx - 1, 0.01), -1)
+        A[i] = Ai
+        B[i] = np.eye(nx, nu)
+    Q = np.ones((n, nx))
+    R = np.full((n, nu), 10.0)
+    QN = np.ones((n, nx))
+    av = np.full(n, float(a))
+    xmin, xmax = _box(n, nx, 1.0)
+    umin, umax = _box(n, nu, 1.5)
+    x0 = np.full(nx, 0.1)
+    return dict(anc=anc, prob=prob, nx=nx, nu=nu, A=A, B=B, Q=Q, R=R, QN=QN,
+                a=av, xmin=xmin, xmax=xmax, umin=umin, umax=umax, x0=x0)
+
+
+def fig1_tree():
+    """The 9-node scenario tree drawn in Fig. 1 (node 1 has children {3,4},
+    node 2 has children {5,6,7,8})."""
+    return np.asarray([-1, 0, 0, 1, 1, 2, 2, 2, 2], np.int32)
+
+
+def with_tree(anc, seed=0, nx=3, nu=2, a=0.5, box=(5.0, 1.0)):
+    """Gaussian data (as ``small_binary``) on a given tree."""
+    rng = np.random.default_rng(seed)
+    anc = np.asarray(anc, np.int32)
+    n = len(anc)
+    prob = _conditional_probs(rng, anc, "dirichlet")
+    A = np.eye(nx)[None] + 0.1 * rng.standard_normal((n, nx, nx))
+    B = rng.standard_normal((n, nx, nu))
+    A[0] = 0.0
+    B[0] = 0.0
+    Q = rng.uniform(0.5, 2.0, size=(n, nx))
+    R = rng.uniform(0.05, 0.5, size=(n, nu))
+    QN = rng.uniform(0.5, 2.0, size=(n, nx))
+    av = np.full(n, float(a))
+    xmin, xmax = _box(n, nx, box[0])
+    umin, umax = _box(n, nu, box[1])
+    x0 = _draw_x0(rng, nx, box[0])
+    return dict(anc=anc, prob=prob, nx=nx, nu=nu, A=A, B=B, Q=Q, R=R, QN=QN,
+                a=av, xmin=xmin, xmax=xmax, umin=umin, umax=umax, x0=x0)
+
+
+def random_vectors(n_z, n_eta, seed=0, scale=1.0):
+    """Seeded test points (z, eta) for operator-level comparisons."""
+    rng = np.random.default_rng(seed)
+    return scale * rng.standard_normal(n_z), scale * rng.standard_normal(n_eta)
