@@ -1,0 +1,230 @@
+/*
+ * spock.h -- C ABI of the GB300 SPOCK library (libspock.so).
+ *
+ * SPOCK solves the multistage risk-averse optimal control problem (RAOCP)
+ * of arXiv 2212.01110 on a scenario tree: the Chambolle-Pock (CP) operator
+ * T of Eq. (chambolle-pock-operator) applied to the splitting
+ * min f(z) + g(Lz) of Sec. "Operator splitting", accelerated by SuperMann
+ * with Anderson directions (Algorithm 3).  Every step of the iteration runs
+ * in this library's CUDA kernels on one GPU.
+ *
+ * Conventions common to every entry point
+ * ---------------------------------------
+ *  - Return value: 0 (SPOCK_OK) on success, > 0 for a non-fatal outcome of a
+ *    solve, < 0 for an error (see spock_status).  On error, out-parameters
+ *    are left untouched and spock_last_error() describes the failure.
+ *    No C++ exception crosses this boundary.
+ *  - All host arrays are read during the call only; the library copies what
+ *    it keeps.  Device pointers ("_dev" entry points) must point to memory of
+ *    the current CUDA device and stay valid until the call returns; those
+ *    calls are ordered on the given stream (cudaStream_t passed as void*,
+ *    NULL = legacy default stream) and return after the stream has
+ *    completed the work, except where stated.
+ *  - Node ids are the caller's ("user") ids 0..n-1 with node 0 the root.
+ *    Children of a node are ordered by increasing user id.
+ *  - A handle is used by one host thread at a time.
+ *
+ * Layout of the primal vector z (length n_z) and the dual vector eta
+ * (length n_eta), Sec. "Operator splitting" with box constraints
+ * (Gamma = I in Eq. (constraints)) and AV@R risks
+ * (Sec. "Conic representation of risk measures"); m_i = #children of i:
+ *   z   = [ s^0,
+ *           x^i (nx) for every node i in user order,
+ *           u^i (nu) for every nonleaf i in user order,
+ *           (y^i (2 m_i + 1), tau^c (m_i), s^c (m_i)) for every nonleaf i in
+ *             user order, c running over the children of i ]
+ *   eta = [ (y^i (2 m_i + 1), s^i - b^iT y^i (1), x^i (nx), u^i (nu))
+ *             for every nonleaf i,
+ *           (Q^c^1/2 x^anc(c) (nx), R^c^1/2 u^anc(c) (nu), tau^c/2, tau^c/2)
+ *             for every nonroot c,
+ *           (x^j (nx), Q_N^j^1/2 x^j (nx), s^j/2, s^j/2) for every leaf j ]
+ *   with b^i = (p^ch(i), 0_{m_i}, 1) built from conditional probabilities.
+ */
+#ifndef SPOCK_H
+#define SPOCK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum spock_status {
+  SPOCK_OK = 0,
+  SPOCK_MAX_ITER = 1,          /* iteration cap reached; buffers hold T(v) of the last iterate */
+  SPOCK_ERR_INVALID_ARG = -1,  /* NULL pointer, size out of range, x0 outside its box, ... */
+  SPOCK_ERR_BAD_TREE = -2,     /* ancestor array is not a tree with all leaves at one stage */
+  SPOCK_ERR_NOT_POSDEF = -3,   /* a cost weight is not positive */
+  SPOCK_ERR_NUMERICAL = -4,    /* NaN/Inf in inputs or during the iteration */
+  SPOCK_ERR_CUDA = -5,         /* a CUDA runtime call failed */
+  SPOCK_ERR_OOM = -6,          /* device or host allocation failed */
+  SPOCK_ERR_UNSUPPORTED = -7   /* option not implemented by this build */
+} spock_status;
+
+typedef enum spock_precision {
+  SPOCK_FP64 = 0,  /* every vector and factor in double precision */
+  SPOCK_FP32 = 1   /* operator T in single precision (factors rounded from the
+                      FP64 Algorithm 1), residual, M-norms, Anderson Gram and
+                      least squares accumulated/solved in double */
+} spock_precision;
+
+typedef struct spock_tree spock_tree;
+typedef struct spock_problem spock_problem;
+
+/* Settings of Algorithm 3.  spock_default_settings() fills the defaults. */
+typedef struct spock_settings {
+  double eps_abs;       /* stop when xi <= max(eps_abs, eps_rel * xi_0)      (1e-6) */
+  double eps_rel;       /*                                                    (1e-6) */
+  double alpha;         /* CP step; <= 0 selects 0.99 / ||L||                  (0)    */
+  int32_t memory;       /* Anderson memory m (difference columns), 0..16      (3)    */
+  double c0, c1, c2;    /* SuperMann K0/K1 constants, in [0, 1)               (0.99) */
+  double beta;          /* line-search reduction, (0, 1)                      (0.5)  */
+  double sigma;         /* K2 acceptance, (0, 1)                              (0.1)  */
+  double lambda;        /* K2 relaxation, (0, 2)                              (1.0)  */
+  double rho_coef;      /* coefficient of <r~, v~ - v>_M in rho               (1.0)  */
+  int32_t max_iter;     /* SuperMann iteration cap                            (100000) */
+  int32_t max_backtracks; /* line-search cap; at the cap tau = 0             (30)   */
+  int32_t precision;    /* spock_precision                                   (FP64) */
+  int32_t* trace;       /* optional host array of 2*max_iter int32: per iteration
+                           (branch, backtracks), branch 0=K0 1=K1 2=K2 3=cap  (NULL) */
+} spock_settings;
+
+/* Outcome of a solve. */
+typedef struct spock_info {
+  int32_t status;       /* spock_status of the solve */
+  int32_t iterations;   /* SuperMann iterations k */
+  int32_t n_T;          /* evaluations of the CP operator T */
+  int32_t n_K0, n_K1, n_K2, n_cap, n_backtracks;
+  double xi;            /* termination residual xi at the returned pair */
+  double xi0;           /* xi at the initial point */
+  double alpha;         /* CP step used */
+  double solve_ms;      /* device time of the solve (CUDA events) */
+} spock_info;
+
+/* Fills *s with the defaults listed above.  Returns SPOCK_ERR_INVALID_ARG
+   if s is NULL. */
+int spock_default_settings(spock_settings* s);
+
+/*
+ * spock_tree_create -- scenario tree of Sec. "Scenario trees".
+ *   n_nodes : number of nodes, >= 2.
+ *   anc     : [n_nodes] ancestor of each node; anc[0] = -1 (root), others
+ *             in [0, n_nodes).  All leaves must lie at the same stage N >= 1.
+ *   prob    : [n_nodes] conditional probability p^i = pi^i / pi^anc(i) of
+ *             each nonroot node (prob[0] ignored); positive, summing to 1
+ *             over the children of each node within 1e-9.
+ *   out     : receives the new handle (free with spock_free).
+ * Errors: SPOCK_ERR_INVALID_ARG (NULL pointer, n_nodes < 2, bad
+ * probabilities), SPOCK_ERR_BAD_TREE (not a tree / uneven leaf depth).
+ * Host only; no GPU work.
+ */
+int spock_tree_create(int32_t n_nodes, const int32_t* anc, const double* prob,
+                      spock_tree** out);
+
+/* Number of nodes, horizon N and number of nonleaf nodes of a tree. */
+int spock_tree_info(const spock_tree* tree, int32_t* n_nodes, int32_t* horizon,
+                    int32_t* n_nonleaf);
+
+/*
+ * spock_problem_create -- RAOCP data on a tree (Sec. "Multistage nested
+ * risk-averse OCPs"), with diagonal costs and box constraints, and the
+ * offline factorisation of the projection on the dynamics (Algorithm 1, in
+ * FP64 on the host).  All arrays are host arrays indexed by user node id;
+ * entries of nodes where a quantity does not exist are ignored.
+ *   nx, nu    : state / input dimension, 1 <= nx, nu and nx + nu <= 128.
+ *   A         : [n][nx][nx] row-major, A^i of the edge into node i (Eq.
+ *               (finite-horizon-evolution-2)); A[0] ignored.
+ *   B         : [n][nx][nu] row-major, B^i; B[0] ignored.
+ *   Q         : [n][nx] diagonal of Q^i (> 0), stage cost of the edge into i.
+ *   R         : [n][nu] diagonal of R^i (> 0).
+ *   QN        : [n][nx] diagonal of the terminal weight Q_N^j (> 0), leaves.
+ *   a         : [n] AV@R parameter of each nonleaf node, in [0, 1].
+ *   xmin,xmax : [n][nx] state box of every node (xmin <= xmax).
+ *   umin,umax : [n][nu] input box of every nonleaf node.
+ *   flags     : reserved, pass 0.
+ *   out       : receives the handle; it owns a copy of the data, the FP64
+ *               factors (and their FP32 copies) in device memory.
+ * The current CUDA device at creation is used for every later call.
+ * Errors: INVALID_ARG, NOT_POSDEF, NUMERICAL (non-finite input), CUDA, OOM.
+ */
+int spock_problem_create(const spock_tree* tree, int32_t nx, int32_t nu,
+                         const double* A, const double* B, const double* Q,
+                         const double* R, const double* QN, const double* a,
+                         const double* xmin, const double* xmax,
+                         const double* umin, const double* umax,
+                         int32_t flags, spock_problem** out);
+
+/* Sizes of z and eta, ||L|| (closed form, remark after the definition of L)
+   and the seconds spent in Algorithm 1. */
+int spock_problem_info(const spock_problem* p, int64_t* n_z, int64_t* n_eta,
+                       double* norm_L, double* factor_seconds);
+
+/*
+ * spock_solve -- Algorithm 3 (SPOCK) from (z, eta), host buffers.
+ *   x0       : [nx] initial state (must satisfy the root's box).
+ *   settings : NULL for the defaults.
+ *   z_io     : [n_z]  in: initial z if warm != 0; out: z of T(v) at termination.
+ *   eta_io   : [n_eta] likewise for eta.
+ *   warm     : 0 = cold start from v = 0 (inputs of z_io/eta_io ignored).
+ *   info     : optional outcome.
+ * Copies inputs to the device and results back inside the call.  Returns
+ * SPOCK_OK on convergence, SPOCK_MAX_ITER at the iteration cap (outputs
+ * written in both cases), or an error.
+ */
+int spock_solve(spock_problem* p, const double* x0, const spock_settings* settings,
+                double* z_io, double* eta_io, int32_t warm, spock_info* info);
+
+/* As spock_solve with device buffers x0_dev [nx], z_dev [n_z], eta_dev
+   [n_eta] (FP64) on stream `stream`. */
+int spock_solve_dev(spock_problem* p, const double* x0_dev, const spock_settings* settings,
+                    double* z_dev, double* eta_dev, int32_t warm, spock_info* info,
+                    void* stream);
+
+/*
+ * spock_cp_step -- k iterations of the vanilla CP method v <- T(v)
+ * (Eq. (chambolle-pock-operator)) on host buffers z_io [n_z], eta_io
+ * [n_eta] (in: v_0, out: v_k).  xi_out (optional) receives xi of the pair
+ * (v_{k-1}, v_k) (Sec. "The Chambolle-Pock method").  precision as in
+ * spock_settings; alpha <= 0 selects 0.99/||L||.
+ */
+int spock_cp_step(spock_problem* p, const double* x0, int32_t k, double alpha,
+                  int32_t precision, double* z_io, double* eta_io, double* xi_out);
+
+/* Device-buffer variant of spock_cp_step. */
+int spock_cp_step_dev(spock_problem* p, const double* x0_dev, int32_t k, double alpha,
+                      int32_t precision, double* z_dev, double* eta_dev, double* xi_out,
+                      void* stream);
+
+/*
+ * Operator-level entry points (device buffers, FP64, ordered on `stream`;
+ * alpha <= 0 selects 0.99/||L||).  They expose the steps of T one by one:
+ *   spock_apply_L_dev      eta_out = L z             (definition of L)
+ *   spock_apply_Lt_dev     z_out   = L* eta          (adjoint, Sec. "Notation")
+ *   spock_prox_f_dev       z_out   = prox_{alpha f}(z): s^0 - alpha, proj_S1 on
+ *                          z_1 (Algorithm 2 with the factors of Algorithm 1),
+ *                          proj_S2 on z_2 (Sec. "Proximal operator of f")
+ *   spock_prox_gconj_dev   eta_out = prox_{alpha g*}(eta)
+ *                                  = eta - alpha proj_S3(eta / alpha)
+ *   spock_T_dev            (z_out, eta_out) = T(z, eta)
+ * Output buffers must not alias inputs.
+ */
+int spock_apply_L_dev(spock_problem* p, const double* z, double* eta_out, void* stream);
+int spock_apply_Lt_dev(spock_problem* p, const double* eta, double* z_out, void* stream);
+int spock_prox_f_dev(spock_problem* p, const double* x0_dev, double alpha, const double* z,
+                     double* z_out, void* stream);
+int spock_prox_gconj_dev(spock_problem* p, double alpha, const double* eta, double* eta_out,
+                         void* stream);
+int spock_T_dev(spock_problem* p, const double* x0_dev, double alpha, const double* z,
+                const double* eta, double* z_out, double* eta_out, void* stream);
+
+/* Frees a handle returned by any *_create call; NULL is a no-op. */
+void spock_free(void* handle);
+
+/* Description of the last error raised on the calling thread ("" if none). */
+const char* spock_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPOCK_H */

@@ -1,0 +1,119 @@
+// Device-side building blocks of the CP operator T (Eq.
+// (chambolle-pock-operator)) for the tree layout of spock_internal.h.
+//
+// Mapping: one warp per tree node for the vector work (every block of z and
+// eta belongs to exactly one node), lanes over the entries of the node's
+// blocks.  Vectors are in the caller's layout (offset tables per node), the
+// Riccati factors and scratch in breadth-first ("internal") order.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace spock {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarpsPerBlock = 4;        // 128-thread blocks for the warp-per-node kernels
+constexpr int kVecPad = 136;             // per-warp shared vector length (>= kMaxDim + 2)
+
+// Residual statistics accumulated by the dual / primal-statistics kernels.
+enum Stat : int {
+  ST_RZ2 = 0,      // sum r_z^2
+  ST_RE2 = 1,      // sum r_eta^2
+  ST_RE_LRZ = 2,   // sum r_eta . (L r_z)
+  ST_XIP = 3,      // max |r_z / alpha - L* r_eta|
+  ST_XID = 4,      // max |r_eta / alpha - L r_z|
+  ST_RD = 5,       // sum r . d              (line search, d = direction)
+  ST_LRZ_DE = 6,   // sum (L r_z) . d_eta
+  ST_RE_LDZ = 7,   // sum r_eta . (L d_z)
+};
+
+template <typename S>
+struct KP {
+  int32_t n, nl, nx, nu, N, chain_stage, n_chains;
+  int64_t n_z, n_eta;
+  S alpha;
+  const int32_t* __restrict__ parent;
+  const int32_t* __restrict__ ch_begin;
+  const int32_t* __restrict__ ch_count;
+  const int32_t* __restrict__ stage_begin;   // device copy [N + 2]
+  const int64_t* __restrict__ zx;
+  const int64_t* __restrict__ zu;
+  const int64_t* __restrict__ zz2;
+  const int64_t* __restrict__ zs;
+  const int64_t* __restrict__ ztau;
+  const int64_t* __restrict__ enl;
+  const int64_t* __restrict__ enr;
+  const int64_t* __restrict__ elf;
+  const S* __restrict__ Gb;
+  const S* __restrict__ Gf;
+  const S* __restrict__ NB;
+  const S* __restrict__ Kt;
+  const S* __restrict__ qs;
+  const S* __restrict__ rs;
+  const S* __restrict__ qns;
+  const S* __restrict__ xlo;
+  const S* __restrict__ xhi;
+  const S* __restrict__ ulo;
+  const S* __restrict__ uhi;
+  const S* __restrict__ av;
+  const S* __restrict__ prob;
+  S* __restrict__ xbar;
+  S* __restrict__ ubar;
+  S* __restrict__ q;
+  S* __restrict__ d;
+  const S* __restrict__ x0;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+
+template <typename S>
+__device__ __forceinline__ S clampv(S v, S lo, S hi) {
+  return v < lo ? lo : (v > hi ? hi : v);
+}
+
+// Statistics accumulator of one lane (always FP64).
+struct StatAcc {
+  double s[8];
+  __device__ void zero() {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s[i] = 0.0;
+  }
+};
+
+// Reduces the per-lane statistics of a block and writes one row of partials.
+// Sums for sums, maxima for ST_XIP / ST_XID.
+__device__ __forceinline__ void block_stats_store(StatAcc& a, double* partials) {
+  __shared__ double red[kWarpsPerBlock][8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    double v = a.s[i];
+    v = (i == ST_XIP || i == ST_XID) ? warp_max(v) : warp_sum(v);
+    if (lane == 0) red[w][i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    const int i = threadIdx.x;
+    double v = red[0][i];
+    for (int k = 1; k < kWarpsPerBlock; ++k)
+      v = (i == ST_XIP || i == ST_XID) ? fmax(v, red[k][i]) : v + red[k][i];
+    partials[(int64_t)blockIdx.x * 8 + i] = v;
+  }
+}
+
+}  // namespace spock

@@ -1,0 +1,994 @@
+// Host side of libspock: problem setup (layout, Algorithm 1, uploads), the
+// evaluation of T as a sequence of kernel launches, the driver loop of
+// Algorithm 3 whose decisions are taken on the device (supermann.cu), the
+// vanilla CP loop and the C ABI of include/spock.h.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <exception>
+#include <stdexcept>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "kernels.cuh"
+#include "spock_internal.h"
+#include "supermann.cuh"
+
+namespace spock {
+
+// launchers defined in ops.cu / riccati.cu
+template <typename S>
+void launch_prep(const KP<S>& p, const S* z, const S* eta, S* zo, int max_blocks, cudaStream_t st);
+template <typename S>
+void launch_dual(const KP<S>& p, int mode, bool stats, const S* z, const S* zp, const S* eta, S* out,
+                 const S* dir, double* partials, int grid, cudaStream_t st);
+template <typename S>
+void launch_primal(const KP<S>& p, int mode, const S* eta, const S* etap, const S* z, const S* zp, S* zout,
+                   const S* dir, double* partials, int grid, cudaStream_t st);
+void launch_reduce_stats(const double* pd, int nd, const double* pp, int np, double* out, cudaStream_t st);
+template <typename S>
+void launch_riccati(const KP<S>& p, const std::vector<int32_t>& stage_begin, S* zo, cudaStream_t st);
+
+enum { DM_APPLY_L_ = 0, DM_PROXG_ = 1, DM_DUAL_ = 2, PM_APPLY_LT_ = 0, PM_STATS_ = 1 };
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+struct SpockError : std::runtime_error {
+  int code;
+  SpockError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define CUDA_TRY(x)                                                                               \
+  do {                                                                                            \
+    cudaError_t e_ = (x);                                                                         \
+    if (e_ != cudaSuccess)                                                                        \
+      throw SpockError(e_ == cudaErrorMemoryAllocation ? SPOCK_ERR_OOM : SPOCK_ERR_CUDA,          \
+                       std::string(#x) + ": " + cudaGetErrorString(e_));                          \
+  } while (0)
+
+template <typename F>
+int guarded(F&& f) {
+  try {
+    return f();
+  } catch (const SpockError& e) {
+    return fail(e.code, e.what());
+  } catch (const std::bad_alloc&) {
+    return fail(SPOCK_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(SPOCK_ERR_CUDA, e.what());
+  }
+}
+
+static void check_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw SpockError(SPOCK_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------
+struct Workspace {
+  int prec = 0;
+  int64_t n_v = 0;
+  int mem = -1;
+  void* v[3] = {nullptr, nullptr, nullptr};
+  void* Tv[3] = {nullptr, nullptr, nullptr};
+  double* stats = nullptr;  // [3][8]
+  void* d = nullptr;
+  void* MR = nullptr;
+  void* D = nullptr;
+  void* zero_eta = nullptr;
+  double* pd = nullptr;
+  double* pp = nullptr;
+  double* paa = nullptr;
+  int grid_d = 0, grid_p = 0, grid_v = 0;
+  SmState* st = nullptr;
+  int32_t* trace = nullptr;
+  int trace_cap = 0;
+  int32_t* h_action = nullptr;  // pinned
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  std::vector<void*> allocs;
+  ~Workspace() {
+    for (void* p : allocs) cudaFree(p);
+    if (h_action) cudaFreeHost(h_action);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+  void* alloc(size_t bytes) {
+    void* p = nullptr;
+    CUDA_TRY(cudaMalloc(&p, bytes > 0 ? bytes : 16));
+    allocs.push_back(p);
+    return p;
+  }
+};
+
+Problem::~Problem() {
+  delete ws64;
+  delete ws32;
+  for (void* p : allocations) cudaFree(p);
+}
+
+static int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 132;
+}
+
+template <typename S>
+static Workspace*& ws_slot(Problem& P) {
+  return sizeof(S) == 8 ? P.ws64 : P.ws32;
+}
+
+template <typename S>
+static Workspace* get_ws_impl(Problem& P, int mem) {
+  Workspace*& w = ws_slot<S>(P);
+  if (w && w->mem >= mem) return w;
+  delete w;
+  w = nullptr;
+  auto* ws = new Workspace();
+  try {
+    ws->prec = sizeof(S) == 8 ? SPOCK_FP64 : SPOCK_FP32;
+    ws->n_v = P.off.n_z + P.off.n_eta;
+    ws->mem = mem;
+    const size_t vb = sizeof(S) * (size_t)ws->n_v;
+    for (int i = 0; i < 3; ++i) {
+      ws->v[i] = ws->alloc(vb);
+      ws->Tv[i] = ws->alloc(vb);
+    }
+    ws->stats = (double*)ws->alloc(3 * 8 * sizeof(double));
+    ws->d = ws->alloc(vb);
+    ws->MR = ws->alloc(vb * (size_t)(mem > 0 ? mem : 1));
+    ws->D = ws->alloc(vb * (size_t)(mem > 0 ? mem : 1));
+    ws->zero_eta = ws->alloc(sizeof(double) * (size_t)P.off.n_eta);
+    CUDA_TRY(cudaMemset(ws->zero_eta, 0, sizeof(double) * (size_t)P.off.n_eta));
+    const int sms = sm_count();
+    ws->grid_d = std::min((P.tree.n + kWarpsPerBlock - 1) / kWarpsPerBlock, sms * 16);
+    ws->grid_d = std::max(ws->grid_d, 1);
+    ws->grid_p = ws->grid_d;
+    ws->grid_v = sms * 8;
+    ws->pd = (double*)ws->alloc(sizeof(double) * 8 * ws->grid_d);
+    ws->pp = (double*)ws->alloc(sizeof(double) * 8 * ws->grid_p);
+    ws->paa = (double*)ws->alloc(sizeof(double) * 2 * kMaxMemory * ws->grid_v);
+    ws->st = (SmState*)ws->alloc(sizeof(SmState));
+    CUDA_TRY(cudaMallocHost(&ws->h_action, sizeof(int32_t) * 4));
+    CUDA_TRY(cudaEventCreate(&ws->e0));
+    CUDA_TRY(cudaEventCreate(&ws->e1));
+  } catch (...) {
+    delete ws;
+    throw;
+  }
+  w = ws;
+  return ws;
+}
+
+// ---------------------------------------------------------------------------
+// kernel parameters
+// ---------------------------------------------------------------------------
+template <typename S>
+static const DevFactors<S>& factors(const Problem& P);
+template <>
+const DevFactors<double>& factors<double>(const Problem& P) { return P.f64; }
+template <>
+const DevFactors<float>& factors<float>(const Problem& P) { return P.f32; }
+
+template <typename S>
+static KP<S> make_kp(const Problem& P, double alpha, const int32_t* stage_begin_dev) {
+  const DevFactors<S>& f = factors<S>(P);
+  KP<S> k;
+  k.n = P.tree.n;
+  k.nl = P.tree.n_nonleaf;
+  k.nx = P.nx;
+  k.nu = P.nu;
+  k.N = P.tree.N;
+  k.chain_stage = P.tree.chain_stage;
+  k.n_chains = P.tree.chain_stage < P.tree.N
+                   ? P.tree.stage_begin[P.tree.chain_stage + 1] - P.tree.stage_begin[P.tree.chain_stage]
+                   : 0;
+  k.n_z = P.off.n_z;
+  k.n_eta = P.off.n_eta;
+  k.alpha = (S)alpha;
+  k.parent = P.idx.parent;
+  k.ch_begin = P.idx.ch_begin;
+  k.ch_count = P.idx.ch_count;
+  k.stage_begin = stage_begin_dev;
+  k.zx = P.idx.zx;
+  k.zu = P.idx.zu;
+  k.zz2 = P.idx.zz2;
+  k.zs = P.idx.zs;
+  k.ztau = P.idx.ztau;
+  k.enl = P.idx.enl;
+  k.enr = P.idx.enr;
+  k.elf = P.idx.elf;
+  k.Gb = f.Gb;
+  k.Gf = f.Gf;
+  k.NB = f.NB;
+  k.Kt = f.Kt;
+  k.qs = f.qs;
+  k.rs = f.rs;
+  k.qns = f.qns;
+  k.xlo = f.xlo;
+  k.xhi = f.xhi;
+  k.ulo = f.ulo;
+  k.uhi = f.uhi;
+  k.av = f.av;
+  k.prob = f.prob;
+  k.xbar = f.xbar;
+  k.ubar = f.ubar;
+  k.q = f.q;
+  k.d = f.d;
+  k.x0 = f.x0;
+  return k;
+}
+
+static double default_alpha(const Problem& P, double alpha) { return alpha > 0.0 ? alpha : 0.99 / P.normL; }
+
+// ---------------------------------------------------------------------------
+// conversion kernels (user FP64 buffers <-> working precision)
+// ---------------------------------------------------------------------------
+template <typename D, typename S>
+__global__ void k_convert(const S* __restrict__ in, D* __restrict__ out, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = (D)in[i];
+}
+template <typename D, typename S>
+static void convert(const S* in, D* out, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
+  k_convert<D, S><<<grid, 256, 0, st>>>(in, out, n);
+}
+
+// ---------------------------------------------------------------------------
+// T and its residual statistics
+// ---------------------------------------------------------------------------
+struct Ctx {
+  Problem* P;
+  Workspace* ws;
+  double alpha;
+  cudaStream_t st;
+  int32_t* stage_dev;
+};
+
+template <typename S>
+static void eval_T(const Ctx& c, const S* v, S* Tv, const S* dir, double* stats) {
+  Problem& P = *c.P;
+  KP<S> kp = make_kp<S>(P, c.alpha, c.stage_dev);
+  const int64_t nz = P.off.n_z;
+  const int maxb = sm_count() * 16;
+  launch_prep<S>(kp, v, v + nz, Tv, maxb, c.st);
+  launch_riccati<S>(kp, P.tree.stage_begin, Tv, c.st);
+  launch_dual<S>(kp, DM_DUAL_, stats != nullptr, v, Tv, v + nz, Tv + nz, dir, c.ws ? c.ws->pd : nullptr,
+                 c.ws ? c.ws->grid_d : std::min((P.tree.n + 3) / 4, maxb), c.st);
+  if (stats) {
+    launch_primal<S>(kp, PM_STATS_, v + nz, Tv + nz, v, Tv, nullptr, dir, c.ws->pp, c.ws->grid_p, c.st);
+    launch_reduce_stats(c.ws->pd, c.ws->grid_d, c.ws->pp, c.ws->grid_p, stats, c.st);
+  }
+  check_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 3 driver
+// ---------------------------------------------------------------------------
+template <typename S>
+static int solve_impl(Problem& P, const double* x0_dev, const spock_settings& s, double* z_dev, double* eta_dev,
+                      int warm, spock_info* info, cudaStream_t st) {
+  const int mem = std::max(0, std::min<int>(s.memory, kMaxMemory));
+  Workspace* ws = get_ws_impl<S>(P, mem);
+  const DevFactors<S>& f = factors<S>(P);
+  const int64_t nz = P.off.n_z, nv = ws->n_v;
+  Ctx c{&P, ws, default_alpha(P, s.alpha), st, P.idx.stage_begin};
+  S* V[3];
+  S* TV[3];
+  for (int i = 0; i < 3; ++i) {
+    V[i] = (S*)ws->v[i];
+    TV[i] = (S*)ws->Tv[i];
+  }
+  S* d = (S*)ws->d;
+  S* MR = (S*)ws->MR;
+  S* Dm = (S*)ws->D;
+  // inputs
+  convert<S, double>(x0_dev, f.x0, P.nx, st);
+  if (warm) {
+    convert<S, double>(z_dev, V[0], nz, st);
+    convert<S, double>(eta_dev, V[0] + nz, P.off.n_eta, st);
+  } else {
+    CUDA_TRY(cudaMemsetAsync(V[0], 0, sizeof(S) * nv, st));
+  }
+  if (mem > 0) {
+    CUDA_TRY(cudaMemsetAsync(MR, 0, sizeof(S) * nv * mem, st));
+    CUDA_TRY(cudaMemsetAsync(Dm, 0, sizeof(S) * nv * mem, st));
+  }
+  const int max_iter = std::max(0, s.max_iter);
+  int32_t* trace_dev = nullptr;
+  if (s.trace && max_iter > 0) {
+    if (ws->trace_cap < max_iter) {
+      ws->trace = (int32_t*)ws->alloc(sizeof(int32_t) * 2 * (size_t)max_iter);
+      ws->trace_cap = max_iter;
+    }
+    trace_dev = ws->trace;
+    CUDA_TRY(cudaMemsetAsync(trace_dev, 0xff, sizeof(int32_t) * 2 * (size_t)max_iter, st));
+  }
+  SmState h{};
+  h.alpha = c.alpha;
+  h.eps_abs = s.eps_abs;
+  h.eps_rel = s.eps_rel;
+  h.c0 = s.c0;
+  h.c1 = s.c1;
+  h.c2 = s.c2;
+  h.beta = s.beta;
+  h.sigma = s.sigma;
+  h.lam = s.lambda;
+  h.rho_coef = s.rho_coef;
+  h.max_iter = max_iter;
+  h.max_back = std::max(0, s.max_backtracks);
+  h.mem = mem;
+  h.record_trace = trace_dev != nullptr;
+  sm_init_state(ws->st, h, st);
+  double* stats[3] = {ws->stats, ws->stats + 8, ws->stats + 16};
+  CUDA_TRY(cudaEventRecord(ws->e0, st));
+  int cur = 0, prev = 1, trial = 2;
+  int nT = 0;
+  eval_T<S>(c, V[cur], TV[cur], nullptr, stats[cur]);
+  ++nT;
+  bool have_prev = false;
+  int stored = 0, next_slot = 0;
+  int final_action = A_NONE;
+  auto read_action = [&]() -> int {
+    CUDA_TRY(cudaMemcpyAsync(ws->h_action, &ws->st->action, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return ws->h_action[0];
+  };
+  for (;;) {
+    launch_sm_after_eval(ws->st, stats[cur], trace_dev, st);
+    const int act = read_action();
+    if (act == A_DONE || act == A_MAXIT || act == A_NUMERICAL) {
+      final_action = act;
+      break;
+    }
+    int cnt = 0;
+    if (have_prev && mem > 0) {
+      const int slot = next_slot;
+      next_slot = (next_slot + 1) % mem;
+      stored = std::min(stored + 1, mem);
+      cnt = stored;
+      int order[kMaxMemory];
+      for (int j = 0; j < kMaxMemory; ++j) order[j] = 0;
+      for (int j = 0; j < cnt; ++j) order[j] = ((slot - j) % mem + mem) % mem;
+      launch_aa_update<S>(ws->st, V[cur], TV[cur], V[prev], TV[prev], MR, Dm, nv, slot, cnt, order, ws->paa,
+                          ws->grid_v, st);
+    }
+    launch_aa_direction<S>(ws->st, V[cur], TV[cur], Dm, nv, cnt, d, V[trial], ws->grid_v, st);
+    check_launch();
+    if (act == A_K0) {
+      eval_T<S>(c, V[trial], TV[trial], nullptr, stats[trial]);
+      ++nT;
+      const int old_prev = prev;
+      prev = cur;
+      cur = trial;
+      trial = old_prev;
+    } else {
+      bool numerical = false;
+      for (;;) {
+        eval_T<S>(c, V[trial], TV[trial], d, stats[trial]);
+        ++nT;
+        launch_sm_line_search(ws->st, stats[trial], trace_dev, st);
+        const int la = read_action();
+        if (la == A_K1) {
+          const int old_prev = prev;
+          prev = cur;
+          cur = trial;
+          trial = old_prev;
+          break;
+        }
+        if (la == A_K2 || la == A_CAP) {
+          if (la == A_K2) {
+            launch_k2_point<S>(ws->st, V[cur], V[trial], TV[trial], V[prev], nv, ws->grid_v, st);
+          } else {
+            launch_km_point<S>(ws->st, V[cur], TV[cur], V[prev], nv, ws->grid_v, st);
+          }
+          eval_T<S>(c, V[prev], TV[prev], nullptr, stats[prev]);
+          ++nT;
+          const int newcur = prev;
+          prev = cur;
+          cur = newcur;
+          break;
+        }
+        if (la == A_NUMERICAL) {
+          numerical = true;
+          break;
+        }
+        launch_ls_point<S>(ws->st, V[cur], d, V[trial], nv, ws->grid_v, st);
+      }
+      if (numerical) {
+        final_action = A_NUMERICAL;
+        break;
+      }
+    }
+    have_prev = true;
+  }
+  CUDA_TRY(cudaEventRecord(ws->e1, st));
+  // outputs: T(v) of the final iterate
+  convert<double, S>(TV[cur], z_dev, nz, st);
+  convert<double, S>(TV[cur] + nz, eta_dev, P.off.n_eta, st);
+  check_launch();
+  SmState fin;
+  CUDA_TRY(cudaMemcpyAsync(&fin, ws->st, sizeof(SmState), cudaMemcpyDeviceToHost, st));
+  if (trace_dev)
+    CUDA_TRY(cudaMemcpyAsync(s.trace, trace_dev, sizeof(int32_t) * 2 * (size_t)max_iter, cudaMemcpyDeviceToHost,
+                             st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ws->e0, ws->e1);
+  int status = final_action == A_DONE ? SPOCK_OK
+                                      : (final_action == A_MAXIT ? SPOCK_MAX_ITER : SPOCK_ERR_NUMERICAL);
+  if (info) {
+    info->status = status;
+    info->iterations = fin.k;
+    info->n_T = nT;
+    info->n_K0 = fin.n_k0;
+    info->n_K1 = fin.n_k1;
+    info->n_K2 = fin.n_k2;
+    info->n_cap = fin.n_cap;
+    info->n_backtracks = fin.n_back;
+    info->xi = fin.xi;
+    info->xi0 = fin.xi0;
+    info->alpha = c.alpha;
+    info->solve_ms = ms;
+  }
+  if (status == SPOCK_ERR_NUMERICAL) return fail(status, "non-finite residual during the iteration");
+  return status;
+}
+
+template <typename S>
+static int cp_impl(Problem& P, const double* x0_dev, int k, double alpha, double* z_dev, double* eta_dev,
+                   double* xi_out, cudaStream_t st) {
+  Workspace* ws = get_ws_impl<S>(P, 0);
+  const DevFactors<S>& f = factors<S>(P);
+  const int64_t nz = P.off.n_z;
+  Ctx c{&P, ws, default_alpha(P, alpha), st, P.idx.stage_begin};
+  S* a = (S*)ws->v[0];
+  S* b = (S*)ws->v[1];
+  convert<S, double>(x0_dev, f.x0, P.nx, st);
+  convert<S, double>(z_dev, a, nz, st);
+  convert<S, double>(eta_dev, a + nz, P.off.n_eta, st);
+  for (int i = 0; i < k; ++i) {
+    eval_T<S>(c, a, b, nullptr, (i == k - 1 && xi_out) ? ws->stats : nullptr);
+    std::swap(a, b);
+  }
+  convert<double, S>(a, z_dev, nz, st);
+  convert<double, S>(a + nz, eta_dev, P.off.n_eta, st);
+  check_launch();
+  if (xi_out) {
+    if (k > 0) {
+      double h[8];
+      CUDA_TRY(cudaMemcpyAsync(h, ws->stats, sizeof(h), cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(cudaStreamSynchronize(st));
+      *xi_out = std::max(h[ST_XIP], h[ST_XID]);
+    } else {
+      *xi_out = NAN;
+    }
+  }
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return SPOCK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// problem creation
+// ---------------------------------------------------------------------------
+template <typename T>
+static T* upload(Problem& P, const std::vector<T>& h) {
+  void* p = nullptr;
+  CUDA_TRY(cudaMalloc(&p, sizeof(T) * std::max<size_t>(h.size(), 1)));
+  P.allocations.push_back(p);
+  if (!h.empty()) CUDA_TRY(cudaMemcpy(p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+  return (T*)p;
+}
+template <typename S>
+static S* dalloc(Problem& P, size_t n) {
+  void* p = nullptr;
+  CUDA_TRY(cudaMalloc(&p, sizeof(S) * std::max<size_t>(n, 1)));
+  P.allocations.push_back(p);
+  return (S*)p;
+}
+
+template <typename S>
+static void upload_factors(Problem& P, DevFactors<S>& f, const std::vector<double>& Gb,
+                           const std::vector<double>& Gf, const std::vector<double>& NB,
+                           const std::vector<double>& Kt, const std::vector<std::vector<double>>& par) {
+  auto cast = [](const std::vector<double>& v) {
+    std::vector<S> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = (S)v[i];
+    return o;
+  };
+  f.Gb = upload(P, cast(Gb));
+  f.Gf = upload(P, cast(Gf));
+  f.NB = upload(P, cast(NB));
+  f.Kt = upload(P, cast(Kt));
+  f.qs = upload(P, cast(par[0]));
+  f.rs = upload(P, cast(par[1]));
+  f.qns = upload(P, cast(par[2]));
+  f.xlo = upload(P, cast(par[3]));
+  f.xhi = upload(P, cast(par[4]));
+  f.ulo = upload(P, cast(par[5]));
+  f.uhi = upload(P, cast(par[6]));
+  f.av = upload(P, cast(par[7]));
+  f.prob = upload(P, cast(par[8]));
+  const Tree& t = P.tree;
+  f.xbar = dalloc<S>(P, (size_t)t.n * P.nx);
+  f.ubar = dalloc<S>(P, (size_t)t.n_nonleaf * P.nu);
+  f.q = dalloc<S>(P, (size_t)t.n * P.nx);
+  f.d = dalloc<S>(P, (size_t)t.n_nonleaf * P.nu);
+  f.x0 = dalloc<S>(P, (size_t)P.nx);
+}
+
+static bool all_finite(const double* a, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+static int problem_create(const Tree& tree, int32_t nx, int32_t nu, const double* A, const double* B,
+                          const double* Q, const double* R, const double* QN, const double* a, const double* xmin,
+                          const double* xmax, const double* umin, const double* umax, spock_problem** out) {
+  if (!A || !B || !Q || !R || !QN || !a || !xmin || !xmax || !umin || !umax || !out)
+    return fail(SPOCK_ERR_INVALID_ARG, "NULL argument");
+  if (nx < 1 || nu < 1 || nx + nu > kMaxDim)
+    return fail(SPOCK_ERR_INVALID_ARG, "need nx >= 1, nu >= 1, nx + nu <= 128");
+  const int32_t n = tree.n;
+  const size_t nn = (size_t)n;
+  // validation (user numbering)
+  if (!all_finite(A + (size_t)nx * nx, (nn - 1) * nx * nx) || !all_finite(B + (size_t)nx * nu, (nn - 1) * nx * nu))
+    return fail(SPOCK_ERR_NUMERICAL, "non-finite dynamics");
+  for (int32_t u = 0; u < n; ++u) {
+    const int32_t k = tree.int_of[u];
+    const bool nonroot = k > 0, leaf = k >= tree.n_nonleaf, nonleaf = !leaf;
+    for (int r = 0; r < nx; ++r) {
+      if (nonroot && !(Q[(size_t)u * nx + r] > 0.0 && std::isfinite(Q[(size_t)u * nx + r])))
+        return fail(SPOCK_ERR_NOT_POSDEF, "Q must be positive and finite");
+      if (leaf && !(QN[(size_t)u * nx + r] > 0.0 && std::isfinite(QN[(size_t)u * nx + r])))
+        return fail(SPOCK_ERR_NOT_POSDEF, "QN must be positive and finite");
+      const double lo = xmin[(size_t)u * nx + r], hi = xmax[(size_t)u * nx + r];
+      if (std::isnan(lo) || std::isnan(hi) || lo > hi) return fail(SPOCK_ERR_INVALID_ARG, "xmin > xmax");
+    }
+    for (int r = 0; r < nu; ++r) {
+      if (nonroot && !(R[(size_t)u * nu + r] > 0.0 && std::isfinite(R[(size_t)u * nu + r])))
+        return fail(SPOCK_ERR_NOT_POSDEF, "R must be positive and finite");
+      if (nonleaf) {
+        const double lo = umin[(size_t)u * nu + r], hi = umax[(size_t)u * nu + r];
+        if (std::isnan(lo) || std::isnan(hi) || lo > hi) return fail(SPOCK_ERR_INVALID_ARG, "umin > umax");
+      }
+    }
+    if (nonleaf && !(a[u] >= 0.0 && a[u] <= 1.0)) return fail(SPOCK_ERR_INVALID_ARG, "AV@R parameter must be in [0, 1]");
+  }
+  auto* P = new Problem();
+  try {
+    CUDA_TRY(cudaGetDevice(&P->device));
+    P->tree = tree;
+    P->nx = nx;
+    P->nu = nu;
+    build_offsets(P->tree, nx, nu, P->off);
+    const Tree& t = P->tree;
+    const int nl = t.n_nonleaf, ncol = nx + nu;
+    // internal-order dynamics
+    std::vector<double> Ai(nn * nx * nx), Bi(nn * nx * nu);
+    for (int32_t k = 1; k < n; ++k) {
+      const int32_t u = t.user_of[k];
+      std::memcpy(&Ai[(size_t)k * nx * nx], A + (size_t)u * nx * nx, sizeof(double) * nx * nx);
+      std::memcpy(&Bi[(size_t)k * nx * nu], B + (size_t)u * nx * nu, sizeof(double) * nx * nu);
+    }
+    std::vector<double> Gb, NB;
+    const auto t0 = std::chrono::steady_clock::now();
+    int threads = (int)std::thread::hardware_concurrency();
+    if (threads <= 0) threads = 4;
+    if (!riccati_factor(t, nx, nu, Ai, Bi, Gb, NB, threads)) {
+      delete P;
+      return fail(SPOCK_ERR_NUMERICAL, "Cholesky of I + sum B'PB failed");
+    }
+    P->factor_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (!all_finite(Gb.data(), Gb.size()) || !all_finite(NB.data(), NB.size())) {
+      delete P;
+      return fail(SPOCK_ERR_NUMERICAL, "non-finite Riccati factors");
+    }
+    // forward layouts: transpose of [Abar | B], and K^T
+    std::vector<double> Gf(Gb.size()), Kt((size_t)nl * nx * nu);
+    const size_t gsz = (size_t)nx * ncol, nbsz = 2 * (size_t)nu * nx + (size_t)nu * nu;
+    for (int32_t c = 1; c < n; ++c) {
+      const double* g = &Gb[(size_t)(c - 1) * gsz];
+      double* h = &Gf[(size_t)(c - 1) * gsz];
+      for (int r = 0; r < nx; ++r)
+        for (int j = 0; j < ncol; ++j) h[(size_t)j * nx + r] = g[(size_t)r * ncol + j];
+    }
+    for (int32_t k = 0; k < nl; ++k)
+      for (int r = 0; r < nu; ++r)
+        for (int q = 0; q < nx; ++q) Kt[(size_t)k * nx * nu + (size_t)q * nu + r] = NB[(size_t)k * nbsz + (size_t)r * nx + q];
+    // node parameters (internal order)
+    std::vector<std::vector<double>> par(9);
+    par[0].assign(nn * nx, 0.0);
+    par[1].assign(nn * nu, 0.0);
+    par[2].assign(nn * nx, 0.0);
+    par[3].assign(nn * nx, 0.0);
+    par[4].assign(nn * nx, 0.0);
+    par[5].assign(nn * nu, 0.0);
+    par[6].assign(nn * nu, 0.0);
+    par[7].assign(nn, 0.0);
+    par[8].assign(nn, 1.0);
+    for (int32_t k = 0; k < n; ++k) {
+      const int32_t u = t.user_of[k];
+      for (int r = 0; r < nx; ++r) {
+        if (k > 0) par[0][(size_t)k * nx + r] = std::sqrt(Q[(size_t)u * nx + r]);
+        if (k >= nl) par[2][(size_t)k * nx + r] = std::sqrt(QN[(size_t)u * nx + r]);
+        par[3][(size_t)k * nx + r] = xmin[(size_t)u * nx + r];
+        par[4][(size_t)k * nx + r] = xmax[(size_t)u * nx + r];
+      }
+      for (int r = 0; r < nu; ++r) {
+        if (k > 0) par[1][(size_t)k * nu + r] = std::sqrt(R[(size_t)u * nu + r]);
+        if (k < nl) {
+          par[5][(size_t)k * nu + r] = umin[(size_t)u * nu + r];
+          par[6][(size_t)k * nu + r] = umax[(size_t)u * nu + r];
+        }
+      }
+      if (k < nl) par[7][k] = a[u];
+      par[8][k] = t.prob[k];
+    }
+    // ||L||^2 as the largest block norm (remark after the definition of L)
+    double best = 0.5;
+    for (int32_t k = 0; k < nl; ++k) {
+      const int c0 = t.ch_begin[k], m = t.ch_count[k];
+      for (int r = 0; r < nx; ++r) {
+        double s = 1.0;
+        for (int j = 0; j < m; ++j) s += par[0][(size_t)(c0 + j) * nx + r] * par[0][(size_t)(c0 + j) * nx + r];
+        best = std::max(best, s);
+      }
+      for (int r = 0; r < nu; ++r) {
+        double s = 1.0;
+        for (int j = 0; j < m; ++j) s += par[1][(size_t)(c0 + j) * nu + r] * par[1][(size_t)(c0 + j) * nu + r];
+        best = std::max(best, s);
+      }
+      double b2 = 1.0;
+      for (int j = 0; j < m; ++j) b2 += t.prob[c0 + j] * t.prob[c0 + j];
+      const double bb = std::sqrt(b2);
+      best = std::max(best, (2.0 + b2 + bb * std::sqrt(b2 + 4.0)) / 2.0);
+    }
+    for (int32_t k = nl; k < n; ++k)
+      for (int r = 0; r < nx; ++r) best = std::max(best, 1.0 + par[2][(size_t)k * nx + r] * par[2][(size_t)k * nx + r]);
+    P->normL = std::sqrt(best);
+    // device index
+    P->idx.parent = upload(*P, t.parent);
+    P->idx.ch_begin = upload(*P, t.ch_begin);
+    P->idx.ch_count = upload(*P, t.ch_count);
+    P->idx.sib = upload(*P, t.sib);
+    P->idx.zx = upload(*P, P->off.zx);
+    P->idx.zu = upload(*P, P->off.zu);
+    P->idx.zz2 = upload(*P, P->off.zz2);
+    P->idx.zs = upload(*P, P->off.zs);
+    P->idx.ztau = upload(*P, P->off.ztau);
+    P->idx.enl = upload(*P, P->off.enl);
+    P->idx.enr = upload(*P, P->off.enr);
+    P->idx.elf = upload(*P, P->off.elf);
+    upload_factors<double>(*P, P->f64, Gb, Gf, NB, Kt, par);
+    upload_factors<float>(*P, P->f32, Gb, Gf, NB, Kt, par);
+    P->idx.stage_begin = upload(*P, t.stage_begin);
+    CUDA_TRY(cudaDeviceSynchronize());
+  } catch (const SpockError& e) {
+    delete P;
+    return fail(e.code, e.what());
+  }
+  *out = reinterpret_cast<spock_problem*>(P);
+  return SPOCK_OK;
+}
+
+}  // namespace spock
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+using namespace spock;
+
+static Problem* as_problem(void* h) {
+  Problem* p = reinterpret_cast<Problem*>(h);
+  return (p && p->tag == TAG_PROBLEM) ? p : nullptr;
+}
+static const Tree* as_tree(const void* h) {
+  const Tree* t = reinterpret_cast<const Tree*>(h);
+  return (t && t->tag == TAG_TREE) ? t : nullptr;
+}
+
+extern "C" {
+
+int spock_default_settings(spock_settings* s) {
+  if (!s) return fail(SPOCK_ERR_INVALID_ARG, "settings is NULL");
+  s->eps_abs = 1e-6;
+  s->eps_rel = 1e-6;
+  s->alpha = 0.0;
+  s->memory = 3;
+  s->c0 = s->c1 = s->c2 = 0.99;
+  s->beta = 0.5;
+  s->sigma = 0.1;
+  s->lambda = 1.0;
+  s->rho_coef = 1.0;
+  s->max_iter = 100000;
+  s->max_backtracks = 30;
+  s->precision = SPOCK_FP64;
+  s->trace = nullptr;
+  return SPOCK_OK;
+}
+
+int spock_tree_create(int32_t n_nodes, const int32_t* anc, const double* prob, spock_tree** out) {
+  return guarded([&]() -> int {
+    if (!out) return fail(SPOCK_ERR_INVALID_ARG, "out is NULL");
+    auto* t = new Tree();
+    int rc = build_tree(n_nodes, anc, prob, *t);
+    if (rc != SPOCK_OK) {
+      delete t;
+      return rc;
+    }
+    *out = reinterpret_cast<spock_tree*>(t);
+    return SPOCK_OK;
+  });
+}
+
+int spock_tree_info(const spock_tree* tree, int32_t* n_nodes, int32_t* horizon, int32_t* n_nonleaf) {
+  const Tree* t = as_tree(tree);
+  if (!t) return fail(SPOCK_ERR_INVALID_ARG, "not a tree handle");
+  if (n_nodes) *n_nodes = t->n;
+  if (horizon) *horizon = t->N;
+  if (n_nonleaf) *n_nonleaf = t->n_nonleaf;
+  return SPOCK_OK;
+}
+
+int spock_problem_create(const spock_tree* tree, int32_t nx, int32_t nu, const double* A, const double* B,
+                         const double* Q, const double* R, const double* QN, const double* a, const double* xmin,
+                         const double* xmax, const double* umin, const double* umax, int32_t flags,
+                         spock_problem** out) {
+  return guarded([&]() -> int {
+    const Tree* t = as_tree(tree);
+    if (!t) return fail(SPOCK_ERR_INVALID_ARG, "not a tree handle");
+    if (flags != 0) return fail(SPOCK_ERR_UNSUPPORTED, "flags must be 0");
+    return problem_create(*t, nx, nu, A, B, Q, R, QN, a, xmin, xmax, umin, umax, out);
+  });
+}
+
+int spock_problem_info(const spock_problem* p, int64_t* n_z, int64_t* n_eta, double* norm_L, double* factor_seconds) {
+  Problem* P = as_problem((void*)p);
+  if (!P) return fail(SPOCK_ERR_INVALID_ARG, "not a problem handle");
+  if (n_z) *n_z = P->off.n_z;
+  if (n_eta) *n_eta = P->off.n_eta;
+  if (norm_L) *norm_L = P->normL;
+  if (factor_seconds) *factor_seconds = P->factor_seconds;
+  return SPOCK_OK;
+}
+
+static int solve_dev_impl(Problem* P, const double* x0_dev, const spock_settings* settings, double* z_dev,
+                          double* eta_dev, int32_t warm, spock_info* info, cudaStream_t st) {
+  spock_settings s;
+  spock_default_settings(&s);
+  if (settings) s = *settings;
+  if (!x0_dev || !z_dev || !eta_dev) return fail(SPOCK_ERR_INVALID_ARG, "NULL buffer");
+  if (s.memory < 0 || s.memory > kMaxMemory) return fail(SPOCK_ERR_INVALID_ARG, "memory must be in 0..16");
+  if (!(s.eps_abs > 0) || !(s.eps_rel >= 0)) return fail(SPOCK_ERR_INVALID_ARG, "tolerances must be positive");
+  if (s.max_iter < 0 || s.max_backtracks < 0) return fail(SPOCK_ERR_INVALID_ARG, "negative cap");
+  if (s.alpha > 0 && s.alpha * P->normL >= 1.0) return fail(SPOCK_ERR_INVALID_ARG, "alpha ||L|| must be < 1");
+  CUDA_TRY(cudaSetDevice(P->device));
+  if (s.precision == SPOCK_FP64) return solve_impl<double>(*P, x0_dev, s, z_dev, eta_dev, warm, info, st);
+  if (s.precision == SPOCK_FP32) return solve_impl<float>(*P, x0_dev, s, z_dev, eta_dev, warm, info, st);
+  return fail(SPOCK_ERR_INVALID_ARG, "unknown precision");
+}
+
+// Root box check on a host copy of x0.
+static int root_box_ok(const Problem& P, const double* x0, cudaStream_t st, bool x0_on_device) {
+  std::vector<double> h(P.nx);
+  if (x0_on_device) {
+    CUDA_TRY(cudaMemcpyAsync(h.data(), x0, sizeof(double) * P.nx, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+  } else {
+    std::memcpy(h.data(), x0, sizeof(double) * P.nx);
+  }
+  std::vector<double> lo(P.nx), hi(P.nx);
+  CUDA_TRY(cudaMemcpy(lo.data(), P.f64.xlo, sizeof(double) * P.nx, cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(hi.data(), P.f64.xhi, sizeof(double) * P.nx, cudaMemcpyDeviceToHost));
+  for (int r = 0; r < P.nx; ++r) {
+    if (!std::isfinite(h[r])) return fail(SPOCK_ERR_NUMERICAL, "x0 is not finite");
+    if (h[r] < lo[r] || h[r] > hi[r]) return fail(SPOCK_ERR_INVALID_ARG, "x0 violates the box of the root node");
+  }
+  return SPOCK_OK;
+}
+
+int spock_solve_dev(spock_problem* p, const double* x0_dev, const spock_settings* settings, double* z_dev,
+                    double* eta_dev, int32_t warm, spock_info* info, void* stream) {
+  return guarded([&]() -> int {
+    Problem* P = as_problem(p);
+    if (!P) return fail(SPOCK_ERR_INVALID_ARG, "not a problem handle");
+    if (!x0_dev) return fail(SPOCK_ERR_INVALID_ARG, "x0 is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = root_box_ok(*P, x0_dev, st, true);
+    if (rc != SPOCK_OK) return rc;
+    return solve_dev_impl(P, x0_dev, settings, z_dev, eta_dev, warm, info, st);
+  });
+}
+
+int spock_solve(spock_problem* p, const double* x0, const spock_settings* settings, double* z_io, double* eta_io,
+                int32_t warm, spock_info* info) {
+  return guarded([&]() -> int {
+    Problem* P = as_problem(p);
+    if (!P) return fail(SPOCK_ERR_INVALID_ARG, "not a problem handle");
+    if (!x0 || !z_io || !eta_io) return fail(SPOCK_ERR_INVALID_ARG, "NULL buffer");
+    CUDA_TRY(cudaSetDevice(P->device));
+    int rc = root_box_ok(*P, x0, nullptr, false);
+    if (rc != SPOCK_OK) return rc;
+    const int64_t nz = P->off.n_z, ne = P->off.n_eta;
+    double *dx0 = nullptr, *dz = nullptr, *de = nullptr;
+    CUDA_TRY(cudaMalloc(&dx0, sizeof(double) * P->nx));
+    CUDA_TRY(cudaMalloc(&dz, sizeof(double) * nz));
+    CUDA_TRY(cudaMalloc(&de, sizeof(double) * ne));
+    struct Guard {
+      void* a[3];
+      ~Guard() {
+        for (void* p : a) cudaFree(p);
+      }
+    } g{{dx0, dz, de}};
+    CUDA_TRY(cudaMemcpy(dx0, x0, sizeof(double) * P->nx, cudaMemcpyHostToDevice));
+    if (warm) {
+      CUDA_TRY(cudaMemcpy(dz, z_io, sizeof(double) * nz, cudaMemcpyHostToDevice));
+      CUDA_TRY(cudaMemcpy(de, eta_io, sizeof(double) * ne, cudaMemcpyHostToDevice));
+    }
+    rc = solve_dev_impl(P, dx0, settings, dz, de, warm, info, nullptr);
+    if (rc == SPOCK_OK || rc == SPOCK_MAX_ITER) {
+      CUDA_TRY(cudaMemcpy(z_io, dz, sizeof(double) * nz, cudaMemcpyDeviceToHost));
+      CUDA_TRY(cudaMemcpy(eta_io, de, sizeof(double) * ne, cudaMemcpyDeviceToHost));
+    }
+    return rc;
+  });
+}
+
+int spock_cp_step_dev(spock_problem* p, const double* x0_dev, int32_t k, double alpha, int32_t precision,
+                      double* z_dev, double* eta_dev, double* xi_out, void* stream) {
+  return guarded([&]() -> int {
+    Problem* P = as_problem(p);
+    if (!P) return fail(SPOCK_ERR_INVALID_ARG, "not a problem handle");
+    if (!x0_dev || !z_dev || !eta_dev || k < 0) return fail(SPOCK_ERR_INVALID_ARG, "NULL buffer or k < 0");
+    if (alpha > 0 && alpha * P->normL >= 1.0) return fail(SPOCK_ERR_INVALID_ARG, "alpha ||L|| must be < 1");
+    CUDA_TRY(cudaSetDevice(P->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = root_box_ok(*P, x0_dev, st, true);
+    if (rc != SPOCK_OK) return rc;
+    if (precision == SPOCK_FP64) return cp_impl<double>(*P, x0_dev, k, alpha, z_dev, eta_dev, xi_out, st);
+    if (precision == SPOCK_FP32) return cp_impl<float>(*P, x0_dev, k, alpha, z_dev, eta_dev, xi_out, st);
+    return fail(SPOCK_ERR_INVALID_ARG, "unknown precision");
+  });
+}
+
+int spock_cp_step(spock_problem* p, const double* x0, int32_t k, double alpha, int32_t precision, double* z_io,
+                  double* eta_io, double* xi_out) {
+  return guarded([&]() -> int {
+    Problem* P = as_problem(p);
+    if (!P) return fail(SPOCK_ERR_INVALID_ARG, "not a problem handle");
+    if (!x0 || !z_io || !eta_io) return fail(SPOCK_ERR_INVALID_ARG, "NULL buffer");
+    CUDA_TRY(cudaSetDevice(P->device));
+    const int64_t nz = P->off.n_z, ne = P->off.n_eta;
+    double *dx0 = nullptr, *dz = nullptr, *de = nullptr;
+    CUDA_TRY(cudaMalloc(&dx0, sizeof(double) * P->nx));
+    CUDA_TRY(cudaMalloc(&dz, sizeof(double) * nz));
+    CUDA_TRY(cudaMalloc(&de, sizeof(double) * ne));
+    struct Guard {
+      void* a[3];
+      ~Guard() {
+        for (void* p : a) cudaFree(p);
+      }
+    } g{{dx0, dz, de}};
+    CUDA_TRY(cudaMemcpy(dx0, x0, sizeof(double) * P->nx, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(dz, z_io, sizeof(double) * nz, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(de, eta_io, sizeof(double) * ne, cudaMemcpyHostToDevice));
+    int rc = spock_cp_step_dev(p, dx0, k, alpha, precision, dz, de, xi_out, nullptr);
+    if (rc != SPOCK_OK) return rc;
+    CUDA_TRY(cudaMemcpy(z_io, dz, sizeof(double) * nz, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(eta_io, de, sizeof(double) * ne, cudaMemcpyDeviceToHost));
+    return SPOCK_OK;
+  });
+}
+
+// ---- operator-level entry points (FP64, device buffers) --------------------
+static KP<double> op_kp(Problem* P, double alpha) {
+  return make_kp<double>(*P, default_alpha(*P, alpha), P->idx.stage_begin);
+}
+
+int spock_apply_L_dev(spock_problem* p, const double* z, double* eta_out, void* stream) {
+  return guarded([&]() -> int {
+    Problem* P = as_problem(p);
+    if (!P || !z || !eta_out) return fail(SPOCK_ERR_INVALID_ARG, "NULL argument");
+    CUDA_TRY(cudaSetDevice(P->device));
+    KP<double> kp = op_kp(P, 0.0);
+    const int grid = std::min((P->tree.n + 3) / 4, sm_count() * 16);
+    launch_dual<double>(kp, DM_APPLY_L_, false, z, nullptr, nullptr, eta_out, nullptr, nullptr, grid,
+                        (cudaStream_t)stream);
+    check_launch();
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    return SPOCK_OK;
+  });
+}
+
+int spock_apply_Lt_dev(spock_problem* p, const double* eta, double* z_out, void* stream) {
+  return guarded([&]() -> int {
+    Problem* P = as_problem(p);
+    if (!P || !eta || !z_out) return fail(SPOCK_ERR_INVALID_ARG, "NULL argument");
+    CUDA_TRY(cudaSetDevice(P->device));
+    KP<double> kp = op_kp(P, 0.0);
+    const int grid = std::min((P->tree.n + 3) / 4, sm_count() * 16);
+    launch_primal<double>(kp, PM_APPLY_LT_, eta, nullptr, nullptr, nullptr, z_out, nullptr, nullptr, grid,
+                          (cudaStream_t)stream);
+    check_launch();
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    return SPOCK_OK;
+  });
+}
+
+int spock_prox_f_dev(spock_problem* p, const double* x0_dev, double alpha, const double* z, double* z_out,
+                     void* stream) {
+  return guarded([&]() -> int {
+    Problem* P = as_problem(p);
+    if (!P || !x0_dev || !z || !z_out) return fail(SPOCK_ERR_INVALID_ARG, "NULL argument");
+    CUDA_TRY(cudaSetDevice(P->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace* ws = get_ws_impl<double>(*P, 0);
+    KP<double> kp = op_kp(P, alpha);
+    CUDA_TRY(cudaMemcpyAsync(P->f64.x0, x0_dev, sizeof(double) * P->nx, cudaMemcpyDeviceToDevice, st));
+    launch_prep<double>(kp, z, (const double*)ws->zero_eta, z_out, sm_count() * 16, st);
+    launch_riccati<double>(kp, P->tree.stage_begin, z_out, st);
+    check_launch();
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return SPOCK_OK;
+  });
+}
+
+int spock_prox_gconj_dev(spock_problem* p, double alpha, const double* eta, double* eta_out, void* stream) {
+  return guarded([&]() -> int {
+    Problem* P = as_problem(p);
+    if (!P || !eta || !eta_out) return fail(SPOCK_ERR_INVALID_ARG, "NULL argument");
+    CUDA_TRY(cudaSetDevice(P->device));
+    KP<double> kp = op_kp(P, alpha);
+    const int grid = std::min((P->tree.n + 3) / 4, sm_count() * 16);
+    launch_dual<double>(kp, DM_PROXG_, false, nullptr, nullptr, eta, eta_out, nullptr, nullptr, grid,
+                        (cudaStream_t)stream);
+    check_launch();
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    return SPOCK_OK;
+  });
+}
+
+int spock_T_dev(spock_problem* p, const double* x0_dev, double alpha, const double* z, const double* eta,
+                double* z_out, double* eta_out, void* stream) {
+  return guarded([&]() -> int {
+    Problem* P = as_problem(p);
+    if (!P || !x0_dev || !z || !eta || !z_out || !eta_out) return fail(SPOCK_ERR_INVALID_ARG, "NULL argument");
+    CUDA_TRY(cudaSetDevice(P->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    KP<double> kp = op_kp(P, alpha);
+    CUDA_TRY(cudaMemcpyAsync(P->f64.x0, x0_dev, sizeof(double) * P->nx, cudaMemcpyDeviceToDevice, st));
+    launch_prep<double>(kp, z, eta, z_out, sm_count() * 16, st);
+    launch_riccati<double>(kp, P->tree.stage_begin, z_out, st);
+    launch_dual<double>(kp, DM_DUAL_, false, z, z_out, eta, eta_out, nullptr, nullptr,
+                        std::min((P->tree.n + 3) / 4, sm_count() * 16), st);
+    check_launch();
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return SPOCK_OK;
+  });
+}
+
+void spock_free(void* handle) {
+  if (!handle) return;
+  const int32_t tag = *reinterpret_cast<const int32_t*>(handle);
+  if (tag == TAG_TREE) delete reinterpret_cast<Tree*>(handle);
+  else if (tag == TAG_PROBLEM) delete reinterpret_cast<Problem*>(handle);
+}
+
+const char* spock_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

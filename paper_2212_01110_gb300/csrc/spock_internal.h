@@ -1,0 +1,119 @@
+// Internal data structures of libspock (not part of the ABI).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/spock.h"
+
+namespace spock {
+
+enum : int32_t { TAG_TREE = 0x54524545, TAG_PROBLEM = 0x50524f42 };
+
+// Maximum Anderson memory and per-node dimension handled by the kernels.
+constexpr int kMaxMemory = 16;
+constexpr int kMaxDim = 128;   // nx + nu
+constexpr int kNumStats = 8;   // residual statistics, see kernels.cuh
+
+struct Error {
+  int code;
+  std::string msg;
+};
+
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+// Scenario tree in the caller's numbering plus a breadth-first ("internal")
+// renumbering: nodes of a stage are contiguous, children of a node are
+// contiguous and in increasing user id, so the nonleaf nodes are the
+// internal ids [0, n_nonleaf) and the nonroot nodes [1, n).
+struct Tree {
+  int32_t tag = TAG_TREE;
+  int32_t n = 0, N = 0, n_nonleaf = 0, n_leaf = 0;
+  std::vector<int32_t> anc_user;
+  std::vector<double> prob_user;
+  std::vector<int32_t> user_of, int_of;        // internal -> user, user -> internal
+  std::vector<int32_t> parent, ch_begin, ch_count, stage, sib;  // internal
+  std::vector<int32_t> stage_begin;            // [N + 2]
+  std::vector<double> prob;                    // internal, conditional
+  // chain region: every node at stages >= chain_stage (and < N) has one child
+  int32_t chain_stage = 0;
+};
+
+// Offsets of every node's blocks inside the user-layout z and eta vectors
+// (documented in spock.h), indexed by internal id; -1 where absent.
+struct Offsets {
+  int64_t n_z = 0, n_eta = 0;
+  std::vector<int64_t> zx, zu, zz2, zs, ztau;   // ztau/zs of nonroot nodes (zs[0] = 0)
+  std::vector<int64_t> enl, enr, elf;
+};
+
+// Device copy of the problem for one scalar type S.
+template <typename S>
+struct DevFactors {
+  S* Gb = nullptr;   // [n-1][nx][nx+nu]  rows of [Abar^c | B^c], nonroot c
+  S* Gf = nullptr;   // [n-1][nx+nu][nx]  transpose of the above
+  S* NB = nullptr;   // [nl][K (nu x nx) | W^T (nu x nx) | Rtilde^-1 (nu x nu)]
+  S* Kt = nullptr;   // [nl][nx][nu]      K^T
+  S* qs = nullptr;   // [n][nx]  sqrt(Q) of the edge into the node
+  S* rs = nullptr;   // [n][nu]  sqrt(R)
+  S* qns = nullptr;  // [n][nx]  sqrt(Q_N) (leaves)
+  S* xlo = nullptr; S* xhi = nullptr;   // [n][nx]
+  S* ulo = nullptr; S* uhi = nullptr;   // [n][nu]
+  S* av = nullptr;   // [n] AV@R parameter
+  S* prob = nullptr; // [n] conditional probability
+  // scratch of the Riccati passes
+  S* xbar = nullptr;  // [n][nx]
+  S* ubar = nullptr;  // [nl][nu]
+  S* q = nullptr;     // [n][nx]
+  S* d = nullptr;     // [nl][nu]
+  S* x0 = nullptr;    // [nx]
+};
+
+struct DevIndex {
+  int32_t* parent = nullptr;
+  int32_t* ch_begin = nullptr;
+  int32_t* ch_count = nullptr;
+  int32_t* sib = nullptr;
+  int64_t *zx = nullptr, *zu = nullptr, *zz2 = nullptr, *zs = nullptr, *ztau = nullptr;
+  int64_t *enl = nullptr, *enr = nullptr, *elf = nullptr;
+  int32_t* stage_begin = nullptr;  // [N + 2]
+};
+
+struct Problem {
+  int32_t tag = TAG_PROBLEM;
+  int device = 0;
+  Tree tree;
+  Offsets off;
+  int32_t nx = 0, nu = 0;
+  double normL = 0.0;
+  double factor_seconds = 0.0;
+  DevIndex idx;
+  DevFactors<double> f64;
+  DevFactors<float> f32;
+  std::vector<void*> allocations;
+  // solver workspace, allocated on first use per precision
+  struct Workspace* ws64 = nullptr;
+  struct Workspace* ws32 = nullptr;
+  ~Problem();
+};
+
+// host-side helpers (tree.cpp, factor.cpp)
+int build_tree(int32_t n, const int32_t* anc, const double* prob, Tree& t);
+void build_offsets(const Tree& t, int nx, int nu, Offsets& o);
+
+// Offline factorisation of the projection on S1 (Algorithm 1), FP64.
+// Inputs in internal numbering: A [n][nx][nx], B [n][nx][nu].
+// Outputs (internal numbering):
+//   Gb  [n-1][nx][nx+nu]  [Abar^c | B^c]     (c = 1..n-1)
+//   NB  [nl][K | W^T | Rtilde^-1]
+// Returns false if some Rtilde is numerically singular (cannot happen for
+// finite data since Rtilde >= I).
+bool riccati_factor(const Tree& t, int nx, int nu, const std::vector<double>& A,
+                    const std::vector<double>& B, std::vector<double>& Gb,
+                    std::vector<double>& NB, int threads);
+
+}  // namespace spock

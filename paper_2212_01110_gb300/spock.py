@@ -1,0 +1,252 @@
+"""Python binding of libspock (include/spock.h): argument marshalling only.
+
+Every function named ``spock_*`` calls the C entry point of the same name.
+Host-buffer calls take numpy arrays; ``*_dev`` calls take CUDA tensors
+(torch is used only as the owner of device memory and streams).  The
+library must be built (``paper_2212_01110_gb300.build.build()``); importing
+this module without it raises ``ImportError`` -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libspock.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libspock.so is not built ({LIB_PATH}); run paper_2212_01110_gb300.build.build()")
+_lib = C.CDLL(LIB_PATH)
+
+SPOCK_OK = 0
+SPOCK_MAX_ITER = 1
+SPOCK_FP64 = 0
+SPOCK_FP32 = 1
+ERRORS = {-1: "INVALID_ARG", -2: "BAD_TREE", -3: "NOT_POSDEF", -4: "NUMERICAL", -5: "CUDA", -6: "OOM",
+          -7: "UNSUPPORTED"}
+BRANCHES = {0: "K0", 1: "K1", 2: "K2", 3: "CAP"}
+
+
+class SpockError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Settings(C.Structure):
+    _fields_ = [("eps_abs", C.c_double), ("eps_rel", C.c_double), ("alpha", C.c_double),
+                ("memory", C.c_int32), ("c0", C.c_double), ("c1", C.c_double), ("c2", C.c_double),
+                ("beta", C.c_double), ("sigma", C.c_double), ("lambda_", C.c_double),
+                ("rho_coef", C.c_double), ("max_iter", C.c_int32), ("max_backtracks", C.c_int32),
+                ("precision", C.c_int32), ("trace", C.POINTER(C.c_int32))]
+
+
+class Info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("n_T", C.c_int32),
+                ("n_K0", C.c_int32), ("n_K1", C.c_int32), ("n_K2", C.c_int32), ("n_cap", C.c_int32),
+                ("n_backtracks", C.c_int32), ("xi", C.c_double), ("xi0", C.c_double),
+                ("alpha", C.c_double), ("solve_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_I32 = C.POINTER(C.c_int32)
+_I64 = C.POINTER(C.c_int64)
+
+_sig = {
+    "spock_default_settings": ([C.POINTER(Settings)], C.c_int),
+    "spock_tree_create": ([C.c_int32, _I32, _D, C.POINTER(_P)], C.c_int),
+    "spock_tree_info": ([_P, _I32, _I32, _I32], C.c_int),
+    "spock_problem_create": ([_P, C.c_int32, C.c_int32] + [_D] * 10 + [C.c_int32, C.POINTER(_P)], C.c_int),
+    "spock_problem_info": ([_P, _I64, _I64, _D, _D], C.c_int),
+    "spock_solve": ([_P, _D, C.POINTER(Settings), _D, _D, C.c_int32, C.POINTER(Info)], C.c_int),
+    "spock_solve_dev": ([_P, _P, C.POINTER(Settings), _P, _P, C.c_int32, C.POINTER(Info), _P], C.c_int),
+    "spock_cp_step": ([_P, _D, C.c_int32, C.c_double, C.c_int32, _D, _D, _D], C.c_int),
+    "spock_cp_step_dev": ([_P, _P, C.c_int32, C.c_double, C.c_int32, _P, _P, _D, _P], C.c_int),
+    "spock_apply_L_dev": ([_P, _P, _P, _P], C.c_int),
+    "spock_apply_Lt_dev": ([_P, _P, _P, _P], C.c_int),
+    "spock_prox_f_dev": ([_P, _P, C.c_double, _P, _P, _P], C.c_int),
+    "spock_prox_gconj_dev": ([_P, C.c_double, _P, _P, _P], C.c_int),
+    "spock_T_dev": ([_P, _P, C.c_double, _P, _P, _P, _P, _P], C.c_int),
+    "spock_free": ([_P], None),
+    "spock_last_error": ([], C.c_char_p),
+}
+for _name, (_args, _res) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+EXPORTED = tuple(_sig)
+
+
+def _check(rc, ok=(SPOCK_OK,)):
+    if rc not in ok:
+        raise SpockError(rc, _lib.spock_last_error().decode())
+    return rc
+
+
+def _dptr(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_D)
+
+
+def _tptr(t, numel=None, dtype=None):
+    """Device pointer of a contiguous CUDA tensor (checked)."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected dtype {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} elements, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# thin wrappers with the C names
+# ---------------------------------------------------------------------------
+
+def spock_default_settings(**overrides):
+    s = Settings()
+    _check(_lib.spock_default_settings(C.byref(s)))
+    for k, v in overrides.items():
+        setattr(s, "lambda_" if k == "lambda" else k, v)
+    return s
+
+
+def spock_tree_create(anc, prob):
+    anc = np.ascontiguousarray(anc, dtype=np.int32)
+    prob, pp = _dptr(prob)
+    h = _P()
+    _check(_lib.spock_tree_create(len(anc), anc.ctypes.data_as(_I32), pp, C.byref(h)))
+    return h
+
+
+def spock_problem_create(tree, d):
+    nx, nu = int(d["nx"]), int(d["nu"])
+    arrs = [_dptr(d[k]) for k in ("A", "B", "Q", "R", "QN", "a", "xmin", "xmax", "umin", "umax")]
+    h = _P()
+    _check(_lib.spock_problem_create(tree, nx, nu, *[p for _, p in arrs], 0, C.byref(h)))
+    return h
+
+
+def spock_problem_info(problem):
+    nz, ne = C.c_int64(), C.c_int64()
+    nl, fs = C.c_double(), C.c_double()
+    _check(_lib.spock_problem_info(problem, C.byref(nz), C.byref(ne), C.byref(nl), C.byref(fs)))
+    return nz.value, ne.value, nl.value, fs.value
+
+
+def spock_solve(problem, x0, settings, z, eta, warm):
+    """Host buffers (float64 numpy arrays, modified in place)."""
+    info = Info()
+    x0, px = _dptr(x0)
+    assert z.dtype == np.float64 and eta.dtype == np.float64 and z.flags.c_contiguous and eta.flags.c_contiguous
+    rc = _lib.spock_solve(problem, px, C.byref(settings) if settings is not None else None,
+                          z.ctypes.data_as(_D), eta.ctypes.data_as(_D), int(warm), C.byref(info))
+    _check(rc, (SPOCK_OK, SPOCK_MAX_ITER))
+    return info
+
+
+def spock_solve_dev(problem, x0, settings, z, eta, warm, stream=None):
+    import torch
+    info = Info()
+    rc = _lib.spock_solve_dev(problem, _tptr(x0, dtype=torch.float64), C.byref(settings) if settings is not None else None,
+                              _tptr(z, dtype=torch.float64), _tptr(eta, dtype=torch.float64), int(warm),
+                              C.byref(info), _stream(stream))
+    _check(rc, (SPOCK_OK, SPOCK_MAX_ITER))
+    return info
+
+
+def spock_cp_step(problem, x0, k, alpha, precision, z, eta):
+    x0, px = _dptr(x0)
+    xi = C.c_double()
+    _check(_lib.spock_cp_step(problem, px, int(k), float(alpha), int(precision), z.ctypes.data_as(_D),
+                              eta.ctypes.data_as(_D), C.byref(xi)))
+    return xi.value
+
+
+def spock_cp_step_dev(problem, x0, k, alpha, precision, z, eta, stream=None):
+    import torch
+    xi = C.c_double()
+    _check(_lib.spock_cp_step_dev(problem, _tptr(x0, dtype=torch.float64), int(k), float(alpha), int(precision),
+                                  _tptr(z, dtype=torch.float64), _tptr(eta, dtype=torch.float64), C.byref(xi),
+                                  _stream(stream)))
+    return xi.value
+
+
+def spock_apply_L_dev(problem, z, eta_out, stream=None):
+    _check(_lib.spock_apply_L_dev(problem, _tptr(z), _tptr(eta_out), _stream(stream)))
+
+
+def spock_apply_Lt_dev(problem, eta, z_out, stream=None):
+    _check(_lib.spock_apply_Lt_dev(problem, _tptr(eta), _tptr(z_out), _stream(stream)))
+
+
+def spock_prox_f_dev(problem, x0, alpha, z, z_out, stream=None):
+    _check(_lib.spock_prox_f_dev(problem, _tptr(x0), float(alpha), _tptr(z), _tptr(z_out), _stream(stream)))
+
+
+def spock_prox_gconj_dev(problem, alpha, eta, eta_out, stream=None):
+    _check(_lib.spock_prox_gconj_dev(problem, float(alpha), _tptr(eta), _tptr(eta_out), _stream(stream)))
+
+
+def spock_T_dev(problem, x0, alpha, z, eta, z_out, eta_out, stream=None):
+    _check(_lib.spock_T_dev(problem, _tptr(x0), float(alpha), _tptr(z), _tptr(eta), _tptr(z_out), _tptr(eta_out),
+                            _stream(stream)))
+
+
+def spock_free(handle):
+    _lib.spock_free(handle)
+
+
+def spock_last_error():
+    return _lib.spock_last_error().decode()
+
+
+# ---------------------------------------------------------------------------
+# convenience owner of a tree + problem pair
+# ---------------------------------------------------------------------------
+
+class Problem:
+    """Tree and problem handles built from a workload dict (see
+    ``workloads``); frees both on close / garbage collection."""
+
+    def __init__(self, d):
+        self.tree = spock_tree_create(d["anc"], d["prob"])
+        try:
+            self.handle = spock_problem_create(self.tree, d)
+        except Exception:
+            spock_free(self.tree)
+            raise
+        self.nx, self.nu = int(d["nx"]), int(d["nu"])
+        self.n_z, self.n_eta, self.norm_L, self.factor_seconds = spock_problem_info(self.handle)
+
+    @property
+    def n_v(self):
+        return self.n_z + self.n_eta
+
+    def close(self):
+        if getattr(self, "handle", None):
+            spock_free(self.handle)
+            self.handle = None
+        if getattr(self, "tree", None):
+            spock_free(self.tree)
+            self.tree = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,51 @@
+"""Helpers shared by the GPU parity tests: build the oracle and the CUDA
+problem from the same seeded workload, compare element by element."""
+import numpy as np
+
+from oracle.cp import CP
+from oracle.problem import Problem as OProblem
+
+RTOL = 1e-10   # FP64 parity: relative to max(1, |reference|_inf)
+
+
+def rel_err(a, b):
+    a = np.asarray(a, float)
+    b = np.asarray(b, float)
+    return float(np.max(np.abs(a - b)) / max(1.0, float(np.max(np.abs(b))))) if b.size else 0.0
+
+
+class Pair:
+    def __init__(self, d):
+        import torch
+        from paper_2212_01110_gb300 import spock
+        self.d = d
+        self.op = OProblem(d)
+        self.cp = CP(self.op)
+        self.gp = spock.Problem(d)
+        assert (self.gp.n_z, self.gp.n_eta) == (self.op.lay.n_z, self.op.lay.n_eta)
+        assert abs(self.gp.norm_L - self.cp.normL) < 1e-12 * self.cp.normL
+        self.alpha = self.cp.alpha
+        self.dev = torch.device("cuda:0")
+        self.x0 = torch.tensor(d["x0"], dtype=torch.float64, device=self.dev)
+
+    def t(self, a):
+        import torch
+        return torch.tensor(np.asarray(a, float), dtype=torch.float64, device=self.dev)
+
+
+# trees spanning the code paths: full branching (no chain region), chains
+# below branching stages, a pure chain (every node one child), ragged
+# branching, the tree of Fig. 1, and state/input sizes crossing 32/64/96 lanes
+def cases():
+    from paper_2212_01110_gb300 import workloads as W
+    return {
+        "binary_N3": W.small_binary(0),
+        "fig1": W.with_tree(W.fig1_tree(), seed=1, nx=3, nu=2),
+        "ragged": W.random_tree(3, N=4, max_branch=3, nx=4, nu=3),
+        "chains": W.random_tree(4, N=6, max_branch=3, nx=5, nu=2, chain_after=2),
+        "pure_chain": W.random_tree(5, N=5, max_branch=1, nx=3, nu=2),
+        "nx1_nu1": W.random_tree(6, N=3, max_branch=2, nx=1, nu=1),
+        "wide_50_20": W.large_tree(0, branching_stages=2, branch=3, N=5, nx=50, nu=20),
+        "wide_100_28": W.random_tree(7, N=3, max_branch=2, nx=100, nu=28, stable=True),
+        "a0_a1": W.random_tree(8, N=3, max_branch=3, nx=3, nu=2, a_range=(0.0, 0.0)),
+    }

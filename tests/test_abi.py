@@ -1,0 +1,80 @@
+"""The C-ABI library builds, loads and exports every entry point declared in
+include/spock.h; host-only entry points behave (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2212_01110_gb300 import build
+    path = build.build()
+    return C.CDLL(path)
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "spock.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(spock_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_header(lib):
+    from paper_2212_01110_gb300 import spock
+    assert set(declared_functions()) == set(spock.EXPORTED)
+
+
+def test_host_only_calls(lib):
+    from paper_2212_01110_gb300 import spock, workloads
+    s = spock.spock_default_settings()
+    assert s.eps_abs == 1e-6 and s.memory == 3 and s.max_backtracks == 30
+    d = workloads.small_binary(0)
+    t = spock.spock_tree_create(d["anc"], d["prob"])
+    n, N, nl = C.c_int32(), C.c_int32(), C.c_int32()
+    assert lib.spock_tree_info(t, C.byref(n), C.byref(N), C.byref(nl)) == 0
+    assert (n.value, N.value, nl.value) == (15, 3, 7)
+    spock.spock_free(t)
+    spock.spock_free(None)
+
+
+@pytest.mark.parametrize("anc,code", [([-1], -1), ([0, 0], -2), ([-1, 0, 0, 1], -2), ([-1, 2, 1], -2),
+                                       ([-1, 7], -2)])
+def test_bad_tree_codes(lib, anc, code):
+    from paper_2212_01110_gb300 import spock
+    with pytest.raises(spock.SpockError) as e:
+        spock.spock_tree_create(np.array(anc, np.int32), np.ones(len(anc)))
+    assert e.value.code == code
+
+
+def test_bad_probabilities(lib):
+    from paper_2212_01110_gb300 import spock
+    with pytest.raises(spock.SpockError) as e:
+        spock.spock_tree_create(np.array([-1, 0, 0], np.int32), np.array([1.0, 0.3, 0.3]))
+    assert e.value.code == -1
+    assert "sum to 1" in spock.spock_last_error()
+
+
+def test_fig1_tree_accepted(lib):
+    import json
+    from paper_2212_01110_gb300 import spock
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "fig1_tree.json")))
+    anc = np.array(g["anc"], np.int32)
+    prob = np.ones(len(anc))
+    for k, ch in g["children"].items():
+        prob[ch] = 1.0 / len(ch)
+    t = spock.spock_tree_create(anc, prob)
+    n, N, nl = C.c_int32(), C.c_int32(), C.c_int32()
+    assert lib.spock_tree_info(t, C.byref(n), C.byref(N), C.byref(nl)) == 0
+    assert (n.value, N.value, nl.value) == (9, g["N"], len(g["nonleaf"]))
+    spock.spock_free(t)

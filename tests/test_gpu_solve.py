@@ -1,0 +1,138 @@
+"""CUDA iterations through the C-ABI against the oracle: fixed-k vanilla CP
+iterates (1e-10 relative), SPOCK fixed-k iterates with the GPU's branch
+trace replayed in the oracle, converged solutions within the solve
+tolerance, host-buffer and device-buffer entry points, warm start, FP32
+mode errors against the FP64 oracle, error paths."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from oracle.cp import vanilla_cp
+from oracle.spock import Settings as OSettings, spock as ospock
+from paper_2212_01110_gb300 import workloads as W
+from tests.gpu_common import RTOL, Pair, cases, rel_err
+
+pytestmark = pytest.mark.gpu
+CASES = cases()
+NAMES = ["binary_N3", "fig1", "ragged", "chains", "pure_chain", "wide_50_20", "a0_a1"]
+
+
+@pytest.fixture(scope="module", params=NAMES)
+def pair(request):
+    return Pair(CASES[request.param])
+
+
+def _run_cp(pair, k, z0, e0, precision=0):
+    from paper_2212_01110_gb300 import spock
+    z = pair.t(z0)
+    e = pair.t(e0)
+    xi = spock.spock_cp_step_dev(pair.gp.handle, pair.x0, k, pair.alpha, precision, z, e)
+    return np.concatenate([z.cpu().numpy(), e.cpu().numpy()]), xi
+
+
+def test_vanilla_cp_fixed_k(pair):
+    rng = np.random.default_rng(4)
+    z0 = rng.standard_normal(pair.gp.n_z)
+    e0 = rng.standard_normal(pair.gp.n_eta)
+    k = 25
+    got, xi = _run_cp(pair, k, z0, e0)
+    ref, xi_ref = vanilla_cp(pair.cp, np.concatenate([z0, e0]), pair.d["x0"], k)
+    assert rel_err(got, ref) < RTOL
+    assert abs(xi - xi_ref) < 1e-8 * max(1, xi_ref)
+
+
+def test_spock_fixed_k_replayed(pair):
+    """k SPOCK iterations on the GPU with its branch trace recorded; the
+    oracle replays the same branches; the returned T(v) must agree."""
+    from paper_2212_01110_gb300 import spock
+    K = 30
+    trace = (C.c_int32 * (2 * K))()
+    s = spock.spock_default_settings(max_iter=K, alpha=pair.alpha, eps_abs=1e-14, eps_rel=1e-14)
+    s.trace = C.cast(trace, C.POINTER(C.c_int32))
+    z = pair.t(np.zeros(pair.gp.n_z))
+    e = pair.t(np.zeros(pair.gp.n_eta))
+    info = spock.spock_solve_dev(pair.gp.handle, pair.x0, s, z, e, 0)
+    assert info.status == spock.SPOCK_MAX_ITER and info.iterations == K
+    tr = [(spock.BRANCHES[trace[2 * i]], trace[2 * i + 1]) for i in range(K)]
+    res = ospock(pair.cp, pair.d["x0"], s=OSettings(eps_abs=1e-14, eps_rel=1e-14, max_iter=K), forced=tr)
+    got = np.concatenate([z.cpu().numpy(), e.cpu().numpy()])
+    assert res.trace == tr
+    assert rel_err(got, res.v) < RTOL
+    # free-running oracle decisions: report near ties, require equality otherwise
+    free = ospock(pair.cp, pair.d["x0"], s=OSettings(eps_abs=1e-14, eps_rel=1e-14, max_iter=K))
+    same = sum(a == b for a, b in zip(free.trace, tr))
+    assert same >= K - 2, (free.trace, tr)
+
+
+@pytest.mark.parametrize("name", ["binary_N3", "fig1", "ragged", "chains"])
+def test_spock_converged(name):
+    from paper_2212_01110_gb300 import spock
+    pair = Pair(CASES[name])
+    s = spock.spock_default_settings(alpha=pair.alpha)
+    z = np.zeros(pair.gp.n_z)
+    e = np.zeros(pair.gp.n_eta)
+    info = spock.spock_solve(pair.gp.handle, pair.d["x0"], s, z, e, 0)
+    assert info.status == spock.SPOCK_OK
+    assert info.xi <= max(1e-6, 1e-6 * info.xi0) * 1.0000001
+    ref = ospock(pair.cp, pair.d["x0"], s=OSettings())
+    assert ref.status == "converged"
+    # both are 1e-6-accurate solutions: the optimal cost and the trajectory agree to the tolerance scale
+    assert abs(z[0] - ref.v[0]) < 1e-4 * max(1, abs(ref.v[0]))
+    x_idx = slice(1, 1 + pair.op.tree.n * pair.op.nx)
+    assert np.max(np.abs(z[x_idx] - ref.v[x_idx])) < 1e-3
+
+
+def test_warm_start_converges_immediately():
+    from paper_2212_01110_gb300 import spock
+    pair = Pair(CASES["binary_N3"])
+    s = spock.spock_default_settings(alpha=pair.alpha)
+    z = np.zeros(pair.gp.n_z)
+    e = np.zeros(pair.gp.n_eta)
+    info1 = spock.spock_solve(pair.gp.handle, pair.d["x0"], s, z, e, 0)
+    info2 = spock.spock_solve(pair.gp.handle, pair.d["x0"], s, z, e, 1)
+    assert info2.status == spock.SPOCK_OK
+    assert info2.iterations < max(5, info1.iterations // 10)
+
+
+def test_fp32_mode_against_fp64_oracle():
+    """FP32 operator, FP64 residual/Anderson: error against the FP64 oracle
+    stated for the cost and the trajectory (config-1 tree)."""
+    from paper_2212_01110_gb300 import spock
+    pair = Pair(CASES["binary_N3"])
+    s = spock.spock_default_settings(alpha=pair.alpha, precision=spock.SPOCK_FP32, memory=5,
+                                     eps_abs=1e-5, eps_rel=1e-5, max_iter=20000)
+    z = np.zeros(pair.gp.n_z)
+    e = np.zeros(pair.gp.n_eta)
+    info = spock.spock_solve(pair.gp.handle, pair.d["x0"], s, z, e, 0)
+    ref = ospock(pair.cp, pair.d["x0"], s=OSettings(eps_abs=1e-9, eps_rel=1e-9))
+    assert info.status in (spock.SPOCK_OK, spock.SPOCK_MAX_ITER)
+    assert abs(z[0] - ref.v[0]) < 1e-3 * max(1, abs(ref.v[0]))
+
+
+def test_errors():
+    from paper_2212_01110_gb300 import spock
+    d = W.small_binary(0)
+    pair = Pair(d)
+    x0 = d["x0"].copy()
+    x0[0] = 100.0  # outside the root's box
+    z = np.zeros(pair.gp.n_z)
+    e = np.zeros(pair.gp.n_eta)
+    with pytest.raises(spock.SpockError) as ex:
+        spock.spock_solve(pair.gp.handle, x0, None, z, e, 0)
+    assert ex.value.code == -1
+    bad = dict(d)
+    bad["Q"] = d["Q"].copy()
+    bad["Q"][3, 0] = -1.0
+    with pytest.raises(spock.SpockError) as ex:
+        spock.Problem(bad)
+    assert ex.value.code == -3
+    bad = dict(d)
+    bad["A"] = d["A"].copy()
+    bad["A"][2, 0, 0] = np.nan
+    with pytest.raises(spock.SpockError) as ex:
+        spock.Problem(bad)
+    assert ex.value.code == -4
+    s = spock.spock_default_settings(alpha=10.0)
+    with pytest.raises(spock.SpockError):
+        spock.spock_solve(pair.gp.handle, d["x0"], s, z, e, 0)
