@@ -1,0 +1,380 @@
+"""Benchmark: SPOCK on the 62,805-node scenario tree on one GB300.
+
+Workload: branching 4 for 6 stages then chains, N = 20, nx = 50, nu = 20
+(4.62 M primal / 9.29 M dual variables), seeded synthetic data, inputs
+resident in HBM.  One step = one SPOCK iteration (Algorithm 3: residual
+r = v - T(v), termination test, Anderson update and direction, K0 or the
+SuperMann line search with its extra T evaluations); K steps are timed as one
+cold-start solve capped at K iterations.  value = CP operator evaluations per
+second over the timed steps ("CP iters/s").  A separate cold-start solve,
+capped by a time budget, reports the time to the 1e-6 residual.  The FP64
+path is the headline (the problem is stated in double precision); the FP32
+operator path (FP64 residual and Anderson least squares) is reported in the
+same line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves its own seeded instance (replicas,
+weak scaling, no collective on the data path); the timed region is bracketed
+by barriers and the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+METRIC = "time-to-1e-6 residual and CP iters/s (FP64 vs FP32/batched); % HBM peak"
+WORKLOAD = dict(branching_stages=6, branch=4, N=20, nx=50, nu=20)
+SAMPLE = dict(branching_stages=2, branch=4, N=20, nx=50, nu=20)   # oracle sample (309 nodes)
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(HERE, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# Measured FP64 FMA throughput of this GB300 pool (microbenchmark of 8
+# independent FMA chains per thread, 152 x 8 blocks of 256 threads): about
+# 2 FP64 FMA per clock per SM.  Used as the ALU roofline of the FP64 path.
+FP64_PEAK_TFLOPS = 1.193
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        os.makedirs(os.path.join(HERE, "gpurun_out"), exist_ok=True)
+        self.path = os.path.join(HERE, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def bytes_bwd_chain(d, n_chains, chain_len, elt):
+    """Algorithmic bytes of one launch of the Riccati backward chain kernel:
+    per chain node [Abar|B] (nx (nx+nu)), K, W^T (2 nu nx), Rt^-1 (nu^2),
+    xbar and ubar reads (nx + nu), d write (nu); per chain the leaf's xbar
+    (nx) and the q of its top node (nx)."""
+    nx, nu = d["nx"], d["nu"]
+    per_node = nx * (nx + nu) + 2 * nu * nx + nu * nu + nx + 2 * nu
+    return elt * (n_chains * chain_len * per_node + n_chains * 2 * nx)
+
+
+def flops_bwd_chain(d, n_chains, chain_len):
+    nx, nu = d["nx"], d["nu"]
+    return 2.0 * n_chains * chain_len * (nx * (nx + nu) + nu * nu + 2 * nu * nx)
+
+
+def bytes_fwd_chain(d, n_chains, chain_len, elt):
+    nx, nu = d["nx"], d["nu"]
+    per_node = (nx + nu) * nx + nx * nu + nu + nx + nu   # Gf, K^T, d read, x and u writes
+    return elt * (n_chains * chain_len * per_node + n_chains * nx)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2212_01110_gb300 import build
+    build.build()
+    from paper_2212_01110_gb300 import spock, workloads
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    t0 = time.time()
+    wl = dict(WORKLOAD, branching_stages=args.branching_stages)
+    d = workloads.large_tree(seed=rank, **wl)
+    gen_s = time.time() - t0
+    P = spock.Problem(d)
+    n = len(d["anc"])
+    nl = n - int(np.sum(np.bincount(d["anc"][1:], minlength=n) == 0))
+    n_chains, chain_len = 4 ** wl["branching_stages"], wl["N"] - wl["branching_stages"]
+    x0 = torch.tensor(d["x0"], dtype=torch.float64, device=dev)
+    z = torch.zeros(P.n_z, dtype=torch.float64, device=dev)
+    e = torch.zeros(P.n_eta, dtype=torch.float64, device=dev)
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+
+    def settings(prec, profile, max_iter):
+        return spock.spock_default_settings(precision=prec, memory=args.memory, max_iter=max_iter,
+                                            profile=int(profile))
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed(prec):
+        infos = []
+        spock.spock_solve_dev(P.handle, x0, settings(prec, False, args.warmup), z, e, 0)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with Clocks(local_rank) as clk:
+            ev0.record(st)
+            infos.append(spock.spock_solve_dev(P.handle, x0, settings(prec, True, args.steps), z, e, 0))
+            ev1.record(st)
+            torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        if world > 1:
+            t = torch.tensor([ms], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        nT = sum(i.n_T for i in infos)
+        if world > 1:
+            t = torch.tensor([nT], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t)
+            nT_all = float(t.item())
+        else:
+            nT_all = float(nT)
+        return ms, nT, nT_all, infos, clk.summary()
+
+    def roofline(infos, prec):
+        elt = 8 if prec == spock.SPOCK_FP64 else 4
+        timed_T = sum(i.n_timed for i in infos)
+        t_bwd = sum(i.t_group_ms[1] for i in infos) / max(timed_T, 1)
+        t_fwd = sum(i.t_group_ms[4] for i in infos) / max(timed_T, 1)
+        bb = bytes_bwd_chain(d, n_chains, chain_len, elt)
+        fl = flops_bwd_chain(d, n_chains, chain_len)
+        groups = {g: sum(i.t_group_ms[k] for i in infos) / max(timed_T, 1)
+                  for k, g in enumerate(spock.Info.GROUPS)}
+        if prec == spock.SPOCK_FP64:
+            ach = fl / (t_bwd * 1e-3) / 1e12
+            r = {"kernel": "k_bwd_chain<double>", "bound": "alu", "achieved": round(ach, 4),
+                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
+                 "peak_source": "measured FP64 FMA microbenchmark on this pool",
+                 "traffic": None, "algorithmic_bytes": bb, "algorithmic_flops": fl,
+                 "hbm_achieved_gbs": round(bb / (t_bwd * 1e-3) / 1e9, 1),
+                 "hbm_frac_of_measured": round(bb / (t_bwd * 1e-3) / 1e9 / hbm, 4),
+                 "avg_launch_ms": round(t_bwd, 4)}
+        else:
+            ach = bb / (t_bwd * 1e-3) / 1e9
+            r = {"kernel": "k_bwd_chain<float>", "bound": "hbm", "achieved": round(ach, 1), "peak": hbm,
+                 "unit": "GB/s", "frac": round(ach / hbm, 4), "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                 "traffic": None, "algorithmic_bytes": bb, "avg_launch_ms": round(t_bwd, 4)}
+        fb = bytes_fwd_chain(d, n_chains, chain_len, elt)
+        r["fwd_chain"] = {"avg_launch_ms": round(t_fwd, 4), "algorithmic_bytes": fb,
+                          "achieved_gbs": round(fb / (t_fwd * 1e-3) / 1e9, 1) if t_fwd > 0 else None}
+        r["per_T_group_ms"] = {k: round(v, 4) for k, v in groups.items()}
+        return r
+
+    def time_to_tol(prec, ms_per_iter):
+        """Cold-start solve to xi <= 1e-6, capped by the time budget."""
+        cap = max(10, int(args.tol_budget_s * 1e3 / max(ms_per_iter, 1e-3)))
+        inf = spock.spock_solve_dev(P.handle, x0, settings(prec, False, cap), z, e, 0)
+        return {"seconds": round(inf.solve_ms * 1e-3, 3), "iterations": inf.iterations, "n_T": inf.n_T,
+                "xi": inf.xi, "xi0": inf.xi0, "tol": max(1e-6, 1e-6 * inf.xi0),
+                "status": "converged" if inf.status == 0 else f"not reached within the {args.tol_budget_s:.0f} s cap",
+                "K0_K1_K2": [inf.n_K0, inf.n_K1, inf.n_K2]}
+
+    out = {}
+    precs = [spock.SPOCK_FP64, spock.SPOCK_FP32] if args.precision == "both" else \
+        [spock.SPOCK_FP64 if args.precision == "fp64" else spock.SPOCK_FP32]
+    for prec in precs:
+        ms, nT, nT_all, infos, clk = timed(prec)
+        i0 = infos[0]
+        out[prec] = dict(
+            value=nT_all / (ms * 1e-3), ms_per_step=ms / max(i0.iterations, 1), n_T=nT, infos=infos, clocks=clk,
+            iterations=i0.iterations, n_T_steps=i0.n_T, branches=[i0.n_K0, i0.n_K1, i0.n_K2, i0.n_cap],
+            gpu_launches=sum(i.n_launches for i in infos), roofline=roofline(infos, prec))
+        if args.tol_budget_s > 0:
+            out[prec]["time_to_tol"] = time_to_tol(prec, out[prec]["ms_per_step"])
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    head = precs[0]
+    zh = torch.zeros(P.n_z, dtype=torch.float64).pin_memory().numpy()
+    eh = torch.zeros(P.n_eta, dtype=torch.float64).pin_memory().numpy()
+    x0h = torch.tensor(d["x0"], dtype=torch.float64).pin_memory().numpy()
+    spock.spock_solve(P.handle, x0h, settings(head, False, args.warmup), zh, eh, 0)
+    barrier()
+    t0 = time.perf_counter()
+    inf = spock.spock_solve(P.handle, x0h, settings(head, False, args.steps), zh, eh, 0)
+    nT_e2e = inf.n_T
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    if world > 1:
+        t = torch.tensor([e2e_s, nT_e2e], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t[:1], op=torch.distributed.ReduceOp.MAX)
+        tt = torch.tensor([float(nT_e2e)], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt)
+        e2e_s, nT_e2e = float(t[0].item()), float(tt.item())
+    e2e = {"value": nT_e2e / e2e_s, "unit": "CP iters/s", "h2d_bytes_per_step": 8 * P.nx / args.steps,
+           "d2h_bytes_per_step": 8 * (P.n_z + P.n_eta) / args.steps, "ms_per_step": 1e3 * e2e_s / args.steps,
+           "api": "spock_solve: host buffers (pinned), x0 copied in and (z, eta) copied out inside the timed "
+                  "call, K iterations from a cold start"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(n, seconds=args.cpu_seconds)
+
+    if rank == 0:
+        h = out[head]
+        line = {
+            "metric": METRIC, "value": round(h["value"], 2), "unit": "CP iters/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(h["ms_per_step"], 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if head == spock.SPOCK_FP64 else "f32", "data": "synthetic (seeded, rank = seed)",
+            "config": {"workload": f"large scenario tree: branching 4 for {wl['branching_stages']} stages then 1, "
+                                   f"N=20 ({n:,} nodes, {n_chains:,} scenarios), nx=50, nu=20, AV@R a~U(0.1,0.9), "
+                                   "box |x|<=5 |u|<=1",
+                       "n_z": P.n_z, "n_eta": P.n_eta, "nodes": n, "nonleaf": nl,
+                       "step": "one SPOCK iteration (Anderson m=%d), K steps = one cold-start solve capped "
+                               "at K iterations" % args.memory,
+                       "l2": "inputs larger than L2 (factors 5.1 GB FP64 / 2.6 GB FP32 per T)",
+                       "parallelism": f"replicas x{world}"},
+            "time_to_tol": h.get("time_to_tol"), "iterations": h["iterations"], "n_T_steps": h["n_T_steps"],
+            "branches_K0_K1_K2_cap": h["branches"], "roofline": h["roofline"], "clocks": h["clocks"], "gpu_launches": h["gpu_launches"], "e2e": e2e,
+            "setup": {"instance_generation_s": round(gen_s, 2), "factor_seconds_alg1_fp64_host": round(P.factor_seconds, 3)},
+        }
+        for prec, nm in ((spock.SPOCK_FP32, "fp32"), (spock.SPOCK_FP64, "fp64")):
+            if prec in out and prec != head:
+                o = out[prec]
+                tt, tf = o.get("time_to_tol"), out.get(spock.SPOCK_FP64, {}).get("time_to_tol")
+                line[nm] = {"value": round(o["value"], 2), "unit": "CP iters/s",
+                            "ms_per_step": round(o["ms_per_step"], 3), "time_to_tol": tt,
+                            "iterations": o["iterations"], "n_T_steps": o["n_T_steps"],
+                            "branches_K0_K1_K2_cap": o["branches"], "roofline": o["roofline"],
+                            "clocks": o["clocks"], "gpu_launches": o["gpu_launches"],
+                            "speedup_vs_fp64_per_step": round(out[spock.SPOCK_FP64]["ms_per_step"] / o["ms_per_step"], 3)
+                            if spock.SPOCK_FP64 in out else None,
+                            "speedup_vs_fp64_time_to_tol": round(tf["seconds"] / tt["seconds"], 3)
+                            if (tt and tf and tt["status"] == "converged" and tf["status"] == "converged") else None}
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(n_full, seconds=15.0):
+    """The oracle (FP64 numpy/scipy, dense-structure KKT solve for S1) timed on
+    a bounded sample: T evaluations on a 309-node tree of the same family,
+    scaled to the full tree by the node count."""
+    from oracle.cp import CP
+    from oracle.problem import Problem as OP
+    from paper_2212_01110_gb300 import workloads
+    d = workloads.large_tree(seed=0, **SAMPLE)
+    cp = CP(OP(d))
+    v = np.zeros(cp.n_z + cp.n_eta)
+    cp.T(v, d["x0"])
+    k, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        v = cp.T(v, d["x0"])
+        k += 1
+    dt = time.perf_counter() - t0
+    n_s = len(d["anc"])
+    rate = k / dt * n_s / n_full
+    return {"value": rate, "unit": "CP iters/s", "cores": 1, "kind": "oracle",
+            "sample": f"{k} oracle T evaluations in {dt:.1f} s on a {n_s}-node tree of the same family "
+                      f"(branching 4 for 2 stages, N=20, nx=50, nu=20), scaled by nodes {n_s}/{n_full}; "
+                      "scipy sparse LU solve + sparse matvecs, single-threaded"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2212_01110_gb300 import workloads
+    d = workloads.large_tree(seed=0, **WORKLOAD)
+    n_full = len(d["anc"])
+    del d
+    samples = []
+    cpu_baseline(n_full, seconds=min(args.cpu_seconds, 3.0))
+    samples.append(cpu_baseline(n_full, seconds=args.cpu_seconds))
+    v = statistics.mean(s["value"] for s in samples)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "CP iters/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "config": {"workload": "large scenario tree: branching 4 for 6 stages then 1, N=20 (62,805 nodes), nx=50, nu=20",
+                       "step": "oracle T evaluations on a bounded sample, scaled to the full tree"},
+            "cpu_baseline": {"value": v, "unit": "CP iters/s", "cores": 1, "kind": "oracle",
+                             "sample": samples[0]["sample"]},
+            "e2e": {"value": v, "unit": "CP iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="both", choices=["fp64", "fp32", "both"])
+    ap.add_argument("--memory", type=int, default=3)
+    ap.add_argument("--tol-budget-s", type=float, default=60.0,
+                    help="time budget of the time-to-1e-6 solve per precision (0 skips it)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--branching-stages", type=int, default=6,
+                    help="stages with 4 children (6 = the 62,805-node tree; smaller trees for profiling)")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -87,6 +87,8 @@ typedef struct spock_settings {
   int32_t precision;    /* spock_precision                                   (FP64) */
   int32_t* trace;       /* optional host array of 2*max_iter int32: per iteration
                            (branch, backtracks), branch 0=K0 1=K1 2=K2 3=cap  (NULL) */
+  int32_t profile;      /* nonzero: time the kernel groups of every T evaluation
+                           with CUDA events on the solve's stream (info.t_*)  (0)    */
 } spock_settings;
 
 /* Outcome of a solve. */
@@ -99,6 +101,14 @@ typedef struct spock_info {
   double xi0;           /* xi at the initial point */
   double alpha;         /* CP step used */
   double solve_ms;      /* device time of the solve (CUDA events) */
+  int32_t n_launches;   /* kernels launched by the solve */
+  int32_t n_timed;      /* T evaluations timed when settings.profile != 0 */
+  /* summed device time (ms) of the kernel groups of the timed T evaluations:
+     [0] zbar = z - alpha L* eta and proj_S2, [1] Riccati backward, chain
+     region, [2] Riccati backward, branching stages, [3] Riccati forward,
+     branching stages, [4] Riccati forward, chain region, [5] L and
+     prox_{alpha g*} (dual update), [6] residual statistics */
+  double t_group_ms[7];
 } spock_info;
 
 /* Fills *s with the defaults listed above.  Returns SPOCK_ERR_INVALID_ARG

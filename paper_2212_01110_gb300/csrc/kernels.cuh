@@ -33,6 +33,7 @@ struct KP {
   int32_t n, nl, nx, nu, N, chain_stage, n_chains;
   int64_t n_z, n_eta;
   S alpha;
+  S inv_alpha;        // 1 / alpha (multiplications instead of FP64 divisions)
   const int32_t* __restrict__ parent;
   const int32_t* __restrict__ ch_begin;
   const int32_t* __restrict__ ch_count;
@@ -86,12 +87,31 @@ __device__ __forceinline__ S clampv(S v, S lo, S hi) {
   return v < lo ? lo : (v > hi ? hi : v);
 }
 
-// Statistics accumulator of one lane (always FP64).
+// Statistics accumulator of one lane: sums in FP64; the terms of one node
+// block are first summed in the working precision S (a handful of entries
+// per lane), so that the FP64 pipe -- 1/64 of the FP32 rate on this GPU --
+// sees one add per node and statistic instead of one per entry.
 struct StatAcc {
   double s[8];
   __device__ void zero() {
 #pragma unroll
     for (int i = 0; i < 8; ++i) s[i] = 0.0;
+  }
+};
+template <typename S>
+struct NodeAcc {
+  S s[8];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s[i] = S(0);
+  }
+  __device__ __forceinline__ void flush(StatAcc& a) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (i == 3 || i == 4) a.s[i] = fmax(a.s[i], (double)s[i]);
+      else a.s[i] += (double)s[i];
+    }
+    zero();
   }
 };
 

@@ -104,21 +104,21 @@ __global__ void __launch_bounds__(128) k_prep(KP<S> p, const S* __restrict__ z,
 // residual row of L is L r_z = Lz - Lzp.
 
 template <typename S, int MODE, bool STATS, bool DIR>
-__device__ __forceinline__ void dual_emit(const KP<S>& p, StatAcc& acc, const S* __restrict__ eta,
+__device__ __forceinline__ void dual_emit(const KP<S>& p, NodeAcc<S>& acc, const S* __restrict__ eta,
                                           S* __restrict__ out, const S* __restrict__ deta,
                                           int64_t ie, S Lz, S Lzp, S Ld, S outv) {
   out[ie] = outv;
   if (MODE == DM_DUAL && STATS) {
-    const double re = (double)eta[ie] - (double)outv;
-    const double lrz = (double)Lz - (double)Lzp;
+    const S re = eta[ie] - outv;
+    const S lrz = Lz - Lzp;
     acc.s[ST_RE2] += re * re;
     acc.s[ST_RE_LRZ] += re * lrz;
-    acc.s[ST_XID] = fmax(acc.s[ST_XID], fabs(re / (double)p.alpha - lrz));
+    acc.s[ST_XID] = fmax(acc.s[ST_XID], fabs(re * p.inv_alpha - lrz));
     if (DIR) {
-      const double de = (double)deta[ie];
+      const S de = deta[ie];
       acc.s[ST_RD] += re * de;
       acc.s[ST_LRZ_DE] += lrz * de;
-      acc.s[ST_RE_LDZ] += re * (double)Ld;
+      acc.s[ST_RE_LDZ] += re * Ld;
     }
   }
 }
@@ -134,22 +134,25 @@ __device__ __forceinline__ S dual_w(const KP<S>& p, const S* __restrict__ eta, i
 // projects w / alpha onto SOC + (0, .., 1/2, -1/2) and returns, per entry,
 // w - alpha * projection.  SOC = {(v, t) : ||v|| <= t}, t the last entry.
 template <typename S>
-__device__ __forceinline__ void soc_prox(const S* wb, int dim, S al, int lane, S& nv_out, S& t_out) {
+__device__ __forceinline__ void soc_prox(const S* wb, int dim, S ial, int lane, S& nv_out, S& t_out,
+                                         S& scale_out) {
   S s2 = 0;
   for (int e = lane; e < dim - 1; e += 32) {
-    S v = wb[e] / al;
+    S v = wb[e] * ial;
     if (e == dim - 2) v -= S(0.5);
     s2 += v * v;
   }
   s2 = warp_sum(s2);
   nv_out = sqrt(s2);
-  t_out = wb[dim - 1] / al + S(0.5);
+  t_out = wb[dim - 1] * ial + S(0.5);
+  // one division per block: scale of the v part when projecting on the boundary
+  scale_out = (nv_out > t_out && nv_out > -t_out) ? S(0.5) * (nv_out + t_out) / nv_out : S(0);
 }
 
 template <typename S>
-__device__ __forceinline__ S soc_out(const S* wb, int dim, int e, S al, S nv, S t) {
+__device__ __forceinline__ S soc_out(const S* wb, int dim, int e, S al, S ial, S nv, S t, S scale) {
   // projection of (v, t) = w / alpha - shift
-  S v = wb[e] / al;
+  S v = wb[e] * ial;
   if (e == dim - 2) v -= S(0.5);
   if (e == dim - 1) v = t;
   S pr;
@@ -158,8 +161,7 @@ __device__ __forceinline__ S soc_out(const S* wb, int dim, int e, S al, S nv, S 
   } else if (nv <= -t) {
     pr = S(0);
   } else {
-    const S h = S(0.5) * (nv + t);
-    pr = (e == dim - 1) ? h : h * v / nv;
+    pr = (e == dim - 1) ? S(0.5) * (nv + t) : scale * v;
   }
   if (e == dim - 2) pr += S(0.5);
   if (e == dim - 1) pr -= S(0.5);
@@ -182,6 +184,9 @@ __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, 
   const S* deta = DIR ? dir + p.n_z : nullptr;
   StatAcc acc;
   acc.zero();
+  NodeAcc<S> nacc;
+  nacc.zero();
+  const S ial = p.inv_alpha;
   S* wb = wbuf[wl];
   S* lb = lbuf[wl];
   S* db = dbuf[wl];
@@ -204,7 +209,7 @@ __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, 
         row(z2 + e, S(1), Lz, Lzp, Ld);
         const S w = dual_w<S, MODE>(p, eta, el + e, Lz, Lzp);
         const S o = (MODE == DM_APPLY_L) ? w : (e < 2 * m ? fmin(w, S(0)) : S(0));
-        dual_emit<S, MODE, STATS, DIR>(p, acc, eta, out, deta, el + e, Lz, Lzp, Ld, o);
+        dual_emit<S, MODE, STATS, DIR>(p, nacc, eta, out, deta, el + e, Lz, Lzp, Ld, o);
       }
       {  // s^k - b^T y^k, b = (p^children, 0, 1)
         S bz = 0, bzp = 0, bd = 0;
@@ -225,7 +230,7 @@ __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, 
           const int64_t ie = el + 2 * m + 1;
           const S w = dual_w<S, MODE>(p, eta, ie, Lz, Lzp);
           const S o = (MODE == DM_APPLY_L) ? w : fmin(w, S(0));
-          dual_emit<S, MODE, STATS, DIR>(p, acc, eta, out, deta, ie, Lz, Lzp, Ld, o);
+          dual_emit<S, MODE, STATS, DIR>(p, nacc, eta, out, deta, ie, Lz, Lzp, Ld, o);
         }
       }
       const int64_t ex = el + 2 * m + 2;
@@ -241,8 +246,8 @@ __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, 
           hi = p.uhi[(int64_t)k * nu + (e - nx)];
         }
         const S w = dual_w<S, MODE>(p, eta, ex + e, Lz, Lzp);
-        const S o = (MODE == DM_APPLY_L) ? w : w - al * clampv(w / al, lo, hi);
-        dual_emit<S, MODE, STATS, DIR>(p, acc, eta, out, deta, ex + e, Lz, Lzp, Ld, o);
+        const S o = (MODE == DM_APPLY_L) ? w : w - al * clampv(w * ial, lo, hi);
+        dual_emit<S, MODE, STATS, DIR>(p, nacc, eta, out, deta, ex + e, Lz, Lzp, Ld, o);
       }
     }
     // ---- nonroot block (Q^1/2 x^anc, R^1/2 u^anc, tau/2, tau/2)
@@ -262,12 +267,12 @@ __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, 
       }
       __syncwarp();
       if (MODE != DM_APPLY_L) {
-        S nv, t;
-        soc_prox(wb, dim, al, lane, nv, t);
+        S nv, t, sc;
+        soc_prox(wb, dim, ial, lane, nv, t, sc);
         for (int e = lane; e < dim; e += 32) {
-          const S o = soc_out(wb, dim, e, al, nv, t);
+          const S o = soc_out(wb, dim, e, al, ial, nv, t, sc);
           // Lz - Lzp = lb[e]; pass (lb, 0) so that dual_emit sees L r_z
-          dual_emit<S, MODE, STATS, DIR>(p, acc, eta, out, deta, er + e, lb[e], S(0), db[e], o);
+          dual_emit<S, MODE, STATS, DIR>(p, nacc, eta, out, deta, er + e, lb[e], S(0), db[e], o);
         }
       }
       __syncwarp();
@@ -280,8 +285,8 @@ __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, 
         row(p.zx[k] + e, S(1), Lz, Lzp, Ld);
         const S w = dual_w<S, MODE>(p, eta, ef + e, Lz, Lzp);
         const S o = (MODE == DM_APPLY_L) ? w
-                                         : w - al * clampv(w / al, p.xlo[(int64_t)k * nx + e], p.xhi[(int64_t)k * nx + e]);
-        dual_emit<S, MODE, STATS, DIR>(p, acc, eta, out, deta, ef + e, Lz, Lzp, Ld, o);
+                                         : w - al * clampv(w * ial, p.xlo[(int64_t)k * nx + e], p.xhi[(int64_t)k * nx + e]);
+        dual_emit<S, MODE, STATS, DIR>(p, nacc, eta, out, deta, ef + e, Lz, Lzp, Ld, o);
       }
       const int dim = nx + 2;
       const int64_t es = ef + nx;
@@ -296,15 +301,16 @@ __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, 
       }
       __syncwarp();
       if (MODE != DM_APPLY_L) {
-        S nv, t;
-        soc_prox(wb, dim, al, lane, nv, t);
+        S nv, t, sc;
+        soc_prox(wb, dim, ial, lane, nv, t, sc);
         for (int e = lane; e < dim; e += 32) {
-          const S o = soc_out(wb, dim, e, al, nv, t);
-          dual_emit<S, MODE, STATS, DIR>(p, acc, eta, out, deta, es + e, lb[e], S(0), db[e], o);
+          const S o = soc_out(wb, dim, e, al, ial, nv, t, sc);
+          dual_emit<S, MODE, STATS, DIR>(p, nacc, eta, out, deta, es + e, lb[e], S(0), db[e], o);
         }
       }
       __syncwarp();
     }
+    if (MODE == DM_DUAL && STATS) nacc.flush(acc);
   }
   if (MODE == DM_DUAL && STATS) block_stats_store(acc, partials);
 }
@@ -324,15 +330,17 @@ __global__ void __launch_bounds__(128) k_primal(KP<S> p, const S* __restrict__ e
   const int nx = p.nx, nu = p.nu;
   StatAcc acc;
   acc.zero();
+  NodeAcc<S> nacc;
+  nacc.zero();
   auto E = [&](int64_t i) -> S { return MODE == PM_APPLY_LT ? eta[i] : eta[i] - etap[i]; };
   auto emit = [&](int64_t zi, S lt) {
     if (MODE == PM_APPLY_LT) {
       zout[zi] = lt;
     } else {
-      const double rz = (double)z[zi] - (double)zp[zi];
-      acc.s[ST_RZ2] += rz * rz;
-      acc.s[ST_XIP] = fmax(acc.s[ST_XIP], fabs(rz / (double)p.alpha - (double)lt));
-      if (DIR) acc.s[ST_RD] += rz * (double)dir[zi];
+      const S rz = z[zi] - zp[zi];
+      nacc.s[ST_RZ2] += rz * rz;
+      nacc.s[ST_XIP] = fmax(nacc.s[ST_XIP], fabs(rz * p.inv_alpha - lt));
+      if (DIR) nacc.s[ST_RD] += rz * dir[zi];
     }
   };
   for (int k = gw; k < p.n; k += nw) {
@@ -373,6 +381,7 @@ __global__ void __launch_bounds__(128) k_primal(KP<S> p, const S* __restrict__ e
       for (int r = lane; r < nx; r += 32)
         emit(p.zx[k] + r, E(ef + r) + p.qns[(int64_t)k * nx + r] * E(ef + nx + r));
     }
+    if (MODE == PM_STATS) nacc.flush(acc);
   }
   if (MODE == PM_STATS) block_stats_store(acc, partials);
 }

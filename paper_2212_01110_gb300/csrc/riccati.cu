@@ -304,39 +304,55 @@ __global__ void __launch_bounds__(128) k_fwd_chain(KP<S> p, S* __restrict__ zo) 
 // ---------------------------------------------------------------------------
 // launcher: the whole S1 projection (prep kernel already ran)
 // ---------------------------------------------------------------------------
+// Launches both passes; ev (optional, 3 events) is recorded after the
+// backward chain kernel, the backward stage kernels and the forward stage
+// kernels.  Returns the number of kernels launched.
 template <typename S, int SL>
-void riccati_passes_sl(const KP<S>& p, const std::vector<int32_t>& stage_begin, S* zo, cudaStream_t st) {
+int riccati_passes_sl(const KP<S>& p, const std::vector<int32_t>& stage_begin, S* zo, cudaStream_t st,
+                      cudaEvent_t* ev) {
   const int cs = p.chain_stage;
+  int launches = 0;
   if (p.n_chains > 0 && cs < p.N) {
     const int grid = (p.n_chains + kWarpsPerBlock - 1) / kWarpsPerBlock;
     k_bwd_chain<S, SL><<<grid, 128, 0, st>>>(p);
+    ++launches;
   }
+  if (ev) cudaEventRecord(ev[0], st);
   for (int t = cs - 1; t >= 0; --t) {
     const int cnt = stage_begin[t + 1] - stage_begin[t];
     k_bwd_stage<S, SL><<<(cnt + kWarpsPerBlock - 1) / kWarpsPerBlock, 128, 0, st>>>(p, t);
+    ++launches;
   }
+  if (ev) cudaEventRecord(ev[1], st);
   for (int t = 0; t < cs; ++t) {
     const int cnt = stage_begin[t + 1] - stage_begin[t];
     k_fwd_stage<S, SL><<<(cnt + kWarpsPerBlock - 1) / kWarpsPerBlock, 128, 0, st>>>(p, t, zo);
+    ++launches;
   }
+  if (ev) cudaEventRecord(ev[2], st);
   if (p.n_chains > 0 && cs < p.N) {
     const int grid = (p.n_chains + kWarpsPerBlock - 1) / kWarpsPerBlock;
     k_fwd_chain<S, SL><<<grid, 128, 0, st>>>(p, zo);
+    ++launches;
   }
+  return launches;
 }
 
 template <typename S>
-void launch_riccati(const KP<S>& p, const std::vector<int32_t>& stage_begin, S* zo, cudaStream_t st) {
+int launch_riccati(const KP<S>& p, const std::vector<int32_t>& stage_begin, S* zo, cudaStream_t st,
+                   cudaEvent_t* ev) {
   const int sl = (p.nx + p.nu + 31) / 32;
   switch (sl) {
-    case 1: riccati_passes_sl<S, 1>(p, stage_begin, zo, st); break;
-    case 2: riccati_passes_sl<S, 2>(p, stage_begin, zo, st); break;
-    case 3: riccati_passes_sl<S, 3>(p, stage_begin, zo, st); break;
-    default: riccati_passes_sl<S, 4>(p, stage_begin, zo, st); break;
+    case 1: return riccati_passes_sl<S, 1>(p, stage_begin, zo, st, ev);
+    case 2: return riccati_passes_sl<S, 2>(p, stage_begin, zo, st, ev);
+    case 3: return riccati_passes_sl<S, 3>(p, stage_begin, zo, st, ev);
+    default: return riccati_passes_sl<S, 4>(p, stage_begin, zo, st, ev);
   }
 }
 
-template void launch_riccati<double>(const KP<double>&, const std::vector<int32_t>&, double*, cudaStream_t);
-template void launch_riccati<float>(const KP<float>&, const std::vector<int32_t>&, float*, cudaStream_t);
+template int launch_riccati<double>(const KP<double>&, const std::vector<int32_t>&, double*, cudaStream_t,
+                                    cudaEvent_t*);
+template int launch_riccati<float>(const KP<float>&, const std::vector<int32_t>&, float*, cudaStream_t,
+                                   cudaEvent_t*);
 
 }  // namespace spock

@@ -28,7 +28,8 @@ void launch_primal(const KP<S>& p, int mode, const S* eta, const S* etap, const 
                    const S* dir, double* partials, int grid, cudaStream_t st);
 void launch_reduce_stats(const double* pd, int nd, const double* pp, int np, double* out, cudaStream_t st);
 template <typename S>
-void launch_riccati(const KP<S>& p, const std::vector<int32_t>& stage_begin, S* zo, cudaStream_t st);
+int launch_riccati(const KP<S>& p, const std::vector<int32_t>& stage_begin, S* zo, cudaStream_t st,
+                   cudaEvent_t* ev);
 
 enum { DM_APPLY_L_ = 0, DM_PROXG_ = 1, DM_DUAL_ = 2, PM_APPLY_LT_ = 0, PM_STATS_ = 1 };
 
@@ -74,6 +75,46 @@ static void check_launch() {
 }
 
 // ---------------------------------------------------------------------------
+// in-solve timing of the kernel groups of T (CUDA events on the solve stream)
+// ---------------------------------------------------------------------------
+struct Profiler {
+  static constexpr int kGroups = 7, kSlots = 64;
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  int used = 0, n = 0;
+  double acc[kGroups] = {0, 0, 0, 0, 0, 0, 0};
+  ~Profiler() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+  void start() {
+    if (ev.empty()) {
+      ev.resize((size_t)kSlots * (kGroups + 1));
+      for (auto& e : ev) CUDA_TRY(cudaEventCreate(&e));
+    }
+    used = n = 0;
+    for (double& a : acc) a = 0.0;
+    on = true;
+  }
+  cudaEvent_t* slot() {
+    if (used == kSlots) harvest();
+    return &ev[(size_t)(used++) * (kGroups + 1)];
+  }
+  void harvest() {
+    for (int s = 0; s < used; ++s) {
+      cudaEvent_t* e = &ev[(size_t)s * (kGroups + 1)];
+      CUDA_TRY(cudaEventSynchronize(e[kGroups]));
+      for (int g = 0; g < kGroups; ++g) {
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, e[g], e[g + 1]));
+        acc[g] += ms;
+      }
+    }
+    n += used;
+    used = 0;
+  }
+};
+
+// ---------------------------------------------------------------------------
 // workspace
 // ---------------------------------------------------------------------------
 struct Workspace {
@@ -96,6 +137,8 @@ struct Workspace {
   int trace_cap = 0;
   int32_t* h_action = nullptr;  // pinned
   cudaEvent_t e0 = nullptr, e1 = nullptr;
+  Profiler prof;
+  int64_t launches = 0;
   std::vector<void*> allocs;
   ~Workspace() {
     for (void* p : allocs) cudaFree(p);
@@ -197,6 +240,7 @@ static KP<S> make_kp(const Problem& P, double alpha, const int32_t* stage_begin_
   k.n_z = P.off.n_z;
   k.n_eta = P.off.n_eta;
   k.alpha = (S)alpha;
+  k.inv_alpha = (S)(1.0 / alpha);
   k.parent = P.idx.parent;
   k.ch_begin = P.idx.ch_begin;
   k.ch_count = P.idx.ch_count;
@@ -261,17 +305,26 @@ struct Ctx {
 template <typename S>
 static void eval_T(const Ctx& c, const S* v, S* Tv, const S* dir, double* stats) {
   Problem& P = *c.P;
+  Workspace* ws = c.ws;
   KP<S> kp = make_kp<S>(P, c.alpha, c.stage_dev);
   const int64_t nz = P.off.n_z;
   const int maxb = sm_count() * 16;
+  cudaEvent_t* ev = (ws && ws->prof.on) ? ws->prof.slot() : nullptr;
+  if (ev) cudaEventRecord(ev[0], c.st);
   launch_prep<S>(kp, v, v + nz, Tv, maxb, c.st);
-  launch_riccati<S>(kp, P.tree.stage_begin, Tv, c.st);
-  launch_dual<S>(kp, DM_DUAL_, stats != nullptr, v, Tv, v + nz, Tv + nz, dir, c.ws ? c.ws->pd : nullptr,
-                 c.ws ? c.ws->grid_d : std::min((P.tree.n + 3) / 4, maxb), c.st);
+  if (ev) cudaEventRecord(ev[1], c.st);
+  int launches = 2 + launch_riccati<S>(kp, P.tree.stage_begin, Tv, c.st, ev ? ev + 2 : nullptr);
+  if (ev) cudaEventRecord(ev[5], c.st);
+  launch_dual<S>(kp, DM_DUAL_, stats != nullptr, v, Tv, v + nz, Tv + nz, dir, ws ? ws->pd : nullptr,
+                 ws ? ws->grid_d : std::min((P.tree.n + 3) / 4, maxb), c.st);
+  if (ev) cudaEventRecord(ev[6], c.st);
   if (stats) {
-    launch_primal<S>(kp, PM_STATS_, v + nz, Tv + nz, v, Tv, nullptr, dir, c.ws->pp, c.ws->grid_p, c.st);
-    launch_reduce_stats(c.ws->pd, c.ws->grid_d, c.ws->pp, c.ws->grid_p, stats, c.st);
+    launch_primal<S>(kp, PM_STATS_, v + nz, Tv + nz, v, Tv, nullptr, dir, ws->pp, ws->grid_p, c.st);
+    launch_reduce_stats(ws->pd, ws->grid_d, ws->pp, ws->grid_p, stats, c.st);
+    launches += 2;
   }
+  if (ev) cudaEventRecord(ev[7], c.st);
+  if (ws) ws->launches += launches;
   check_launch();
 }
 
@@ -333,6 +386,9 @@ static int solve_impl(Problem& P, const double* x0_dev, const spock_settings& s,
   h.mem = mem;
   h.record_trace = trace_dev != nullptr;
   sm_init_state(ws->st, h, st);
+  ws->launches = 0;
+  if (s.profile) ws->prof.start();
+  else ws->prof.on = false;
   double* stats[3] = {ws->stats, ws->stats + 8, ws->stats + 16};
   CUDA_TRY(cudaEventRecord(ws->e0, st));
   int cur = 0, prev = 1, trial = 2;
@@ -345,10 +401,12 @@ static int solve_impl(Problem& P, const double* x0_dev, const spock_settings& s,
   auto read_action = [&]() -> int {
     CUDA_TRY(cudaMemcpyAsync(ws->h_action, &ws->st->action, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
+    if (ws->prof.on) ws->prof.harvest();
     return ws->h_action[0];
   };
   for (;;) {
     launch_sm_after_eval(ws->st, stats[cur], trace_dev, st);
+    ws->launches += 1;
     const int act = read_action();
     if (act == A_DONE || act == A_MAXIT || act == A_NUMERICAL) {
       final_action = act;
@@ -365,8 +423,10 @@ static int solve_impl(Problem& P, const double* x0_dev, const spock_settings& s,
       for (int j = 0; j < cnt; ++j) order[j] = ((slot - j) % mem + mem) % mem;
       launch_aa_update<S>(ws->st, V[cur], TV[cur], V[prev], TV[prev], MR, Dm, nv, slot, cnt, order, ws->paa,
                           ws->grid_v, st);
+      ws->launches += 2;
     }
     launch_aa_direction<S>(ws->st, V[cur], TV[cur], Dm, nv, cnt, d, V[trial], ws->grid_v, st);
+    ws->launches += 1;
     check_launch();
     if (act == A_K0) {
       eval_T<S>(c, V[trial], TV[trial], nullptr, stats[trial]);
@@ -381,6 +441,7 @@ static int solve_impl(Problem& P, const double* x0_dev, const spock_settings& s,
         eval_T<S>(c, V[trial], TV[trial], d, stats[trial]);
         ++nT;
         launch_sm_line_search(ws->st, stats[trial], trace_dev, st);
+        ws->launches += 1;
         const int la = read_action();
         if (la == A_K1) {
           const int old_prev = prev;
@@ -395,6 +456,7 @@ static int solve_impl(Problem& P, const double* x0_dev, const spock_settings& s,
           } else {
             launch_km_point<S>(ws->st, V[cur], TV[cur], V[prev], nv, ws->grid_v, st);
           }
+          ws->launches += 1;
           eval_T<S>(c, V[prev], TV[prev], nullptr, stats[prev]);
           ++nT;
           const int newcur = prev;
@@ -407,6 +469,7 @@ static int solve_impl(Problem& P, const double* x0_dev, const spock_settings& s,
           break;
         }
         launch_ls_point<S>(ws->st, V[cur], d, V[trial], nv, ws->grid_v, st);
+        ws->launches += 1;
       }
       if (numerical) {
         final_action = A_NUMERICAL;
@@ -426,6 +489,7 @@ static int solve_impl(Problem& P, const double* x0_dev, const spock_settings& s,
     CUDA_TRY(cudaMemcpyAsync(s.trace, trace_dev, sizeof(int32_t) * 2 * (size_t)max_iter, cudaMemcpyDeviceToHost,
                              st));
   CUDA_TRY(cudaStreamSynchronize(st));
+  if (ws->prof.on) ws->prof.harvest();
   float ms = 0.f;
   cudaEventElapsedTime(&ms, ws->e0, ws->e1);
   int status = final_action == A_DONE ? SPOCK_OK
@@ -443,7 +507,11 @@ static int solve_impl(Problem& P, const double* x0_dev, const spock_settings& s,
     info->xi0 = fin.xi0;
     info->alpha = c.alpha;
     info->solve_ms = ms;
+    info->n_launches = (int32_t)ws->launches;
+    info->n_timed = ws->prof.on ? ws->prof.n : 0;
+    for (int g = 0; g < Profiler::kGroups; ++g) info->t_group_ms[g] = ws->prof.on ? ws->prof.acc[g] : 0.0;
   }
+  ws->prof.on = false;
   if (status == SPOCK_ERR_NUMERICAL) return fail(status, "non-finite residual during the iteration");
   return status;
 }
@@ -815,6 +883,22 @@ int spock_solve_dev(spock_problem* p, const double* x0_dev, const spock_settings
   });
 }
 
+// Device staging buffers of the host-buffer entry points (allocated once per
+// problem, reused by every call).
+static void host_io_buffers(Problem& P, double** dx0, double** dz, double** de) {
+  if (!P.io_x0) {
+    CUDA_TRY(cudaMalloc(&P.io_x0, sizeof(double) * P.nx));
+    P.allocations.push_back(P.io_x0);
+    CUDA_TRY(cudaMalloc(&P.io_z, sizeof(double) * P.off.n_z));
+    P.allocations.push_back(P.io_z);
+    CUDA_TRY(cudaMalloc(&P.io_eta, sizeof(double) * P.off.n_eta));
+    P.allocations.push_back(P.io_eta);
+  }
+  *dx0 = P.io_x0;
+  *dz = P.io_z;
+  *de = P.io_eta;
+}
+
 int spock_solve(spock_problem* p, const double* x0, const spock_settings* settings, double* z_io, double* eta_io,
                 int32_t warm, spock_info* info) {
   return guarded([&]() -> int {
@@ -826,15 +910,7 @@ int spock_solve(spock_problem* p, const double* x0, const spock_settings* settin
     if (rc != SPOCK_OK) return rc;
     const int64_t nz = P->off.n_z, ne = P->off.n_eta;
     double *dx0 = nullptr, *dz = nullptr, *de = nullptr;
-    CUDA_TRY(cudaMalloc(&dx0, sizeof(double) * P->nx));
-    CUDA_TRY(cudaMalloc(&dz, sizeof(double) * nz));
-    CUDA_TRY(cudaMalloc(&de, sizeof(double) * ne));
-    struct Guard {
-      void* a[3];
-      ~Guard() {
-        for (void* p : a) cudaFree(p);
-      }
-    } g{{dx0, dz, de}};
+    host_io_buffers(*P, &dx0, &dz, &de);
     CUDA_TRY(cudaMemcpy(dx0, x0, sizeof(double) * P->nx, cudaMemcpyHostToDevice));
     if (warm) {
       CUDA_TRY(cudaMemcpy(dz, z_io, sizeof(double) * nz, cudaMemcpyHostToDevice));
@@ -875,15 +951,7 @@ int spock_cp_step(spock_problem* p, const double* x0, int32_t k, double alpha, i
     CUDA_TRY(cudaSetDevice(P->device));
     const int64_t nz = P->off.n_z, ne = P->off.n_eta;
     double *dx0 = nullptr, *dz = nullptr, *de = nullptr;
-    CUDA_TRY(cudaMalloc(&dx0, sizeof(double) * P->nx));
-    CUDA_TRY(cudaMalloc(&dz, sizeof(double) * nz));
-    CUDA_TRY(cudaMalloc(&de, sizeof(double) * ne));
-    struct Guard {
-      void* a[3];
-      ~Guard() {
-        for (void* p : a) cudaFree(p);
-      }
-    } g{{dx0, dz, de}};
+    host_io_buffers(*P, &dx0, &dz, &de);
     CUDA_TRY(cudaMemcpy(dx0, x0, sizeof(double) * P->nx, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(dz, z_io, sizeof(double) * nz, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(de, eta_io, sizeof(double) * ne, cudaMemcpyHostToDevice));
@@ -941,7 +1009,7 @@ int spock_prox_f_dev(spock_problem* p, const double* x0_dev, double alpha, const
     KP<double> kp = op_kp(P, alpha);
     CUDA_TRY(cudaMemcpyAsync(P->f64.x0, x0_dev, sizeof(double) * P->nx, cudaMemcpyDeviceToDevice, st));
     launch_prep<double>(kp, z, (const double*)ws->zero_eta, z_out, sm_count() * 16, st);
-    launch_riccati<double>(kp, P->tree.stage_begin, z_out, st);
+    launch_riccati<double>(kp, P->tree.stage_begin, z_out, st, nullptr);
     check_launch();
     CUDA_TRY(cudaStreamSynchronize(st));
     return SPOCK_OK;
@@ -973,7 +1041,7 @@ int spock_T_dev(spock_problem* p, const double* x0_dev, double alpha, const doub
     KP<double> kp = op_kp(P, alpha);
     CUDA_TRY(cudaMemcpyAsync(P->f64.x0, x0_dev, sizeof(double) * P->nx, cudaMemcpyDeviceToDevice, st));
     launch_prep<double>(kp, z, eta, z_out, sm_count() * 16, st);
-    launch_riccati<double>(kp, P->tree.stage_begin, z_out, st);
+    launch_riccati<double>(kp, P->tree.stage_begin, z_out, st, nullptr);
     launch_dual<double>(kp, DM_DUAL_, false, z, z_out, eta, eta_out, nullptr, nullptr,
                         std::min((P->tree.n + 3) / 4, sm_count() * 16), st);
     check_launch();

@@ -95,6 +95,10 @@ struct Problem {
   DevFactors<double> f64;
   DevFactors<float> f32;
   std::vector<void*> allocations;
+  // device staging buffers of the host-buffer entry points
+  double* io_x0 = nullptr;
+  double* io_z = nullptr;
+  double* io_eta = nullptr;
   // solver workspace, allocated on first use per precision
   struct Workspace* ws64 = nullptr;
   struct Workspace* ws32 = nullptr;

@@ -124,10 +124,17 @@ __global__ void __launch_bounds__(256) k_aa_update(const S* __restrict__ v, cons
                                                    const S* __restrict__ vp, const S* __restrict__ Tvp,
                                                    S* __restrict__ MR, S* __restrict__ D, int64_t n, int slot,
                                                    int cnt, double* __restrict__ partials) {
+  // Dot products: terms in the working precision, summed over chunks of 8
+  // grid-stride steps in S, then accumulated in FP64.
   double gr[kMaxMemory], rh[kMaxMemory];
+  S cg[kMaxMemory], cr[kMaxMemory];
 #pragma unroll
-  for (int j = 0; j < kMaxMemory; ++j) gr[j] = rh[j] = 0.0;
+  for (int j = 0; j < kMaxMemory; ++j) {
+    gr[j] = rh[j] = 0.0;
+    cg[j] = cr[j] = S(0);
+  }
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int chunk = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const S r = v[i] - Tv[i];
     const S dc = r - (vp[i] - Tvp[i]);
@@ -137,10 +144,28 @@ __global__ void __launch_bounds__(256) k_aa_update(const S* __restrict__ v, cons
 #pragma unroll
     for (int j = 0; j < kMaxMemory; ++j) {
       if (j < cnt) {
-        const double c = (j == slot) ? (double)dc : (double)MR[(int64_t)j * n + i];
-        gr[j] += c * (double)dc;
-        rh[j] += c * (double)r;
+        const S c = (j == slot) ? dc : MR[(int64_t)j * n + i];
+        cg[j] += c * dc;
+        cr[j] += c * r;
       }
+    }
+    if (++chunk == 8) {
+      chunk = 0;
+#pragma unroll
+      for (int j = 0; j < kMaxMemory; ++j) {
+        if (j < cnt) {
+          gr[j] += (double)cg[j];
+          rh[j] += (double)cr[j];
+          cg[j] = cr[j] = S(0);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kMaxMemory; ++j) {
+    if (j < cnt) {
+      gr[j] += (double)cg[j];
+      rh[j] += (double)cr[j];
     }
   }
   __shared__ double red[8][2 * kMaxMemory];

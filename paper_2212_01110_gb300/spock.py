@@ -40,17 +40,22 @@ class Settings(C.Structure):
                 ("memory", C.c_int32), ("c0", C.c_double), ("c1", C.c_double), ("c2", C.c_double),
                 ("beta", C.c_double), ("sigma", C.c_double), ("lambda_", C.c_double),
                 ("rho_coef", C.c_double), ("max_iter", C.c_int32), ("max_backtracks", C.c_int32),
-                ("precision", C.c_int32), ("trace", C.POINTER(C.c_int32))]
+                ("precision", C.c_int32), ("trace", C.POINTER(C.c_int32)), ("profile", C.c_int32)]
 
 
 class Info(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("n_T", C.c_int32),
                 ("n_K0", C.c_int32), ("n_K1", C.c_int32), ("n_K2", C.c_int32), ("n_cap", C.c_int32),
                 ("n_backtracks", C.c_int32), ("xi", C.c_double), ("xi0", C.c_double),
-                ("alpha", C.c_double), ("solve_ms", C.c_double)]
+                ("alpha", C.c_double), ("solve_ms", C.c_double), ("n_launches", C.c_int32),
+                ("n_timed", C.c_int32), ("t_group_ms", C.c_double * 7)]
+
+    GROUPS = ("prep", "bwd_chain", "bwd_stages", "fwd_stages", "fwd_chain", "dual", "stats")
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "t_group_ms"}
+        d["t_group_ms"] = dict(zip(self.GROUPS, list(self.t_group_ms)))
+        return d
 
 
 _P = C.c_void_p
