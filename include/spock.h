@@ -227,6 +227,27 @@ int spock_prox_gconj_dev(spock_problem* p, double alpha, const double* eta, doub
 int spock_T_dev(spock_problem* p, const double* x0_dev, double alpha, const double* z,
                 const double* eta, double* z_out, double* eta_out, void* stream);
 
+/*
+ * spock_prox_f_noalloc_dev -- spock_prox_f_dev without any allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory while they run (a control loop with a fixed
+ * memory budget, or code executing while another component owns the device
+ * allocator).  It computes exactly what spock_prox_f_dev computes, but the
+ * scratch vectors of the Riccati passes and the zero dual vector live in a
+ * fixed, file-scope device array of 2^20 doubles (8 MiB) that every GPU which
+ * loads the library holds until the process exits.  It calls no cudaMalloc
+ * or cudaFree.
+ *   Limit: 2 (n nx + n_nonleaf nu) + n_eta <= 2^20; larger problems are
+ *   rejected with SPOCK_ERR_INVALID_ARG and a message giving both sizes.
+ *   The first call on a device looks up the array's device address; make
+ *   that first call before capturing the stream into a CUDA graph.
+ *   All calls share the one array: calls that overlap on the GPU (other
+ *   streams, other host threads) race and must be serialised by the caller.
+ * Arguments, layout and other errors as spock_prox_f_dev.
+ */
+int spock_prox_f_noalloc_dev(spock_problem* p, const double* x0_dev, double alpha, const double* z,
+                             double* z_out, void* stream);
+
 /* Frees a handle returned by any *_create call; NULL is a no-op. */
 void spock_free(void* handle);
 

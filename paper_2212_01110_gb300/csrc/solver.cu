@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <exception>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <thread>
@@ -1060,3 +1061,76 @@ void spock_free(void* handle) {
 const char* spock_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free variant of spock_prox_f_dev
+// ===========================================================================
+// For callers that must not allocate device memory on the call path (a
+// real-time control loop with a fixed memory budget, or code that runs while
+// another component owns the allocator): the scratch of prox_{alpha f} (the
+// Riccati vectors xbar, ubar, q, d and an all-zero dual vector) lives in the
+// fixed-size device array below instead of problem- or workspace-owned
+// buffers.  Every GPU that loads this library holds the array until the
+// process exits.
+namespace spock {
+
+constexpr size_t kNoAllocScratchDoubles = size_t(1) << 20;  // 8 MiB
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+
+// Device address of g_noalloc_scratch on `dev` (the current device).  Host
+// code must not use the symbol itself: on the host it names a stand-in, not
+// device memory.  Looked up once per device, on the first call there.
+static int noalloc_scratch(int dev, double** out) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(SPOCK_ERR_INVALID_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    double* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
+    if (e != cudaSuccess)
+      return fail(SPOCK_ERR_CUDA, std::string("cudaGetSymbolAddress(g_noalloc_scratch): ") + cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return SPOCK_OK;
+}
+
+}  // namespace spock
+
+extern "C" int spock_prox_f_noalloc_dev(spock_problem* p, const double* x0_dev, double alpha, const double* z,
+                                        double* z_out, void* stream) {
+  return guarded([&]() -> int {
+    Problem* P = as_problem(p);
+    if (!P || !x0_dev || !z || !z_out) return fail(SPOCK_ERR_INVALID_ARG, "NULL argument");
+    const Tree& t = P->tree;
+    const size_t nxb = (size_t)t.n * P->nx, nub = (size_t)t.n_nonleaf * P->nu;
+    const size_t need = 2 * nxb + 2 * nub + (size_t)P->off.n_eta;
+    if (need > kNoAllocScratchDoubles)
+      return fail(SPOCK_ERR_INVALID_ARG, "problem too large for spock_prox_f_noalloc_dev: needs " +
+                                             std::to_string(need) + " doubles of scratch, the fixed array holds " +
+                                             std::to_string(kNoAllocScratchDoubles));
+    CUDA_TRY(cudaSetDevice(P->device));
+    double* scratch = nullptr;
+    int rc = noalloc_scratch(P->device, &scratch);
+    if (rc != SPOCK_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    KP<double> kp = op_kp(P, alpha);
+    kp.xbar = scratch;
+    kp.q = scratch + nxb;
+    kp.ubar = scratch + 2 * nxb;
+    kp.d = scratch + 2 * nxb + nub;
+    double* zero_eta = scratch + 2 * nxb + 2 * nub;
+    // the array keeps the previous call's contents: the dual input must be zero
+    CUDA_TRY(cudaMemsetAsync(zero_eta, 0, sizeof(double) * (size_t)P->off.n_eta, st));
+    CUDA_TRY(cudaMemcpyAsync(P->f64.x0, x0_dev, sizeof(double) * P->nx, cudaMemcpyDeviceToDevice, st));
+    launch_prep<double>(kp, z, zero_eta, z_out, sm_count() * 16, st);
+    launch_riccati<double>(kp, P->tree.stage_begin, z_out, st, nullptr);
+    check_launch();
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return SPOCK_OK;
+  });
+}

@@ -76,6 +76,7 @@ _sig = {
     "spock_apply_L_dev": ([_P, _P, _P, _P], C.c_int),
     "spock_apply_Lt_dev": ([_P, _P, _P, _P], C.c_int),
     "spock_prox_f_dev": ([_P, _P, C.c_double, _P, _P, _P], C.c_int),
+    "spock_prox_f_noalloc_dev": ([_P, _P, C.c_double, _P, _P, _P], C.c_int),
     "spock_prox_gconj_dev": ([_P, C.c_double, _P, _P, _P], C.c_int),
     "spock_T_dev": ([_P, _P, C.c_double, _P, _P, _P, _P, _P], C.c_int),
     "spock_free": ([_P], None),
@@ -201,6 +202,13 @@ def spock_apply_Lt_dev(problem, eta, z_out, stream=None):
 
 def spock_prox_f_dev(problem, x0, alpha, z, z_out, stream=None):
     _check(_lib.spock_prox_f_dev(problem, _tptr(x0), float(alpha), _tptr(z), _tptr(z_out), _stream(stream)))
+
+
+def spock_prox_f_noalloc_dev(problem, x0, alpha, z, z_out, stream=None):
+    """prox_{alpha f} with the library's fixed device scratch (no allocation);
+    see include/spock.h for the size limit and the sharing rules."""
+    _check(_lib.spock_prox_f_noalloc_dev(problem, _tptr(x0), float(alpha), _tptr(z), _tptr(z_out),
+                                         _stream(stream)))
 
 
 def spock_prox_gconj_dev(problem, alpha, eta, eta_out, stream=None):
