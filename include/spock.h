@@ -237,7 +237,8 @@ int spock_T_dev(spock_problem* p, const double* x0_dev, double alpha, const doub
  * fixed, file-scope device array of 2^20 doubles (8 MiB) that every GPU which
  * loads the library holds until the process exits.  It calls no cudaMalloc
  * or cudaFree.
- *   Limit: 2 (n nx + n_nonleaf nu) + n_eta <= 2^20; larger problems are
+ *   Limit: 2 (n nx' + n_nonleaf nu') + n_eta <= 2^20 with nx', nu' the
+ *   dimensions rounded up to even numbers; larger problems are
  *   rejected with SPOCK_ERR_INVALID_ARG and a message giving both sizes.
  *   The first call on a device looks up the array's device address; make
  *   that first call before capturing the stream into a CUDA graph.

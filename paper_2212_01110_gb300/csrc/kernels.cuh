@@ -34,6 +34,10 @@ struct KP {
   int64_t n_z, n_eta;
   S alpha;
   S inv_alpha;        // 1 / alpha (multiplications instead of FP64 divisions)
+  // per-node strides (elements), padded to 16 bytes for bulk copies
+  int32_t xs, us;                     // xbar / q, ubar / d
+  int32_t gstride, nbstride, ktstride;  // Gb and Gf, NB, Kt
+  int32_t* err;                       // pipeline timeout flag (device)
   const int32_t* __restrict__ parent;
   const int32_t* __restrict__ ch_begin;
   const int32_t* __restrict__ ch_count;

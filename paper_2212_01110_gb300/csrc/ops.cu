@@ -35,12 +35,12 @@ __global__ void __launch_bounds__(128) k_prep(KP<S> p, const S* __restrict__ z,
       for (int r = lane; r < nx; r += 32) {
         S acc = eta[ex + r];
         for (int j = 0; j < m; ++j) acc += p.qs[(int64_t)(c0 + j) * nx + r] * eta[p.enr[c0 + j] + r];
-        p.xbar[(int64_t)k * nx + r] = z[p.zx[k] + r] - al * acc;
+        p.xbar[(int64_t)k * p.xs + r] = z[p.zx[k] + r] - al * acc;
       }
       for (int r = lane; r < nu; r += 32) {
         S acc = eta[eu + r];
         for (int j = 0; j < m; ++j) acc += p.rs[(int64_t)(c0 + j) * nu + r] * eta[p.enr[c0 + j] + nx + r];
-        p.ubar[(int64_t)k * nu + r] = z[p.zu[k] + r] - al * acc;
+        p.ubar[(int64_t)k * p.us + r] = z[p.zu[k] + r] - al * acc;
       }
       // z_2 block: zbar = z - alpha L* eta, then projection on ker [E^T, -I, -I]
       // with (M M^T)^-1 = (I - 11^T / (c + m)) / c, c = a^2 + 3 (Sherman-Morrison).
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(128) k_prep(KP<S> p, const S* __restrict__ z,
     } else {
       const int64_t ef = p.elf[k];
       for (int r = lane; r < nx; r += 32)
-        p.xbar[(int64_t)k * nx + r] =
+        p.xbar[(int64_t)k * p.xs + r] =
             z[p.zx[k] + r] - al * (eta[ef + r] + p.qns[(int64_t)k * nx + r] * eta[ef + nx + r]);
     }
   }

@@ -24,6 +24,8 @@
 // The backward layout [Abar^c | B^c] (nx x (nx+nu), row-major) serves
 // h = [Abar^c | B^c]^T q^c; the forward layout is its transpose so that
 // x^c = [Abar^c | B^c] (x; d) is again lanes-over-outputs.
+#include <cstdlib>
+
 #include "kernels.cuh"
 #include "spock_internal.h"
 
@@ -65,24 +67,23 @@ __device__ __forceinline__ void node_bwd(const KP<S>& p, int k, const S (&h)[SL]
     const int col = 32 * s + lane;
     if (col < ncol) v.h[col] = h[s];
   }
-  const S* ub = p.ubar + (int64_t)k * nu;
+  const S* ub = p.ubar + (int64_t)k * p.us;
   for (int b = lane; b < nu; b += 32) v.u[b] = ub[b];
   __syncwarp();
   for (int b = lane; b < nu; b += 32) v.g[b] = v.u[b] - v.h[nx + b];
   __syncwarp();
-  const int64_t nbsz = 2 * (int64_t)nu * nx + (int64_t)nu * nu;
-  const S* __restrict__ Km = p.NB + (int64_t)k * nbsz;
+  const S* __restrict__ Km = p.NB + (int64_t)k * p.nbstride;
   const S* __restrict__ Wt = Km + (int64_t)nu * nx;
   const S* __restrict__ Ri = Km + 2 * (int64_t)nu * nx;
   for (int a = lane; a < nu; a += 32) {
     S acc = 0;
     for (int b = 0; b < nu; ++b) acc += __ldg(Ri + a * nu + b) * v.g[b];
     v.d[a] = acc;
-    p.d[(int64_t)k * nu + a] = acc;
+    p.d[(int64_t)k * p.us + a] = acc;
   }
   __syncwarp();
   S qn[SL];
-  const S* xb = p.xbar + (int64_t)k * nx;
+  const S* xb = p.xbar + (int64_t)k * p.xs;
 #pragma unroll
   for (int s = 0; s < SL; ++s) {
     const int r = 32 * s + lane;
@@ -114,9 +115,9 @@ __device__ __forceinline__ void node_bwd(const KP<S>& p, int k, const S (&h)[SL]
 template <typename S>
 __device__ __forceinline__ void node_fwd(const KP<S>& p, int k, WarpVecs<S>& v, S* __restrict__ zo, int lane) {
   const int nx = p.nx, nu = p.nu;
-  for (int a = lane; a < nu; a += 32) v.w[nx + a] = p.d[(int64_t)k * nu + a];
+  for (int a = lane; a < nu; a += 32) v.w[nx + a] = p.d[(int64_t)k * p.us + a];
   __syncwarp();
-  const S* __restrict__ Kt = p.Kt + (int64_t)k * nx * nu;
+  const S* __restrict__ Kt = p.Kt + (int64_t)k * p.ktstride;
   const int64_t zu = p.zu[k];
   for (int a = lane; a < nu; a += 32) {
     S acc = v.w[nx + a];
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(128) k_bwd_chain(KP<S> p) {
   const int nx = p.nx, ncol = p.nx + p.nu;
   for (int ci = gw; ci < p.n_chains; ci += nw) {
     const int leaf = p.stage_begin[p.N] + ci;
-    for (int r = lane; r < nx; r += 32) v.q[r] = -p.xbar[(int64_t)leaf * nx + r];
+    for (int r = lane; r < nx; r += 32) v.q[r] = -p.xbar[(int64_t)leaf * p.xs + r];
     __syncwarp();
     int k = -1;
     for (int t = p.N - 1; t >= p.chain_stage; --t) {
@@ -175,11 +176,11 @@ __global__ void __launch_bounds__(128) k_bwd_chain(KP<S> p) {
       S h[SL];
 #pragma unroll
       for (int s = 0; s < SL; ++s) h[s] = S(0);
-      acc_GTq<S, SL>(p.Gb + (int64_t)(c - 1) * nx * ncol, v.q, nx, ncol, lane, h);
+      acc_GTq<S, SL>(p.Gb + (int64_t)(c - 1) * p.gstride, v.q, nx, ncol, lane, h);
       __syncwarp();
       node_bwd<S, SL>(p, k, h, v, lane);
     }
-    for (int r = lane; r < nx; r += 32) p.q[(int64_t)k * nx + r] = v.q[r];
+    for (int r = lane; r < nx; r += 32) p.q[(int64_t)k * p.xs + r] = v.q[r];
     __syncwarp();
   }
 }
@@ -204,16 +205,16 @@ __global__ void __launch_bounds__(128) k_bwd_stage(KP<S> p, int t) {
     for (int j = 0; j < m; ++j) {
       const int c = c0 + j;
       if (c >= p.nl) {
-        for (int r = lane; r < nx; r += 32) v.q[r] = -p.xbar[(int64_t)c * nx + r];
+        for (int r = lane; r < nx; r += 32) v.q[r] = -p.xbar[(int64_t)c * p.xs + r];
       } else {
-        for (int r = lane; r < nx; r += 32) v.q[r] = p.q[(int64_t)c * nx + r];
+        for (int r = lane; r < nx; r += 32) v.q[r] = p.q[(int64_t)c * p.xs + r];
       }
       __syncwarp();
-      acc_GTq<S, SL>(p.Gb + (int64_t)(c - 1) * nx * ncol, v.q, nx, ncol, lane, h);
+      acc_GTq<S, SL>(p.Gb + (int64_t)(c - 1) * p.gstride, v.q, nx, ncol, lane, h);
       __syncwarp();
     }
     node_bwd<S, SL>(p, k, h, v, lane);
-    for (int r = lane; r < nx; r += 32) p.q[(int64_t)k * nx + r] = v.q[r];
+    for (int r = lane; r < nx; r += 32) p.q[(int64_t)k * p.xs + r] = v.q[r];
     __syncwarp();
   }
 }
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(128) k_fwd_stage(KP<S> p, int t, S* __restrict
     for (int j = 0; j < m; ++j) {
       const int c = c0 + j;
       S x[SL];
-      child_fwd<S, SL>(p.Gf + (int64_t)(c - 1) * ncol * nx, v.w, nx, ncol, lane, x);
+      child_fwd<S, SL>(p.Gf + (int64_t)(c - 1) * p.gstride, v.w, nx, ncol, lane, x);
       const int64_t zx = p.zx[c];
 #pragma unroll
       for (int s = 0; s < SL; ++s) {
@@ -285,7 +286,7 @@ __global__ void __launch_bounds__(128) k_fwd_chain(KP<S> p, S* __restrict__ zo) 
       node_fwd<S>(p, k, v, zo, lane);
       __syncwarp();
       S x[SL];
-      child_fwd<S, SL>(p.Gf + (int64_t)(c - 1) * ncol * nx, v.w, nx, ncol, lane, x);
+      child_fwd<S, SL>(p.Gf + (int64_t)(c - 1) * p.gstride, v.w, nx, ncol, lane, x);
       __syncwarp();
       const int64_t zx = p.zx[c];
 #pragma unroll
@@ -304,55 +305,95 @@ __global__ void __launch_bounds__(128) k_fwd_chain(KP<S> p, S* __restrict__ zo) 
 // ---------------------------------------------------------------------------
 // launcher: the whole S1 projection (prep kernel already ran)
 // ---------------------------------------------------------------------------
+// bulk-copy pipelined variants (riccati_tma.cu)
+template <typename S>
+bool tma_chain_fits(const KP<S>& p);
+template <typename S>
+bool tma_stage_fits(const KP<S>& p);
+template <typename S, int SL>
+int launch_bwd_chain_tma(const KP<S>& p, cudaStream_t st);
+template <typename S, int SL>
+int launch_fwd_chain_tma(const KP<S>& p, S* zo, cudaStream_t st);
+template <typename S, int SL>
+int launch_bwd_stage_tma(const KP<S>& p, int t, int cnt, int max_children, cudaStream_t st);
+template <typename S, int SL>
+int launch_fwd_stage_tma(const KP<S>& p, int t, int cnt, int max_children, S* zo, cudaStream_t st);
+
+// Kernel family: shared-memory staged (default, when a node's blocks fit)
+// or the direct-load kernels above.  SPOCK_RICCATI_KERNELS=direct selects
+// the latter (used by the tests to cover both).
+static bool want_tma() {
+  const char* e = getenv("SPOCK_RICCATI_KERNELS");
+  return !(e && e[0] == 'd');
+}
+
 // Launches both passes; ev (optional, 3 events) is recorded after the
 // backward chain kernel, the backward stage kernels and the forward stage
 // kernels.  Returns the number of kernels launched.
 template <typename S, int SL>
-int riccati_passes_sl(const KP<S>& p, const std::vector<int32_t>& stage_begin, S* zo, cudaStream_t st,
-                      cudaEvent_t* ev) {
+int riccati_passes_sl(const KP<S>& p, const std::vector<int32_t>& stage_begin,
+                      const std::vector<int32_t>& stage_maxch, S* zo, cudaStream_t st, cudaEvent_t* ev) {
   const int cs = p.chain_stage;
+  const bool tma = want_tma();
+  const bool tma_chain = tma && tma_chain_fits(p), tma_stage = tma && tma_stage_fits(p);
   int launches = 0;
   if (p.n_chains > 0 && cs < p.N) {
-    const int grid = (p.n_chains + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    k_bwd_chain<S, SL><<<grid, 128, 0, st>>>(p);
-    ++launches;
+    if (tma_chain) {
+      launches += launch_bwd_chain_tma<S, SL>(p, st);
+    } else {
+      const int grid = (p.n_chains + kWarpsPerBlock - 1) / kWarpsPerBlock;
+      k_bwd_chain<S, SL><<<grid, 128, 0, st>>>(p);
+      ++launches;
+    }
   }
   if (ev) cudaEventRecord(ev[0], st);
   for (int t = cs - 1; t >= 0; --t) {
     const int cnt = stage_begin[t + 1] - stage_begin[t];
-    k_bwd_stage<S, SL><<<(cnt + kWarpsPerBlock - 1) / kWarpsPerBlock, 128, 0, st>>>(p, t);
-    ++launches;
+    if (tma_stage) {
+      launches += launch_bwd_stage_tma<S, SL>(p, t, cnt, stage_maxch[t], st);
+    } else {
+      k_bwd_stage<S, SL><<<(cnt + kWarpsPerBlock - 1) / kWarpsPerBlock, 128, 0, st>>>(p, t);
+      ++launches;
+    }
   }
   if (ev) cudaEventRecord(ev[1], st);
   for (int t = 0; t < cs; ++t) {
     const int cnt = stage_begin[t + 1] - stage_begin[t];
-    k_fwd_stage<S, SL><<<(cnt + kWarpsPerBlock - 1) / kWarpsPerBlock, 128, 0, st>>>(p, t, zo);
-    ++launches;
+    if (tma_stage) {
+      launches += launch_fwd_stage_tma<S, SL>(p, t, cnt, stage_maxch[t], zo, st);
+    } else {
+      k_fwd_stage<S, SL><<<(cnt + kWarpsPerBlock - 1) / kWarpsPerBlock, 128, 0, st>>>(p, t, zo);
+      ++launches;
+    }
   }
   if (ev) cudaEventRecord(ev[2], st);
   if (p.n_chains > 0 && cs < p.N) {
-    const int grid = (p.n_chains + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    k_fwd_chain<S, SL><<<grid, 128, 0, st>>>(p, zo);
-    ++launches;
+    if (tma_chain) {
+      launches += launch_fwd_chain_tma<S, SL>(p, zo, st);
+    } else {
+      const int grid = (p.n_chains + kWarpsPerBlock - 1) / kWarpsPerBlock;
+      k_fwd_chain<S, SL><<<grid, 128, 0, st>>>(p, zo);
+      ++launches;
+    }
   }
   return launches;
 }
 
 template <typename S>
-int launch_riccati(const KP<S>& p, const std::vector<int32_t>& stage_begin, S* zo, cudaStream_t st,
-                   cudaEvent_t* ev) {
+int launch_riccati(const KP<S>& p, const std::vector<int32_t>& stage_begin, const std::vector<int32_t>& stage_maxch,
+                   S* zo, cudaStream_t st, cudaEvent_t* ev) {
   const int sl = (p.nx + p.nu + 31) / 32;
   switch (sl) {
-    case 1: return riccati_passes_sl<S, 1>(p, stage_begin, zo, st, ev);
-    case 2: return riccati_passes_sl<S, 2>(p, stage_begin, zo, st, ev);
-    case 3: return riccati_passes_sl<S, 3>(p, stage_begin, zo, st, ev);
-    default: return riccati_passes_sl<S, 4>(p, stage_begin, zo, st, ev);
+    case 1: return riccati_passes_sl<S, 1>(p, stage_begin, stage_maxch, zo, st, ev);
+    case 2: return riccati_passes_sl<S, 2>(p, stage_begin, stage_maxch, zo, st, ev);
+    case 3: return riccati_passes_sl<S, 3>(p, stage_begin, stage_maxch, zo, st, ev);
+    default: return riccati_passes_sl<S, 4>(p, stage_begin, stage_maxch, zo, st, ev);
   }
 }
 
-template int launch_riccati<double>(const KP<double>&, const std::vector<int32_t>&, double*, cudaStream_t,
-                                    cudaEvent_t*);
-template int launch_riccati<float>(const KP<float>&, const std::vector<int32_t>&, float*, cudaStream_t,
-                                   cudaEvent_t*);
+template int launch_riccati<double>(const KP<double>&, const std::vector<int32_t>&, const std::vector<int32_t>&,
+                                    double*, cudaStream_t, cudaEvent_t*);
+template int launch_riccati<float>(const KP<float>&, const std::vector<int32_t>&, const std::vector<int32_t>&,
+                                   float*, cudaStream_t, cudaEvent_t*);
 
 }  // namespace spock

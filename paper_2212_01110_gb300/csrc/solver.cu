@@ -29,8 +29,8 @@ void launch_primal(const KP<S>& p, int mode, const S* eta, const S* etap, const 
                    const S* dir, double* partials, int grid, cudaStream_t st);
 void launch_reduce_stats(const double* pd, int nd, const double* pp, int np, double* out, cudaStream_t st);
 template <typename S>
-int launch_riccati(const KP<S>& p, const std::vector<int32_t>& stage_begin, S* zo, cudaStream_t st,
-                   cudaEvent_t* ev);
+int launch_riccati(const KP<S>& p, const std::vector<int32_t>& stage_begin, const std::vector<int32_t>& stage_maxch,
+                   S* zo, cudaStream_t st, cudaEvent_t* ev);
 
 enum { DM_APPLY_L_ = 0, DM_PROXG_ = 1, DM_DUAL_ = 2, PM_APPLY_LT_ = 0, PM_STATS_ = 1 };
 
@@ -67,6 +67,19 @@ int guarded(F&& f) {
     return fail(SPOCK_ERR_OOM, "host allocation failed");
   } catch (const std::exception& e) {
     return fail(SPOCK_ERR_CUDA, e.what());
+  }
+}
+
+// A kernel whose bounded wait on a bulk copy gave up sets *P.err; report it
+// (and clear the flag) after the work on `st` has completed.
+static void check_device_flag(Problem& P, cudaStream_t st) {
+  int32_t h = 0;
+  CUDA_TRY(cudaMemcpyAsync(&h, P.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (h) {
+    CUDA_TRY(cudaMemsetAsync(P.err, 0, sizeof(int32_t), st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    throw SpockError(SPOCK_ERR_CUDA, "a kernel's bounded wait for a bulk copy timed out");
   }
 }
 
@@ -272,6 +285,12 @@ static KP<S> make_kp(const Problem& P, double alpha, const int32_t* stage_begin_
   k.q = f.q;
   k.d = f.d;
   k.x0 = f.x0;
+  k.xs = f.xs;
+  k.us = f.us;
+  k.gstride = f.gstride;
+  k.nbstride = f.nbstride;
+  k.ktstride = f.ktstride;
+  k.err = P.err;
   return k;
 }
 
@@ -314,7 +333,7 @@ static void eval_T(const Ctx& c, const S* v, S* Tv, const S* dir, double* stats)
   if (ev) cudaEventRecord(ev[0], c.st);
   launch_prep<S>(kp, v, v + nz, Tv, maxb, c.st);
   if (ev) cudaEventRecord(ev[1], c.st);
-  int launches = 2 + launch_riccati<S>(kp, P.tree.stage_begin, Tv, c.st, ev ? ev + 2 : nullptr);
+  int launches = 2 + launch_riccati<S>(kp, P.tree.stage_begin, P.tree.stage_maxch, Tv, c.st, ev ? ev + 2 : nullptr);
   if (ev) cudaEventRecord(ev[5], c.st);
   launch_dual<S>(kp, DM_DUAL_, stats != nullptr, v, Tv, v + nz, Tv + nz, dir, ws ? ws->pd : nullptr,
                  ws ? ws->grid_d : std::min((P.tree.n + 3) / 4, maxb), c.st);
@@ -513,6 +532,7 @@ static int solve_impl(Problem& P, const double* x0_dev, const spock_settings& s,
     for (int g = 0; g < Profiler::kGroups; ++g) info->t_group_ms[g] = ws->prof.on ? ws->prof.acc[g] : 0.0;
   }
   ws->prof.on = false;
+  check_device_flag(P, st);
   if (status == SPOCK_ERR_NUMERICAL) return fail(status, "non-finite residual during the iteration");
   return status;
 }
@@ -547,6 +567,7 @@ static int cp_impl(Problem& P, const double* x0_dev, int k, double alpha, double
     }
   }
   CUDA_TRY(cudaStreamSynchronize(st));
+  check_device_flag(P, st);
   return SPOCK_OK;
 }
 
@@ -569,6 +590,11 @@ static S* dalloc(Problem& P, size_t n) {
   return (S*)p;
 }
 
+static int32_t pad16(int64_t elems, size_t elt) {
+  const int64_t a = (int64_t)(16 / elt);
+  return (int32_t)((elems + a - 1) / a * a);
+}
+
 template <typename S>
 static void upload_factors(Problem& P, DevFactors<S>& f, const std::vector<double>& Gb,
                            const std::vector<double>& Gf, const std::vector<double>& NB,
@@ -578,10 +604,24 @@ static void upload_factors(Problem& P, DevFactors<S>& f, const std::vector<doubl
     for (size_t i = 0; i < v.size(); ++i) o[i] = (S)v[i];
     return o;
   };
-  f.Gb = upload(P, cast(Gb));
-  f.Gf = upload(P, cast(Gf));
-  f.NB = upload(P, cast(NB));
-  f.Kt = upload(P, cast(Kt));
+  // blocks of `len` entries re-laid out with a padded stride
+  auto padded = [](const std::vector<double>& v, size_t len, size_t stride) {
+    const size_t cnt = len ? v.size() / len : 0;
+    std::vector<S> o(cnt * stride, S(0));
+    for (size_t b = 0; b < cnt; ++b)
+      for (size_t i = 0; i < len; ++i) o[b * stride + i] = (S)v[b * len + i];
+    return o;
+  };
+  const int nx = P.nx, nu = P.nu, ncol = nx + nu;
+  f.xs = pad16(nx, sizeof(S));
+  f.us = pad16(nu, sizeof(S));
+  f.gstride = pad16((int64_t)nx * ncol, sizeof(S));
+  f.nbstride = pad16(2 * (int64_t)nu * nx + (int64_t)nu * nu, sizeof(S));
+  f.ktstride = pad16((int64_t)nx * nu, sizeof(S));
+  f.Gb = upload(P, padded(Gb, (size_t)nx * ncol, f.gstride));
+  f.Gf = upload(P, padded(Gf, (size_t)nx * ncol, f.gstride));
+  f.NB = upload(P, padded(NB, 2 * (size_t)nu * nx + (size_t)nu * nu, f.nbstride));
+  f.Kt = upload(P, padded(Kt, (size_t)nx * nu, f.ktstride));
   f.qs = upload(P, cast(par[0]));
   f.rs = upload(P, cast(par[1]));
   f.qns = upload(P, cast(par[2]));
@@ -592,10 +632,10 @@ static void upload_factors(Problem& P, DevFactors<S>& f, const std::vector<doubl
   f.av = upload(P, cast(par[7]));
   f.prob = upload(P, cast(par[8]));
   const Tree& t = P.tree;
-  f.xbar = dalloc<S>(P, (size_t)t.n * P.nx);
-  f.ubar = dalloc<S>(P, (size_t)t.n_nonleaf * P.nu);
-  f.q = dalloc<S>(P, (size_t)t.n * P.nx);
-  f.d = dalloc<S>(P, (size_t)t.n_nonleaf * P.nu);
+  f.xbar = dalloc<S>(P, (size_t)t.n * f.xs);
+  f.ubar = dalloc<S>(P, (size_t)t.n_nonleaf * f.us);
+  f.q = dalloc<S>(P, (size_t)t.n * f.xs);
+  f.d = dalloc<S>(P, (size_t)t.n_nonleaf * f.us);
   f.x0 = dalloc<S>(P, (size_t)P.nx);
 }
 
@@ -746,6 +786,7 @@ static int problem_create(const Tree& tree, int32_t nx, int32_t nu, const double
     upload_factors<double>(*P, P->f64, Gb, Gf, NB, Kt, par);
     upload_factors<float>(*P, P->f32, Gb, Gf, NB, Kt, par);
     P->idx.stage_begin = upload(*P, t.stage_begin);
+    P->err = upload(*P, std::vector<int32_t>(1, 0));
     CUDA_TRY(cudaDeviceSynchronize());
   } catch (const SpockError& e) {
     delete P;
@@ -1010,9 +1051,10 @@ int spock_prox_f_dev(spock_problem* p, const double* x0_dev, double alpha, const
     KP<double> kp = op_kp(P, alpha);
     CUDA_TRY(cudaMemcpyAsync(P->f64.x0, x0_dev, sizeof(double) * P->nx, cudaMemcpyDeviceToDevice, st));
     launch_prep<double>(kp, z, (const double*)ws->zero_eta, z_out, sm_count() * 16, st);
-    launch_riccati<double>(kp, P->tree.stage_begin, z_out, st, nullptr);
+    launch_riccati<double>(kp, P->tree.stage_begin, P->tree.stage_maxch, z_out, st, nullptr);
     check_launch();
     CUDA_TRY(cudaStreamSynchronize(st));
+    check_device_flag(*P, st);
     return SPOCK_OK;
   });
 }
@@ -1042,11 +1084,12 @@ int spock_T_dev(spock_problem* p, const double* x0_dev, double alpha, const doub
     KP<double> kp = op_kp(P, alpha);
     CUDA_TRY(cudaMemcpyAsync(P->f64.x0, x0_dev, sizeof(double) * P->nx, cudaMemcpyDeviceToDevice, st));
     launch_prep<double>(kp, z, eta, z_out, sm_count() * 16, st);
-    launch_riccati<double>(kp, P->tree.stage_begin, z_out, st, nullptr);
+    launch_riccati<double>(kp, P->tree.stage_begin, P->tree.stage_maxch, z_out, st, nullptr);
     launch_dual<double>(kp, DM_DUAL_, false, z, z_out, eta, eta_out, nullptr, nullptr,
                         std::min((P->tree.n + 3) / 4, sm_count() * 16), st);
     check_launch();
     CUDA_TRY(cudaStreamSynchronize(st));
+    check_device_flag(*P, st);
     return SPOCK_OK;
   });
 }
@@ -1107,7 +1150,7 @@ extern "C" int spock_prox_f_noalloc_dev(spock_problem* p, const double* x0_dev, 
     Problem* P = as_problem(p);
     if (!P || !x0_dev || !z || !z_out) return fail(SPOCK_ERR_INVALID_ARG, "NULL argument");
     const Tree& t = P->tree;
-    const size_t nxb = (size_t)t.n * P->nx, nub = (size_t)t.n_nonleaf * P->nu;
+    const size_t nxb = (size_t)t.n * P->f64.xs, nub = (size_t)t.n_nonleaf * P->f64.us;
     const size_t need = 2 * nxb + 2 * nub + (size_t)P->off.n_eta;
     if (need > kNoAllocScratchDoubles)
       return fail(SPOCK_ERR_INVALID_ARG, "problem too large for spock_prox_f_noalloc_dev: needs " +
@@ -1128,9 +1171,10 @@ extern "C" int spock_prox_f_noalloc_dev(spock_problem* p, const double* x0_dev, 
     CUDA_TRY(cudaMemsetAsync(zero_eta, 0, sizeof(double) * (size_t)P->off.n_eta, st));
     CUDA_TRY(cudaMemcpyAsync(P->f64.x0, x0_dev, sizeof(double) * P->nx, cudaMemcpyDeviceToDevice, st));
     launch_prep<double>(kp, z, zero_eta, z_out, sm_count() * 16, st);
-    launch_riccati<double>(kp, P->tree.stage_begin, z_out, st, nullptr);
+    launch_riccati<double>(kp, P->tree.stage_begin, P->tree.stage_maxch, z_out, st, nullptr);
     check_launch();
     CUDA_TRY(cudaStreamSynchronize(st));
+    check_device_flag(*P, st);
     return SPOCK_OK;
   });
 }

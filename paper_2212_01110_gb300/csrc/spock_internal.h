@@ -38,6 +38,7 @@ struct Tree {
   std::vector<int32_t> user_of, int_of;        // internal -> user, user -> internal
   std::vector<int32_t> parent, ch_begin, ch_count, stage, sib;  // internal
   std::vector<int32_t> stage_begin;            // [N + 2]
+  std::vector<int32_t> stage_maxch;            // [N + 1] most children of a node at each stage
   std::vector<double> prob;                    // internal, conditional
   // chain region: every node at stages >= chain_stage (and < N) has one child
   int32_t chain_stage = 0;
@@ -71,6 +72,8 @@ struct DevFactors {
   S* q = nullptr;     // [n][nx]
   S* d = nullptr;     // [nl][nu]
   S* x0 = nullptr;    // [nx]
+  // per-node strides in elements, padded to a multiple of 16 bytes
+  int32_t xs = 0, us = 0, gstride = 0, nbstride = 0, ktstride = 0;
 };
 
 struct DevIndex {
@@ -92,6 +95,7 @@ struct Problem {
   double normL = 0.0;
   double factor_seconds = 0.0;
   DevIndex idx;
+  int32_t* err = nullptr;  // device flag set by a kernel whose bounded wait gave up
   DevFactors<double> f64;
   DevFactors<float> f32;
   std::vector<void*> allocations;

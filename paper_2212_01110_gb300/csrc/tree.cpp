@@ -78,6 +78,8 @@ int build_tree(int32_t n, const int32_t* anc, const double* prob, Tree& t) {
   t.stage_begin.assign(N + 2, n);
   for (int32_t k = n - 1; k >= 0; --k) t.stage_begin[t.stage[k]] = k;
   t.stage_begin[N + 1] = n;
+  t.stage_maxch.assign(N + 1, 0);
+  for (int32_t k = 0; k < n; ++k) t.stage_maxch[t.stage[k]] = std::max(t.stage_maxch[t.stage[k]], t.ch_count[k]);
   // probabilities
   for (int32_t k = 0; k < t.n_nonleaf; ++k) {
     double s = 0.0;

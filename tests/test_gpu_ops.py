@@ -47,7 +47,14 @@ def test_prox_gconj(pair, alpha_scale):
     assert rel_err(out.cpu().numpy(), prox_gconj(eta, alpha, pair.op)) < RTOL
 
 
-def test_prox_f(pair):
+@pytest.fixture(params=["tma", "direct"])
+def kernels(request, monkeypatch):
+    """Both Riccati kernel families: bulk-copy staged (default) and direct loads."""
+    monkeypatch.setenv("SPOCK_RICCATI_KERNELS", request.param)
+    return request.param
+
+
+def test_prox_f(pair, kernels):
     import torch
     from paper_2212_01110_gb300 import spock
     rng = np.random.default_rng(2)
@@ -58,7 +65,7 @@ def test_prox_f(pair):
     assert rel_err(out.cpu().numpy(), ref) < RTOL
 
 
-def test_T(pair):
+def test_T(pair, kernels):
     import torch
     from paper_2212_01110_gb300 import spock
     rng = np.random.default_rng(3)
