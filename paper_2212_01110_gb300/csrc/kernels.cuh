@@ -28,8 +28,21 @@ enum Stat : int {
   ST_RE_LDZ = 7,   // sum r_eta . (L d_z)
 };
 
+// Everything a warp needs to locate node k's blocks in z and eta, in one
+// 128-byte record (one memory round trip instead of a chain of table loads).
+struct alignas(16) NodeDesc {
+  int64_t zx, zu, zz2, zs, ztau;   // x^k, u^k, z2 block, s^k, tau^k in z
+  int64_t enl, enr, elf;           // nonleaf / nonroot / leaf block of k in eta
+  int64_t zxp, zup;                // x and u of the parent in z
+  int64_t es;                      // eta row holding s^k: enl + 2m + 1 (nonleaf) or elf + 2 nx (leaf)
+  int32_t par, m, c0, pad0;        // parent, number of children, first child
+  int64_t pad1[2];
+};
+static_assert(sizeof(NodeDesc) == 128, "NodeDesc must be 128 bytes");
+
 template <typename S>
 struct KP {
+  const NodeDesc* __restrict__ desc;
   int32_t n, nl, nx, nu, N, chain_stage, n_chains;
   int64_t n_z, n_eta;
   S alpha;

@@ -29,18 +29,19 @@ __global__ void __launch_bounds__(128) k_prep(KP<S> p, const S* __restrict__ z,
   const S al = p.alpha;
   const int nx = p.nx, nu = p.nu;
   for (int k = gw; k < p.n; k += nw) {
+    const NodeDesc D = p.desc[k];
     if (k < p.nl) {
-      const int m = p.ch_count[k], c0 = p.ch_begin[k];
-      const int64_t el = p.enl[k], ex = el + 2 * m + 2, eu = ex + nx, z2 = p.zz2[k];
+      const int m = D.m, c0 = D.c0;
+      const int64_t el = D.enl, ex = el + 2 * m + 2, eu = ex + nx, z2 = D.zz2;
       for (int r = lane; r < nx; r += 32) {
         S acc = eta[ex + r];
-        for (int j = 0; j < m; ++j) acc += p.qs[(int64_t)(c0 + j) * nx + r] * eta[p.enr[c0 + j] + r];
-        p.xbar[(int64_t)k * p.xs + r] = z[p.zx[k] + r] - al * acc;
+        for (int j = 0; j < m; ++j) acc += p.qs[(int64_t)(c0 + j) * nx + r] * eta[p.desc[c0 + j].enr + r];
+        p.xbar[(int64_t)k * p.xs + r] = z[D.zx + r] - al * acc;
       }
       for (int r = lane; r < nu; r += 32) {
         S acc = eta[eu + r];
-        for (int j = 0; j < m; ++j) acc += p.rs[(int64_t)(c0 + j) * nu + r] * eta[p.enr[c0 + j] + nx + r];
-        p.ubar[(int64_t)k * p.us + r] = z[p.zu[k] + r] - al * acc;
+        for (int j = 0; j < m; ++j) acc += p.rs[(int64_t)(c0 + j) * nu + r] * eta[p.desc[c0 + j].enr + nx + r];
+        p.ubar[(int64_t)k * p.us + r] = z[D.zu + r] - al * acc;
       }
       // z_2 block: zbar = z - alpha L* eta, then projection on ker [E^T, -I, -I]
       // with (M M^T)^-1 = (I - 11^T / (c + m)) / c, c = a^2 + 3 (Sherman-Morrison).
@@ -50,17 +51,12 @@ __global__ void __launch_bounds__(128) k_prep(KP<S> p, const S* __restrict__ z,
       const S y3 = z[z2 + 2 * m] - al * (eta[el + 2 * m] - sb);
       auto bars = [&](int j, S& y1, S& y2, S& ta, S& sv) {
         const int c = c0 + j;
-        const int64_t er = p.enr[c];
+        const NodeDesc& Dc = p.desc[c];
+        const int64_t er = Dc.enr, es = Dc.es;
         y1 = z[z2 + j] - al * (eta[el + j] - p.prob[c] * sb);
         y2 = z[z2 + m + j] - al * eta[el + m + j];
         ta = z[z2 + 2 * m + 1 + j] - al * S(0.5) * (eta[er + nx + nu] + eta[er + nx + nu + 1]);
-        S ls;
-        if (c < p.nl) {
-          ls = eta[p.enl[c] + 2 * p.ch_count[c] + 1];
-        } else {
-          const int64_t ef = p.elf[c];
-          ls = S(0.5) * (eta[ef + 2 * nx] + eta[ef + 2 * nx + 1]);
-        }
+        const S ls = (c < p.nl) ? eta[es] : S(0.5) * (eta[es] + eta[es + 1]);
         sv = z[z2 + 3 * m + 1 + j] - al * ls;
       };
       S sumMw = 0;
@@ -88,10 +84,10 @@ __global__ void __launch_bounds__(128) k_prep(KP<S> p, const S* __restrict__ z,
         if (k == 0) zo[0] = (z[0] - al * sb) - al;   // prox of alpha * s^0
       }
     } else {
-      const int64_t ef = p.elf[k];
+      const int64_t ef = D.elf;
       for (int r = lane; r < nx; r += 32)
         p.xbar[(int64_t)k * p.xs + r] =
-            z[p.zx[k] + r] - al * (eta[ef + r] + p.qns[(int64_t)k * nx + r] * eta[ef + nx + r]);
+            z[D.zx + r] - al * (eta[ef + r] + p.qns[(int64_t)k * nx + r] * eta[ef + nx + r]);
     }
   }
 }
@@ -200,10 +196,11 @@ __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, 
     Ld = DIR ? coef * dz[zi] : S(0);
   };
   for (int k = gw; k < p.n; k += nw) {
+    const NodeDesc D = p.desc[k];
     // ---- nonleaf block (y, s - b'y, x, u)
     if (k < p.nl) {
-      const int m = p.ch_count[k], c0 = p.ch_begin[k];
-      const int64_t el = p.enl[k], z2 = p.zz2[k];
+      const int m = D.m, c0 = D.c0;
+      const int64_t el = D.enl, z2 = D.zz2;
       for (int e = lane; e < 2 * m + 1; e += 32) {
         S Lz, Lzp, Ld;
         row(z2 + e, S(1), Lz, Lzp, Ld);
@@ -223,7 +220,7 @@ __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, 
         if (MODE == DM_DUAL) bzp = warp_sum(bzp);
         if (DIR) bd = warp_sum(bd);
         if (lane == 0) {
-          const int64_t si = p.zs[k];
+          const int64_t si = D.zs;
           const S Lz = (MODE == DM_PROXG) ? S(0) : z[si] - (bz + z[z2 + 2 * m]);
           const S Lzp = (MODE == DM_DUAL) ? zp[si] - (bzp + zp[z2 + 2 * m]) : S(0);
           const S Ld = DIR ? dz[si] - (bd + dz[z2 + 2 * m]) : S(0);
@@ -237,11 +234,11 @@ __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, 
       for (int e = lane; e < nx + nu; e += 32) {
         S Lz, Lzp, Ld, lo, hi;
         if (e < nx) {
-          row(p.zx[k] + e, S(1), Lz, Lzp, Ld);
+          row(D.zx + e, S(1), Lz, Lzp, Ld);
           lo = p.xlo[(int64_t)k * nx + e];
           hi = p.xhi[(int64_t)k * nx + e];
         } else {
-          row(p.zu[k] + (e - nx), S(1), Lz, Lzp, Ld);
+          row(D.zu + (e - nx), S(1), Lz, Lzp, Ld);
           lo = p.ulo[(int64_t)k * nu + (e - nx)];
           hi = p.uhi[(int64_t)k * nu + (e - nx)];
         }
@@ -252,14 +249,13 @@ __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, 
     }
     // ---- nonroot block (Q^1/2 x^anc, R^1/2 u^anc, tau/2, tau/2)
     if (k > 0) {
-      const int par = p.parent[k];
-      const int64_t er = p.enr[k];
+      const int64_t er = D.enr;
       const int dim = nx + nu + 2;
       for (int e = lane; e < dim; e += 32) {
         S Lz, Lzp, Ld;
-        if (e < nx) row(p.zx[par] + e, p.qs[(int64_t)k * nx + e], Lz, Lzp, Ld);
-        else if (e < nx + nu) row(p.zu[par] + (e - nx), p.rs[(int64_t)k * nu + (e - nx)], Lz, Lzp, Ld);
-        else row(p.ztau[k], S(0.5), Lz, Lzp, Ld);
+        if (e < nx) row(D.zxp + e, p.qs[(int64_t)k * nx + e], Lz, Lzp, Ld);
+        else if (e < nx + nu) row(D.zup + (e - nx), p.rs[(int64_t)k * nu + (e - nx)], Lz, Lzp, Ld);
+        else row(D.ztau, S(0.5), Lz, Lzp, Ld);
         wb[e] = dual_w<S, MODE>(p, eta, er + e, Lz, Lzp);
         lb[e] = Lz - Lzp;
         db[e] = Ld;
@@ -279,10 +275,10 @@ __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, 
     }
     // ---- leaf block (x, Q_N^1/2 x, s/2, s/2)
     if (k >= p.nl) {
-      const int64_t ef = p.elf[k];
+      const int64_t ef = D.elf;
       for (int e = lane; e < nx; e += 32) {
         S Lz, Lzp, Ld;
-        row(p.zx[k] + e, S(1), Lz, Lzp, Ld);
+        row(D.zx + e, S(1), Lz, Lzp, Ld);
         const S w = dual_w<S, MODE>(p, eta, ef + e, Lz, Lzp);
         const S o = (MODE == DM_APPLY_L) ? w
                                          : w - al * clampv(w * ial, p.xlo[(int64_t)k * nx + e], p.xhi[(int64_t)k * nx + e]);
@@ -292,8 +288,8 @@ __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, 
       const int64_t es = ef + nx;
       for (int e = lane; e < dim; e += 32) {
         S Lz, Lzp, Ld;
-        if (e < nx) row(p.zx[k] + e, p.qns[(int64_t)k * nx + e], Lz, Lzp, Ld);
-        else row(p.zs[k], S(0.5), Lz, Lzp, Ld);
+        if (e < nx) row(D.zx + e, p.qns[(int64_t)k * nx + e], Lz, Lzp, Ld);
+        else row(D.zs, S(0.5), Lz, Lzp, Ld);
         wb[e] = dual_w<S, MODE>(p, eta, es + e, Lz, Lzp);
         lb[e] = Lz - Lzp;
         db[e] = Ld;
@@ -344,18 +340,19 @@ __global__ void __launch_bounds__(128) k_primal(KP<S> p, const S* __restrict__ e
     }
   };
   for (int k = gw; k < p.n; k += nw) {
+    const NodeDesc D = p.desc[k];
     if (k < p.nl) {
-      const int m = p.ch_count[k], c0 = p.ch_begin[k];
-      const int64_t el = p.enl[k], ex = el + 2 * m + 2, eu = ex + nx, z2 = p.zz2[k];
+      const int m = D.m, c0 = D.c0;
+      const int64_t el = D.enl, ex = el + 2 * m + 2, eu = ex + nx, z2 = D.zz2;
       for (int r = lane; r < nx; r += 32) {
         S acc2 = E(ex + r);
-        for (int j = 0; j < m; ++j) acc2 += p.qs[(int64_t)(c0 + j) * nx + r] * E(p.enr[c0 + j] + r);
-        emit(p.zx[k] + r, acc2);
+        for (int j = 0; j < m; ++j) acc2 += p.qs[(int64_t)(c0 + j) * nx + r] * E(p.desc[c0 + j].enr + r);
+        emit(D.zx + r, acc2);
       }
       for (int r = lane; r < nu; r += 32) {
         S acc2 = E(eu + r);
-        for (int j = 0; j < m; ++j) acc2 += p.rs[(int64_t)(c0 + j) * nu + r] * E(p.enr[c0 + j] + nx + r);
-        emit(p.zu[k] + r, acc2);
+        for (int j = 0; j < m; ++j) acc2 += p.rs[(int64_t)(c0 + j) * nu + r] * E(p.desc[c0 + j].enr + nx + r);
+        emit(D.zu + r, acc2);
       }
       const S sb = E(el + 2 * m + 1);
       for (int l = lane; l < 2 * m + 1; l += 32) {
@@ -364,22 +361,16 @@ __global__ void __launch_bounds__(128) k_primal(KP<S> p, const S* __restrict__ e
       }
       for (int j = lane; j < m; j += 32) {
         const int c = c0 + j;
-        const int64_t er = p.enr[c];
+        const NodeDesc& Dc = p.desc[c];
+        const int64_t er = Dc.enr, es = Dc.es;
         emit(z2 + 2 * m + 1 + j, S(0.5) * (E(er + nx + nu) + E(er + nx + nu + 1)));
-        S ls;
-        if (c < p.nl) {
-          ls = E(p.enl[c] + 2 * p.ch_count[c] + 1);
-        } else {
-          const int64_t ef = p.elf[c];
-          ls = S(0.5) * (E(ef + 2 * nx) + E(ef + 2 * nx + 1));
-        }
-        emit(z2 + 3 * m + 1 + j, ls);
+        emit(z2 + 3 * m + 1 + j, (c < p.nl) ? E(es) : S(0.5) * (E(es) + E(es + 1)));
       }
       if (k == 0 && lane == 0) emit(0, sb);
     } else {
-      const int64_t ef = p.elf[k];
+      const int64_t ef = D.elf;
       for (int r = lane; r < nx; r += 32)
-        emit(p.zx[k] + r, E(ef + r) + p.qns[(int64_t)k * nx + r] * E(ef + nx + r));
+        emit(D.zx + r, E(ef + r) + p.qns[(int64_t)k * nx + r] * E(ef + nx + r));
     }
     if (MODE == PM_STATS) nacc.flush(acc);
   }

@@ -319,12 +319,30 @@ int launch_bwd_stage_tma(const KP<S>& p, int t, int cnt, int max_children, cudaS
 template <typename S, int SL>
 int launch_fwd_stage_tma(const KP<S>& p, int t, int cnt, int max_children, S* zo, cudaStream_t st);
 
-// Kernel family: shared-memory staged (default, when a node's blocks fit)
-// or the direct-load kernels above.  SPOCK_RICCATI_KERNELS=direct selects
-// the latter (used by the tests to cover both).
-static bool want_tma() {
+template <typename S>
+bool grp_chain_fits(const KP<S>& p);
+template <typename S>
+int launch_bwd_chain_grp(const KP<S>& p, cudaStream_t st);
+template <typename S>
+int launch_fwd_chain_grp(const KP<S>& p, S* zo, cudaStream_t st);
+
+// Kernel family for the chain region: "grp" (three warps per chain, staged),
+// "tma" (one warp per chain, staged) or "direct" (one warp per chain, loads
+// straight from global memory); the branching stages use the staged
+// block-per-node kernels unless "direct".  Default (measured on the
+// 62,805-node tree): forward pass "grp"; backward pass "tma" (FP32) -- its
+// node update keeps only one warp busy, so splitting it over three warps
+// loses more at the barriers than it gains -- and "direct" for FP64 where
+// the staged variant fits too few warps per SM (tma_chain_fits).
+// SPOCK_RICCATI_KERNELS forces one family everywhere (the tests cover each).
+enum ChainFamily { CF_AUTO = -1, CF_GRP = 0, CF_TMA = 1, CF_DIRECT = 2 };
+static int chain_family() {
   const char* e = getenv("SPOCK_RICCATI_KERNELS");
-  return !(e && e[0] == 'd');
+  if (!e || !e[0]) return CF_AUTO;
+  if (e[0] == 'd') return CF_DIRECT;
+  if (e[0] == 't') return CF_TMA;
+  if (e[0] == 'g') return CF_GRP;
+  return CF_AUTO;
 }
 
 // Launches both passes; ev (optional, 3 events) is recorded after the
@@ -334,11 +352,17 @@ template <typename S, int SL>
 int riccati_passes_sl(const KP<S>& p, const std::vector<int32_t>& stage_begin,
                       const std::vector<int32_t>& stage_maxch, S* zo, cudaStream_t st, cudaEvent_t* ev) {
   const int cs = p.chain_stage;
-  const bool tma = want_tma();
-  const bool tma_chain = tma && tma_chain_fits(p), tma_stage = tma && tma_stage_fits(p);
+  const int fam = chain_family();
+  const bool grp_ok = fam != CF_DIRECT && fam != CF_TMA && grp_chain_fits(p);
+  const bool bwd_grp = fam == CF_GRP && grp_ok;
+  const bool fwd_grp = (fam == CF_GRP || fam == CF_AUTO) && grp_ok;
+  const bool tma_chain = fam != CF_DIRECT && tma_chain_fits(p);
+  const bool tma_stage = fam != CF_DIRECT && tma_stage_fits(p);
   int launches = 0;
   if (p.n_chains > 0 && cs < p.N) {
-    if (tma_chain) {
+    if (bwd_grp) {
+      launches += launch_bwd_chain_grp<S>(p, st);
+    } else if (tma_chain) {
       launches += launch_bwd_chain_tma<S, SL>(p, st);
     } else {
       const int grid = (p.n_chains + kWarpsPerBlock - 1) / kWarpsPerBlock;
@@ -368,7 +392,9 @@ int riccati_passes_sl(const KP<S>& p, const std::vector<int32_t>& stage_begin,
   }
   if (ev) cudaEventRecord(ev[2], st);
   if (p.n_chains > 0 && cs < p.N) {
-    if (tma_chain) {
+    if (fwd_grp) {
+      launches += launch_fwd_chain_grp<S>(p, zo, st);
+    } else if (tma_chain) {
       launches += launch_fwd_chain_tma<S, SL>(p, zo, st);
     } else {
       const int grid = (p.n_chains + kWarpsPerBlock - 1) / kWarpsPerBlock;

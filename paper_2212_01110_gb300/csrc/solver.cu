@@ -134,6 +134,7 @@ struct Profiler {
 struct Workspace {
   int prec = 0;
   int64_t n_v = 0;
+  int64_t ld = 0;  // column stride of the Anderson buffers
   int mem = -1;
   void* v[3] = {nullptr, nullptr, nullptr};
   void* Tv[3] = {nullptr, nullptr, nullptr};
@@ -204,15 +205,17 @@ static Workspace* get_ws_impl(Problem& P, int mem) {
     }
     ws->stats = (double*)ws->alloc(3 * 8 * sizeof(double));
     ws->d = ws->alloc(vb);
-    ws->MR = ws->alloc(vb * (size_t)(mem > 0 ? mem : 1));
-    ws->D = ws->alloc(vb * (size_t)(mem > 0 ? mem : 1));
+    ws->ld = (ws->n_v + 63) / 64 * 64;  // column stride: 256-byte aligned columns
+    const size_t cb = sizeof(S) * (size_t)ws->ld;
+    ws->MR = ws->alloc(cb * (size_t)(mem > 0 ? mem : 1));
+    ws->D = ws->alloc(cb * (size_t)(mem > 0 ? mem : 1));
     ws->zero_eta = ws->alloc(sizeof(double) * (size_t)P.off.n_eta);
     CUDA_TRY(cudaMemset(ws->zero_eta, 0, sizeof(double) * (size_t)P.off.n_eta));
     const int sms = sm_count();
     ws->grid_d = std::min((P.tree.n + kWarpsPerBlock - 1) / kWarpsPerBlock, sms * 16);
     ws->grid_d = std::max(ws->grid_d, 1);
     ws->grid_p = ws->grid_d;
-    ws->grid_v = sms * 8;
+    ws->grid_v = sms * 4;
     ws->pd = (double*)ws->alloc(sizeof(double) * 8 * ws->grid_d);
     ws->pp = (double*)ws->alloc(sizeof(double) * 8 * ws->grid_p);
     ws->paa = (double*)ws->alloc(sizeof(double) * 2 * kMaxMemory * ws->grid_v);
@@ -242,6 +245,7 @@ template <typename S>
 static KP<S> make_kp(const Problem& P, double alpha, const int32_t* stage_begin_dev) {
   const DevFactors<S>& f = factors<S>(P);
   KP<S> k;
+  k.desc = P.idx.desc;
   k.n = P.tree.n;
   k.nl = P.tree.n_nonleaf;
   k.nx = P.nx;
@@ -377,8 +381,8 @@ static int solve_impl(Problem& P, const double* x0_dev, const spock_settings& s,
     CUDA_TRY(cudaMemsetAsync(V[0], 0, sizeof(S) * nv, st));
   }
   if (mem > 0) {
-    CUDA_TRY(cudaMemsetAsync(MR, 0, sizeof(S) * nv * mem, st));
-    CUDA_TRY(cudaMemsetAsync(Dm, 0, sizeof(S) * nv * mem, st));
+    CUDA_TRY(cudaMemsetAsync(MR, 0, sizeof(S) * ws->ld * mem, st));
+    CUDA_TRY(cudaMemsetAsync(Dm, 0, sizeof(S) * ws->ld * mem, st));
   }
   const int max_iter = std::max(0, s.max_iter);
   int32_t* trace_dev = nullptr;
@@ -441,11 +445,11 @@ static int solve_impl(Problem& P, const double* x0_dev, const spock_settings& s,
       int order[kMaxMemory];
       for (int j = 0; j < kMaxMemory; ++j) order[j] = 0;
       for (int j = 0; j < cnt; ++j) order[j] = ((slot - j) % mem + mem) % mem;
-      launch_aa_update<S>(ws->st, V[cur], TV[cur], V[prev], TV[prev], MR, Dm, nv, slot, cnt, order, ws->paa,
-                          ws->grid_v, st);
+      launch_aa_update<S>(ws->st, V[cur], TV[cur], V[prev], TV[prev], MR, Dm, nv, ws->ld, slot, cnt, order,
+                          ws->paa, ws->grid_v, st);
       ws->launches += 2;
     }
-    launch_aa_direction<S>(ws->st, V[cur], TV[cur], Dm, nv, cnt, d, V[trial], ws->grid_v, st);
+    launch_aa_direction<S>(ws->st, V[cur], TV[cur], Dm, nv, ws->ld, cnt, d, V[trial], ws->grid_v, st);
     ws->launches += 1;
     check_launch();
     if (act == A_K0) {
@@ -786,6 +790,29 @@ static int problem_create(const Tree& tree, int32_t nx, int32_t nu, const double
     upload_factors<double>(*P, P->f64, Gb, Gf, NB, Kt, par);
     upload_factors<float>(*P, P->f32, Gb, Gf, NB, Kt, par);
     P->idx.stage_begin = upload(*P, t.stage_begin);
+    {
+      std::vector<NodeDesc> dh(nn);
+      const Offsets& o = P->off;
+      for (int32_t k = 0; k < n; ++k) {
+        NodeDesc& q = dh[k];
+        std::memset(&q, 0, sizeof(q));
+        q.zx = o.zx[k];
+        q.zu = o.zu[k];
+        q.zz2 = o.zz2[k];
+        q.zs = o.zs[k];
+        q.ztau = o.ztau[k];
+        q.enl = o.enl[k];
+        q.enr = o.enr[k];
+        q.elf = o.elf[k];
+        q.par = t.parent[k];
+        q.m = t.ch_count[k];
+        q.c0 = t.ch_begin[k];
+        q.zxp = k > 0 ? o.zx[t.parent[k]] : -1;
+        q.zup = k > 0 ? o.zu[t.parent[k]] : -1;
+        q.es = k < nl ? o.enl[k] + 2 * t.ch_count[k] + 1 : o.elf[k] + 2 * nx;
+      }
+      P->idx.desc = upload(*P, dh);
+    }
     P->err = upload(*P, std::vector<int32_t>(1, 0));
     CUDA_TRY(cudaDeviceSynchronize());
   } catch (const SpockError& e) {

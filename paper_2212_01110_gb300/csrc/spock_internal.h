@@ -84,6 +84,7 @@ struct DevIndex {
   int64_t *zx = nullptr, *zu = nullptr, *zz2 = nullptr, *zs = nullptr, *ztau = nullptr;
   int64_t *enl = nullptr, *enr = nullptr, *elf = nullptr;
   int32_t* stage_begin = nullptr;  // [N + 2]
+  struct NodeDesc* desc = nullptr; // [n] per-node record (kernels.cuh)
 };
 
 struct Problem {

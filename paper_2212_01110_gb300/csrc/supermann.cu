@@ -117,74 +117,106 @@ void launch_sm_line_search(SmState* st, const double* stats, int32_t* trace, cud
 // ---------------------------------------------------------------------------
 // Anderson
 // ---------------------------------------------------------------------------
+// Streaming kernels move 16 bytes per load (float4 / double2); every vector
+// and every Anderson column starts on a 256-byte boundary (column stride
+// `ld` padded by the host), so only the tail of a vector is scalar.
+template <typename S>
+struct Pack;
+template <>
+struct Pack<float> {
+  using T = float4;
+  static constexpr int N = 4;
+};
+template <>
+struct Pack<double> {
+  using T = double2;
+  static constexpr int N = 2;
+};
+template <typename S>
+__device__ __forceinline__ S& pk(typename Pack<S>::T& v, int e) {
+  return reinterpret_cast<S*>(&v)[e];
+}
+template <typename S>
+__device__ __forceinline__ typename Pack<S>::T ldp(const S* p, int64_t q) {
+  return reinterpret_cast<const typename Pack<S>::T*>(p)[q];
+}
+template <typename S>
+__device__ __forceinline__ void stp(S* p, int64_t q, const typename Pack<S>::T& v) {
+  reinterpret_cast<typename Pack<S>::T*>(p)[q] = v;
+}
 // Block partials: [0, cnt) = <M^R_j, M^R_slot>, [kMaxMemory, kMaxMemory+cnt)
 // = <M^R_j, r> (j over the stored slots, the new column included).
-template <typename S>
-__global__ void __launch_bounds__(256) k_aa_update(const S* __restrict__ v, const S* __restrict__ Tv,
-                                                   const S* __restrict__ vp, const S* __restrict__ Tvp,
-                                                   S* __restrict__ MR, S* __restrict__ D, int64_t n, int slot,
-                                                   int cnt, double* __restrict__ partials) {
-  // Dot products: terms in the working precision, summed over chunks of 8
-  // grid-stride steps in S, then accumulated in FP64.
-  double gr[kMaxMemory], rh[kMaxMemory];
-  S cg[kMaxMemory], cr[kMaxMemory];
+template <typename S, int CNT>
+__global__ void __launch_bounds__(256, 4) k_aa_update(const S* __restrict__ v, const S* __restrict__ Tv,
+                                                      const S* __restrict__ vp, const S* __restrict__ Tvp,
+                                                      S* __restrict__ MR, S* __restrict__ D, int64_t n, int64_t ld,
+                                                      int slot, double* __restrict__ partials) {
+  // Writes column `slot` of M^R and of D = M^P - M^R and accumulates
+  // <M^R_j, new column> and <M^R_j, r>: terms in the working precision, one
+  // pack at a time, added into FP64 per pack.  CNT (stored columns, the new
+  // one included) is a template parameter so the accumulators stay in
+  // registers.
+  constexpr int NP = Pack<S>::N;
+  using PT = typename Pack<S>::T;
+  double gr[CNT], rh[CNT];
 #pragma unroll
-  for (int j = 0; j < kMaxMemory; ++j) {
-    gr[j] = rh[j] = 0.0;
-    cg[j] = cr[j] = S(0);
-  }
+  for (int j = 0; j < CNT; ++j) gr[j] = rh[j] = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  int chunk = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t npack = n / NP;
+  S* mrs = MR + (int64_t)slot * ld;
+  S* ds = D + (int64_t)slot * ld;
+  for (int64_t q = gt; q < npack; q += stride) {
+    PT a = ldp(v, q), b = ldp(Tv, q), c = ldp(vp, q), e = ldp(Tvp, q);
+    PT rr, dc, dd;
+#pragma unroll
+    for (int t = 0; t < NP; ++t) {
+      pk<S>(rr, t) = pk<S>(a, t) - pk<S>(b, t);
+      pk<S>(dc, t) = pk<S>(rr, t) - (pk<S>(c, t) - pk<S>(e, t));
+      pk<S>(dd, t) = (pk<S>(a, t) - pk<S>(c, t)) - pk<S>(dc, t);
+    }
+    stp(mrs, q, dc);
+    stp(ds, q, dd);
+#pragma unroll
+    for (int j = 0; j < CNT; ++j) {
+      PT col = (j == slot) ? dc : ldp(MR + (int64_t)j * ld, q);
+      S g = 0, h = 0;
+#pragma unroll
+      for (int t = 0; t < NP; ++t) {
+        g += pk<S>(col, t) * pk<S>(dc, t);
+        h += pk<S>(col, t) * pk<S>(rr, t);
+      }
+      gr[j] += (double)g;
+      rh[j] += (double)h;
+    }
+  }
+  for (int64_t i = npack * NP + gt; i < n; i += stride) {  // tail
     const S r = v[i] - Tv[i];
     const S dc = r - (vp[i] - Tvp[i]);
-    const S dv = v[i] - vp[i];
-    MR[(int64_t)slot * n + i] = dc;
-    D[(int64_t)slot * n + i] = dv - dc;
+    mrs[i] = dc;
+    ds[i] = (v[i] - vp[i]) - dc;
 #pragma unroll
-    for (int j = 0; j < kMaxMemory; ++j) {
-      if (j < cnt) {
-        const S c = (j == slot) ? dc : MR[(int64_t)j * n + i];
-        cg[j] += c * dc;
-        cr[j] += c * r;
-      }
-    }
-    if (++chunk == 8) {
-      chunk = 0;
-#pragma unroll
-      for (int j = 0; j < kMaxMemory; ++j) {
-        if (j < cnt) {
-          gr[j] += (double)cg[j];
-          rh[j] += (double)cr[j];
-          cg[j] = cr[j] = S(0);
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < kMaxMemory; ++j) {
-    if (j < cnt) {
-      gr[j] += (double)cg[j];
-      rh[j] += (double)cr[j];
+    for (int j = 0; j < CNT; ++j) {
+      const S c = (j == slot) ? dc : MR[(int64_t)j * ld + i];
+      gr[j] += (double)(c * dc);
+      rh[j] += (double)(c * r);
     }
   }
   __shared__ double red[8][2 * kMaxMemory];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-  for (int j = 0; j < kMaxMemory; ++j) {
-    if (j < cnt) {
-      const double a = warp_sum(gr[j]), b = warp_sum(rh[j]);
-      if (lane == 0) {
-        red[w][j] = a;
-        red[w][kMaxMemory + j] = b;
-      }
+  for (int j = 0; j < CNT; ++j) {
+    const double a = warp_sum(gr[j]), b = warp_sum(rh[j]);
+    if (lane == 0) {
+      red[w][j] = a;
+      red[w][kMaxMemory + j] = b;
     }
   }
   __syncthreads();
   if (threadIdx.x < 2 * kMaxMemory) {
     const int j = threadIdx.x % kMaxMemory;
     double s = 0.0;
-    if (j < cnt)
+    if (j < CNT)
       for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) s += red[ww][threadIdx.x];
     partials[(int64_t)blockIdx.x * 2 * kMaxMemory + threadIdx.x] = s;
   }
@@ -196,13 +228,22 @@ struct SlotOrder {
   int32_t s[kMaxMemory];
 };
 
-__global__ void k_aa_solve(SmState* st, const double* __restrict__ partials, int nblocks, int slot, int cnt,
-                           SlotOrder order) {
+__global__ void __launch_bounds__(256) k_aa_solve(SmState* st, const double* __restrict__ partials, int nblocks,
+                                                  int slot, int cnt, SlotOrder order) {
+  // 256 threads: value t % 32 of the block partials, blocks t / 32, t / 32 + 8, ...
+  __shared__ double part[8][2 * kMaxMemory];
   __shared__ double sums[2 * kMaxMemory];
   const int t = threadIdx.x;
+  {
+    const int val = t & 31, grp = t >> 5;
+    double s = 0.0;
+    for (int b = grp; b < nblocks; b += 8) s += partials[(int64_t)b * 2 * kMaxMemory + val];
+    part[grp][val] = s;
+  }
+  __syncthreads();
   if (t < 2 * kMaxMemory) {
     double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partials[(int64_t)b * 2 * kMaxMemory + t];
+    for (int g = 0; g < 8; ++g) s += part[g][t];
     sums[t] = s;
   }
   __syncthreads();
@@ -254,31 +295,64 @@ __global__ void k_aa_solve(SmState* st, const double* __restrict__ partials, int
   }
 }
 
-template <typename S>
-void launch_aa_update(SmState* st, const S* v, const S* Tv, const S* vp, const S* Tvp, S* MR, S* D, int64_t n,
-                      int slot, int cnt, int order[kMaxMemory], double* partials, int grid, cudaStream_t s) {
-  k_aa_update<S><<<grid, 256, 0, s>>>(v, Tv, vp, Tvp, MR, D, n, slot, cnt, partials);
-  SlotOrder o;
-  for (int j = 0; j < kMaxMemory; ++j) o.s[j] = order[j];
-  k_aa_solve<<<1, 64, 0, s>>>(st, partials, grid, slot, cnt, o);
+template <typename S, int CNT>
+static void aa_update_cnt(const S* v, const S* Tv, const S* vp, const S* Tvp, S* MR, S* D, int64_t n, int64_t ld,
+                          int slot, double* partials, int grid, cudaStream_t s) {
+  k_aa_update<S, CNT><<<grid, 256, 0, s>>>(v, Tv, vp, Tvp, MR, D, n, ld, slot, partials);
 }
 
 template <typename S>
+void launch_aa_update(SmState* st, const S* v, const S* Tv, const S* vp, const S* Tvp, S* MR, S* D, int64_t n,
+                      int64_t ld, int slot, int cnt, int order[kMaxMemory], double* partials, int grid,
+                      cudaStream_t s) {
+  switch (cnt) {
+#define SPOCK_AA_CASE(C) \
+  case C: aa_update_cnt<S, C>(v, Tv, vp, Tvp, MR, D, n, ld, slot, partials, grid, s); break;
+    SPOCK_AA_CASE(1) SPOCK_AA_CASE(2) SPOCK_AA_CASE(3) SPOCK_AA_CASE(4) SPOCK_AA_CASE(5) SPOCK_AA_CASE(6)
+    SPOCK_AA_CASE(7) SPOCK_AA_CASE(8) SPOCK_AA_CASE(9) SPOCK_AA_CASE(10) SPOCK_AA_CASE(11) SPOCK_AA_CASE(12)
+    SPOCK_AA_CASE(13) SPOCK_AA_CASE(14) SPOCK_AA_CASE(15) SPOCK_AA_CASE(16)
+#undef SPOCK_AA_CASE
+    default: return;
+  }
+  SlotOrder o;
+  for (int j = 0; j < kMaxMemory; ++j) o.s[j] = order[j];
+  k_aa_solve<<<1, 256, 0, s>>>(st, partials, grid, slot, cnt, o);
+}
+
+template <typename S, int CNT>
 __global__ void __launch_bounds__(256) k_aa_direction(const SmState* __restrict__ st, const S* __restrict__ v,
                                                       const S* __restrict__ Tv, const S* __restrict__ D, int64_t n,
-                                                      int cnt, S* __restrict__ d, S* __restrict__ vt) {
-  S g[kMaxMemory];
+                                                      int64_t ld, S* __restrict__ d, S* __restrict__ vt) {
+  constexpr int NP = Pack<S>::N;
+  using PT = typename Pack<S>::T;
+  S g[CNT > 0 ? CNT : 1];
 #pragma unroll
-  for (int j = 0; j < kMaxMemory; ++j) g[j] = (j < cnt) ? (S)st->gamma[j] : S(0);
+  for (int j = 0; j < CNT; ++j) g[j] = (S)st->gamma[j];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const S vi = v[i];
-    S di = -(vi - Tv[i]);
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t npack = n / NP;
+  for (int64_t q = gt; q < npack; q += stride) {
+    PT a = ldp(v, q), b = ldp(Tv, q), dd;
 #pragma unroll
-    for (int j = 0; j < kMaxMemory; ++j)
-      if (j < cnt) di -= g[j] * D[(int64_t)j * n + i];
+    for (int t = 0; t < NP; ++t) pk<S>(dd, t) = pk<S>(b, t) - pk<S>(a, t);
+#pragma unroll
+    for (int j = 0; j < CNT; ++j) {
+      PT c = ldp(D + (int64_t)j * ld, q);
+#pragma unroll
+      for (int t = 0; t < NP; ++t) pk<S>(dd, t) -= g[j] * pk<S>(c, t);
+    }
+    PT w;
+#pragma unroll
+    for (int t = 0; t < NP; ++t) pk<S>(w, t) = pk<S>(a, t) + pk<S>(dd, t);
+    stp(d, q, dd);
+    stp(vt, q, w);
+  }
+  for (int64_t i = npack * NP + gt; i < n; i += stride) {
+    S di = Tv[i] - v[i];
+#pragma unroll
+    for (int j = 0; j < CNT; ++j) di -= g[j] * D[(int64_t)j * ld + i];
     d[i] = di;
-    vt[i] = vi + di;
+    vt[i] = v[i] + di;
   }
 }
 
@@ -287,7 +361,15 @@ __global__ void __launch_bounds__(256) k_ls_point(const SmState* __restrict__ st
                                                   const S* __restrict__ d, S* __restrict__ vt, int64_t n) {
   const S tau = (S)st->tau;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) vt[i] = v[i] + tau * d[i];
+  constexpr int NP = Pack<S>::N;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, npack = n / NP;
+  for (int64_t q = gt; q < npack; q += stride) {
+    typename Pack<S>::T a = ldp(v, q), b = ldp(d, q);
+#pragma unroll
+    for (int t = 0; t < NP; ++t) pk<S>(a, t) += tau * pk<S>(b, t);
+    stp(vt, q, a);
+  }
+  for (int64_t i = npack * NP + gt; i < n; i += stride) vt[i] = v[i] + tau * d[i];
 }
 
 template <typename S>
@@ -296,8 +378,15 @@ __global__ void __launch_bounds__(256) k_k2_point(const SmState* __restrict__ st
                                                   S* __restrict__ vn, int64_t n) {
   const S c = (S)st->coef;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-    vn[i] = v[i] - c * (vt[i] - Tvt[i]);
+  constexpr int NP = Pack<S>::N;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, npack = n / NP;
+  for (int64_t q = gt; q < npack; q += stride) {
+    typename Pack<S>::T a = ldp(v, q), b = ldp(vt, q), e = ldp(Tvt, q);
+#pragma unroll
+    for (int t = 0; t < NP; ++t) pk<S>(a, t) -= c * (pk<S>(b, t) - pk<S>(e, t));
+    stp(vn, q, a);
+  }
+  for (int64_t i = npack * NP + gt; i < n; i += stride) vn[i] = v[i] - c * (vt[i] - Tvt[i]);
 }
 
 template <typename S>
@@ -305,14 +394,29 @@ __global__ void __launch_bounds__(256) k_km_point(const SmState* __restrict__ st
                                                   const S* __restrict__ Tv, S* __restrict__ vn, int64_t n) {
   const S c = (S)st->lam;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-    vn[i] = v[i] - c * (v[i] - Tv[i]);
+  constexpr int NP = Pack<S>::N;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, npack = n / NP;
+  for (int64_t q = gt; q < npack; q += stride) {
+    typename Pack<S>::T a = ldp(v, q), b = ldp(Tv, q);
+#pragma unroll
+    for (int t = 0; t < NP; ++t) pk<S>(a, t) -= c * (pk<S>(a, t) - pk<S>(b, t));
+    stp(vn, q, a);
+  }
+  for (int64_t i = npack * NP + gt; i < n; i += stride) vn[i] = v[i] - c * (v[i] - Tv[i]);
 }
 
 template <typename S>
-void launch_aa_direction(const SmState* st, const S* v, const S* Tv, const S* D, int64_t n, int cnt, S* d, S* vt,
-                         int grid, cudaStream_t s) {
-  k_aa_direction<S><<<grid, 256, 0, s>>>(st, v, Tv, D, n, cnt, d, vt);
+void launch_aa_direction(const SmState* st, const S* v, const S* Tv, const S* D, int64_t n, int64_t ld, int cnt,
+                         S* d, S* vt, int grid, cudaStream_t s) {
+  switch (cnt) {
+#define SPOCK_DIR_CASE(C) \
+  case C: k_aa_direction<S, C><<<grid, 256, 0, s>>>(st, v, Tv, D, n, ld, d, vt); break;
+    SPOCK_DIR_CASE(0) SPOCK_DIR_CASE(1) SPOCK_DIR_CASE(2) SPOCK_DIR_CASE(3) SPOCK_DIR_CASE(4) SPOCK_DIR_CASE(5)
+    SPOCK_DIR_CASE(6) SPOCK_DIR_CASE(7) SPOCK_DIR_CASE(8) SPOCK_DIR_CASE(9) SPOCK_DIR_CASE(10) SPOCK_DIR_CASE(11)
+    SPOCK_DIR_CASE(12) SPOCK_DIR_CASE(13) SPOCK_DIR_CASE(14) SPOCK_DIR_CASE(15) SPOCK_DIR_CASE(16)
+#undef SPOCK_DIR_CASE
+    default: break;
+  }
 }
 template <typename S>
 void launch_ls_point(const SmState* st, const S* v, const S* d, S* vt, int64_t n, int grid, cudaStream_t s) {
@@ -329,10 +433,10 @@ void launch_km_point(const SmState* st, const S* v, const S* Tv, S* vn, int64_t 
 }
 
 #define SPOCK_INST(S)                                                                                         \
-  template void launch_aa_update<S>(SmState*, const S*, const S*, const S*, const S*, S*, S*, int64_t, int,  \
-                                    int, int*, double*, int, cudaStream_t);                                   \
-  template void launch_aa_direction<S>(const SmState*, const S*, const S*, const S*, int64_t, int, S*, S*,    \
-                                       int, cudaStream_t);                                                    \
+  template void launch_aa_update<S>(SmState*, const S*, const S*, const S*, const S*, S*, S*, int64_t,       \
+                                    int64_t, int, int, int*, double*, int, cudaStream_t);                     \
+  template void launch_aa_direction<S>(const SmState*, const S*, const S*, const S*, int64_t, int64_t, int,   \
+                                       S*, S*, int, cudaStream_t);                                            \
   template void launch_ls_point<S>(const SmState*, const S*, const S*, S*, int64_t, int, cudaStream_t);       \
   template void launch_k2_point<S>(const SmState*, const S*, const S*, const S*, S*, int64_t, int,            \
                                    cudaStream_t);                                                             \

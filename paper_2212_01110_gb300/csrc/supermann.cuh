@@ -37,14 +37,15 @@ void launch_sm_line_search(SmState* st, const double* stats, int32_t* trace, cud
 // Anderson update: writes column `slot` of M^R and of D = M^P - M^R from the
 // current (v, Tv) and previous (vp, Tvp) iterates, then the Gram row of the
 // new column and the right-hand side M^RT r, and solves for gamma (FP64).
+// Column j of M^R / D starts at j * ld (ld >= n, 256-byte aligned columns).
 template <typename S>
 void launch_aa_update(SmState* st, const S* v, const S* Tv, const S* vp, const S* Tvp, S* MR, S* D, int64_t n,
-                      int slot, int cnt, int newest_first_order[kMaxMemory], double* partials, int grid,
+                      int64_t ld, int slot, int cnt, int newest_first_order[kMaxMemory], double* partials, int grid,
                       cudaStream_t s);
 // d = -(v - Tv) - sum_j gamma_j D_j over the cnt stored columns; vt = v + d.
 template <typename S>
-void launch_aa_direction(const SmState* st, const S* v, const S* Tv, const S* D, int64_t n, int cnt, S* d, S* vt,
-                         int grid, cudaStream_t s);
+void launch_aa_direction(const SmState* st, const S* v, const S* Tv, const S* D, int64_t n, int64_t ld, int cnt,
+                         S* d, S* vt, int grid, cudaStream_t s);
 // vt = v + tau d (tau from the state).
 template <typename S>
 void launch_ls_point(const SmState* st, const S* v, const S* d, S* vt, int64_t n, int grid, cudaStream_t s);

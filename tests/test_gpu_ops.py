@@ -47,9 +47,10 @@ def test_prox_gconj(pair, alpha_scale):
     assert rel_err(out.cpu().numpy(), prox_gconj(eta, alpha, pair.op)) < RTOL
 
 
-@pytest.fixture(params=["tma", "direct"])
+@pytest.fixture(params=["auto", "grp", "tma", "direct"])
 def kernels(request, monkeypatch):
-    """Both Riccati kernel families: bulk-copy staged (default) and direct loads."""
+    """Every Riccati kernel family: the default per-pass choice, three warps
+    per chain, one warp per chain with bulk-copy staging, direct loads."""
     monkeypatch.setenv("SPOCK_RICCATI_KERNELS", request.param)
     return request.param
 
