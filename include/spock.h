@@ -89,6 +89,14 @@ typedef struct spock_settings {
                            (branch, backtracks), branch 0=K0 1=K1 2=K2 3=cap  (NULL) */
   int32_t profile;      /* nonzero: time the kernel groups of every T evaluation
                            with CUDA events on the solve's stream (info.t_*)  (0)    */
+  int32_t fp64_tail;    /* SPOCK_FP32 only: when the FP32 iteration meets the
+                           tolerance, certify it with one FP64 evaluation of T,
+                           and continue in FP64 (warm start, Anderson memory
+                           reset) until the FP64 residual meets it too; also
+                           taken when FP32 stagnates                       (1)    */
+  int32_t stall_window; /* FP32 stagnation: no halving of xi in this many
+                           iterations while xi <= 30 x tolerance hands over
+                           to FP64 (0 = never)                              (500)  */
 } spock_settings;
 
 /* Outcome of a solve. */
@@ -109,6 +117,9 @@ typedef struct spock_info {
      branching stages, [4] Riccati forward, chain region, [5] L and
      prox_{alpha g*} (dual update), [6] residual statistics */
   double t_group_ms[7];
+  int32_t fp64_iterations; /* SPOCK_FP32 with fp64_tail: iterations run in FP64 */
+  int32_t certified;       /* 1 if the returned pair's xi was computed in FP64 */
+  double xi_fp32;          /* xi reported by the FP32 iteration when it stopped */
 } spock_info;
 
 /* Fills *s with the defaults listed above.  Returns SPOCK_ERR_INVALID_ARG

@@ -336,6 +336,7 @@ int launch_fwd_chain_grp(const KP<S>& p, S* zo, cudaStream_t st);
 // the staged variant fits too few warps per SM (tma_chain_fits).
 // SPOCK_RICCATI_KERNELS forces one family everywhere (the tests cover each).
 enum ChainFamily { CF_AUTO = -1, CF_GRP = 0, CF_TMA = 1, CF_DIRECT = 2 };
+constexpr int kStagedMaxNodes = 2048;  // FP64 stages with more nodes use the direct kernels
 static int chain_family() {
   const char* e = getenv("SPOCK_RICCATI_KERNELS");
   if (!e || !e[0]) return CF_AUTO;
@@ -371,9 +372,14 @@ int riccati_passes_sl(const KP<S>& p, const std::vector<int32_t>& stage_begin,
     }
   }
   if (ev) cudaEventRecord(ev[0], st);
+  // Branching stages: the staged block-per-node kernels cut the latency of
+  // every stage in FP32 (measured); in FP64 a stage with many nodes runs
+  // better on the direct warp-per-node kernels, which keep far more warps
+  // resident (FP64 needs one per SM sub-partition).
+  auto staged = [&](int cnt) { return tma_stage && (sizeof(S) == 4 || cnt < kStagedMaxNodes); };
   for (int t = cs - 1; t >= 0; --t) {
     const int cnt = stage_begin[t + 1] - stage_begin[t];
-    if (tma_stage) {
+    if (staged(cnt)) {
       launches += launch_bwd_stage_tma<S, SL>(p, t, cnt, stage_maxch[t], st);
     } else {
       k_bwd_stage<S, SL><<<(cnt + kWarpsPerBlock - 1) / kWarpsPerBlock, 128, 0, st>>>(p, t);
@@ -383,7 +389,7 @@ int riccati_passes_sl(const KP<S>& p, const std::vector<int32_t>& stage_begin,
   if (ev) cudaEventRecord(ev[1], st);
   for (int t = 0; t < cs; ++t) {
     const int cnt = stage_begin[t + 1] - stage_begin[t];
-    if (tma_stage) {
+    if (staged(cnt)) {
       launches += launch_fwd_stage_tma<S, SL>(p, t, cnt, stage_maxch[t], zo, st);
     } else {
       k_fwd_stage<S, SL><<<(cnt + kWarpsPerBlock - 1) / kWarpsPerBlock, 128, 0, st>>>(p, t, zo);

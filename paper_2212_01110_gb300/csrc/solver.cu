@@ -355,9 +355,14 @@ static void eval_T(const Ctx& c, const S* v, S* Tv, const S* dir, double* stats)
 // ---------------------------------------------------------------------------
 // Algorithm 3 driver
 // ---------------------------------------------------------------------------
+// One run of Algorithm 3 in precision S.  tol_given > 0 replaces the
+// tolerance max(eps_abs, eps_rel xi_0) (FP64 continuation of an FP32 run);
+// stall_window > 0 stops with A_STALL when xi has not halved for that many
+// iterations.  *final_action receives the last decision.
 template <typename S>
 static int solve_impl(Problem& P, const double* x0_dev, const spock_settings& s, double* z_dev, double* eta_dev,
-                      int warm, spock_info* info, cudaStream_t st) {
+                      int warm, spock_info* info, cudaStream_t st, double tol_given = 0.0, int stall_window = 0,
+                      int* final_action_out = nullptr) {
   const int mem = std::max(0, std::min<int>(s.memory, kMaxMemory));
   Workspace* ws = get_ws_impl<S>(P, mem);
   const DevFactors<S>& f = factors<S>(P);
@@ -409,6 +414,8 @@ static int solve_impl(Problem& P, const double* x0_dev, const spock_settings& s,
   h.max_back = std::max(0, s.max_backtracks);
   h.mem = mem;
   h.record_trace = trace_dev != nullptr;
+  h.tol = tol_given;
+  h.stall_window = stall_window;
   sm_init_state(ws->st, h, st);
   ws->launches = 0;
   if (s.profile) ws->prof.start();
@@ -432,7 +439,7 @@ static int solve_impl(Problem& P, const double* x0_dev, const spock_settings& s,
     launch_sm_after_eval(ws->st, stats[cur], trace_dev, st);
     ws->launches += 1;
     const int act = read_action();
-    if (act == A_DONE || act == A_MAXIT || act == A_NUMERICAL) {
+    if (act == A_DONE || act == A_MAXIT || act == A_NUMERICAL || act == A_STALL) {
       final_action = act;
       break;
     }
@@ -516,8 +523,10 @@ static int solve_impl(Problem& P, const double* x0_dev, const spock_settings& s,
   if (ws->prof.on) ws->prof.harvest();
   float ms = 0.f;
   cudaEventElapsedTime(&ms, ws->e0, ws->e1);
+  if (final_action_out) *final_action_out = final_action;
   int status = final_action == A_DONE ? SPOCK_OK
-                                      : (final_action == A_MAXIT ? SPOCK_MAX_ITER : SPOCK_ERR_NUMERICAL);
+                                      : ((final_action == A_MAXIT || final_action == A_STALL) ? SPOCK_MAX_ITER
+                                                                                              : SPOCK_ERR_NUMERICAL);
   if (info) {
     info->status = status;
     info->iterations = fin.k;
@@ -534,6 +543,9 @@ static int solve_impl(Problem& P, const double* x0_dev, const spock_settings& s,
     info->n_launches = (int32_t)ws->launches;
     info->n_timed = ws->prof.on ? ws->prof.n : 0;
     for (int g = 0; g < Profiler::kGroups; ++g) info->t_group_ms[g] = ws->prof.on ? ws->prof.acc[g] : 0.0;
+    info->fp64_iterations = sizeof(S) == 8 ? fin.k : 0;
+    info->certified = sizeof(S) == 8 ? 1 : 0;
+    info->xi_fp32 = sizeof(S) == 8 ? NAN : fin.xi;
   }
   ws->prof.on = false;
   check_device_flag(P, st);
@@ -856,6 +868,9 @@ int spock_default_settings(spock_settings* s) {
   s->max_backtracks = 30;
   s->precision = SPOCK_FP64;
   s->trace = nullptr;
+  s->profile = 0;
+  s->fp64_tail = 1;
+  s->stall_window = 500;
   return SPOCK_OK;
 }
 
@@ -904,6 +919,48 @@ int spock_problem_info(const spock_problem* p, int64_t* n_z, int64_t* n_eta, dou
   return SPOCK_OK;
 }
 
+// FP32 iteration with FP64 certification and FP64 tail: the FP32 run stops
+// at its tolerance, its iteration cap, or stagnation; its result T32(v) (in
+// the FP64 output buffers) warm-starts an FP64 run with the same tolerance
+// (from the FP32 run's xi_0), whose first evaluation of T is the FP64
+// certificate -- zero FP64 iterations when the FP32 result already meets it.
+static int solve_mixed(Problem& P, const double* x0_dev, const spock_settings& s, double* z_dev, double* eta_dev,
+                       int warm, spock_info* info, cudaStream_t st) {
+  spock_info i32{};
+  int act32 = A_NONE;
+  int rc = solve_impl<float>(P, x0_dev, s, z_dev, eta_dev, warm, &i32, st, 0.0, s.fp64_tail ? s.stall_window : 0,
+                             &act32);
+  if (rc < 0 || !s.fp64_tail) {
+    if (info) *info = i32;
+    return rc;
+  }
+  spock_settings s64 = s;
+  s64.max_iter = std::max(0, s.max_iter - i32.iterations);
+  s64.trace = nullptr;
+  const double tol = std::max(s.eps_abs, s.eps_rel * i32.xi0);
+  spock_info i64{};
+  rc = solve_impl<double>(P, x0_dev, s64, z_dev, eta_dev, 1, &i64, st, tol, 0, nullptr);
+  if (info) {
+    *info = i64;
+    info->iterations = i32.iterations + i64.iterations;
+    info->n_T = i32.n_T + i64.n_T;
+    info->n_K0 = i32.n_K0 + i64.n_K0;
+    info->n_K1 = i32.n_K1 + i64.n_K1;
+    info->n_K2 = i32.n_K2 + i64.n_K2;
+    info->n_cap = i32.n_cap + i64.n_cap;
+    info->n_backtracks = i32.n_backtracks + i64.n_backtracks;
+    info->xi0 = i32.xi0;
+    info->solve_ms = i32.solve_ms + i64.solve_ms;
+    info->n_launches = i32.n_launches + i64.n_launches;
+    info->n_timed = i32.n_timed + i64.n_timed;
+    for (int g = 0; g < 7; ++g) info->t_group_ms[g] = i32.t_group_ms[g] + i64.t_group_ms[g];
+    info->fp64_iterations = i64.iterations;
+    info->certified = 1;
+    info->xi_fp32 = i32.xi;
+  }
+  return rc;
+}
+
 static int solve_dev_impl(Problem* P, const double* x0_dev, const spock_settings* settings, double* z_dev,
                           double* eta_dev, int32_t warm, spock_info* info, cudaStream_t st) {
   spock_settings s;
@@ -916,7 +973,7 @@ static int solve_dev_impl(Problem* P, const double* x0_dev, const spock_settings
   if (s.alpha > 0 && s.alpha * P->normL >= 1.0) return fail(SPOCK_ERR_INVALID_ARG, "alpha ||L|| must be < 1");
   CUDA_TRY(cudaSetDevice(P->device));
   if (s.precision == SPOCK_FP64) return solve_impl<double>(*P, x0_dev, s, z_dev, eta_dev, warm, info, st);
-  if (s.precision == SPOCK_FP32) return solve_impl<float>(*P, x0_dev, s, z_dev, eta_dev, warm, info, st);
+  if (s.precision == SPOCK_FP32) return solve_mixed(*P, x0_dev, s, z_dev, eta_dev, warm, info, st);
   return fail(SPOCK_ERR_INVALID_ARG, "unknown precision");
 }
 

@@ -37,17 +37,27 @@ __global__ void k_sm_after_eval(SmState* st, const double* __restrict__ stats, i
     st->zeta = omega;
     st->omega_safe = omega;
     st->xi0 = xi;
-    st->tol = fmax(st->eps_abs, st->eps_rel * xi);
+    if (!(st->tol > 0.0)) st->tol = fmax(st->eps_abs, st->eps_rel * xi);  // tol > 0: given by the host
+    st->best_xi = xi;
+    st->best_k = 0;
     st->initialized = 1;
   }
   st->omega = omega;
   st->xi = xi;
+  if (xi < 0.5 * st->best_xi) {
+    st->best_xi = xi;
+    st->best_k = st->k;
+  }
   if (!isfinite(om2) || !isfinite(xi)) {
     st->action = A_NUMERICAL;
   } else if (xi <= st->tol) {
     st->action = A_DONE;
   } else if (st->k >= st->max_iter) {
     st->action = A_MAXIT;
+  } else if (st->stall_window > 0 && st->k - st->best_k > st->stall_window && xi <= 30.0 * st->tol) {
+    // no halving of xi for stall_window iterations close to the tolerance:
+    // the FP32 operator's rounding floor, hand over to FP64
+    st->action = A_STALL;
   } else if (omega <= st->c0 * st->zeta) {
     st->action = A_K0;  // blind step v + d; zeta_{k+1} = omega_k
     st->zeta = omega;

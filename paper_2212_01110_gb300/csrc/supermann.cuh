@@ -11,7 +11,7 @@ namespace spock {
 
 enum SmAction : int32_t {
   A_NONE = 0, A_DONE = 1, A_MAXIT = 2, A_K0 = 3, A_LS = 4,
-  A_K1 = 5, A_K2 = 6, A_CAP = 7, A_RETRY = 8, A_NUMERICAL = 9
+  A_K1 = 5, A_K2 = 6, A_CAP = 7, A_RETRY = 8, A_NUMERICAL = 9, A_STALL = 10
 };
 
 struct SmState {
@@ -22,6 +22,9 @@ struct SmState {
   double zeta, omega_safe, omega, xi, xi0, tol, tau, omega_t, rho, coef;
   int32_t k, nb, action, initialized;
   int32_t n_k0, n_k1, n_k2, n_cap, n_back, pad_;
+  // stagnation test (FP32 mode): best xi so far and the iteration it was seen
+  double best_xi;
+  int32_t best_k, stall_window;
   // Anderson: Gram of the stored M^R columns (slot-indexed), right-hand side,
   // least-squares coefficients
   double G[kMaxMemory * kMaxMemory];

@@ -40,7 +40,8 @@ class Settings(C.Structure):
                 ("memory", C.c_int32), ("c0", C.c_double), ("c1", C.c_double), ("c2", C.c_double),
                 ("beta", C.c_double), ("sigma", C.c_double), ("lambda_", C.c_double),
                 ("rho_coef", C.c_double), ("max_iter", C.c_int32), ("max_backtracks", C.c_int32),
-                ("precision", C.c_int32), ("trace", C.POINTER(C.c_int32)), ("profile", C.c_int32)]
+                ("precision", C.c_int32), ("trace", C.POINTER(C.c_int32)), ("profile", C.c_int32),
+                ("fp64_tail", C.c_int32), ("stall_window", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -48,7 +49,8 @@ class Info(C.Structure):
                 ("n_K0", C.c_int32), ("n_K1", C.c_int32), ("n_K2", C.c_int32), ("n_cap", C.c_int32),
                 ("n_backtracks", C.c_int32), ("xi", C.c_double), ("xi0", C.c_double),
                 ("alpha", C.c_double), ("solve_ms", C.c_double), ("n_launches", C.c_int32),
-                ("n_timed", C.c_int32), ("t_group_ms", C.c_double * 7)]
+                ("n_timed", C.c_int32), ("t_group_ms", C.c_double * 7), ("fp64_iterations", C.c_int32),
+                ("certified", C.c_int32), ("xi_fp32", C.c_double)]
 
     GROUPS = ("prep", "bwd_chain", "bwd_stages", "fwd_stages", "fwd_chain", "dual", "stats")
 
