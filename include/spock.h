@@ -260,6 +260,30 @@ int spock_T_dev(spock_problem* p, const double* x0_dev, double alpha, const doub
 int spock_prox_f_noalloc_dev(spock_problem* p, const double* x0_dev, double alpha, const double* z,
                              double* z_out, void* stream);
 
+/*
+ * spock_grad_dev -- gradient of the optimal cost V* = s^0 with respect to
+ * the problem data, from a converged pair (z, eta) = T(v*) (device buffers,
+ * FP64, layout as above), e.g. the output of spock_solve_dev.
+ * Method: at the saddle point of the Lagrangian
+ *   s^0 + lambda^T (G z_1 - h) + mu^T M z_2 + <eta, L z> - g*(eta)
+ * of the splitting (Sec. "Operator splitting": G z_1 = h the dynamics of S1,
+ * M z_2 = 0 the kernel of S2, g* the conjugate of g of Eq. (g)), the
+ * multipliers of the dynamics solve G^T lambda = -(L* eta)_{z_1} (one tree
+ * recursion from the leaves on the stored [Abar | B] blocks) and the
+ * derivative of V* in each datum is the Lagrangian's partial derivative
+ * (envelope theorem):
+ *   g_x0 = -lambda^0, g_A[c] = -lambda^c x^anc(c)T, g_B[c] = -lambda^c u^anc(c)T,
+ *   g_Q[c][k] = eta_{c,Qx,k} x^anc(c)_k / (2 sqrt Q^c_kk), g_R likewise,
+ *   g_QN[j][k] = eta_{j,QNx,k} x^j_k / (2 sqrt QN^j_kk).
+ * Outputs (device, FP64, caller's node numbering; any may be NULL):
+ *   g_x0 [nx], g_A [n][nx][nx], g_B [n][nx][nu], g_Q [n][nx], g_R [n][nu],
+ *   g_QN [n][nx]; entries of nodes where a quantity does not exist are 0.
+ * precision: SPOCK_FP64 or SPOCK_FP32 (arithmetic and factors of that
+ * precision; inputs rounded).  Accuracy follows the accuracy of (z, eta).
+ */
+int spock_grad_dev(spock_problem* p, const double* z, const double* eta, int32_t precision, double* g_x0,
+                   double* g_A, double* g_B, double* g_Q, double* g_R, double* g_QN, void* stream);
+
 /* Frees a handle returned by any *_create call; NULL is a no-op. */
 void spock_free(void* handle);
 

@@ -35,7 +35,7 @@ struct alignas(16) NodeDesc {
   int64_t enl, enr, elf;           // nonleaf / nonroot / leaf block of k in eta
   int64_t zxp, zup;                // x and u of the parent in z
   int64_t es;                      // eta row holding s^k: enl + 2m + 1 (nonleaf) or elf + 2 nx (leaf)
-  int32_t par, m, c0, pad0;        // parent, number of children, first child
+  int32_t par, m, c0, user;        // parent, number of children, first child, caller's node id
   int64_t pad1[2];
 };
 static_assert(sizeof(NodeDesc) == 128, "NodeDesc must be 128 bytes");

@@ -587,6 +587,39 @@ static int cp_impl(Problem& P, const double* x0_dev, int k, double alpha, double
   return SPOCK_OK;
 }
 
+template <typename S>
+int launch_gradient(const KP<S>& p, const std::vector<int32_t>& stage_begin, const S* z, const S* eta, const S* w,
+                    S* lam, double* gx0, double* gA, double* gB, double* gQ, double* gR, double* gQN, int max_blocks,
+                    cudaStream_t st);
+
+template <typename S>
+static int grad_impl(Problem& P, const double* z, const double* eta, double* gx0, double* gA, double* gB,
+                     double* gQ, double* gR, double* gQN, cudaStream_t st) {
+  Workspace* ws = get_ws_impl<S>(P, 0);
+  const DevFactors<S>& f = factors<S>(P);
+  const int64_t nz = P.off.n_z, ne = P.off.n_eta;
+  const size_t n = (size_t)P.tree.n;
+  S* zs = (S*)ws->v[0];
+  S* es = zs + nz;
+  S* w = (S*)ws->Tv[0];
+  convert<S, double>(z, zs, nz, st);
+  convert<S, double>(eta, es, ne, st);
+  KP<S> kp = make_kp<S>(P, default_alpha(P, 0.0), P.idx.stage_begin);
+  const int maxb = sm_count() * 16;
+  launch_primal<S>(kp, PM_APPLY_LT_, es, nullptr, nullptr, nullptr, w, nullptr, nullptr,
+                   std::min((P.tree.n + 3) / 4, maxb), st);  // w = L* eta
+  const int nx = P.nx, nu = P.nu;
+  if (gA) CUDA_TRY(cudaMemsetAsync(gA, 0, sizeof(double) * n * nx * nx, st));
+  if (gB) CUDA_TRY(cudaMemsetAsync(gB, 0, sizeof(double) * n * nx * nu, st));
+  if (gQ) CUDA_TRY(cudaMemsetAsync(gQ, 0, sizeof(double) * n * nx, st));
+  if (gR) CUDA_TRY(cudaMemsetAsync(gR, 0, sizeof(double) * n * nu, st));
+  if (gQN) CUDA_TRY(cudaMemsetAsync(gQN, 0, sizeof(double) * n * nx, st));
+  launch_gradient<S>(kp, P.tree.stage_begin, zs, es, w, f.q, gx0, gA, gB, gQ, gR, gQN, maxb, st);
+  check_launch();
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return SPOCK_OK;
+}
+
 // ---------------------------------------------------------------------------
 // problem creation
 // ---------------------------------------------------------------------------
@@ -819,6 +852,7 @@ static int problem_create(const Tree& tree, int32_t nx, int32_t nu, const double
         q.par = t.parent[k];
         q.m = t.ch_count[k];
         q.c0 = t.ch_begin[k];
+        q.user = t.user_of[k];
         q.zxp = k > 0 ? o.zx[t.parent[k]] : -1;
         q.zup = k > 0 ? o.zu[t.parent[k]] : -1;
         q.es = k < nl ? o.enl[k] + 2 * t.ch_count[k] + 1 : o.elf[k] + 2 * nx;
@@ -1175,6 +1209,19 @@ int spock_T_dev(spock_problem* p, const double* x0_dev, double alpha, const doub
     CUDA_TRY(cudaStreamSynchronize(st));
     check_device_flag(*P, st);
     return SPOCK_OK;
+  });
+}
+
+int spock_grad_dev(spock_problem* p, const double* z, const double* eta, int32_t precision, double* g_x0,
+                   double* g_A, double* g_B, double* g_Q, double* g_R, double* g_QN, void* stream) {
+  return guarded([&]() -> int {
+    Problem* P = as_problem(p);
+    if (!P || !z || !eta) return fail(SPOCK_ERR_INVALID_ARG, "NULL argument");
+    CUDA_TRY(cudaSetDevice(P->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == SPOCK_FP64) return grad_impl<double>(*P, z, eta, g_x0, g_A, g_B, g_Q, g_R, g_QN, st);
+    if (precision == SPOCK_FP32) return grad_impl<float>(*P, z, eta, g_x0, g_A, g_B, g_Q, g_R, g_QN, st);
+    return fail(SPOCK_ERR_INVALID_ARG, "unknown precision");
   });
 }
 

@@ -81,6 +81,7 @@ _sig = {
     "spock_prox_f_noalloc_dev": ([_P, _P, C.c_double, _P, _P, _P], C.c_int),
     "spock_prox_gconj_dev": ([_P, C.c_double, _P, _P, _P], C.c_int),
     "spock_T_dev": ([_P, _P, C.c_double, _P, _P, _P, _P, _P], C.c_int),
+    "spock_grad_dev": ([_P, _P, _P, C.c_int32, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "spock_free": ([_P], None),
     "spock_last_error": ([], C.c_char_p),
 }
@@ -222,6 +223,17 @@ def spock_T_dev(problem, x0, alpha, z, eta, z_out, eta_out, stream=None):
                             _stream(stream)))
 
 
+def spock_grad_dev(problem, z, eta, precision, g_x0=None, g_A=None, g_B=None, g_Q=None, g_R=None, g_QN=None,
+                   stream=None):
+    """Gradient of the optimal cost from a converged (z, eta); outputs are
+    float64 CUDA tensors (or None) in the caller's node numbering."""
+    import torch
+    ptr = lambda t: None if t is None else _tptr(t, dtype=torch.float64)
+    _check(_lib.spock_grad_dev(problem, _tptr(z, dtype=torch.float64), _tptr(eta, dtype=torch.float64),
+                               int(precision), ptr(g_x0), ptr(g_A), ptr(g_B), ptr(g_Q), ptr(g_R), ptr(g_QN),
+                               _stream(stream)))
+
+
 def spock_free(handle):
     _lib.spock_free(handle)
 
@@ -246,6 +258,7 @@ class Problem:
             spock_free(self.tree)
             raise
         self.nx, self.nu = int(d["nx"]), int(d["nu"])
+        self.n_nodes = len(d["anc"])
         self.n_z, self.n_eta, self.norm_L, self.factor_seconds = spock_problem_info(self.handle)
 
     @property
