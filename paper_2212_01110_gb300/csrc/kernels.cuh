@@ -51,6 +51,7 @@ struct KP {
   int32_t xs, us;                     // xbar / q, ubar / d
   int32_t gstride, nbstride, ktstride;  // Gb and Gf, NB, Kt
   int32_t* err;                       // pipeline timeout flag (device)
+  const int32_t* skip;                // nonzero: the solve has finished, kernels return at once
   const int32_t* __restrict__ parent;
   const int32_t* __restrict__ ch_begin;
   const int32_t* __restrict__ ch_count;
@@ -82,6 +83,16 @@ struct KP {
   S* __restrict__ d;
   const S* __restrict__ x0;
 };
+
+// Records `ev` on `st`; while `st` is being captured into a graph the record
+// becomes an event-record node (timing of every replay), otherwise a plain
+// record.
+inline void record_event(cudaEvent_t ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+  else cudaEventRecord(ev, st);
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

@@ -23,6 +23,7 @@ enum PrimalMode : int { PM_APPLY_LT = 0, PM_STATS = 1 };
 template <typename S>
 __global__ void __launch_bounds__(128) k_prep(KP<S> p, const S* __restrict__ z,
                                               const S* __restrict__ eta, S* __restrict__ zo) {
+  if (p.skip && *p.skip) return;
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -168,6 +169,7 @@ template <typename S, int MODE, bool STATS, bool DIR>
 __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, const S* __restrict__ zp,
                                               const S* __restrict__ eta, S* __restrict__ out,
                                               const S* __restrict__ dir, double* __restrict__ partials) {
+  if (p.skip && *p.skip) return;
   __shared__ S wbuf[kWarpsPerBlock][kVecPad];
   __shared__ S lbuf[kWarpsPerBlock][kVecPad];   // L r_z of SOC rows (statistics)
   __shared__ S dbuf[kWarpsPerBlock][kVecPad];   // L d_z of SOC rows
@@ -320,6 +322,7 @@ __global__ void __launch_bounds__(128) k_primal(KP<S> p, const S* __restrict__ e
                                                 const S* __restrict__ z, const S* __restrict__ zp,
                                                 S* __restrict__ zout, const S* __restrict__ dir,
                                                 double* __restrict__ partials) {
+  if (p.skip && *p.skip) return;
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -380,7 +383,8 @@ __global__ void __launch_bounds__(128) k_primal(KP<S> p, const S* __restrict__ e
 // Sums (maxima for xi) of the per-block partial statistics of the dual and
 // primal kernels; one block, fixed order (deterministic).
 __global__ void k_reduce_stats(const double* __restrict__ pd, int nd, const double* __restrict__ pp, int np,
-                               double* __restrict__ out) {
+                               double* __restrict__ out, const int32_t* __restrict__ skip) {
+  if (skip && *skip) return;
   __shared__ double red[8][32];
   const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;  // 8 warps, one per statistic
   const bool mx = (i == ST_XIP || i == ST_XID);
@@ -434,8 +438,9 @@ void launch_primal(const KP<S>& p, int mode, const S* eta, const S* etap, const 
   }
 }
 
-void launch_reduce_stats(const double* pd, int nd, const double* pp, int np, double* out, cudaStream_t st) {
-  k_reduce_stats<<<1, 256, 0, st>>>(pd, nd, pp, np, out);
+void launch_reduce_stats(const double* pd, int nd, const double* pp, int np, double* out, cudaStream_t st,
+                         const int32_t* skip) {
+  k_reduce_stats<<<1, 256, 0, st>>>(pd, nd, pp, np, out, skip);
 }
 
 template void launch_prep<double>(const KP<double>&, const double*, const double*, double*, int, cudaStream_t);

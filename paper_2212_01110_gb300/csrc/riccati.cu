@@ -160,6 +160,7 @@ __device__ __forceinline__ void child_fwd(const S* __restrict__ Gf, const S* w, 
 // ---------------------------------------------------------------------------
 template <typename S, int SL>
 __global__ void __launch_bounds__(128) k_bwd_chain(KP<S> p) {
+  if (p.skip && *p.skip) return;
   SPOCK_WARP_VECS(S)
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -190,6 +191,7 @@ __global__ void __launch_bounds__(128) k_bwd_chain(KP<S> p) {
 // ---------------------------------------------------------------------------
 template <typename S, int SL>
 __global__ void __launch_bounds__(128) k_bwd_stage(KP<S> p, int t) {
+  if (p.skip && *p.skip) return;
   SPOCK_WARP_VECS(S)
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -224,6 +226,7 @@ __global__ void __launch_bounds__(128) k_bwd_stage(KP<S> p, int t) {
 // ---------------------------------------------------------------------------
 template <typename S, int SL>
 __global__ void __launch_bounds__(128) k_fwd_stage(KP<S> p, int t, S* __restrict__ zo) {
+  if (p.skip && *p.skip) return;
   SPOCK_WARP_VECS(S)
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -264,6 +267,7 @@ __global__ void __launch_bounds__(128) k_fwd_stage(KP<S> p, int t, S* __restrict
 // ---------------------------------------------------------------------------
 template <typename S, int SL>
 __global__ void __launch_bounds__(128) k_fwd_chain(KP<S> p, S* __restrict__ zo) {
+  if (p.skip && *p.skip) return;
   SPOCK_WARP_VECS(S)
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -371,7 +375,7 @@ int riccati_passes_sl(const KP<S>& p, const std::vector<int32_t>& stage_begin,
       ++launches;
     }
   }
-  if (ev) cudaEventRecord(ev[0], st);
+  if (ev) record_event(ev[0], st);
   // Branching stages: the staged block-per-node kernels cut the latency of
   // every stage in FP32 (measured); in FP64 a stage with many nodes runs
   // better on the direct warp-per-node kernels, which keep far more warps
@@ -386,7 +390,7 @@ int riccati_passes_sl(const KP<S>& p, const std::vector<int32_t>& stage_begin,
       ++launches;
     }
   }
-  if (ev) cudaEventRecord(ev[1], st);
+  if (ev) record_event(ev[1], st);
   for (int t = 0; t < cs; ++t) {
     const int cnt = stage_begin[t + 1] - stage_begin[t];
     if (staged(cnt)) {
@@ -396,7 +400,7 @@ int riccati_passes_sl(const KP<S>& p, const std::vector<int32_t>& stage_begin,
       ++launches;
     }
   }
-  if (ev) cudaEventRecord(ev[2], st);
+  if (ev) record_event(ev[2], st);
   if (p.n_chains > 0 && cs < p.N) {
     if (fwd_grp) {
       launches += launch_fwd_chain_grp<S>(p, zo, st);

@@ -65,6 +65,7 @@ __device__ __forceinline__ bool grp_wait(uint64_t* bar, uint32_t parity, int* vo
 
 template <typename S, int SLG>
 __global__ void __launch_bounds__(kGrpThreads* kMaxGroups) k_bwd_chain_grp(KP<S> p) {
+  if (p.skip && *p.skip) return;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bars[kMaxGroups][2];
   __shared__ int votes[kMaxGroups][4];
@@ -204,6 +205,7 @@ __global__ void __launch_bounds__(kGrpThreads* kMaxGroups) k_bwd_chain_grp(KP<S>
 
 template <typename S, int SLG>
 __global__ void __launch_bounds__(kGrpThreads* kMaxGroups) k_fwd_chain_grp(KP<S> p, S* __restrict__ zo) {
+  if (p.skip && *p.skip) return;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bars[kMaxGroups][2];
   __shared__ int votes[kMaxGroups][4];

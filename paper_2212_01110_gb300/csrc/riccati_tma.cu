@@ -165,6 +165,7 @@ __host__ __device__ inline ChainLayout<S> chain_layout_fwd(const KP<S>& p) {
 
 template <typename S, int SL>
 __global__ void __launch_bounds__(32 * kMaxChainWarps) k_bwd_chain_tma(KP<S> p) {
+  if (p.skip && *p.skip) return;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bars[kMaxChainWarps][2];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
@@ -242,6 +243,7 @@ __global__ void __launch_bounds__(32 * kMaxChainWarps) k_bwd_chain_tma(KP<S> p) 
 
 template <typename S, int SL>
 __global__ void __launch_bounds__(32 * kMaxChainWarps) k_fwd_chain_tma(KP<S> p, S* __restrict__ zo) {
+  if (p.skip && *p.skip) return;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bars[kMaxChainWarps][2];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
@@ -340,6 +342,7 @@ __host__ __device__ inline uint32_t stage_smem_fwd(const KP<S>& p, int nwarps) {
 
 template <typename S, int SL>
 __global__ void __launch_bounds__(32 * kMaxStageWarps) k_bwd_stage_tma(KP<S> p, int t) {
+  if (p.skip && *p.skip) return;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bars[kMaxStageWarps + 1];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5, NW = blockDim.x >> 5;
@@ -423,6 +426,7 @@ __global__ void __launch_bounds__(32 * kMaxStageWarps) k_bwd_stage_tma(KP<S> p, 
 
 template <typename S, int SL>
 __global__ void __launch_bounds__(32 * kMaxStageWarps) k_fwd_stage_tma(KP<S> p, int t, S* __restrict__ zo) {
+  if (p.skip && *p.skip) return;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bars[kMaxStageWarps + 1];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5, NW = blockDim.x >> 5;

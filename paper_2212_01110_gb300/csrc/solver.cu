@@ -27,7 +27,8 @@ void launch_dual(const KP<S>& p, int mode, bool stats, const S* z, const S* zp, 
 template <typename S>
 void launch_primal(const KP<S>& p, int mode, const S* eta, const S* etap, const S* z, const S* zp, S* zout,
                    const S* dir, double* partials, int grid, cudaStream_t st);
-void launch_reduce_stats(const double* pd, int nd, const double* pp, int np, double* out, cudaStream_t st);
+void launch_reduce_stats(const double* pd, int nd, const double* pp, int np, double* out, cudaStream_t st,
+                         const int32_t* skip = nullptr);
 template <typename S>
 int launch_riccati(const KP<S>& p, const std::vector<int32_t>& stage_begin, const std::vector<int32_t>& stage_maxch,
                    S* zo, cudaStream_t st, cudaEvent_t* ev);
@@ -113,6 +114,11 @@ struct Profiler {
     if (used == kSlots) harvest();
     return &ev[(size_t)(used++) * (kGroups + 1)];
   }
+  // Graph replays: slots 0..k-1 were recorded by the rounds that ran.
+  void harvest_first(int k) {
+    used = std::min(k, used);
+    harvest();
+  }
   void harvest() {
     for (int s = 0; s < used; ++s) {
       cudaEvent_t* e = &ev[(size_t)s * (kGroups + 1)];
@@ -154,8 +160,17 @@ struct Workspace {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   Profiler prof;
   int64_t launches = 0;
+  // device-driven rounds: internal stream, cached graph of kRounds rounds
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  double g_alpha = 0.0;
+  int g_trace = -1, g_launches_per_round = 0;
+  int32_t* h_done = nullptr;  // pinned
   std::vector<void*> allocs;
   ~Workspace() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (stream) cudaStreamDestroy(stream);
+    if (h_done) cudaFreeHost(h_done);
     for (void* p : allocs) cudaFree(p);
     if (h_action) cudaFreeHost(h_action);
     if (e0) cudaEventDestroy(e0);
@@ -221,6 +236,8 @@ static Workspace* get_ws_impl(Problem& P, int mem) {
     ws->paa = (double*)ws->alloc(sizeof(double) * 2 * kMaxMemory * ws->grid_v);
     ws->st = (SmState*)ws->alloc(sizeof(SmState));
     CUDA_TRY(cudaMallocHost(&ws->h_action, sizeof(int32_t) * 4));
+    CUDA_TRY(cudaMallocHost(&ws->h_done, sizeof(int32_t) * 4));
+    CUDA_TRY(cudaStreamCreateWithFlags(&ws->stream, cudaStreamNonBlocking));
     CUDA_TRY(cudaEventCreate(&ws->e0));
     CUDA_TRY(cudaEventCreate(&ws->e1));
   } catch (...) {
@@ -295,6 +312,7 @@ static KP<S> make_kp(const Problem& P, double alpha, const int32_t* stage_begin_
   k.nbstride = f.nbstride;
   k.ktstride = f.ktstride;
   k.err = P.err;
+  k.skip = nullptr;
   return k;
 }
 
@@ -327,27 +345,28 @@ struct Ctx {
 };
 
 template <typename S>
-static void eval_T(const Ctx& c, const S* v, S* Tv, const S* dir, double* stats) {
+static void eval_T(const Ctx& c, const S* v, S* Tv, const S* dir, double* stats, const int32_t* skip = nullptr) {
   Problem& P = *c.P;
   Workspace* ws = c.ws;
   KP<S> kp = make_kp<S>(P, c.alpha, c.stage_dev);
+  kp.skip = skip;
   const int64_t nz = P.off.n_z;
   const int maxb = sm_count() * 16;
   cudaEvent_t* ev = (ws && ws->prof.on) ? ws->prof.slot() : nullptr;
-  if (ev) cudaEventRecord(ev[0], c.st);
+  if (ev) record_event(ev[0], c.st);
   launch_prep<S>(kp, v, v + nz, Tv, maxb, c.st);
-  if (ev) cudaEventRecord(ev[1], c.st);
+  if (ev) record_event(ev[1], c.st);
   int launches = 2 + launch_riccati<S>(kp, P.tree.stage_begin, P.tree.stage_maxch, Tv, c.st, ev ? ev + 2 : nullptr);
-  if (ev) cudaEventRecord(ev[5], c.st);
+  if (ev) record_event(ev[5], c.st);
   launch_dual<S>(kp, DM_DUAL_, stats != nullptr, v, Tv, v + nz, Tv + nz, dir, ws ? ws->pd : nullptr,
                  ws ? ws->grid_d : std::min((P.tree.n + 3) / 4, maxb), c.st);
-  if (ev) cudaEventRecord(ev[6], c.st);
+  if (ev) record_event(ev[6], c.st);
   if (stats) {
     launch_primal<S>(kp, PM_STATS_, v + nz, Tv + nz, v, Tv, nullptr, dir, ws->pp, ws->grid_p, c.st);
-    launch_reduce_stats(ws->pd, ws->grid_d, ws->pp, ws->grid_p, stats, c.st);
+    launch_reduce_stats(ws->pd, ws->grid_d, ws->pp, ws->grid_p, stats, c.st, skip);
     launches += 2;
   }
-  if (ev) cudaEventRecord(ev[7], c.st);
+  if (ev) record_event(ev[7], c.st);
   if (ws) ws->launches += launches;
   check_launch();
 }
@@ -360,9 +379,9 @@ static void eval_T(const Ctx& c, const S* v, S* Tv, const S* dir, double* stats)
 // stall_window > 0 stops with A_STALL when xi has not halved for that many
 // iterations.  *final_action receives the last decision.
 template <typename S>
-static int solve_impl(Problem& P, const double* x0_dev, const spock_settings& s, double* z_dev, double* eta_dev,
-                      int warm, spock_info* info, cudaStream_t st, double tol_given = 0.0, int stall_window = 0,
-                      int* final_action_out = nullptr) {
+static int solve_host(Problem& P, const double* x0_dev, const spock_settings& s, double* z_dev, double* eta_dev,
+                      int warm, spock_info* info, cudaStream_t st, double tol_given, int stall_window,
+                      int* final_action_out) {
   const int mem = std::max(0, std::min<int>(s.memory, kMaxMemory));
   Workspace* ws = get_ws_impl<S>(P, mem);
   const DevFactors<S>& f = factors<S>(P);
@@ -551,6 +570,190 @@ static int solve_impl(Problem& P, const double* x0_dev, const spock_settings& s,
   check_device_flag(P, st);
   if (status == SPOCK_ERR_NUMERICAL) return fail(status, "non-finite residual during the iteration");
   return status;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 3, device-driven: fixed rounds replayed from a CUDA graph
+// ---------------------------------------------------------------------------
+constexpr int kRounds = 8;  // rounds per graph launch (one host check per launch)
+
+template <typename S>
+static int solve_graph(Problem& P, const double* x0_dev, const spock_settings& s, double* z_dev, double* eta_dev,
+                       int warm, spock_info* info, cudaStream_t user_st, double tol_given, int stall_window,
+                       int* final_action_out) {
+  const int mem = std::max(0, std::min<int>(s.memory, kMaxMemory));
+  Workspace* ws = get_ws_impl<S>(P, mem);
+  const DevFactors<S>& f = factors<S>(P);
+  const int64_t nz = P.off.n_z, nv = ws->n_v;
+  cudaStream_t st = ws->stream;
+  CUDA_TRY(cudaStreamSynchronize(user_st));  // inputs produced on the caller's stream
+  const double alpha = default_alpha(P, s.alpha);
+  Ctx c{&P, ws, alpha, st, P.idx.stage_begin};
+  S* V = (S*)ws->v[0];
+  S* TV = (S*)ws->Tv[0];
+  S* Vp = (S*)ws->v[1];
+  S* TVp = (S*)ws->Tv[1];
+  S* Vt = (S*)ws->v[2];
+  S* TVt = (S*)ws->Tv[2];
+  S* d = (S*)ws->d;
+  S* MR = (S*)ws->MR;
+  S* Dm = (S*)ws->D;
+  double* stats_t = ws->stats;
+  convert<S, double>(x0_dev, f.x0, P.nx, st);
+  if (warm) {
+    convert<S, double>(z_dev, Vt, nz, st);
+    convert<S, double>(eta_dev, Vt + nz, P.off.n_eta, st);
+  } else {
+    CUDA_TRY(cudaMemsetAsync(Vt, 0, sizeof(S) * nv, st));
+  }
+  CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(S) * nv, st));
+  const int max_iter = std::max(0, s.max_iter);
+  int32_t* trace_dev = nullptr;
+  if (s.trace && max_iter > 0) {
+    if (ws->trace_cap < max_iter) {
+      ws->trace = (int32_t*)ws->alloc(sizeof(int32_t) * 2 * (size_t)max_iter);
+      ws->trace_cap = max_iter;
+      if (ws->gexec) {
+        cudaGraphExecDestroy(ws->gexec);
+        ws->gexec = nullptr;
+      }
+    }
+    trace_dev = ws->trace;
+    CUDA_TRY(cudaMemsetAsync(trace_dev, 0xff, sizeof(int32_t) * 2 * (size_t)max_iter, st));
+  }
+  SmState h{};
+  h.alpha = alpha;
+  h.eps_abs = s.eps_abs;
+  h.eps_rel = s.eps_rel;
+  h.c0 = s.c0;
+  h.c1 = s.c1;
+  h.c2 = s.c2;
+  h.beta = s.beta;
+  h.sigma = s.sigma;
+  h.lam = s.lambda;
+  h.rho_coef = s.rho_coef;
+  h.max_iter = max_iter;
+  h.max_back = std::max(0, s.max_backtracks);
+  h.mem = mem;
+  h.record_trace = trace_dev != nullptr;
+  h.tol = tol_given;
+  h.stall_window = stall_window;
+  h.pending = P_INIT;
+  h.n_T = 1;
+  sm_init_state(ws->st, h, st);
+  const int32_t* skip = &ws->st->done;
+  // the graph of kRounds rounds (captured once per workspace and settings)
+  const int grid_v = ws->grid_v;
+  auto round = [&](cudaStream_t s2) {
+    Ctx c2 = c;
+    c2.st = s2;
+    launch_round_decide(ws->st, stats_t, trace_dev, s2);
+    launch_round_commit<S>(ws->st, V, TV, Vp, TVp, Vt, TVt, MR, Dm, nv, ws->ld, mem, ws->paa, grid_v, s2);
+    launch_round_aa_solve(ws->st, ws->paa, grid_v, s2);
+    launch_round_point<S>(ws->st, V, TV, Vt, TVt, d, Dm, nv, ws->ld, mem, grid_v, s2);
+    const int64_t before = ws->launches;
+    eval_T<S>(c2, Vt, TVt, d, stats_t, skip);
+    return 4 + (int)(ws->launches - before);
+  };
+  ws->launches = 0;
+  CUDA_TRY(cudaEventRecord(ws->e0, st));
+  eval_T<S>(c, Vt, TVt, nullptr, stats_t, nullptr);  // T(v0); also sets kernel attributes outside capture
+  const int64_t launches0 = ws->launches;
+  const char* fam = getenv("SPOCK_RICCATI_KERNELS");
+  const int trace_key = (trace_dev ? 1 : 0) + 2 * (s.profile ? 1 : 0) +
+                        4 * (fam && fam[0] ? (int)(unsigned char)fam[0] : 0);
+  if (s.profile) ws->prof.start();  // event slot r is recorded by round r of every replay
+  if (!ws->gexec || ws->g_alpha != alpha || ws->g_trace != trace_key) {
+    if (ws->gexec) {
+      cudaGraphExecDestroy(ws->gexec);
+      ws->gexec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    int per = 0;
+    for (int r = 0; r < kRounds; ++r) per = round(st);
+    CUDA_TRY(cudaStreamEndCapture(st, &g));
+    cudaError_t e = cudaGraphInstantiate(&ws->gexec, g, 0);
+    cudaGraphDestroy(g);
+    CUDA_TRY(e);
+    ws->g_alpha = alpha;
+    ws->g_trace = trace_key;
+    ws->g_launches_per_round = per;
+  }
+  int64_t launches = launches0;
+  const int64_t max_rounds = (int64_t)(max_iter + 1) * (h.max_back + 3) + 2;
+  int64_t rounds = 0;
+  int32_t rounds_done = 0;
+  for (;;) {
+    CUDA_TRY(cudaGraphLaunch(ws->gexec, st));
+    rounds += kRounds;
+    launches += (int64_t)kRounds * ws->g_launches_per_round;
+    CUDA_TRY(cudaMemcpyAsync(ws->h_done, &ws->st->done, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(ws->h_done + 1, &ws->st->rounds, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (s.profile) {  // rounds that evaluated T in this replay: the first (rounds now - rounds before)
+      const int ran = ws->h_done[1] - rounds_done - (ws->h_done[0] ? 1 : 0);
+      ws->prof.used = kRounds;
+      ws->prof.harvest_first(std::max(0, std::min(ran, kRounds)));
+    }
+    rounds_done = ws->h_done[1];
+    if (ws->h_done[0] || rounds > max_rounds) break;
+  }
+  CUDA_TRY(cudaEventRecord(ws->e1, st));
+  convert<double, S>(TV, z_dev, nz, st);
+  convert<double, S>(TV + nz, eta_dev, P.off.n_eta, st);
+  check_launch();
+  SmState fin;
+  CUDA_TRY(cudaMemcpyAsync(&fin, ws->st, sizeof(SmState), cudaMemcpyDeviceToHost, st));
+  if (trace_dev)
+    CUDA_TRY(cudaMemcpyAsync(s.trace, trace_dev, sizeof(int32_t) * 2 * (size_t)max_iter, cudaMemcpyDeviceToHost,
+                             st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ws->e0, ws->e1);
+  const int final_action = fin.done ? fin.action : A_MAXIT;
+  if (final_action_out) *final_action_out = final_action;
+  const int status = final_action == A_DONE ? SPOCK_OK
+                                            : ((final_action == A_MAXIT || final_action == A_STALL)
+                                                   ? SPOCK_MAX_ITER
+                                                   : SPOCK_ERR_NUMERICAL);
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->status = status;
+    info->iterations = fin.k;
+    info->n_T = fin.n_T;
+    info->n_K0 = fin.n_k0;
+    info->n_K1 = fin.n_k1;
+    info->n_K2 = fin.n_k2;
+    info->n_cap = fin.n_cap;
+    info->n_backtracks = fin.n_back;
+    info->xi = fin.xi;
+    info->xi0 = fin.xi0;
+    info->alpha = alpha;
+    info->solve_ms = ms;
+    info->n_launches = (int32_t)std::min<int64_t>(launches, INT32_MAX);
+    info->fp64_iterations = sizeof(S) == 8 ? fin.k : 0;
+    info->certified = sizeof(S) == 8 ? 1 : 0;
+    info->xi_fp32 = sizeof(S) == 8 ? NAN : fin.xi;
+    info->n_timed = ws->prof.on ? ws->prof.n : 0;
+    for (int g = 0; g < Profiler::kGroups; ++g) info->t_group_ms[g] = ws->prof.on ? ws->prof.acc[g] : 0.0;
+  }
+  ws->prof.on = false;
+  check_device_flag(P, st);
+  if (status == SPOCK_ERR_NUMERICAL) return fail(status, "non-finite residual during the iteration");
+  return status;
+}
+
+// Device-driven rounds replayed from a CUDA graph; SPOCK_DRIVER=host selects
+// the host-driven loop (one host decision per SuperMann step) instead.
+template <typename S>
+static int solve_impl(Problem& P, const double* x0_dev, const spock_settings& s, double* z_dev, double* eta_dev,
+                      int warm, spock_info* info, cudaStream_t st, double tol_given = 0.0, int stall_window = 0,
+                      int* final_action_out = nullptr) {
+  const char* drv = getenv("SPOCK_DRIVER");
+  if (drv && drv[0] == 'h')
+    return solve_host<S>(P, x0_dev, s, z_dev, eta_dev, warm, info, st, tol_given, stall_window, final_action_out);
+  return solve_graph<S>(P, x0_dev, s, z_dev, eta_dev, warm, info, st, tol_given, stall_window, final_action_out);
 }
 
 template <typename S>

@@ -31,7 +31,30 @@ struct SmState {
   double rhs[kMaxMemory];
   double gamma[kMaxMemory];
   int32_t aa_dropped;
+  // device-driven rounds (rounds.cu): what the last evaluation of T was for,
+  // what this round does, and whether the solve has finished
+  int32_t pending, op_accept, op_aa, op_point;
+  int32_t done, have_prev, aa_cnt, aa_next;
+  int32_t aa_slot, n_T, rounds, pad2_;
+  double stats_cur[8];
 };
+
+// Round-driver codes.
+enum SmPending : int32_t { P_INIT = 0, P_K0 = 1, P_LS = 2, P_K2 = 3 };
+enum SmPoint : int32_t { PT_NONE = 0, PT_DIR = 1, PT_LS = 2, PT_K2 = 3, PT_KM = 4 };
+
+// One round = decide (from the statistics of the last T evaluation) ->
+// commit/Anderson update -> Gram solve -> next evaluation point; the T
+// evaluation of that point follows (skipped once done).  Every kernel reads
+// its orders from the state, so the sequence can be captured in a graph.
+void launch_round_decide(SmState* st, const double* stats_t, int32_t* trace, cudaStream_t s);
+template <typename S>
+void launch_round_commit(SmState* st, S* V, S* TV, S* Vp, S* TVp, const S* Vt, const S* TVt, S* MR, S* D,
+                         int64_t n, int64_t ld, int mem, double* partials, int grid, cudaStream_t s);
+void launch_round_aa_solve(SmState* st, const double* partials, int nblocks, cudaStream_t s);
+template <typename S>
+void launch_round_point(SmState* st, const S* V, const S* TV, S* Vt, const S* TVt, S* d, const S* D, int64_t n,
+                        int64_t ld, int mem, int grid, cudaStream_t s);
 
 void sm_init_state(SmState* st_dev, const SmState& host_init, cudaStream_t s);
 void launch_sm_after_eval(SmState* st, const double* stats, int32_t* trace, cudaStream_t s);

@@ -159,3 +159,40 @@ def test_errors():
     s = spock.spock_default_settings(alpha=10.0)
     with pytest.raises(spock.SpockError):
         spock.spock_solve(pair.gp.handle, d["x0"], s, z, e, 0)
+
+
+def test_graph_and_host_drivers_agree(monkeypatch):
+    """The device-driven rounds (CUDA graph) and the host-driven loop take
+    the same decisions and return the same iterate."""
+    import ctypes as C
+    from paper_2212_01110_gb300 import spock
+    pair = Pair(CASES["ragged"])
+    K = 40
+    out = {}
+    for drv in ("graph", "host"):
+        monkeypatch.setenv("SPOCK_DRIVER", drv)
+        trace = (C.c_int32 * (2 * K))()
+        s = spock.spock_default_settings(max_iter=K, alpha=pair.alpha, eps_abs=1e-14, eps_rel=1e-14)
+        s.trace = C.cast(trace, C.POINTER(C.c_int32))
+        z = pair.t(np.zeros(pair.gp.n_z))
+        e = pair.t(np.zeros(pair.gp.n_eta))
+        info = spock.spock_solve_dev(pair.gp.handle, pair.x0, s, z, e, 0)
+        out[drv] = (np.concatenate([z.cpu().numpy(), e.cpu().numpy()]), list(trace), info.n_T)
+    assert out["graph"][1] == out["host"][1]
+    assert out["graph"][2] == out["host"][2]
+    assert rel_err(out["graph"][0], out["host"][0]) < 1e-13
+
+
+@pytest.mark.parametrize("drv", ["graph", "host"])
+def test_profiled_solve_times_kernel_groups(drv, monkeypatch):
+    """settings.profile: every evaluated T is timed per kernel group with CUDA
+    events (event-record nodes when the rounds replay from a graph)."""
+    from paper_2212_01110_gb300 import spock
+    monkeypatch.setenv("SPOCK_DRIVER", drv)
+    pair = Pair(CASES["chains"])
+    s = spock.spock_default_settings(max_iter=30, alpha=pair.alpha, profile=1)
+    z = pair.t(np.zeros(pair.gp.n_z))
+    e = pair.t(np.zeros(pair.gp.n_eta))
+    info = spock.spock_solve_dev(pair.gp.handle, pair.x0, s, z, e, 0)
+    assert info.n_timed >= info.n_T - 1 > 0
+    assert all(t >= 0 for t in info.t_group_ms) and sum(info.t_group_ms) > 0
