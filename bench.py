@@ -257,6 +257,7 @@ def run_ours(args, rank, world, local_rank):
                   "call, K iterations from a cold start"}
 
     paper = paper_workload(args, spock, workloads, dev) if (rank == 0 and args.paper_workload) else None
+    batch = batch_workload(args, spock, workloads, dev, seed=rank) if args.batch > 0 else None
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -296,6 +297,8 @@ def run_ours(args, rank, world, local_rank):
                             if (tt and tf and tt["status"] == "converged" and tf["status"] == "converged") else None}
         if paper:
             line["paper_workload"] = paper
+        if batch:
+            line["batch"] = batch
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
@@ -334,6 +337,45 @@ def paper_workload(args, spock, workloads, dev):
         P.close()
         del P, z, e
         torch.cuda.empty_cache()
+    return out
+
+
+def batch_workload(args, spock, workloads, dev, seed=0):
+    """Batched SPOCK: args.batch heterogeneous instances (branching 2-4,
+    N 5-15, nx 10-30, nu 4-10, scenario cap 64; data as the large tree) in
+    one spock_batch_solve_dev call -- one CUDA graph with a parallel branch
+    of rounds per instance.  A warm-up solve (autotuning, capture) is
+    excluded; the timed solve runs args.batch_iter SPOCK iterations per
+    instance from a cold start, FP32 (FP64 residual/Anderson) and FP64."""
+    import torch
+    t0 = time.time()
+    ds = workloads.batch_instances(seed=seed, count=args.batch)
+    probs = [spock.Problem(d) for d in ds]
+    setup = time.time() - t0
+    b = spock.spock_batch_create([p.handle for p in probs])
+    x0s = [torch.tensor(d["x0"], dtype=torch.float64, device=dev) for d in ds]
+    zs = [torch.zeros(p.n_z, dtype=torch.float64, device=dev) for p in probs]
+    es = [torch.zeros(p.n_eta, dtype=torch.float64, device=dev) for p in probs]
+    out = {"instances": len(ds), "nodes_total": int(sum(len(d["anc"]) for d in ds)),
+           "variables_total": int(sum(p.n_z + p.n_eta for p in probs)), "setup_s": round(setup, 1),
+           "iterations_per_instance": args.batch_iter}
+    for prec, nm in ((spock.SPOCK_FP32, "fp32"), (spock.SPOCK_FP64, "fp64")):
+        st = spock.spock_default_settings(precision=prec, max_iter=args.batch_iter, memory=args.memory, fp64_tail=0)
+        spock.spock_batch_solve_dev(b, x0s, st, zs, es, 0)   # warm-up: autotune + capture
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos = spock.spock_batch_solve_dev(b, x0s, st, zs, es, 0)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        nT = sum(i.n_T for i in infos)
+        out[nm] = {"value": round(nT / infos[0].solve_ms * 1e3, 1), "unit": "instance CP iters/s",
+                   "device_ms": round(infos[0].solve_ms, 2), "wall_ms": round(wall * 1e3, 2), "n_T_total": nT,
+                   "converged": sum(1 for i in infos if i.status == 0),
+                   "median_xi": float(np.median([i.xi for i in infos]))}
+    spock.spock_free(b)
+    for p in probs:
+        p.close()
+    torch.cuda.empty_cache()
     return out
 
 
@@ -398,6 +440,8 @@ def main():
     ap.add_argument("--paper-workload", type=int, default=1,
                     help="also time SPOCK to tolerance on the paper's data-center system (1) or not (0)")
     ap.add_argument("--paper-max-iter", type=int, default=20000)
+    ap.add_argument("--batch", type=int, default=512, help="instances of the batched measurement (0 skips it)")
+    ap.add_argument("--batch-iter", type=int, default=50)
     ap.add_argument("--branching-stages", type=int, default=6,
                     help="stages with 4 children (6 = the 62,805-node tree; smaller trees for profiling)")
     args = ap.parse_args()

@@ -70,6 +70,7 @@ typedef enum spock_precision {
 
 typedef struct spock_tree spock_tree;
 typedef struct spock_problem spock_problem;
+typedef struct spock_batch spock_batch;
 
 /* Settings of Algorithm 3.  spock_default_settings() fills the defaults. */
 typedef struct spock_settings {
@@ -283,6 +284,34 @@ int spock_prox_f_noalloc_dev(spock_problem* p, const double* x0_dev, double alph
  */
 int spock_grad_dev(spock_problem* p, const double* z, const double* eta, int32_t precision, double* g_x0,
                    double* g_A, double* g_B, double* g_Q, double* g_R, double* g_QN, void* stream);
+
+/*
+ * spock_batch_create -- a batch of independent problems (any trees, depths,
+ * nx, nu) solved together by spock_batch_solve_dev.  The problems stay owned
+ * by the caller and must outlive the batch; a problem may belong to one
+ * batch at a time.  n >= 1.
+ */
+int spock_batch_create(int32_t n, spock_problem* const* problems, spock_batch** out);
+
+/*
+ * spock_batch_solve_dev -- Algorithm 3 on every problem of the batch.
+ * All instances advance together: the rounds of every instance (decision,
+ * Anderson update, next point, evaluation of T) are captured once into one
+ * CUDA graph with one parallel branch per instance, and each graph launch
+ * advances every unfinished instance by a fixed number of rounds (finished
+ * instances skip their kernels); the host only reads the done flags after
+ * each launch.  Before the first capture the Riccati kernel family of each
+ * instance is chosen by timing candidate evaluations of T (autotuner).
+ *   x0_dev, z_dev, eta_dev : host arrays of n device pointers (FP64), per
+ *     instance as in spock_solve_dev.
+ *   settings : shared by all instances (alpha <= 0: each instance's own
+ *     0.99/||L||); precision SPOCK_FP64 or SPOCK_FP32 (no FP64 tail here).
+ *   infos    : optional host array of n outcomes.
+ * Returns SPOCK_OK if every instance converged, SPOCK_MAX_ITER if some hit
+ * the iteration cap (outputs written for all), or an error.  Blocking.
+ */
+int spock_batch_solve_dev(spock_batch* batch, const double* const* x0_dev, const spock_settings* settings,
+                          double* const* z_dev, double* const* eta_dev, int32_t warm, spock_info* infos);
 
 /* Frees a handle returned by any *_create call; NULL is a no-op. */
 void spock_free(void* handle);

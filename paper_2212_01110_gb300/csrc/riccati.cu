@@ -341,7 +341,13 @@ int launch_fwd_chain_grp(const KP<S>& p, S* zo, cudaStream_t st);
 // SPOCK_RICCATI_KERNELS forces one family everywhere (the tests cover each).
 enum ChainFamily { CF_AUTO = -1, CF_GRP = 0, CF_TMA = 1, CF_DIRECT = 2 };
 constexpr int kStagedMaxNodes = 2048;  // FP64 stages with more nodes use the direct kernels
+// Per-thread override set by the batch autotuner while it times candidates
+// and captures an instance (-2 = none).
+static thread_local int g_family_override = -2;
+void set_riccati_family_override(int fam) { g_family_override = fam; }
+
 static int chain_family() {
+  if (g_family_override != -2) return g_family_override;
   const char* e = getenv("SPOCK_RICCATI_KERNELS");
   if (!e || !e[0]) return CF_AUTO;
   if (e[0] == 'd') return CF_DIRECT;

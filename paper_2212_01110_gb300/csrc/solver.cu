@@ -34,6 +34,7 @@ int launch_riccati(const KP<S>& p, const std::vector<int32_t>& stage_begin, cons
                    S* zo, cudaStream_t st, cudaEvent_t* ev);
 
 enum { DM_APPLY_L_ = 0, DM_PROXG_ = 1, DM_DUAL_ = 2, PM_APPLY_LT_ = 0, PM_STATS_ = 1 };
+void set_riccati_family_override(int fam);  // riccati.cu
 
 // ---------------------------------------------------------------------------
 // errors
@@ -790,6 +791,264 @@ static int cp_impl(Problem& P, const double* x0_dev, int k, double alpha, double
   return SPOCK_OK;
 }
 
+// ---------------------------------------------------------------------------
+// batches: one graph, one parallel branch of rounds per instance
+// ---------------------------------------------------------------------------
+constexpr int kBatchRounds = 4;
+
+struct Batch {
+  int32_t tag = TAG_BATCH;
+  std::vector<Problem*> probs;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t main = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int g_prec = -1, g_mem = -1;
+  double g_alpha = -1.0;
+  int g_launches = 0;
+  std::vector<void*> g_ws;      // workspaces the graph was captured with
+  SmState** st_ptrs = nullptr;  // device array of the instances' state pointers
+  int32_t* done_dev = nullptr;
+  int32_t* done_host = nullptr;  // pinned
+  ~Batch() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    for (auto s : streams) cudaStreamDestroy(s);
+    for (auto e : joins) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+    if (main) cudaStreamDestroy(main);
+    if (st_ptrs) cudaFree(st_ptrs);
+    if (done_dev) cudaFree(done_dev);
+    if (done_host) cudaFreeHost(done_host);
+  }
+};
+
+__global__ void k_gather_done(SmState* const* __restrict__ sts, int n, int32_t* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = sts[i]->done;
+}
+
+// Kernel family of an instance: candidate families timed on three T
+// evaluations each (the autotuner of the batch path); cached per problem.
+template <typename S>
+static int tune_family(Problem& P, Workspace* ws, double alpha, cudaStream_t st) {
+  int& slot = P.tuned_family[sizeof(S) == 8 ? 0 : 1];
+  if (slot != -3) return slot;
+  Ctx c{&P, ws, alpha, st, P.idx.stage_begin};
+  S* v = (S*)ws->v[2];
+  S* Tv = (S*)ws->Tv[2];
+  const int cands[4] = {-1, 1, 2, 0};  // auto, one warp per chain staged, direct, three warps per chain
+  float best = 1e30f;
+  int pick = -1;
+  cudaEvent_t a, b;
+  CUDA_TRY(cudaEventCreate(&a));
+  CUDA_TRY(cudaEventCreate(&b));
+  for (int f : cands) {
+    set_riccati_family_override(f);
+    eval_T<S>(c, v, Tv, nullptr, nullptr);
+    CUDA_TRY(cudaEventRecord(a, st));
+    for (int r = 0; r < 3; ++r) eval_T<S>(c, v, Tv, nullptr, nullptr);
+    CUDA_TRY(cudaEventRecord(b, st));
+    CUDA_TRY(cudaEventSynchronize(b));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (ms < best) {
+      best = ms;
+      pick = f;
+    }
+  }
+  set_riccati_family_override(-2);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  slot = pick;
+  return pick;
+}
+
+template <typename S>
+static int batch_solve(Batch& B, const double* const* x0, const spock_settings& s, double* const* z,
+                       double* const* eta, int warm, spock_info* infos) {
+  const int n = (int)B.probs.size();
+  const int mem = std::max(0, std::min<int>(s.memory, kMaxMemory));
+  const int max_iter = std::max(0, s.max_iter);
+  std::vector<Workspace*> wss(n);
+  std::vector<double> alphas(n);
+  std::vector<int> fams(n);
+  std::vector<int64_t> launches(n, 0);
+  for (int i = 0; i < n; ++i) {
+    Problem& P = *B.probs[i];
+    CUDA_TRY(cudaSetDevice(P.device));
+    wss[i] = get_ws_impl<S>(P, mem);
+    alphas[i] = default_alpha(P, s.alpha);
+  }
+  // per-instance inputs, state and T(v0) on the instance's stream
+  for (int i = 0; i < n; ++i) {
+    Problem& P = *B.probs[i];
+    Workspace* ws = wss[i];
+    cudaStream_t st = B.streams[i];
+    const DevFactors<S>& f = factors<S>(P);
+    S* Vt = (S*)ws->v[2];
+    convert<S, double>(x0[i], f.x0, P.nx, st);
+    if (warm) {
+      convert<S, double>(z[i], Vt, P.off.n_z, st);
+      convert<S, double>(eta[i], Vt + P.off.n_z, P.off.n_eta, st);
+    } else {
+      CUDA_TRY(cudaMemsetAsync(Vt, 0, sizeof(S) * ws->n_v, st));
+    }
+    CUDA_TRY(cudaMemsetAsync(ws->d, 0, sizeof(S) * ws->n_v, st));
+    fams[i] = tune_family<S>(P, ws, alphas[i], st);
+    if (warm) {  // tuning overwrote the evaluation buffers
+      convert<S, double>(z[i], Vt, P.off.n_z, st);
+      convert<S, double>(eta[i], Vt + P.off.n_z, P.off.n_eta, st);
+    } else {
+      CUDA_TRY(cudaMemsetAsync(Vt, 0, sizeof(S) * ws->n_v, st));
+    }
+    SmState h{};
+    h.alpha = alphas[i];
+    h.eps_abs = s.eps_abs;
+    h.eps_rel = s.eps_rel;
+    h.c0 = s.c0;
+    h.c1 = s.c1;
+    h.c2 = s.c2;
+    h.beta = s.beta;
+    h.sigma = s.sigma;
+    h.lam = s.lambda;
+    h.rho_coef = s.rho_coef;
+    h.max_iter = max_iter;
+    h.max_back = std::max(0, s.max_backtracks);
+    h.mem = mem;
+    h.pending = P_INIT;
+    h.n_T = 1;
+    sm_init_state(ws->st, h, st);
+    Ctx c{&P, ws, alphas[i], st, P.idx.stage_begin};
+    set_riccati_family_override(fams[i]);
+    ws->launches = 0;
+    eval_T<S>(c, Vt, (S*)ws->Tv[2], nullptr, ws->stats, nullptr);
+    launches[i] = ws->launches;
+    set_riccati_family_override(-2);
+  }
+  CUDA_TRY(cudaDeviceSynchronize());
+  // one graph: every instance's kBatchRounds rounds as a parallel branch
+  const bool same_alpha = s.alpha > 0 ? B.g_alpha == s.alpha : B.g_alpha == 0.0;
+  std::vector<void*> ws_now(wss.begin(), wss.end());
+  if (!B.gexec || B.g_prec != (int)sizeof(S) || B.g_mem != mem || !same_alpha || B.g_ws != ws_now) {
+    if (B.gexec) {
+      cudaGraphExecDestroy(B.gexec);
+      B.gexec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(B.main, cudaStreamCaptureModeThreadLocal));
+    CUDA_TRY(cudaEventRecord(B.fork, B.main));
+    int total = 0;
+    for (int i = 0; i < n; ++i) {
+      Problem& P = *B.probs[i];
+      Workspace* ws = wss[i];
+      cudaStream_t st = B.streams[i];
+      CUDA_TRY(cudaStreamWaitEvent(st, B.fork, 0));
+      set_riccati_family_override(fams[i]);
+      Ctx c{&P, ws, alphas[i], st, P.idx.stage_begin};
+      S* V = (S*)ws->v[0];
+      S* TV = (S*)ws->Tv[0];
+      S* Vp = (S*)ws->v[1];
+      S* TVp = (S*)ws->Tv[1];
+      S* Vt = (S*)ws->v[2];
+      S* TVt = (S*)ws->Tv[2];
+      S* d = (S*)ws->d;
+      const int32_t* skip = &ws->st->done;
+      for (int r = 0; r < kBatchRounds; ++r) {
+        launch_round_decide(ws->st, ws->stats, nullptr, st);
+        launch_round_commit<S>(ws->st, V, TV, Vp, TVp, Vt, TVt, (S*)ws->MR, (S*)ws->D, ws->n_v, ws->ld, mem,
+                               ws->paa, ws->grid_v, st);
+        launch_round_aa_solve(ws->st, ws->paa, ws->grid_v, st);
+        launch_round_point<S>(ws->st, V, TV, Vt, TVt, d, (S*)ws->D, ws->n_v, ws->ld, mem, ws->grid_v, st);
+        const int64_t before = ws->launches;
+        eval_T<S>(c, Vt, TVt, d, ws->stats, skip);
+        total += 4 + (int)(ws->launches - before);
+      }
+      set_riccati_family_override(-2);
+      CUDA_TRY(cudaEventRecord(B.joins[i], st));
+      CUDA_TRY(cudaStreamWaitEvent(B.main, B.joins[i], 0));
+    }
+    k_gather_done<<<(n + 127) / 128, 128, 0, B.main>>>(B.st_ptrs, n, B.done_dev);
+    check_launch();
+    CUDA_TRY(cudaStreamEndCapture(B.main, &g));
+    cudaError_t e = cudaGraphInstantiate(&B.gexec, g, 0);
+    cudaGraphDestroy(g);
+    CUDA_TRY(e);
+    B.g_prec = (int)sizeof(S);
+    B.g_mem = mem;
+    B.g_ws = ws_now;
+    B.g_alpha = s.alpha > 0 ? s.alpha : 0.0;
+    B.g_launches = total + 1;
+  }
+  // state pointers for the gather kernel
+  {
+    std::vector<SmState*> h(n);
+    for (int i = 0; i < n; ++i) h[i] = wss[i]->st;
+    CUDA_TRY(cudaMemcpy(B.st_ptrs, h.data(), sizeof(SmState*) * n, cudaMemcpyHostToDevice));
+  }
+  const int64_t max_rounds = (int64_t)(max_iter + 1) * (std::max(0, s.max_backtracks) + 3) + 2;
+  int64_t rounds = 0, graph_launches = 0;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  CUDA_TRY(cudaEventRecord(e0, B.main));
+  for (;;) {
+    CUDA_TRY(cudaGraphLaunch(B.gexec, B.main));
+    rounds += kBatchRounds;
+    ++graph_launches;
+    CUDA_TRY(cudaMemcpyAsync(B.done_host, B.done_dev, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, B.main));
+    CUDA_TRY(cudaStreamSynchronize(B.main));
+    bool all = true;
+    for (int i = 0; i < n; ++i) all = all && B.done_host[i];
+    if (all || rounds > max_rounds) break;
+  }
+  CUDA_TRY(cudaEventRecord(e1, B.main));
+  CUDA_TRY(cudaStreamSynchronize(B.main));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int status = SPOCK_OK;
+  for (int i = 0; i < n; ++i) {
+    Problem& P = *B.probs[i];
+    Workspace* ws = wss[i];
+    cudaStream_t st = B.streams[i];
+    convert<double, S>((S*)ws->Tv[0], z[i], P.off.n_z, st);
+    convert<double, S>((S*)ws->Tv[0] + P.off.n_z, eta[i], P.off.n_eta, st);
+    SmState fin;
+    CUDA_TRY(cudaMemcpyAsync(&fin, ws->st, sizeof(SmState), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    const int act = fin.done ? fin.action : A_MAXIT;
+    const int si = act == A_DONE ? SPOCK_OK : ((act == A_MAXIT || act == A_STALL) ? SPOCK_MAX_ITER : SPOCK_ERR_NUMERICAL);
+    if (si == SPOCK_ERR_NUMERICAL) status = SPOCK_ERR_NUMERICAL;
+    else if (si == SPOCK_MAX_ITER && status == SPOCK_OK) status = SPOCK_MAX_ITER;
+    if (infos) {
+      spock_info& I = infos[i];
+      std::memset(&I, 0, sizeof(I));
+      I.status = si;
+      I.iterations = fin.k;
+      I.n_T = fin.n_T;
+      I.n_K0 = fin.n_k0;
+      I.n_K1 = fin.n_k1;
+      I.n_K2 = fin.n_k2;
+      I.n_cap = fin.n_cap;
+      I.n_backtracks = fin.n_back;
+      I.xi = fin.xi;
+      I.xi0 = fin.xi0;
+      I.alpha = alphas[i];
+      I.solve_ms = ms;  // wall time of the whole batch
+      I.n_launches = (int32_t)std::min<int64_t>(launches[i] + graph_launches * (B.g_launches / std::max(n, 1)),
+                                                INT32_MAX);
+      I.certified = sizeof(S) == 8 ? 1 : 0;
+      I.fp64_iterations = sizeof(S) == 8 ? fin.k : 0;
+      I.xi_fp32 = sizeof(S) == 8 ? NAN : fin.xi;
+    }
+    check_device_flag(P, st);
+  }
+  if (status == SPOCK_ERR_NUMERICAL) return fail(status, "non-finite residual in a batch instance");
+  return status;
+}
+
 template <typename S>
 int launch_gradient(const KP<S>& p, const std::vector<int32_t>& stage_begin, const S* z, const S* eta, const S* w,
                     S* lam, double* gx0, double* gA, double* gB, double* gQ, double* gR, double* gQN, int max_blocks,
@@ -1428,11 +1687,71 @@ int spock_grad_dev(spock_problem* p, const double* z, const double* eta, int32_t
   });
 }
 
+int spock_batch_create(int32_t n, spock_problem* const* problems, spock_batch** out) {
+  return guarded([&]() -> int {
+    if (n < 1 || !problems || !out) return fail(SPOCK_ERR_INVALID_ARG, "need n >= 1 problems and an out pointer");
+    auto* B = new Batch();
+    try {
+      for (int i = 0; i < n; ++i) {
+        Problem* P = as_problem(problems[i]);
+        if (!P) {
+          delete B;
+          return fail(SPOCK_ERR_INVALID_ARG, "not a problem handle in the batch");
+        }
+        B->probs.push_back(P);
+      }
+      CUDA_TRY(cudaSetDevice(B->probs[0]->device));
+      CUDA_TRY(cudaStreamCreateWithFlags(&B->main, cudaStreamNonBlocking));
+      CUDA_TRY(cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming));
+      B->streams.resize(n);
+      B->joins.resize(n);
+      for (int i = 0; i < n; ++i) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&B->streams[i], cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&B->joins[i], cudaEventDisableTiming));
+      }
+      CUDA_TRY(cudaMalloc(&B->st_ptrs, sizeof(SmState*) * n));
+      CUDA_TRY(cudaMalloc(&B->done_dev, sizeof(int32_t) * n));
+      CUDA_TRY(cudaMallocHost(&B->done_host, sizeof(int32_t) * n));
+    } catch (...) {
+      delete B;
+      throw;
+    }
+    *out = reinterpret_cast<spock_batch*>(B);
+    return SPOCK_OK;
+  });
+}
+
+int spock_batch_solve_dev(spock_batch* batch, const double* const* x0_dev, const spock_settings* settings,
+                          double* const* z_dev, double* const* eta_dev, int32_t warm, spock_info* infos) {
+  return guarded([&]() -> int {
+    Batch* B = reinterpret_cast<Batch*>(batch);
+    if (!B || B->tag != TAG_BATCH || !x0_dev || !z_dev || !eta_dev)
+      return fail(SPOCK_ERR_INVALID_ARG, "NULL argument or not a batch handle");
+    spock_settings s;
+    spock_default_settings(&s);
+    if (settings) s = *settings;
+    if (s.memory < 0 || s.memory > kMaxMemory) return fail(SPOCK_ERR_INVALID_ARG, "memory must be in 0..16");
+    if (!(s.eps_abs > 0) || !(s.eps_rel >= 0)) return fail(SPOCK_ERR_INVALID_ARG, "tolerances must be positive");
+    for (size_t i = 0; i < B->probs.size(); ++i) {
+      if (!x0_dev[i] || !z_dev[i] || !eta_dev[i]) return fail(SPOCK_ERR_INVALID_ARG, "NULL instance buffer");
+      if (s.alpha > 0 && s.alpha * B->probs[i]->normL >= 1.0)
+        return fail(SPOCK_ERR_INVALID_ARG, "alpha ||L|| must be < 1 for every instance");
+      int rc = root_box_ok(*B->probs[i], x0_dev[i], nullptr, true);
+      if (rc != SPOCK_OK) return rc;
+    }
+    CUDA_TRY(cudaSetDevice(B->probs[0]->device));
+    if (s.precision == SPOCK_FP64) return batch_solve<double>(*B, x0_dev, s, z_dev, eta_dev, warm, infos);
+    if (s.precision == SPOCK_FP32) return batch_solve<float>(*B, x0_dev, s, z_dev, eta_dev, warm, infos);
+    return fail(SPOCK_ERR_INVALID_ARG, "unknown precision");
+  });
+}
+
 void spock_free(void* handle) {
   if (!handle) return;
   const int32_t tag = *reinterpret_cast<const int32_t*>(handle);
   if (tag == TAG_TREE) delete reinterpret_cast<Tree*>(handle);
   else if (tag == TAG_PROBLEM) delete reinterpret_cast<Problem*>(handle);
+  else if (tag == TAG_BATCH) delete reinterpret_cast<Batch*>(handle);
 }
 
 const char* spock_last_error(void) { return g_last_error.c_str(); }

@@ -11,7 +11,7 @@
 
 namespace spock {
 
-enum : int32_t { TAG_TREE = 0x54524545, TAG_PROBLEM = 0x50524f42 };
+enum : int32_t { TAG_TREE = 0x54524545, TAG_PROBLEM = 0x50524f42, TAG_BATCH = 0x42415443 };
 
 // Maximum Anderson memory and per-node dimension handled by the kernels.
 constexpr int kMaxMemory = 16;
@@ -107,6 +107,9 @@ struct Problem {
   // solver workspace, allocated on first use per precision
   struct Workspace* ws64 = nullptr;
   struct Workspace* ws32 = nullptr;
+  // Riccati kernel family picked by the batch autotuner, per precision
+  // (-3 = not tuned yet)
+  int tuned_family[2] = {-3, -3};
   ~Problem();
 };
 

@@ -82,6 +82,9 @@ _sig = {
     "spock_prox_gconj_dev": ([_P, C.c_double, _P, _P, _P], C.c_int),
     "spock_T_dev": ([_P, _P, C.c_double, _P, _P, _P, _P, _P], C.c_int),
     "spock_grad_dev": ([_P, _P, _P, C.c_int32, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "spock_batch_create": ([C.c_int32, C.POINTER(_P), C.POINTER(_P)], C.c_int),
+    "spock_batch_solve_dev": ([_P, C.POINTER(_P), C.POINTER(Settings), C.POINTER(_P), C.POINTER(_P), C.c_int32,
+                               C.POINTER(Info)], C.c_int),
     "spock_free": ([_P], None),
     "spock_last_error": ([], C.c_char_p),
 }
@@ -232,6 +235,27 @@ def spock_grad_dev(problem, z, eta, precision, g_x0=None, g_A=None, g_B=None, g_
     _check(_lib.spock_grad_dev(problem, _tptr(z, dtype=torch.float64), _tptr(eta, dtype=torch.float64),
                                int(precision), ptr(g_x0), ptr(g_A), ptr(g_B), ptr(g_Q), ptr(g_R), ptr(g_QN),
                                _stream(stream)))
+
+
+def spock_batch_create(problems):
+    """problems: list of problem handles (c_void_p)."""
+    arr = (_P * len(problems))(*[p.value if isinstance(p, _P) else p for p in problems])
+    h = _P()
+    _check(_lib.spock_batch_create(len(problems), arr, C.byref(h)))
+    return h
+
+
+def spock_batch_solve_dev(batch, x0s, settings, zs, etas, warm):
+    """x0s, zs, etas: lists of float64 CUDA tensors, one per instance.
+    Returns the list of per-instance Info."""
+    import torch
+    n = len(x0s)
+    ptrs = lambda ts: (_P * n)(*[_tptr(t, dtype=torch.float64).value for t in ts])
+    infos = (Info * n)()
+    rc = _lib.spock_batch_solve_dev(batch, ptrs(x0s), C.byref(settings) if settings is not None else None,
+                                    ptrs(zs), ptrs(etas), int(warm), infos)
+    _check(rc, (SPOCK_OK, SPOCK_MAX_ITER))
+    return list(infos)
 
 
 def spock_free(handle):

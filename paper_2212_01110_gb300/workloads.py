@@ -273,3 +273,26 @@ def random_vectors(n_z, n_eta, seed=0, scale=1.0):
     """Seeded test points (z, eta) for operator-level comparisons."""
     rng = np.random.default_rng(seed)
     return scale * rng.standard_normal(n_z), scale * rng.standard_normal(n_eta)
+
+
+def batch_instances(seed=0, count=512, max_scenarios=64):
+    """Heterogeneous batch: per instance a branching factor b ~ U{2,3,4},
+    horizon N ~ U{5..15}, nx ~ U{10..30}, nu ~ U{4..10}; the tree branches
+    for the first floor(log_b max_scenarios) stages and then has one child
+    per node (scenario cap: full trees of branching 4 and horizon 15 would
+    have 1.4e9 nodes).  Data as ``large_tree`` (A = 0.95 x Haar-orthogonal,
+    B ~ N(0, 1/nx), Q = diag U(0.5, 2), R = 0.1 I, Q_N = I, AV@R a ~ U(0.1, 0.9),
+    Dirichlet child probabilities, |x| <= 5, |u| <= 1, x0 ~ N(0, 1))."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        b = int(rng.integers(2, 5))
+        N = int(rng.integers(5, 16))
+        nx = int(rng.integers(10, 31))
+        nu = int(rng.integers(4, 11))
+        stages = 0
+        while b ** (stages + 1) <= max_scenarios:
+            stages += 1
+        stages = min(stages, N)
+        out.append(large_tree(seed=1000 * seed + i, branching_stages=stages, branch=b, N=N, nx=nx, nu=nu))
+    return out

@@ -1,0 +1,71 @@
+"""Batched solves (spock_batch_solve_dev): every instance of a heterogeneous
+batch (different trees, depths, nx, nu) must reach what the single-instance
+solver reaches; fixed-iteration runs agree with the single-instance driver."""
+import numpy as np
+import pytest
+
+from paper_2212_01110_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _instances():
+    return [W.small_binary(0), W.with_tree(W.fig1_tree(), seed=1, nx=3, nu=2),
+            W.random_tree(3, N=4, max_branch=3, nx=4, nu=3),
+            W.random_tree(4, N=6, max_branch=3, nx=5, nu=2, chain_after=2),
+            W.random_tree(5, N=5, max_branch=1, nx=3, nu=2),
+            W.datacenter(N=3, nx=4)]
+
+
+def _tensors(P, d, dev):
+    import torch
+    return (torch.tensor(d["x0"], dtype=torch.float64, device=dev),
+            torch.zeros(P.n_z, dtype=torch.float64, device=dev),
+            torch.zeros(P.n_eta, dtype=torch.float64, device=dev))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_matches_single_instance(precision):
+    import torch
+    from paper_2212_01110_gb300 import spock
+    dev = torch.device("cuda:0")
+    ds = _instances()
+    probs = [spock.Problem(d) for d in ds]
+    batch = spock.spock_batch_create([p.handle for p in probs])
+    bufs = [_tensors(P, d, dev) for P, d in zip(probs, ds)]
+    K = 25
+    s = spock.spock_default_settings(max_iter=K, eps_abs=1e-14, eps_rel=1e-14, precision=precision, fp64_tail=0)
+    infos = spock.spock_batch_solve_dev(batch, [b[0] for b in bufs], s, [b[1] for b in bufs], [b[2] for b in bufs], 0)
+    for P, d, (x0, z, e), inf in zip(probs, ds, bufs, infos):
+        assert inf.iterations == K
+        z1, e1 = torch.zeros_like(z), torch.zeros_like(e)
+        inf1 = spock.spock_solve_dev(P.handle, x0, s, z1, e1, 0)
+        a = torch.cat([z, e]).cpu().numpy()
+        b = torch.cat([z1, e1]).cpu().numpy()
+        err = np.max(np.abs(a - b)) / max(1, np.max(np.abs(b)))
+        assert err < (1e-9 if precision == 0 else 1e-4), err
+        assert inf.n_T == inf1.n_T
+    spock.spock_free(batch)
+
+
+def test_batch_converges():
+    import torch
+    from paper_2212_01110_gb300 import spock
+    dev = torch.device("cuda:0")
+    ds = _instances()
+    probs = [spock.Problem(d) for d in ds]
+    batch = spock.spock_batch_create([p.handle for p in probs])
+    bufs = [_tensors(P, d, dev) for P, d in zip(probs, ds)]
+    s = spock.spock_default_settings(max_iter=20000)
+    infos = spock.spock_batch_solve_dev(batch, [b[0] for b in bufs], s, [b[1] for b in bufs], [b[2] for b in bufs], 0)
+    for P, (x0, z, e), inf in zip(probs, bufs, infos):
+        assert inf.status == spock.SPOCK_OK and inf.xi <= max(1e-6, 1e-6 * inf.xi0) * (1 + 1e-9)
+        z1, e1 = torch.zeros_like(z), torch.zeros_like(e)
+        spock.spock_solve_dev(P.handle, x0, s, z1, e1, 0)
+        assert abs(float(z[0]) - float(z1[0])) < 1e-6 * max(1, abs(float(z1[0])))
+    # a second solve reuses the captured graph; warm-started from the solution
+    # it converges in fewer iterations (the relative tolerance is re-based on
+    # the warm point's xi_0, so it still iterates)
+    infos2 = spock.spock_batch_solve_dev(batch, [b[0] for b in bufs], s, [b[1] for b in bufs], [b[2] for b in bufs], 1)
+    assert all(i2.status == spock.SPOCK_OK and i2.iterations < i1.iterations for i1, i2 in zip(infos, infos2))
+    spock.spock_free(batch)
