@@ -51,6 +51,21 @@ def measured_peaks():
 FP64_PEAK_TFLOPS = 1.193
 
 
+
+def replica_reduce(ms, units, dev=None):
+    """Whole-job figures of the replicas: the slowest rank's time and the
+    units (CP evaluations) summed over ranks.  Identity at world size 1."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), float(units)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u)
+    return float(t.item()), float(u.item())
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -168,18 +183,8 @@ def run_ours(args, rank, world, local_rank):
             torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1)
-        if world > 1:
-            t = torch.tensor([ms], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
         nT = sum(i.n_T for i in infos)
-        if world > 1:
-            t = torch.tensor([nT], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t)
-            nT_all = float(t.item())
-        else:
-            nT_all = float(nT)
+        ms, nT_all = replica_reduce(ev0.elapsed_time(ev1), nT, dev)
         return ms, nT, nT_all, infos, clk.summary()
 
     def roofline(infos, prec):
@@ -245,12 +250,7 @@ def run_ours(args, rank, world, local_rank):
     nT_e2e = inf.n_T
     e2e_s = time.perf_counter() - t0
     barrier()
-    if world > 1:
-        t = torch.tensor([e2e_s, nT_e2e], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t[:1], op=torch.distributed.ReduceOp.MAX)
-        tt = torch.tensor([float(nT_e2e)], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt)
-        e2e_s, nT_e2e = float(t[0].item()), float(tt.item())
+    e2e_s, nT_e2e = replica_reduce(e2e_s, nT_e2e, dev)
     e2e = {"value": nT_e2e / e2e_s, "unit": "CP iters/s", "h2d_bytes_per_step": 8 * P.nx / args.steps,
            "d2h_bytes_per_step": 8 * (P.n_z + P.n_eta) / args.steps, "ms_per_step": 1e3 * e2e_s / args.steps,
            "api": "spock_solve: host buffers (pinned), x0 copied in and (z, eta) copied out inside the timed "
@@ -258,6 +258,7 @@ def run_ours(args, rank, world, local_rank):
 
     paper = paper_workload(args, spock, workloads, dev) if (rank == 0 and args.paper_workload) else None
     batch = batch_workload(args, spock, workloads, dev, seed=rank) if args.batch > 0 else None
+    grad = grad_workload(args, spock, workloads, dev) if (rank == 0 and args.grad_instances > 0) else None
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -299,6 +300,8 @@ def run_ours(args, rank, world, local_rank):
             line["paper_workload"] = paper
         if batch:
             line["batch"] = batch
+        if grad:
+            line["gradient"] = grad
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
@@ -379,6 +382,83 @@ def batch_workload(args, spock, workloads, dev, seed=0):
     return out
 
 
+def grad_workload(args, spock, workloads, dev):
+    """Gradients of the optimal cost (envelope theorem at the converged pair)
+    on 64 instances of the tree with branching 3 for 4 stages, N = 10
+    (607 nodes), nx = 20, nu = 8: one batched FP64 solve to 1e-8, then
+    spock_grad_dev per instance in FP64 and FP32 (CUDA events).  Time per
+    gradient is compared with the solve time per instance; instance 0 also
+    gets a central finite-difference check of dV/dx0 along a random
+    direction (h = 1e-6, solves to 1e-11)."""
+    import torch
+    cnt = args.grad_instances
+    ds = [workloads.large_tree(seed=s, branching_stages=4, branch=3, N=10, nx=20, nu=8) for s in range(cnt)]
+    probs = [spock.Problem(d) for d in ds]
+    b = spock.spock_batch_create([p.handle for p in probs])
+    x0s = [torch.tensor(d["x0"], dtype=torch.float64, device=dev) for d in ds]
+    zs = [torch.zeros(p.n_z, dtype=torch.float64, device=dev) for p in probs]
+    es = [torch.zeros(p.n_eta, dtype=torch.float64, device=dev) for p in probs]
+    st = spock.spock_default_settings(precision=spock.SPOCK_FP64, eps_abs=1e-8, eps_rel=1e-8, memory=5,
+                                      max_iter=20000)
+    spock.spock_batch_solve_dev(b, x0s, st, zs, es, 0)
+    torch.cuda.synchronize()
+    infos = spock.spock_batch_solve_dev(b, x0s, st, zs, es, 0)
+    torch.cuda.synchronize()
+    batch_ms = infos[0].solve_ms
+    single = spock.spock_solve_dev(probs[0].handle, x0s[0], st, zs[0].clone(), es[0].clone(), 0)
+    out = {"instances": cnt, "nodes": len(ds[0]["anc"]), "n_z": probs[0].n_z, "n_eta": probs[0].n_eta,
+           "solve_tol": 1e-8, "batch_solve_ms": round(batch_ms, 2),
+           "solve_ms_per_instance_batched": round(batch_ms / cnt, 3),
+           "solve_ms_single_instance0": round(single.solve_ms, 3),
+           "converged": sum(1 for i in infos if i.status == 0)}
+    n, nx, nu = len(ds[0]["anc"]), ds[0]["nx"], ds[0]["nu"]
+    g = {"x0": torch.zeros(nx, dtype=torch.float64, device=dev),
+         "A": torch.zeros(n, nx, nx, dtype=torch.float64, device=dev),
+         "B": torch.zeros(n, nx, nu, dtype=torch.float64, device=dev),
+         "Q": torch.zeros(n, nx, dtype=torch.float64, device=dev),
+         "R": torch.zeros(n, nu, dtype=torch.float64, device=dev),
+         "QN": torch.zeros(n, nx, dtype=torch.float64, device=dev)}
+    cur = torch.cuda.current_stream()
+    for prec, nm in ((spock.SPOCK_FP64, "fp64"), (spock.SPOCK_FP32, "fp32")):
+        for i in range(min(3, cnt)):   # warm-up
+            spock.spock_grad_dev(probs[i].handle, zs[i], es[i], prec, *g.values())
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(cur)
+        for i in range(cnt):
+            spock.spock_grad_dev(probs[i].handle, zs[i], es[i], prec, *g.values())
+        ev1.record(cur)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / cnt
+        out[f"grad_ms_{nm}"] = round(ms, 4)
+        out[f"grad_over_solve_{nm}"] = round(ms / (batch_ms / cnt), 4)
+    # finite-difference check of dV/dx0 on instance 0
+    spock.spock_grad_dev(probs[0].handle, zs[0], es[0], spock.SPOCK_FP64, *g.values())
+    gx0 = g["x0"].cpu().numpy()
+    rng = np.random.default_rng(7)
+    dirv = rng.standard_normal(nx)
+    dirv /= np.linalg.norm(dirv)
+    tight = spock.spock_default_settings(precision=spock.SPOCK_FP64, eps_abs=1e-11, eps_rel=1e-11, memory=5,
+                                         max_iter=100000)
+    h = 1e-6
+    vals = []
+    for sgn in (1.0, -1.0):
+        xp = torch.tensor(ds[0]["x0"] + sgn * h * dirv, dtype=torch.float64, device=dev)
+        z = torch.zeros(probs[0].n_z, dtype=torch.float64, device=dev)
+        e = torch.zeros(probs[0].n_eta, dtype=torch.float64, device=dev)
+        spock.spock_solve_dev(probs[0].handle, xp, tight, z, e, 0)
+        vals.append(float(z[0].item()))
+    fd = (vals[0] - vals[1]) / (2 * h)
+    an = float(gx0 @ dirv)
+    out["fd_check_x0"] = {"analytic": an, "central_fd": fd, "rel_err": abs(an - fd) / max(abs(fd), 1e-12),
+                          "h": h, "solve_tol": 1e-11}
+    spock.spock_free(b)
+    for p in probs:
+        p.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline(n_full, seconds=15.0):
     """The oracle (FP64 numpy/scipy, dense-structure KKT solve for S1) timed on
     a bounded sample: T evaluations on a 309-node tree of the same family,
@@ -442,6 +522,8 @@ def main():
     ap.add_argument("--paper-max-iter", type=int, default=20000)
     ap.add_argument("--batch", type=int, default=512, help="instances of the batched measurement (0 skips it)")
     ap.add_argument("--batch-iter", type=int, default=50)
+    ap.add_argument("--grad-instances", type=int, default=64,
+                    help="instances of the gradient measurement (0 skips it)")
     ap.add_argument("--branching-stages", type=int, default=6,
                     help="stages with 4 children (6 = the 62,805-node tree; smaller trees for profiling)")
     args = ap.parse_args()

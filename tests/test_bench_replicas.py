@@ -1,0 +1,55 @@
+"""Replica aggregation of bench.py on world size 2 (gloo, CPU): the job's
+time is the slowest rank's and its work the sum over ranks; each rank draws
+its own seeded instance."""
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(HERE))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import bench
+        from paper_2212_01110_gb300 import workloads
+        ms, units = bench.replica_reduce(10.0 * (rank + 1), 100 + rank, None)
+        x0 = workloads.large_tree(seed=rank, branching_stages=1, branch=2, N=3, nx=3, nu=2)["x0"]
+        q.put((rank, ms, units, x0.tolist()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_replica_reduce_world2():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ms, units, _ in res:
+        assert ms == 20.0          # max over ranks
+        assert units == 201.0      # sum over ranks
+    assert not np.allclose(res[0][3], res[1][3])   # seed = rank: distinct instances
+
+
+def test_replica_reduce_single_process():
+    import bench
+    assert bench.replica_reduce(3.5, 7, None) == (3.5, 7.0)
