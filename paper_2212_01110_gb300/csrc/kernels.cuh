@@ -7,6 +7,7 @@
 // Riccati factors and scratch in breadth-first ("internal") order.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -36,9 +37,54 @@ struct alignas(16) NodeDesc {
   int64_t zxp, zup;                // x and u of the parent in z
   int64_t es;                      // eta row holding s^k: enl + 2m + 1 (nonleaf) or elf + 2 nx (leaf)
   int32_t par, m, c0, user;        // parent, number of children, first child, caller's node id
-  int64_t pad1[2];
+  int64_t enr_c0, es_c0;           // enr and es of the first child (-1 at leaves)
 };
 static_assert(sizeof(NodeDesc) == 128, "NodeDesc must be 128 bytes");
+
+// A warp reads a NodeDesc as 32 four-byte words, one per lane (one coalesced
+// 128-byte load that can be issued a node ahead), and broadcasts the fields
+// with shuffles.  Word positions of the fields:
+enum NodeWord : int {
+  NW_ZX = 0, NW_ZU = 2, NW_ZZ2 = 4, NW_ZS = 6, NW_ZTAU = 8, NW_ENL = 10, NW_ENR = 12, NW_ELF = 14,
+  NW_ZXP = 16, NW_ZUP = 18, NW_ES = 20, NW_PAR = 22, NW_M = 23, NW_C0 = 24, NW_USER = 25,
+  NW_ENR_C0 = 26, NW_ES_C0 = 28
+};
+static_assert(offsetof(NodeDesc, zz2) == 4 * NW_ZZ2 && offsetof(NodeDesc, es) == 4 * NW_ES &&
+                  offsetof(NodeDesc, m) == 4 * NW_M && offsetof(NodeDesc, c0) == 4 * NW_C0 &&
+                  offsetof(NodeDesc, enr_c0) == 4 * NW_ENR_C0 && offsetof(NodeDesc, es_c0) == 4 * NW_ES_C0,
+              "NodeDesc word positions");
+
+struct NodeF {
+  int64_t zx, zu, zz2, zs, ztau, enl, enr, elf, zxp, zup, es, enr_c0, es_c0;
+  int32_t m, c0;
+};
+
+__device__ __forceinline__ uint32_t desc_word(const NodeDesc* desc, int64_t k, int lane) {
+  return __ldg(reinterpret_cast<const uint32_t*>(desc + k) + lane);
+}
+__device__ __forceinline__ int64_t desc_i64(uint32_t w, int i) {
+  const uint32_t lo = __shfl_sync(0xffffffffu, w, i), hi = __shfl_sync(0xffffffffu, w, i + 1);
+  return (int64_t)(((uint64_t)hi << 32) | (uint64_t)lo);
+}
+__device__ __forceinline__ NodeF node_fields(uint32_t w) {
+  NodeF f;
+  f.zx = desc_i64(w, NW_ZX);
+  f.zu = desc_i64(w, NW_ZU);
+  f.zz2 = desc_i64(w, NW_ZZ2);
+  f.zs = desc_i64(w, NW_ZS);
+  f.ztau = desc_i64(w, NW_ZTAU);
+  f.enl = desc_i64(w, NW_ENL);
+  f.enr = desc_i64(w, NW_ENR);
+  f.elf = desc_i64(w, NW_ELF);
+  f.zxp = desc_i64(w, NW_ZXP);
+  f.zup = desc_i64(w, NW_ZUP);
+  f.es = desc_i64(w, NW_ES);
+  f.enr_c0 = desc_i64(w, NW_ENR_C0);
+  f.es_c0 = desc_i64(w, NW_ES_C0);
+  f.m = (int32_t)__shfl_sync(0xffffffffu, w, NW_M);
+  f.c0 = (int32_t)__shfl_sync(0xffffffffu, w, NW_C0);
+  return f;
+}
 
 template <typename S>
 struct KP {
@@ -115,10 +161,12 @@ __device__ __forceinline__ S clampv(S v, S lo, S hi) {
   return v < lo ? lo : (v > hi ? hi : v);
 }
 
-// Statistics accumulator of one lane: sums in FP64; the terms of one node
-// block are first summed in the working precision S (a handful of entries
-// per lane), so that the FP64 pipe -- 1/64 of the FP32 rate on this GPU --
-// sees one add per node and statistic instead of one per entry.
+// Statistics accumulator of one lane: sums in FP64.  The terms of one node
+// are first summed in the working precision S (a handful of entries per
+// lane); in FP32 the node's sums are then reduced across the warp with
+// shuffles and one lane adds them in FP64, so that the FP64 pipe -- 1/64 of
+// the FP32 rate on this GPU -- sees eight operations per node instead of
+// eight per lane and node.  In FP64 every lane accumulates its own terms.
 struct StatAcc {
   double s[8];
   __device__ void zero() {
@@ -126,6 +174,11 @@ struct StatAcc {
     for (int i = 0; i < 8; ++i) s[i] = 0.0;
   }
 };
+__device__ __forceinline__ float warp_max_f(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
 template <typename S>
 struct NodeAcc {
   S s[8];
@@ -133,11 +186,22 @@ struct NodeAcc {
 #pragma unroll
     for (int i = 0; i < 8; ++i) s[i] = S(0);
   }
+  // called by all lanes of the warp, once per node
   __device__ __forceinline__ void flush(StatAcc& a) {
+    if (sizeof(S) == 4) {
+      const bool lead = (threadIdx.x & 31) == 0;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      if (i == 3 || i == 4) a.s[i] = fmax(a.s[i], (double)s[i]);
-      else a.s[i] += (double)s[i];
+      for (int i = 0; i < 8; ++i) {
+        const bool mx = (i == 3 || i == 4);
+        const float v = mx ? warp_max_f((float)s[i]) : warp_sum((float)s[i]);
+        if (lead) a.s[i] = mx ? fmax(a.s[i], (double)v) : a.s[i] + (double)v;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (i == 3 || i == 4) a.s[i] = fmax(a.s[i], (double)s[i]);
+        else a.s[i] += (double)s[i];
+      }
     }
     zero();
   }

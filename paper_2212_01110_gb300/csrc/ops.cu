@@ -1,96 +1,218 @@
 // Warp-per-node vector kernels of the CP operator T:
-//   k_prep   zbar = z - alpha L* eta; s^0 - alpha; proj_S2 on z_2; the (x, u)
-//            part goes to the Riccati scratch (prox of f, Sec. "Proximal
-//            operator of f", Sec. "Projection on S2").
+//   k_lstar  L* applied to eta (or to r_eta = eta - eta+), in three uses:
+//            LS_PREP   zbar = z - alpha L* eta; s^0 - alpha; proj_S2 on z_2;
+//                      the (x, u) part goes to the Riccati scratch (prox of
+//                      f, Sec. "Proximal operator of f", Sec. "Projection on
+//                      S2");
+//            LS_APPLY  z_out = L* eta (operator-level ABI);
+//            LS_STATS  primal residual statistics (xi_p, ||r_z||^2, r . d).
 //   k_dual   eta+ = prox_{alpha g*}(eta + alpha L (2 z+ - z)) with the cone
 //            projections of Eq. (S3-def); optional residual statistics
 //            (Sec. "The Chambolle-Pock method", Algorithm 3).  Also L z
 //            and prox_{alpha g*}(eta) alone for the operator-level ABI.
-//   k_primal L* eta, or the primal residual statistics (xi_p, ||r_z||^2).
 // L and its adjoint are never stored: each entry of eta = L z is a sum over
 // the node's own variables and its ancestor's (definition of L).
+//
+// Memory-level parallelism: a lane owns entries e = lane + 32 j, j < J, of
+// the node's blocks (J = ceil((nx + nu + 2) / 32), a template parameter), so
+// every load of a node is a predicated straight-line load into registers,
+// issued before any arithmetic; the node descriptor of the next node is
+// fetched (one word per lane) while the current one is processed.  Cone
+// norms are warp-shuffle reductions over registers: no shared memory and no
+// warp barriers inside the node loop.
 #include "kernels.cuh"
 #include "spock_internal.h"
 
 namespace spock {
 
 enum DualMode : int { DM_APPLY_L = 0, DM_PROXG = 1, DM_DUAL = 2 };
-enum PrimalMode : int { PM_APPLY_LT = 0, PM_STATS = 1 };
+enum LstarMode : int { LS_APPLY = 0, LS_STATS = 1, LS_PREP = 2 };
+constexpr int kMaxJ = (kMaxDim + 2 + 31) / 32;   // entries per lane for the largest blocks
 
 // ---------------------------------------------------------------------------
-// k_prep
+// k_lstar
 // ---------------------------------------------------------------------------
-template <typename S>
-__global__ void __launch_bounds__(128) k_prep(KP<S> p, const S* __restrict__ z,
-                                              const S* __restrict__ eta, S* __restrict__ zo) {
+// (L* w) at the entries of node k, from the rows of L that involve them:
+//   x^k, u^k  (nonleaf):  w_nl[x, u] + sum_c (Q^c or R^c)^1/2 w_nr^c[x, u]
+//   x^k       (leaf):     w_lf[x] + Q_N^1/2 w_lf[soc x]
+//   y^k_l:                w_nl[y_l] - b_l w_nl[s - b'y],   b = (p^children, 0, 1)
+//   tau^c:                (w_nr^c[tau 1] + w_nr^c[tau 2]) / 2
+//   s^c:                  w_nl^c[s - b'y] (c nonleaf) or (w_lf^c[s 1] + w_lf^c[s 2]) / 2
+//   s^0:                  w_nl^0[s - b'y]
+template <typename S, int MODE, bool DIR, int J>
+__global__ void __launch_bounds__(128) k_lstar(KP<S> p, const S* __restrict__ eta, const S* __restrict__ etap,
+                                               const S* __restrict__ z, const S* __restrict__ zp,
+                                               S* __restrict__ zo, const S* __restrict__ dir,
+                                               double* __restrict__ partials) {
   if (p.skip && *p.skip) return;
+  constexpr bool STATS = MODE == LS_STATS;
+  constexpr bool DR = STATS && DIR;
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
-  const S al = p.alpha;
   const int nx = p.nx, nu = p.nu;
+  const S al = p.alpha;
+  StatAcc acc;
+  acc.zero();
+  NodeAcc<S> nacc;
+  nacc.zero();
+  auto E = [&](int64_t i) -> S { return STATS ? eta[i] - etap[i] : eta[i]; };
+  // one z entry with its value of L* w: write it (APPLY) or accumulate the
+  // primal residual statistics (STATS)
+  auto emit = [&](int64_t zi, S lt) {
+    if (MODE == LS_APPLY) {
+      zo[zi] = lt;
+    } else if (STATS) {
+      const S rz = z[zi] - zp[zi];
+      nacc.s[ST_RZ2] += rz * rz;
+      nacc.s[ST_XIP] = fmax(nacc.s[ST_XIP], fabs(rz * p.inv_alpha - lt));
+      if (DR) nacc.s[ST_RD] += rz * dir[zi];
+    }
+  };
+  uint32_t wnext = gw < p.n ? desc_word(p.desc, gw, lane) : 0u;
   for (int k = gw; k < p.n; k += nw) {
-    const NodeDesc D = p.desc[k];
+    const NodeF D = node_fields(wnext);
+    if (k + nw < p.n) wnext = desc_word(p.desc, k + nw, lane);
     if (k < p.nl) {
       const int m = D.m, c0 = D.c0;
-      const int64_t el = D.enl, ex = el + 2 * m + 2, eu = ex + nx, z2 = D.zz2;
-      for (int r = lane; r < nx; r += 32) {
-        S acc = eta[ex + r];
-        for (int j = 0; j < m; ++j) acc += p.qs[(int64_t)(c0 + j) * nx + r] * eta[p.desc[c0 + j].enr + r];
-        p.xbar[(int64_t)k * p.xs + r] = z[D.zx + r] - al * acc;
+      const int nxu = nx + nu;
+      const int64_t ex = D.enl + 2 * m + 2;
+      // ---- (x, u): own rows and the first child's nonroot rows, in registers
+      S lt[J], zv[J], zpv[J], dv[J];
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const int e = lane + 32 * j;
+        lt[j] = zv[j] = zpv[j] = dv[j] = S(0);
+        if (e < nxu) {
+          const S coef = e < nx ? p.qs[(int64_t)c0 * nx + e] : p.rs[(int64_t)c0 * nu + (e - nx)];
+          lt[j] = E(ex + e) + coef * E(D.enr_c0 + e);
+          const int64_t zi = e < nx ? D.zx + e : D.zu + (e - nx);
+          if (MODE != LS_APPLY) zv[j] = z[zi];
+          if (STATS) zpv[j] = zp[zi];
+          if (DR) dv[j] = dir[zi];
+        }
       }
-      for (int r = lane; r < nu; r += 32) {
-        S acc = eta[eu + r];
-        for (int j = 0; j < m; ++j) acc += p.rs[(int64_t)(c0 + j) * nu + r] * eta[p.desc[c0 + j].enr + nx + r];
-        p.ubar[(int64_t)k * p.us + r] = z[D.zu + r] - al * acc;
+      for (int c = 1; c < m; ++c) {   // further children (branching stages only)
+        const int64_t er = __ldg(&p.desc[c0 + c].enr);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const int e = lane + 32 * j;
+          if (e < nxu) {
+            const S coef = e < nx ? p.qs[(int64_t)(c0 + c) * nx + e] : p.rs[(int64_t)(c0 + c) * nu + (e - nx)];
+            lt[j] += coef * E(er + e);
+          }
+        }
       }
-      // z_2 block: zbar = z - alpha L* eta, then projection on ker [E^T, -I, -I]
-      // with (M M^T)^-1 = (I - 11^T / (c + m)) / c, c = a^2 + 3 (Sherman-Morrison).
-      const S sb = eta[el + 2 * m + 1];
-      const S a = p.av[k];
-      const S cc = a * a + S(3);
-      const S y3 = z[z2 + 2 * m] - al * (eta[el + 2 * m] - sb);
-      auto bars = [&](int j, S& y1, S& y2, S& ta, S& sv) {
-        const int c = c0 + j;
-        const NodeDesc& Dc = p.desc[c];
-        const int64_t er = Dc.enr, es = Dc.es;
-        y1 = z[z2 + j] - al * (eta[el + j] - p.prob[c] * sb);
-        y2 = z[z2 + m + j] - al * eta[el + m + j];
-        ta = z[z2 + 2 * m + 1 + j] - al * S(0.5) * (eta[er + nx + nu] + eta[er + nx + nu + 1]);
-        const S ls = (c < p.nl) ? eta[es] : S(0.5) * (eta[es] + eta[es + 1]);
-        sv = z[z2 + 3 * m + 1 + j] - al * ls;
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const int e = lane + 32 * j;
+        if (e < nxu) {
+          if (MODE == LS_PREP) {
+            if (e < nx) p.xbar[(int64_t)k * p.xs + e] = zv[j] - al * lt[j];
+            else p.ubar[(int64_t)k * p.us + (e - nx)] = zv[j] - al * lt[j];
+          } else if (MODE == LS_APPLY) {
+            zo[e < nx ? D.zx + e : D.zu + (e - nx)] = lt[j];
+          } else {
+            const S rz = zv[j] - zpv[j];
+            nacc.s[ST_RZ2] += rz * rz;
+            nacc.s[ST_XIP] = fmax(nacc.s[ST_XIP], fabs(rz * p.inv_alpha - lt[j]));
+            if (DR) nacc.s[ST_RD] += rz * dv[j];
+          }
+        }
+      }
+      // ---- z_2 block
+      const int64_t el = D.enl, z2 = D.zz2;
+      const S sb = E(el + 2 * m + 1);
+      // child j's tau and s rows of L* w
+      auto child_rows = [&](int jc, S& tau_l, S& s_l) {
+        const int c = c0 + jc;
+        const int64_t er = jc == 0 ? D.enr_c0 : __ldg(&p.desc[c].enr);
+        const int64_t es = jc == 0 ? D.es_c0 : __ldg(&p.desc[c].es);
+        tau_l = S(0.5) * (E(er + nxu) + E(er + nxu + 1));
+        s_l = (c < p.nl) ? E(es) : S(0.5) * (E(es) + E(es + 1));
       };
-      S sumMw = 0;
-      for (int j = lane; j < m; j += 32) {
-        S y1, y2, ta, sv;
-        bars(j, y1, y2, ta, sv);
-        sumMw += a * y1 - y2 + y3 - ta - sv;
-      }
-      sumMw = warp_sum(sumMw);
-      S sumlam = 0;
-      for (int j = lane; j < m; j += 32) {
-        S y1, y2, ta, sv;
-        bars(j, y1, y2, ta, sv);
-        const S Mw = a * y1 - y2 + y3 - ta - sv;
-        const S lam = (Mw - sumMw / (cc + S(m))) / cc;
-        zo[z2 + j] = y1 - a * lam;
-        zo[z2 + m + j] = y2 + lam;
-        zo[z2 + 2 * m + 1 + j] = ta + lam;
-        zo[z2 + 3 * m + 1 + j] = sv + lam;
-        sumlam += lam;
-      }
-      sumlam = warp_sum(sumlam);
-      if (lane == 0) {
-        zo[z2 + 2 * m] = y3 - sumlam;
-        if (k == 0) zo[0] = (z[0] - al * sb) - al;   // prox of alpha * s^0
+      if (MODE != LS_PREP) {
+        for (int l = lane; l < 2 * m + 1; l += 32) {
+          const S bl = l < m ? p.prob[c0 + l] : (l < 2 * m ? S(0) : S(1));
+          emit(z2 + l, E(el + l) - bl * sb);
+        }
+        for (int jc = lane; jc < m; jc += 32) {
+          S tl, sl;
+          child_rows(jc, tl, sl);
+          emit(z2 + 2 * m + 1 + jc, tl);
+          emit(z2 + 3 * m + 1 + jc, sl);
+        }
+        if (k == 0 && lane == 0) emit(0, sb);
+      } else {
+        // zbar = z - alpha L* eta on z_2, then the projection on
+        // ker [E^T, -I, -I] with (M M^T)^-1 = (I - 11^T / (c + m)) / c,
+        // c = a^2 + 3 (Sherman-Morrison); M w = a y1 - y2 + y3 - tau - s per child.
+        const S a = p.av[k];
+        const S cc = a * a + S(3);
+        const S y3 = z[z2 + 2 * m] - al * (E(el + 2 * m) - sb);
+        auto bars = [&](int jc, S& y1, S& y2, S& ta, S& sv) {
+          S tl, sl;
+          child_rows(jc, tl, sl);
+          y1 = z[z2 + jc] - al * (E(el + jc) - p.prob[c0 + jc] * sb);
+          y2 = z[z2 + m + jc] - al * E(el + m + jc);
+          ta = z[z2 + 2 * m + 1 + jc] - al * tl;
+          sv = z[z2 + 3 * m + 1 + jc] - al * sl;
+        };
+        // children 0..31 kept in registers; further ones recomputed
+        S y1 = 0, y2 = 0, ta = 0, sv = 0, sumMw = 0;
+        if (lane < m) {
+          bars(lane, y1, y2, ta, sv);
+          sumMw = a * y1 - y2 + y3 - ta - sv;
+        }
+        for (int jc = lane + 32; jc < m; jc += 32) {
+          S b1, b2, bt, bs;
+          bars(jc, b1, b2, bt, bs);
+          sumMw += a * b1 - b2 + y3 - bt - bs;
+        }
+        sumMw = warp_sum(sumMw);
+        const S inv_cc = S(1) / cc;
+        const S shift = sumMw / (cc + S(m));
+        S sumlam = 0;
+        if (lane < m) {
+          const S lam = (a * y1 - y2 + y3 - ta - sv - shift) * inv_cc;
+          zo[z2 + lane] = y1 - a * lam;
+          zo[z2 + m + lane] = y2 + lam;
+          zo[z2 + 2 * m + 1 + lane] = ta + lam;
+          zo[z2 + 3 * m + 1 + lane] = sv + lam;
+          sumlam = lam;
+        }
+        for (int jc = lane + 32; jc < m; jc += 32) {
+          S b1, b2, bt, bs;
+          bars(jc, b1, b2, bt, bs);
+          const S lam = (a * b1 - b2 + y3 - bt - bs - shift) * inv_cc;
+          zo[z2 + jc] = b1 - a * lam;
+          zo[z2 + m + jc] = b2 + lam;
+          zo[z2 + 2 * m + 1 + jc] = bt + lam;
+          zo[z2 + 3 * m + 1 + jc] = bs + lam;
+          sumlam += lam;
+        }
+        sumlam = warp_sum(sumlam);
+        if (lane == 0) {
+          zo[z2 + 2 * m] = y3 - sumlam;
+          if (k == 0) zo[0] = (z[0] - al * sb) - al;   // prox of alpha * s^0
+        }
       }
     } else {
+      // ---- leaf: x^k
       const int64_t ef = D.elf;
-      for (int r = lane; r < nx; r += 32)
-        p.xbar[(int64_t)k * p.xs + r] =
-            z[D.zx + r] - al * (eta[ef + r] + p.qns[(int64_t)k * nx + r] * eta[ef + nx + r]);
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const int e = lane + 32 * j;
+        if (e < nx) {
+          const S lt = E(ef + e) + p.qns[(int64_t)k * nx + e] * E(ef + nx + e);
+          if (MODE == LS_PREP) p.xbar[(int64_t)k * p.xs + e] = z[D.zx + e] - al * lt;
+          else emit(D.zx + e, lt);
+        }
+      }
     }
+    if (STATS) nacc.flush(acc);
   }
+  if (STATS) block_stats_store(acc, partials);
 }
 
 // ---------------------------------------------------------------------------
@@ -100,284 +222,257 @@ __global__ void __launch_bounds__(128) k_prep(KP<S> p, const S* __restrict__ z,
 // direction (Ld).  For DM_DUAL, w = eta + alpha (2 Lzp - Lz) and the
 // residual row of L is L r_z = Lz - Lzp.
 
-template <typename S, int MODE, bool STATS, bool DIR>
-__device__ __forceinline__ void dual_emit(const KP<S>& p, NodeAcc<S>& acc, const S* __restrict__ eta,
-                                          S* __restrict__ out, const S* __restrict__ deta,
-                                          int64_t ie, S Lz, S Lzp, S Ld, S outv) {
-  out[ie] = outv;
-  if (MODE == DM_DUAL && STATS) {
-    const S re = eta[ie] - outv;
-    const S lrz = Lz - Lzp;
-    acc.s[ST_RE2] += re * re;
-    acc.s[ST_RE_LRZ] += re * lrz;
-    acc.s[ST_XID] = fmax(acc.s[ST_XID], fabs(re * p.inv_alpha - lrz));
-    if (DIR) {
-      const S de = deta[ie];
-      acc.s[ST_RD] += re * de;
-      acc.s[ST_LRZ_DE] += lrz * de;
-      acc.s[ST_RE_LDZ] += re * Ld;
-    }
-  }
-}
-
 template <typename S, int MODE>
-__device__ __forceinline__ S dual_w(const KP<S>& p, const S* __restrict__ eta, int64_t ie, S Lz, S Lzp) {
+__device__ __forceinline__ S dual_w(S alpha, S e, S Lz, S Lzp) {
   if (MODE == DM_APPLY_L) return Lz;
-  if (MODE == DM_PROXG) return eta[ie];
-  return eta[ie] + p.alpha * (S(2) * Lzp - Lz);
+  if (MODE == DM_PROXG) return e;
+  return e + alpha * (S(2) * Lzp - Lz);
 }
 
-// Translated SOC block: entries w[0..dim-1] already in the warp's buffer;
-// projects w / alpha onto SOC + (0, .., 1/2, -1/2) and returns, per entry,
-// w - alpha * projection.  SOC = {(v, t) : ||v|| <= t}, t the last entry.
-template <typename S>
-__device__ __forceinline__ void soc_prox(const S* wb, int dim, S ial, int lane, S& nv_out, S& t_out,
-                                         S& scale_out) {
-  S s2 = 0;
-  for (int e = lane; e < dim - 1; e += 32) {
-    S v = wb[e] * ial;
-    if (e == dim - 2) v -= S(0.5);
-    s2 += v * v;
+// Residual statistics of one eta row: r_eta = eta - eta+ against L r_z, and
+// with a direction d the inner products of the line search.
+template <typename S, bool ST, bool DR>
+__device__ __forceinline__ void dual_stat(NodeAcc<S>& a, S inv_alpha, S e_old, S e_new, S lrz, S de, S ld) {
+  if (!ST) return;
+  const S re = e_old - e_new;
+  a.s[ST_RE2] += re * re;
+  a.s[ST_RE_LRZ] += re * lrz;
+  a.s[ST_XID] = fmax(a.s[ST_XID], fabs(re * inv_alpha - lrz));
+  if (DR) {
+    a.s[ST_RD] += re * de;
+    a.s[ST_LRZ_DE] += lrz * de;
+    a.s[ST_RE_LDZ] += re * ld;
   }
-  s2 = warp_sum(s2);
-  nv_out = sqrt(s2);
-  t_out = wb[dim - 1] * ial + S(0.5);
-  // one division per block: scale of the v part when projecting on the boundary
-  scale_out = (nv_out > t_out && nv_out > -t_out) ? S(0.5) * (nv_out + t_out) / nv_out : S(0);
 }
 
+// Translated second-order cone: the block w (entries 0..dim-1, t = entry
+// dim-1) maps to w - alpha P(w / alpha - sh) - alpha sh with
+// sh = (0, .., 1/2, -1/2) and P the projection on SOC = {(v, t): ||v|| <= t}.
+// nv = ||v||, t the cone coordinate, scale = (nv + t) / (2 nv) on the
+// boundary case (one division per block).
 template <typename S>
-__device__ __forceinline__ S soc_out(const S* wb, int dim, int e, S al, S ial, S nv, S t, S scale) {
-  // projection of (v, t) = w / alpha - shift
-  S v = wb[e] * ial;
+__device__ __forceinline__ S soc_entry(S wv, int e, int dim, S al, S ial, S nv, S t, S scale) {
+  S v = wv * ial;
   if (e == dim - 2) v -= S(0.5);
   if (e == dim - 1) v = t;
   S pr;
-  if (nv <= t) {
-    pr = v;
-  } else if (nv <= -t) {
-    pr = S(0);
-  } else {
-    pr = (e == dim - 1) ? S(0.5) * (nv + t) : scale * v;
-  }
+  if (nv <= t) pr = v;
+  else if (nv <= -t) pr = S(0);
+  else pr = (e == dim - 1) ? S(0.5) * (nv + t) : scale * v;
   if (e == dim - 2) pr += S(0.5);
   if (e == dim - 1) pr -= S(0.5);
-  return wb[e] - al * pr;
+  return wv - al * pr;
 }
 
-template <typename S, int MODE, bool STATS, bool DIR>
+// Norm data of the translated SOC block held in registers w[j] (entry
+// lane + 32 j; entries >= dim are ignored).
+template <typename S, int J>
+__device__ __forceinline__ void soc_norm(const S (&w)[J], int dim, S ial, int lane, S& nv, S& t, S& scale) {
+  S s2 = 0, wt = 0;
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int e = lane + 32 * j;
+    if (e < dim - 1) {
+      S v = w[j] * ial;
+      if (e == dim - 2) v -= S(0.5);
+      s2 += v * v;
+    } else if (e == dim - 1) {
+      wt = w[j];
+    }
+  }
+  s2 = warp_sum(s2);
+  wt = __shfl_sync(kFull, wt, (dim - 1) & 31);
+  nv = sqrt(s2);
+  t = wt * ial + S(0.5);
+  scale = (nv > t && nv > -t) ? S(0.5) * (nv + t) / nv : S(0);
+}
+
+template <typename S, int MODE, bool STATS, bool DIR, int J>
 __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, const S* __restrict__ zp,
                                               const S* __restrict__ eta, S* __restrict__ out,
                                               const S* __restrict__ dir, double* __restrict__ partials) {
   if (p.skip && *p.skip) return;
-  __shared__ S wbuf[kWarpsPerBlock][kVecPad];
-  __shared__ S lbuf[kWarpsPerBlock][kVecPad];   // L r_z of SOC rows (statistics)
-  __shared__ S dbuf[kWarpsPerBlock][kVecPad];   // L d_z of SOC rows
-  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  const S al = p.alpha;
-  const int nx = p.nx, nu = p.nu;
-  const S* dz = DIR ? dir : nullptr;
-  const S* deta = DIR ? dir + p.n_z : nullptr;
-  StatAcc acc;
-  acc.zero();
-  NodeAcc<S> nacc;
-  nacc.zero();
-  const S ial = p.inv_alpha;
-  S* wb = wbuf[wl];
-  S* lb = lbuf[wl];
-  S* db = dbuf[wl];
-  auto row = [&](int64_t zi, S coef, S& Lz, S& Lzp, S& Ld) {
-    if (MODE == DM_PROXG) {  // no z in this mode
-      Lz = Lzp = Ld = S(0);
-      return;
-    }
-    Lz = coef * z[zi];
-    Lzp = (MODE == DM_DUAL) ? coef * zp[zi] : S(0);
-    Ld = DIR ? coef * dz[zi] : S(0);
-  };
-  for (int k = gw; k < p.n; k += nw) {
-    const NodeDesc D = p.desc[k];
-    // ---- nonleaf block (y, s - b'y, x, u)
-    if (k < p.nl) {
-      const int m = D.m, c0 = D.c0;
-      const int64_t el = D.enl, z2 = D.zz2;
-      for (int e = lane; e < 2 * m + 1; e += 32) {
-        S Lz, Lzp, Ld;
-        row(z2 + e, S(1), Lz, Lzp, Ld);
-        const S w = dual_w<S, MODE>(p, eta, el + e, Lz, Lzp);
-        const S o = (MODE == DM_APPLY_L) ? w : (e < 2 * m ? fmin(w, S(0)) : S(0));
-        dual_emit<S, MODE, STATS, DIR>(p, nacc, eta, out, deta, el + e, Lz, Lzp, Ld, o);
-      }
-      {  // s^k - b^T y^k, b = (p^children, 0, 1)
-        S bz = 0, bzp = 0, bd = 0;
-        for (int j = lane; j < m && MODE != DM_PROXG; j += 32) {
-          const S pj = p.prob[c0 + j];
-          bz += pj * z[z2 + j];
-          if (MODE == DM_DUAL) bzp += pj * zp[z2 + j];
-          if (DIR) bd += pj * dz[z2 + j];
-        }
-        bz = warp_sum(bz);
-        if (MODE == DM_DUAL) bzp = warp_sum(bzp);
-        if (DIR) bd = warp_sum(bd);
-        if (lane == 0) {
-          const int64_t si = D.zs;
-          const S Lz = (MODE == DM_PROXG) ? S(0) : z[si] - (bz + z[z2 + 2 * m]);
-          const S Lzp = (MODE == DM_DUAL) ? zp[si] - (bzp + zp[z2 + 2 * m]) : S(0);
-          const S Ld = DIR ? dz[si] - (bd + dz[z2 + 2 * m]) : S(0);
-          const int64_t ie = el + 2 * m + 1;
-          const S w = dual_w<S, MODE>(p, eta, ie, Lz, Lzp);
-          const S o = (MODE == DM_APPLY_L) ? w : fmin(w, S(0));
-          dual_emit<S, MODE, STATS, DIR>(p, nacc, eta, out, deta, ie, Lz, Lzp, Ld, o);
-        }
-      }
-      const int64_t ex = el + 2 * m + 2;
-      for (int e = lane; e < nx + nu; e += 32) {
-        S Lz, Lzp, Ld, lo, hi;
-        if (e < nx) {
-          row(D.zx + e, S(1), Lz, Lzp, Ld);
-          lo = p.xlo[(int64_t)k * nx + e];
-          hi = p.xhi[(int64_t)k * nx + e];
-        } else {
-          row(D.zu + (e - nx), S(1), Lz, Lzp, Ld);
-          lo = p.ulo[(int64_t)k * nu + (e - nx)];
-          hi = p.uhi[(int64_t)k * nu + (e - nx)];
-        }
-        const S w = dual_w<S, MODE>(p, eta, ex + e, Lz, Lzp);
-        const S o = (MODE == DM_APPLY_L) ? w : w - al * clampv(w * ial, lo, hi);
-        dual_emit<S, MODE, STATS, DIR>(p, nacc, eta, out, deta, ex + e, Lz, Lzp, Ld, o);
-      }
-    }
-    // ---- nonroot block (Q^1/2 x^anc, R^1/2 u^anc, tau/2, tau/2)
-    if (k > 0) {
-      const int64_t er = D.enr;
-      const int dim = nx + nu + 2;
-      for (int e = lane; e < dim; e += 32) {
-        S Lz, Lzp, Ld;
-        if (e < nx) row(D.zxp + e, p.qs[(int64_t)k * nx + e], Lz, Lzp, Ld);
-        else if (e < nx + nu) row(D.zup + (e - nx), p.rs[(int64_t)k * nu + (e - nx)], Lz, Lzp, Ld);
-        else row(D.ztau, S(0.5), Lz, Lzp, Ld);
-        wb[e] = dual_w<S, MODE>(p, eta, er + e, Lz, Lzp);
-        lb[e] = Lz - Lzp;
-        db[e] = Ld;
-        if (MODE == DM_APPLY_L) out[er + e] = wb[e];
-      }
-      __syncwarp();
-      if (MODE != DM_APPLY_L) {
-        S nv, t, sc;
-        soc_prox(wb, dim, ial, lane, nv, t, sc);
-        for (int e = lane; e < dim; e += 32) {
-          const S o = soc_out(wb, dim, e, al, ial, nv, t, sc);
-          // Lz - Lzp = lb[e]; pass (lb, 0) so that dual_emit sees L r_z
-          dual_emit<S, MODE, STATS, DIR>(p, nacc, eta, out, deta, er + e, lb[e], S(0), db[e], o);
-        }
-      }
-      __syncwarp();
-    }
-    // ---- leaf block (x, Q_N^1/2 x, s/2, s/2)
-    if (k >= p.nl) {
-      const int64_t ef = D.elf;
-      for (int e = lane; e < nx; e += 32) {
-        S Lz, Lzp, Ld;
-        row(D.zx + e, S(1), Lz, Lzp, Ld);
-        const S w = dual_w<S, MODE>(p, eta, ef + e, Lz, Lzp);
-        const S o = (MODE == DM_APPLY_L) ? w
-                                         : w - al * clampv(w * ial, p.xlo[(int64_t)k * nx + e], p.xhi[(int64_t)k * nx + e]);
-        dual_emit<S, MODE, STATS, DIR>(p, nacc, eta, out, deta, ef + e, Lz, Lzp, Ld, o);
-      }
-      const int dim = nx + 2;
-      const int64_t es = ef + nx;
-      for (int e = lane; e < dim; e += 32) {
-        S Lz, Lzp, Ld;
-        if (e < nx) row(D.zx + e, p.qns[(int64_t)k * nx + e], Lz, Lzp, Ld);
-        else row(D.zs, S(0.5), Lz, Lzp, Ld);
-        wb[e] = dual_w<S, MODE>(p, eta, es + e, Lz, Lzp);
-        lb[e] = Lz - Lzp;
-        db[e] = Ld;
-        if (MODE == DM_APPLY_L) out[es + e] = wb[e];
-      }
-      __syncwarp();
-      if (MODE != DM_APPLY_L) {
-        S nv, t, sc;
-        soc_prox(wb, dim, ial, lane, nv, t, sc);
-        for (int e = lane; e < dim; e += 32) {
-          const S o = soc_out(wb, dim, e, al, ial, nv, t, sc);
-          dual_emit<S, MODE, STATS, DIR>(p, nacc, eta, out, deta, es + e, lb[e], S(0), db[e], o);
-        }
-      }
-      __syncwarp();
-    }
-    if (MODE == DM_DUAL && STATS) nacc.flush(acc);
-  }
-  if (MODE == DM_DUAL && STATS) block_stats_store(acc, partials);
-}
-
-// ---------------------------------------------------------------------------
-// k_primal: L* applied to E = eta (PM_APPLY_LT) or to r_eta = eta - eta+
-// (PM_STATS, with r_z = z - z+ and optional direction).
-// ---------------------------------------------------------------------------
-template <typename S, int MODE, bool DIR>
-__global__ void __launch_bounds__(128) k_primal(KP<S> p, const S* __restrict__ eta, const S* __restrict__ etap,
-                                                const S* __restrict__ z, const S* __restrict__ zp,
-                                                S* __restrict__ zout, const S* __restrict__ dir,
-                                                double* __restrict__ partials) {
-  if (p.skip && *p.skip) return;
+  constexpr bool HZ = MODE != DM_PROXG;     // rows of L at z
+  constexpr bool HZP = MODE == DM_DUAL;     // ... and at z+
+  constexpr bool HE = MODE != DM_APPLY_L;   // eta is read
+  constexpr bool ST = MODE == DM_DUAL && STATS;
+  constexpr bool DR = ST && DIR;
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
+  const S al = p.alpha, ial = p.inv_alpha;
   const int nx = p.nx, nu = p.nu;
+  const S* dz = DR ? dir : nullptr;
+  const S* deta = DR ? dir + p.n_z : nullptr;
   StatAcc acc;
   acc.zero();
   NodeAcc<S> nacc;
   nacc.zero();
-  auto E = [&](int64_t i) -> S { return MODE == PM_APPLY_LT ? eta[i] : eta[i] - etap[i]; };
-  auto emit = [&](int64_t zi, S lt) {
-    if (MODE == PM_APPLY_LT) {
-      zout[zi] = lt;
-    } else {
-      const S rz = z[zi] - zp[zi];
-      nacc.s[ST_RZ2] += rz * rz;
-      nacc.s[ST_XIP] = fmax(nacc.s[ST_XIP], fabs(rz * p.inv_alpha - lt));
-      if (DIR) nacc.s[ST_RD] += rz * dir[zi];
-    }
-  };
+  uint32_t wnext = gw < p.n ? desc_word(p.desc, gw, lane) : 0u;
   for (int k = gw; k < p.n; k += nw) {
-    const NodeDesc D = p.desc[k];
-    if (k < p.nl) {
-      const int m = D.m, c0 = D.c0;
-      const int64_t el = D.enl, ex = el + 2 * m + 2, eu = ex + nx, z2 = D.zz2;
-      for (int r = lane; r < nx; r += 32) {
-        S acc2 = E(ex + r);
-        for (int j = 0; j < m; ++j) acc2 += p.qs[(int64_t)(c0 + j) * nx + r] * E(p.desc[c0 + j].enr + r);
-        emit(D.zx + r, acc2);
+    const NodeF D = node_fields(wnext);
+    if (k + nw < p.n) wnext = desc_word(p.desc, k + nw, lane);
+    const bool nonleaf = k < p.nl;
+    const int na = nonleaf ? nx + nu : nx;          // own (x, u) or x entries
+    const int64_t ea = nonleaf ? D.enl + 2 * D.m + 2 : D.elf;   // eta row of the box on x^k
+    const int nb = nx + nu + 2;                      // nonroot block
+    // ---- loads: own (x, u) with its box rows, the nonroot block, s^k
+    S az[J], azp[J], adz[J], ae[J], ade[J], alo[J], ahi[J];
+    S bz[J], bzp[J], bdz[J], bc[J], be[J], bde[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int e = lane + 32 * j;
+      az[j] = azp[j] = adz[j] = ae[j] = ade[j] = alo[j] = ahi[j] = S(0);
+      bz[j] = bzp[j] = bdz[j] = bc[j] = be[j] = bde[j] = S(0);
+      if (e < na) {
+        const int64_t zi = e < nx ? D.zx + e : D.zu + (e - nx);
+        if (HZ) az[j] = z[zi];
+        if (HZP) azp[j] = zp[zi];
+        if (DR) adz[j] = dz[zi];
+        if (HE) ae[j] = eta[ea + e];
+        if (DR) ade[j] = deta[ea + e];
+        if (MODE != DM_APPLY_L) {
+          alo[j] = e < nx ? p.xlo[(int64_t)k * nx + e] : p.ulo[(int64_t)k * nu + (e - nx)];
+          ahi[j] = e < nx ? p.xhi[(int64_t)k * nx + e] : p.uhi[(int64_t)k * nu + (e - nx)];
+        }
       }
-      for (int r = lane; r < nu; r += 32) {
-        S acc2 = E(eu + r);
-        for (int j = 0; j < m; ++j) acc2 += p.rs[(int64_t)(c0 + j) * nu + r] * E(p.desc[c0 + j].enr + nx + r);
-        emit(D.zu + r, acc2);
+      if (k > 0 && e < nb) {
+        const int64_t zi = e < nx ? D.zxp + e : (e < nx + nu ? D.zup + (e - nx) : D.ztau);
+        bc[j] = e < nx ? p.qs[(int64_t)k * nx + e] : (e < nx + nu ? p.rs[(int64_t)k * nu + (e - nx)] : S(0.5));
+        if (HZ) bz[j] = z[zi];
+        if (HZP) bzp[j] = zp[zi];
+        if (DR) bdz[j] = dz[zi];
+        if (HE) be[j] = eta[D.enr + e];
+        if (DR) bde[j] = deta[D.enr + e];
       }
-      const S sb = E(el + 2 * m + 1);
-      for (int l = lane; l < 2 * m + 1; l += 32) {
-        const S bl = l < m ? p.prob[c0 + l] : (l < 2 * m ? S(0) : S(1));
-        emit(z2 + l, E(el + l) - bl * sb);
-      }
-      for (int j = lane; j < m; j += 32) {
-        const int c = c0 + j;
-        const NodeDesc& Dc = p.desc[c];
-        const int64_t er = Dc.enr, es = Dc.es;
-        emit(z2 + 2 * m + 1 + j, S(0.5) * (E(er + nx + nu) + E(er + nx + nu + 1)));
-        emit(z2 + 3 * m + 1 + j, (c < p.nl) ? E(es) : S(0.5) * (E(es) + E(es + 1)));
-      }
-      if (k == 0 && lane == 0) emit(0, sb);
-    } else {
-      const int64_t ef = D.elf;
-      for (int r = lane; r < nx; r += 32)
-        emit(D.zx + r, E(ef + r) + p.qns[(int64_t)k * nx + r] * E(ef + nx + r));
     }
-    if (MODE == PM_STATS) nacc.flush(acc);
+    const S sz = HZ ? z[D.zs] : S(0), szp = HZP ? zp[D.zs] : S(0), sdz = DR ? dz[D.zs] : S(0);
+    // ---- box rows on the node's own x (and u)
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int e = lane + 32 * j;
+      if (e < na) {
+        const S Lz = az[j], Lzp = azp[j];
+        const S w = dual_w<S, MODE>(al, ae[j], Lz, Lzp);
+        const S o = (MODE == DM_APPLY_L) ? w : w - al * clampv(w * ial, alo[j], ahi[j]);
+        out[ea + e] = o;
+        dual_stat<S, ST, DR>(nacc, ial, ae[j], o, Lz - Lzp, ade[j], adz[j]);
+      }
+    }
+    // ---- nonroot block: SOC on (Q^1/2 x^anc, R^1/2 u^anc, tau/2, tau/2)
+    if (k > 0) {
+      S w[J], lrz[J], ld[J];
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const S Lz = bc[j] * bz[j], Lzp = bc[j] * bzp[j];
+        w[j] = dual_w<S, MODE>(al, be[j], Lz, Lzp);
+        lrz[j] = Lz - Lzp;
+        ld[j] = bc[j] * bdz[j];
+      }
+      if (MODE == DM_APPLY_L) {
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+          if (lane + 32 * j < nb) out[D.enr + lane + 32 * j] = w[j];
+      } else {
+        S nv, t, sc;
+        soc_norm<S, J>(w, nb, ial, lane, nv, t, sc);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const int e = lane + 32 * j;
+          if (e < nb) {
+            const S o = soc_entry(w[j], e, nb, al, ial, nv, t, sc);
+            out[D.enr + e] = o;
+            dual_stat<S, ST, DR>(nacc, ial, be[j], o, lrz[j], bde[j], ld[j]);
+          }
+        }
+      }
+    }
+    if (nonleaf) {
+      // ---- y rows (K* cone: y1, y2 <= 0 after the prox, y3 free) and the
+      // s - b'y row, b = (p^children, 0, 1)
+      const int m = D.m, c0 = D.c0;
+      const int64_t el = D.enl, z2 = D.zz2;
+      S bs = 0, bsp = 0, bsd = 0;
+      for (int e = lane; e < 2 * m + 1; e += 32) {
+        const S Lz = HZ ? z[z2 + e] : S(0);
+        const S Lzp = HZP ? zp[z2 + e] : S(0);
+        const S Ld = DR ? dz[z2 + e] : S(0);
+        const S ev = HE ? eta[el + e] : S(0);
+        const S w = dual_w<S, MODE>(al, ev, Lz, Lzp);
+        const S o = (MODE == DM_APPLY_L) ? w : (e < 2 * m ? fmin(w, S(0)) : S(0));
+        out[el + e] = o;
+        dual_stat<S, ST, DR>(nacc, ial, ev, o, Lz - Lzp, DR ? deta[el + e] : S(0), Ld);
+        if (e < m) {
+          const S pj = p.prob[c0 + e];
+          bs += pj * Lz;
+          bsp += pj * Lzp;
+          bsd += pj * Ld;
+        }
+      }
+      if (MODE != DM_PROXG) {
+        bs = warp_sum(bs);
+        if (HZP) bsp = warp_sum(bsp);
+        if (DR) bsd = warp_sum(bsd);
+      }
+      if (lane == 0) {
+        const int64_t ie = el + 2 * m + 1;
+        const S y3 = HZ ? z[z2 + 2 * m] : S(0), y3p = HZP ? zp[z2 + 2 * m] : S(0), y3d = DR ? dz[z2 + 2 * m] : S(0);
+        const S Lz = sz - (bs + y3), Lzp = HZP ? szp - (bsp + y3p) : S(0), Ld = DR ? sdz - (bsd + y3d) : S(0);
+        const S ev = HE ? eta[ie] : S(0);
+        const S w = dual_w<S, MODE>(al, ev, Lz, Lzp);
+        const S o = (MODE == DM_APPLY_L) ? w : fmin(w, S(0));
+        out[ie] = o;
+        dual_stat<S, ST, DR>(nacc, ial, ev, o, Lz - Lzp, DR ? deta[ie] : S(0), Ld);
+      }
+    } else {
+      // ---- leaf SOC on (Q_N^1/2 x, s/2, s/2)
+      const int dim = nx + 2;
+      const int64_t es = D.elf + nx;
+      S w[J], lrz[J], ld[J], ev[J], dev[J];
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const int e = lane + 32 * j;
+        S c = S(0), Lz = S(0), Lzp = S(0), Ld = S(0);
+        ev[j] = dev[j] = S(0);
+        if (e < dim) {
+          if (e < nx) {
+            c = p.qns[(int64_t)k * nx + e];
+            Lz = c * az[j];
+            Lzp = c * azp[j];
+            Ld = c * adz[j];
+          } else {
+            Lz = S(0.5) * sz;
+            Lzp = S(0.5) * szp;
+            Ld = S(0.5) * sdz;
+          }
+          if (HE) ev[j] = eta[es + e];
+          if (DR) dev[j] = deta[es + e];
+        }
+        w[j] = dual_w<S, MODE>(al, ev[j], Lz, Lzp);
+        lrz[j] = Lz - Lzp;
+        ld[j] = Ld;
+      }
+      if (MODE == DM_APPLY_L) {
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+          if (lane + 32 * j < dim) out[es + lane + 32 * j] = w[j];
+      } else {
+        S nv, t, sc;
+        soc_norm<S, J>(w, dim, ial, lane, nv, t, sc);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const int e = lane + 32 * j;
+          if (e < dim) {
+            const S o = soc_entry(w[j], e, dim, al, ial, nv, t, sc);
+            out[es + e] = o;
+            dual_stat<S, ST, DR>(nacc, ial, ev[j], o, lrz[j], dev[j], ld[j]);
+          }
+        }
+      }
+    }
+    if (ST) nacc.flush(acc);
   }
-  if (MODE == PM_STATS) block_stats_store(acc, partials);
+  if (ST) block_stats_store(acc, partials);
 }
 
 // Sums (maxima for xi) of the per-block partial statistics of the dual and
@@ -405,36 +500,65 @@ inline int warp_grid(int n, int max_blocks) {
   return b < max_blocks ? (b > 0 ? b : 1) : max_blocks;
 }
 
+// entries per lane for blocks of nx + nu + 2 entries
+inline int lane_slots(int nx, int nu) { return (nx + nu + 2 + 31) / 32; }
+
+template <typename S, int MODE, bool DIR>
+static void lstar_j(const KP<S>& p, const S* eta, const S* etap, const S* z, const S* zp, S* zo, const S* dir,
+                    double* partials, int grid, cudaStream_t st) {
+  switch (lane_slots(p.nx, p.nu)) {
+    case 1: k_lstar<S, MODE, DIR, 1><<<grid, 128, 0, st>>>(p, eta, etap, z, zp, zo, dir, partials); break;
+    case 2: k_lstar<S, MODE, DIR, 2><<<grid, 128, 0, st>>>(p, eta, etap, z, zp, zo, dir, partials); break;
+    case 3: k_lstar<S, MODE, DIR, 3><<<grid, 128, 0, st>>>(p, eta, etap, z, zp, zo, dir, partials); break;
+    case 4: k_lstar<S, MODE, DIR, 4><<<grid, 128, 0, st>>>(p, eta, etap, z, zp, zo, dir, partials); break;
+    default: k_lstar<S, MODE, DIR, kMaxJ><<<grid, 128, 0, st>>>(p, eta, etap, z, zp, zo, dir, partials); break;
+  }
+}
+
+template <typename S, int MODE, bool STATS, bool DIR>
+static void dual_j(const KP<S>& p, const S* z, const S* zp, const S* eta, S* out, const S* dir, double* partials,
+                   int grid, cudaStream_t st) {
+  switch (lane_slots(p.nx, p.nu)) {
+    case 1: k_dual<S, MODE, STATS, DIR, 1><<<grid, 128, 0, st>>>(p, z, zp, eta, out, dir, partials); break;
+    case 2: k_dual<S, MODE, STATS, DIR, 2><<<grid, 128, 0, st>>>(p, z, zp, eta, out, dir, partials); break;
+    case 3: k_dual<S, MODE, STATS, DIR, 3><<<grid, 128, 0, st>>>(p, z, zp, eta, out, dir, partials); break;
+    case 4: k_dual<S, MODE, STATS, DIR, 4><<<grid, 128, 0, st>>>(p, z, zp, eta, out, dir, partials); break;
+    default: k_dual<S, MODE, STATS, DIR, kMaxJ><<<grid, 128, 0, st>>>(p, z, zp, eta, out, dir, partials); break;
+  }
+}
+
 template <typename S>
 void launch_prep(const KP<S>& p, const S* z, const S* eta, S* zo, int max_blocks, cudaStream_t st) {
-  k_prep<S><<<warp_grid(p.n, max_blocks), 128, 0, st>>>(p, z, eta, zo);
+  lstar_j<S, LS_PREP, false>(p, eta, nullptr, z, nullptr, zo, nullptr, nullptr, warp_grid(p.n, max_blocks), st);
 }
 
 template <typename S>
 void launch_dual(const KP<S>& p, int mode, bool stats, const S* z, const S* zp, const S* eta, S* out,
                  const S* dir, double* partials, int grid, cudaStream_t st) {
+  // operator-level modes (not on the solve path) use the widest lane layout
   if (mode == DM_APPLY_L) {
-    k_dual<S, DM_APPLY_L, false, false><<<grid, 128, 0, st>>>(p, z, zp, eta, out, dir, partials);
+    k_dual<S, DM_APPLY_L, false, false, kMaxJ><<<grid, 128, 0, st>>>(p, z, zp, eta, out, dir, partials);
   } else if (mode == DM_PROXG) {
-    k_dual<S, DM_PROXG, false, false><<<grid, 128, 0, st>>>(p, z, zp, eta, out, dir, partials);
+    k_dual<S, DM_PROXG, false, false, kMaxJ><<<grid, 128, 0, st>>>(p, z, zp, eta, out, dir, partials);
   } else if (!stats) {
-    k_dual<S, DM_DUAL, false, false><<<grid, 128, 0, st>>>(p, z, zp, eta, out, dir, partials);
+    dual_j<S, DM_DUAL, false, false>(p, z, zp, eta, out, dir, partials, grid, st);
   } else if (dir) {
-    k_dual<S, DM_DUAL, true, true><<<grid, 128, 0, st>>>(p, z, zp, eta, out, dir, partials);
+    dual_j<S, DM_DUAL, true, true>(p, z, zp, eta, out, dir, partials, grid, st);
   } else {
-    k_dual<S, DM_DUAL, true, false><<<grid, 128, 0, st>>>(p, z, zp, eta, out, dir, partials);
+    dual_j<S, DM_DUAL, true, false>(p, z, zp, eta, out, dir, partials, grid, st);
   }
 }
 
+// mode 0: z_out = L* eta; mode 1: primal residual statistics
 template <typename S>
 void launch_primal(const KP<S>& p, int mode, const S* eta, const S* etap, const S* z, const S* zp, S* zout,
                    const S* dir, double* partials, int grid, cudaStream_t st) {
-  if (mode == PM_APPLY_LT) {
-    k_primal<S, PM_APPLY_LT, false><<<grid, 128, 0, st>>>(p, eta, etap, z, zp, zout, dir, partials);
+  if (mode == 0) {
+    k_lstar<S, LS_APPLY, false, kMaxJ><<<grid, 128, 0, st>>>(p, eta, etap, z, zp, zout, dir, partials);
   } else if (dir) {
-    k_primal<S, PM_STATS, true><<<grid, 128, 0, st>>>(p, eta, etap, z, zp, zout, dir, partials);
+    lstar_j<S, LS_STATS, true>(p, eta, etap, z, zp, zout, dir, partials, grid, st);
   } else {
-    k_primal<S, PM_STATS, false><<<grid, 128, 0, st>>>(p, eta, etap, z, zp, zout, dir, partials);
+    lstar_j<S, LS_STATS, false>(p, eta, etap, z, zp, zout, dir, partials, grid, st);
   }
 }
 

@@ -1319,6 +1319,10 @@ static int problem_create(const Tree& tree, int32_t nx, int32_t nu, const double
         q.zup = k > 0 ? o.zu[t.parent[k]] : -1;
         q.es = k < nl ? o.enl[k] + 2 * t.ch_count[k] + 1 : o.elf[k] + 2 * nx;
       }
+      for (int32_t k = 0; k < n; ++k) {
+        dh[k].enr_c0 = t.ch_count[k] > 0 ? dh[t.ch_begin[k]].enr : -1;
+        dh[k].es_c0 = t.ch_count[k] > 0 ? dh[t.ch_begin[k]].es : -1;
+      }
       P->idx.desc = upload(*P, dh);
     }
     P->err = upload(*P, std::vector<int32_t>(1, 0));

@@ -48,4 +48,8 @@ def cases():
         "wide_50_20": W.large_tree(0, branching_stages=2, branch=3, N=5, nx=50, nu=20),
         "wide_100_28": W.random_tree(7, N=3, max_branch=2, nx=100, nu=28, stable=True),
         "a0_a1": W.random_tree(8, N=3, max_branch=3, nx=3, nu=2, a_range=(0.0, 0.0)),
+        # nodes with more than 16 and more than 32 children: the y block
+        # (2m + 1 entries) and the children of a node span several warp chunks
+        "root_40": W.with_tree(W.tree_from_branching([40, 1])[0], seed=9, nx=3, nu=2),
+        "root_17_2": W.with_tree(W.tree_from_branching([17, 2])[0], seed=10, nx=4, nu=2, a=0.3),
     }

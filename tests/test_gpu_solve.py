@@ -15,7 +15,7 @@ from tests.gpu_common import RTOL, Pair, cases, rel_err
 
 pytestmark = pytest.mark.gpu
 CASES = cases()
-NAMES = ["binary_N3", "fig1", "ragged", "chains", "pure_chain", "wide_50_20", "a0_a1"]
+NAMES = ["binary_N3", "fig1", "ragged", "chains", "pure_chain", "wide_50_20", "a0_a1", "root_40"]
 
 
 @pytest.fixture(scope="module", params=NAMES)
