@@ -50,6 +50,14 @@ def measured_peaks():
 # 2 FP64 FMA per clock per SM.  Used as the ALU roofline of the FP64 path.
 FP64_PEAK_TFLOPS = 1.193
 
+# DRAM bytes (read + write) per chain of one launch of the backward chain
+# kernels, from ncu captures on the 15,701-node tree (1,024 chains of 14
+# nonleaf nodes, nx = 50, nu = 20; profiles/k_bwd_chain_f64_f32_15701node_tree.md),
+# scaled by the chains of the measured tree (each chain reads its own factors
+# once).  Valid for these kernels as captured; remeasure after changing them.
+NCU_TRAFFIC_PER_CHAIN = {"fp64": 739.82e6 / 1024, "fp32": 372.24e6 / 1024}
+NCU_CHAIN_SHAPE = (14, 50, 20)   # chain length, nx, nu of the capture
+
 
 
 def replica_reduce(ms, units, dev=None):
@@ -187,6 +195,11 @@ def run_ours(args, rank, world, local_rank):
         ms, nT_all = replica_reduce(ev0.elapsed_time(ev1), nT, dev)
         return ms, nT, nT_all, infos, clk.summary()
 
+    def traffic(prec):
+        if (chain_len, d["nx"], d["nu"]) != NCU_CHAIN_SHAPE:
+            return None
+        return round(NCU_TRAFFIC_PER_CHAIN["fp64" if prec == spock.SPOCK_FP64 else "fp32"] * n_chains)
+
     def roofline(infos, prec):
         elt = 8 if prec == spock.SPOCK_FP64 else 4
         timed_T = sum(i.n_timed for i in infos)
@@ -201,7 +214,7 @@ def run_ours(args, rank, world, local_rank):
             r = {"kernel": "k_bwd_chain<double>", "bound": "alu", "achieved": round(ach, 4),
                  "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
                  "peak_source": "measured FP64 FMA microbenchmark on this pool",
-                 "traffic": None, "algorithmic_bytes": bb, "algorithmic_flops": fl,
+                 "traffic": traffic(prec), "algorithmic_bytes": bb, "algorithmic_flops": fl,
                  "hbm_achieved_gbs": round(bb / (t_bwd * 1e-3) / 1e9, 1),
                  "hbm_frac_of_measured": round(bb / (t_bwd * 1e-3) / 1e9 / hbm, 4),
                  "avg_launch_ms": round(t_bwd, 4)}
@@ -209,7 +222,7 @@ def run_ours(args, rank, world, local_rank):
             ach = bb / (t_bwd * 1e-3) / 1e9
             r = {"kernel": "k_bwd_chain<float>", "bound": "hbm", "achieved": round(ach, 1), "peak": hbm,
                  "unit": "GB/s", "frac": round(ach / hbm, 4), "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
-                 "traffic": None, "algorithmic_bytes": bb, "avg_launch_ms": round(t_bwd, 4)}
+                 "traffic": traffic(prec), "algorithmic_bytes": bb, "avg_launch_ms": round(t_bwd, 4)}
         fb = bytes_fwd_chain(d, n_chains, chain_len, elt)
         r["fwd_chain"] = {"avg_launch_ms": round(t_fwd, 4), "algorithmic_bytes": fb,
                           "achieved_gbs": round(fb / (t_fwd * 1e-3) / 1e9, 1) if t_fwd > 0 else None}

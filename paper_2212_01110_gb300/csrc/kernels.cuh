@@ -161,12 +161,13 @@ __device__ __forceinline__ S clampv(S v, S lo, S hi) {
   return v < lo ? lo : (v > hi ? hi : v);
 }
 
-// Statistics accumulator of one lane: sums in FP64.  The terms of one node
-// are first summed in the working precision S (a handful of entries per
-// lane); in FP32 the node's sums are then reduced across the warp with
-// shuffles and one lane adds them in FP64, so that the FP64 pipe -- 1/64 of
-// the FP32 rate on this GPU -- sees eight operations per node instead of
-// eight per lane and node.  In FP64 every lane accumulates its own terms.
+// Statistics accumulator of one lane: sums in FP64.  Terms are first summed
+// in the working precision S; FP32 lanes convert and add to FP64 once every
+// kFlushNodes nodes (a few hundred terms at most), FP64 lanes once per node.
+// Each flush costs eight FP64-pipe warp instructions (plus conversions in
+// FP32) whatever the number of active lanes, and that pipe runs at 1/64 of
+// the FP32 rate on this GPU, so flushing per node would dominate the FP32
+// vector kernels.
 struct StatAcc {
   double s[8];
   __device__ void zero() {
@@ -174,36 +175,27 @@ struct StatAcc {
     for (int i = 0; i < 8; ++i) s[i] = 0.0;
   }
 };
-__device__ __forceinline__ float warp_max_f(float v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
-  return v;
-}
+constexpr int kFlushNodes = 16;
 template <typename S>
 struct NodeAcc {
   S s[8];
+  int nodes;
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int i = 0; i < 8; ++i) s[i] = S(0);
+    nodes = 0;
   }
-  // called by all lanes of the warp, once per node
   __device__ __forceinline__ void flush(StatAcc& a) {
-    if (sizeof(S) == 4) {
-      const bool lead = (threadIdx.x & 31) == 0;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const bool mx = (i == 3 || i == 4);
-        const float v = mx ? warp_max_f((float)s[i]) : warp_sum((float)s[i]);
-        if (lead) a.s[i] = mx ? fmax(a.s[i], (double)v) : a.s[i] + (double)v;
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        if (i == 3 || i == 4) a.s[i] = fmax(a.s[i], (double)s[i]);
-        else a.s[i] += (double)s[i];
-      }
+    for (int i = 0; i < 8; ++i) {
+      if (i == 3 || i == 4) a.s[i] = fmax(a.s[i], (double)s[i]);
+      else a.s[i] += (double)s[i];
     }
     zero();
+  }
+  // end of a node: flush when due
+  __device__ __forceinline__ void node_done(StatAcc& a) {
+    if (sizeof(S) == 8 || ++nodes == kFlushNodes) flush(a);
   }
 };
 

@@ -210,9 +210,12 @@ __global__ void __launch_bounds__(128) k_lstar(KP<S> p, const S* __restrict__ et
         }
       }
     }
-    if (STATS) nacc.flush(acc);
+    if (STATS) nacc.node_done(acc);
   }
-  if (STATS) block_stats_store(acc, partials);
+  if (STATS) {
+    nacc.flush(acc);
+    block_stats_store(acc, partials);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -470,9 +473,12 @@ __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, 
         }
       }
     }
-    if (ST) nacc.flush(acc);
+    if (ST) nacc.node_done(acc);
   }
-  if (ST) block_stats_store(acc, partials);
+  if (ST) {
+    nacc.flush(acc);
+    block_stats_store(acc, partials);
+  }
 }
 
 // Sums (maxima for xi) of the per-block partial statistics of the dual and

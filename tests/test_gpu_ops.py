@@ -47,10 +47,11 @@ def test_prox_gconj(pair, alpha_scale):
     assert rel_err(out.cpu().numpy(), prox_gconj(eta, alpha, pair.op)) < RTOL
 
 
-@pytest.fixture(params=["auto", "grp", "tma", "direct"])
+@pytest.fixture(params=["auto", "grp", "tma", "direct", "pair"])
 def kernels(request, monkeypatch):
     """Every Riccati kernel family: the default per-pass choice, three warps
-    per chain, one warp per chain with bulk-copy staging, direct loads."""
+    per chain, one warp per chain with bulk-copy staging, direct loads, two
+    warps per chain on the backward pass."""
     monkeypatch.setenv("SPOCK_RICCATI_KERNELS", request.param)
     return request.param
 
