@@ -156,6 +156,17 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
+// Working-precision math with the precision fixed by the argument type (no
+// promotion of FP32 arguments to the FP64 pipe).
+__device__ __forceinline__ float vabs(float v) { return fabsf(v); }
+__device__ __forceinline__ double vabs(double v) { return fabs(v); }
+__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float vsqrt(float v) { return sqrtf(v); }
+__device__ __forceinline__ double vsqrt(double v) { return sqrt(v); }
+
 template <typename S>
 __device__ __forceinline__ S clampv(S v, S lo, S hi) {
   return v < lo ? lo : (v > hi ? hi : v);

@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(128) k_lstar(KP<S> p, const S* __restrict__ et
     } else if (STATS) {
       const S rz = z[zi] - zp[zi];
       nacc.s[ST_RZ2] += rz * rz;
-      nacc.s[ST_XIP] = fmax(nacc.s[ST_XIP], fabs(rz * p.inv_alpha - lt));
+      nacc.s[ST_XIP] = vmax(nacc.s[ST_XIP], vabs(rz * p.inv_alpha - lt));
       if (DR) nacc.s[ST_RD] += rz * dir[zi];
     }
   };
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(128) k_lstar(KP<S> p, const S* __restrict__ et
           } else {
             const S rz = zv[j] - zpv[j];
             nacc.s[ST_RZ2] += rz * rz;
-            nacc.s[ST_XIP] = fmax(nacc.s[ST_XIP], fabs(rz * p.inv_alpha - lt[j]));
+            nacc.s[ST_XIP] = vmax(nacc.s[ST_XIP], vabs(rz * p.inv_alpha - lt[j]));
             if (DR) nacc.s[ST_RD] += rz * dv[j];
           }
         }
@@ -240,7 +240,7 @@ __device__ __forceinline__ void dual_stat(NodeAcc<S>& a, S inv_alpha, S e_old, S
   const S re = e_old - e_new;
   a.s[ST_RE2] += re * re;
   a.s[ST_RE_LRZ] += re * lrz;
-  a.s[ST_XID] = fmax(a.s[ST_XID], fabs(re * inv_alpha - lrz));
+  a.s[ST_XID] = vmax(a.s[ST_XID], vabs(re * inv_alpha - lrz));
   if (DR) {
     a.s[ST_RD] += re * de;
     a.s[ST_LRZ_DE] += lrz * de;
@@ -285,7 +285,7 @@ __device__ __forceinline__ void soc_norm(const S (&w)[J], int dim, S ial, int la
   }
   s2 = warp_sum(s2);
   wt = __shfl_sync(kFull, wt, (dim - 1) & 31);
-  nv = sqrt(s2);
+  nv = vsqrt(s2);
   t = wt * ial + S(0.5);
   scale = (nv > t && nv > -t) ? S(0.5) * (nv + t) / nv : S(0);
 }
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, 
         const S Ld = DR ? dz[z2 + e] : S(0);
         const S ev = HE ? eta[el + e] : S(0);
         const S w = dual_w<S, MODE>(al, ev, Lz, Lzp);
-        const S o = (MODE == DM_APPLY_L) ? w : (e < 2 * m ? fmin(w, S(0)) : S(0));
+        const S o = (MODE == DM_APPLY_L) ? w : (e < 2 * m ? vmin(w, S(0)) : S(0));
         out[el + e] = o;
         dual_stat<S, ST, DR>(nacc, ial, ev, o, Lz - Lzp, DR ? deta[el + e] : S(0), Ld);
         if (e < m) {
@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, 
         const S Lz = sz - (bs + y3), Lzp = HZP ? szp - (bsp + y3p) : S(0), Ld = DR ? sdz - (bsd + y3d) : S(0);
         const S ev = HE ? eta[ie] : S(0);
         const S w = dual_w<S, MODE>(al, ev, Lz, Lzp);
-        const S o = (MODE == DM_APPLY_L) ? w : fmin(w, S(0));
+        const S o = (MODE == DM_APPLY_L) ? w : vmin(w, S(0));
         out[ie] = o;
         dual_stat<S, ST, DR>(nacc, ial, ev, o, Lz - Lzp, DR ? deta[ie] : S(0), Ld);
       }

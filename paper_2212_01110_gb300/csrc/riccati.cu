@@ -28,7 +28,6 @@
 
 #include "kernels.cuh"
 #include "spock_internal.h"
-#include "tma.cuh"
 
 namespace spock {
 
@@ -188,120 +187,6 @@ __global__ void __launch_bounds__(128) k_bwd_chain(KP<S> p) {
 }
 
 // ---------------------------------------------------------------------------
-// backward, chain region: two warps per chain ("pair"), loads straight from
-// global memory.  Twice the resident warps of k_bwd_chain for the same
-// chains, which the FP64 pipe needs to stay busy.  Per chain step:
-//   A  h = [Abar | B]^T q   rows split between the warps (r = half mod 2);
-//      warp 1 leaves its partial h in shared memory;
-//   B  warp 0: g = ubar - h_u, d = Rt^-1 g (stored), d - ubar;
-//   C  q = h_x - xbar + K^T (d - ubar) + W d, the sum over b split between
-//      the warps (b = half mod 2), each warp leaving a partial q; the next
-//      step reads q as the sum of the two partials.
-// Named barrier 1 + pair (64 threads) after A, B and C.
-// ---------------------------------------------------------------------------
-template <typename S, int SL>
-__global__ void __launch_bounds__(128) k_bwd_chain_pair(KP<S> p) {
-  if (p.skip && *p.skip) return;
-  __shared__ S sh_h[2][kVecPad];         // [pair] warp 1's partial h
-  __shared__ S sh_q[2][2][kVecPad];      // [pair][warp] partial q
-  __shared__ S sh_g[2][kMaxDim];         // [pair] ubar - h_u
-  __shared__ S sh_d[2][kMaxDim];         // [pair] d
-  __shared__ S sh_m[2][kMaxDim];         // [pair] d - ubar
-  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  const int pr = wl >> 1, half = wl & 1;
-  const int bar = 1 + pr;
-  const int gp = blockIdx.x * 2 + pr, np = gridDim.x * 2;
-  const int nx = p.nx, nu = p.nu, ncol = nx + nu;
-  S* qa = sh_q[pr][0];
-  S* qb = sh_q[pr][1];
-  S* qm = sh_q[pr][half];
-  for (int ci = gp; ci < p.n_chains; ci += np) {
-    const int leaf = p.stage_begin[p.N] + ci;
-    for (int r = lane; r < nx; r += 32) qm[r] = half == 0 ? -p.xbar[(int64_t)leaf * p.xs + r] : S(0);
-    named_bar(bar, 64);
-    int k = -1;
-    for (int t = p.N - 1; t >= p.chain_stage; --t) {
-      k = p.stage_begin[t] + ci;
-      const int c = p.stage_begin[t + 1] + ci;
-      // A
-      S h[SL];
-#pragma unroll
-      for (int s = 0; s < SL; ++s) h[s] = S(0);
-      const S* __restrict__ G = p.Gb + (int64_t)(c - 1) * p.gstride;
-#pragma unroll 5
-      for (int r = half; r < nx; r += 2) {
-        const S qr = qa[r] + qb[r];
-        const S* row = G + (int64_t)r * ncol;
-#pragma unroll
-        for (int s = 0; s < SL; ++s) {
-          const int col = 32 * s + lane;
-          if (col < ncol) h[s] += __ldg(row + col) * qr;
-        }
-      }
-      if (half == 1) {
-#pragma unroll
-        for (int s = 0; s < SL; ++s) {
-          const int col = 32 * s + lane;
-          if (col < ncol) sh_h[pr][col] = h[s];
-        }
-      }
-      named_bar(bar, 64);
-      const S* __restrict__ Km = p.NB + (int64_t)k * p.nbstride;
-      const S* __restrict__ Wt = Km + (int64_t)nu * nx;
-      const S* __restrict__ Ri = Km + 2 * (int64_t)nu * nx;
-      const S* ub = p.ubar + (int64_t)k * p.us;
-      // B
-      if (half == 0) {
-#pragma unroll
-        for (int s = 0; s < SL; ++s) {
-          const int col = 32 * s + lane;
-          if (col < ncol) h[s] += sh_h[pr][col];
-          if (col >= nx && col < ncol) sh_g[pr][col - nx] = ub[col - nx] - h[s];
-        }
-        __syncwarp();
-        for (int a = lane; a < nu; a += 32) {
-          S acc = 0;
-          for (int b = 0; b < nu; ++b) acc += __ldg(Ri + a * nu + b) * sh_g[pr][b];
-          sh_d[pr][a] = acc;
-          sh_m[pr][a] = acc - ub[a];
-          p.d[(int64_t)k * p.us + a] = acc;
-        }
-      }
-      named_bar(bar, 64);
-      // C
-      S qn[SL];
-      const S* xb = p.xbar + (int64_t)k * p.xs;
-#pragma unroll
-      for (int s = 0; s < SL; ++s) {
-        const int r = 32 * s + lane;
-        qn[s] = (half == 0 && r < nx) ? h[s] - xb[r] : S(0);
-      }
-#pragma unroll 5
-      for (int b = half; b < nu; b += 2) {
-        const S db = sh_d[pr][b];
-        const S dmu = sh_m[pr][b];
-        const S* kr = Km + (int64_t)b * nx;
-        const S* wr = Wt + (int64_t)b * nx;
-#pragma unroll
-        for (int s = 0; s < SL; ++s) {
-          const int r = 32 * s + lane;
-          if (r < nx) qn[s] += __ldg(kr + r) * dmu + __ldg(wr + r) * db;
-        }
-      }
-#pragma unroll
-      for (int s = 0; s < SL; ++s) {
-        const int r = 32 * s + lane;
-        if (r < nx) qm[r] = qn[s];
-      }
-      named_bar(bar, 64);
-    }
-    if (half == 0)
-      for (int r = lane; r < nx; r += 32) p.q[(int64_t)k * p.xs + r] = qa[r] + qb[r];
-    named_bar(bar, 64);
-  }
-}
-
-// ---------------------------------------------------------------------------
 // backward, one branching stage: warp per node
 // ---------------------------------------------------------------------------
 template <typename S, int SL>
@@ -454,7 +339,7 @@ int launch_fwd_chain_grp(const KP<S>& p, S* zo, cudaStream_t st);
 // loses more at the barriers than it gains -- and "direct" for FP64 where
 // the staged variant fits too few warps per SM (tma_chain_fits).
 // SPOCK_RICCATI_KERNELS forces one family everywhere (the tests cover each).
-enum ChainFamily { CF_AUTO = -1, CF_GRP = 0, CF_TMA = 1, CF_DIRECT = 2, CF_PAIR = 3 };
+enum ChainFamily { CF_AUTO = -1, CF_GRP = 0, CF_TMA = 1, CF_DIRECT = 2 };
 constexpr int kStagedMaxNodes = 2048;  // FP64 stages with more nodes use the direct kernels
 // Per-thread override set by the batch autotuner while it times candidates
 // and captures an instance (-2 = none).
@@ -468,7 +353,6 @@ static int chain_family() {
   if (e[0] == 'd') return CF_DIRECT;
   if (e[0] == 't') return CF_TMA;
   if (e[0] == 'g') return CF_GRP;
-  if (e[0] == 'p') return CF_PAIR;
   return CF_AUTO;
 }
 
@@ -482,17 +366,13 @@ int riccati_passes_sl(const KP<S>& p, const std::vector<int32_t>& stage_begin,
   const int fam = chain_family();
   const bool grp_ok = fam != CF_DIRECT && fam != CF_TMA && grp_chain_fits(p);
   const bool bwd_grp = fam == CF_GRP && grp_ok;
-  const bool fwd_grp = (fam == CF_GRP || fam == CF_AUTO || fam == CF_PAIR) && grp_ok;
+  const bool fwd_grp = (fam == CF_GRP || fam == CF_AUTO) && grp_ok;
   const bool tma_chain = fam != CF_DIRECT && tma_chain_fits(p);
   const bool tma_stage = fam != CF_DIRECT && tma_stage_fits(p);
   int launches = 0;
   if (p.n_chains > 0 && cs < p.N) {
     if (bwd_grp) {
       launches += launch_bwd_chain_grp<S>(p, st);
-    } else if (fam == CF_PAIR) {
-      const int grid = (p.n_chains + 1) / 2;
-      k_bwd_chain_pair<S, SL><<<grid, 128, 0, st>>>(p);
-      ++launches;
     } else if (tma_chain) {
       launches += launch_bwd_chain_tma<S, SL>(p, st);
     } else {

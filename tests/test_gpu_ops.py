@@ -47,11 +47,10 @@ def test_prox_gconj(pair, alpha_scale):
     assert rel_err(out.cpu().numpy(), prox_gconj(eta, alpha, pair.op)) < RTOL
 
 
-@pytest.fixture(params=["auto", "grp", "tma", "direct", "pair"])
+@pytest.fixture(params=["auto", "grp", "tma", "direct"])
 def kernels(request, monkeypatch):
     """Every Riccati kernel family: the default per-pass choice, three warps
-    per chain, one warp per chain with bulk-copy staging, direct loads, two
-    warps per chain on the backward pass."""
+    per chain, one warp per chain with bulk-copy staging, direct loads."""
     monkeypatch.setenv("SPOCK_RICCATI_KERNELS", request.param)
     return request.param
 
