@@ -289,19 +289,23 @@ int spock_grad_dev(spock_problem* p, const double* z, const double* eta, int32_t
  * spock_batch_create -- a batch of independent problems (any trees, depths,
  * nx, nu) solved together by spock_batch_solve_dev.  The problems stay owned
  * by the caller and must outlive the batch; a problem may belong to one
- * batch at a time.  n >= 1.
+ * batch at a time and appears in it once (SPOCK_ERR_INVALID_ARG otherwise:
+ * every instance needs its own iterate buffers).  n >= 1.
  */
 int spock_batch_create(int32_t n, spock_problem* const* problems, spock_batch** out);
 
 /*
  * spock_batch_solve_dev -- Algorithm 3 on every problem of the batch.
- * All instances advance together: the rounds of every instance (decision,
- * Anderson update, next point, evaluation of T) are captured once into one
- * CUDA graph with one parallel branch per instance, and each graph launch
- * advances every unfinished instance by a fixed number of rounds (finished
- * instances skip their kernels); the host only reads the done flags after
- * each launch.  Before the first capture the Riccati kernel family of each
- * instance is chosen by timing candidate evaluations of T (autotuner).
+ * All instances advance together, round by round (decision, Anderson
+ * update, next point, evaluation of T): each kernel of a round is launched
+ * once for the whole batch, its blocks mapped to (instance, block of that
+ * instance) by tables built once per batch, so a round costs the same
+ * number of launches for 1 or 10,000 instances.  A fixed number of rounds
+ * is captured into one CUDA graph; finished instances skip their work; the
+ * host only reads the done flags after each graph launch.  Before the first
+ * solve in a precision, the node tile of the vector kernels (nodes per
+ * warp: 1, 2 or 4) is picked by timing batched evaluations of T
+ * (autotuner).  info.solve_ms and info.n_launches describe the whole batch.
  *   x0_dev, z_dev, eta_dev : host arrays of n device pointers (FP64), per
  *     instance as in spock_solve_dev.
  *   settings : shared by all instances (alpha <= 0: each instance's own

@@ -1,0 +1,70 @@
+// Batched SPOCK: one launch per kernel type covers every instance of a
+// batch.  Each instance keeps its own problem view, iterate buffers and
+// SuperMann state; a block finds its instance, and its block index within
+// that instance, in the launch's block map (built once per batch on the
+// host), then runs the same body as the single-problem kernel.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+#include "supermann.cuh"
+
+namespace spock {
+
+// One instance as the batched kernels see it.  kp.skip points at st->done,
+// so every kernel of a finished instance returns at once.
+template <typename S>
+struct BInst {
+  KP<S> kp;
+  SmState* st;
+  S* V;     // accepted iterate and T of it
+  S* TV;
+  S* Vp;    // previously accepted pair (Anderson differences)
+  S* TVp;
+  S* Vt;    // evaluation point and T of it
+  S* TVt;
+  S* d;     // direction
+  S* MR;    // Anderson columns (stride ld)
+  S* D;
+  double* stats;   // [8] statistics of the last evaluation
+  double* pd;      // partial statistics of the dual kernel, nb_node rows
+  double* pp;      // ... of the primal statistics kernel, nb_node rows
+  double* paa;     // partial Gram rows of the commit kernel, nb_vec rows
+  int64_t n_v, ld;
+  int32_t nb_node, nb_vec;
+};
+
+// Block -> instance map of one batched launch: block b runs for instance
+// inst[b] as its block b - base[inst[b]] of cnt[inst[b]]; stage[i] is the
+// instance's tree stage for the stage-by-stage Riccati launches.
+struct BMap {
+  const int32_t* inst;
+  const int32_t* base;
+  const int32_t* cnt;
+  const int32_t* stage;
+};
+
+// ops.cu: which = 0 prox-f preparation (L* eta, proj_S2), 1 dual update with
+// statistics, 2 primal statistics, 3 reduction of the statistics (one block
+// per instance; m unused).  J = lane slots for blocks of nx + nu + 2.
+template <typename S>
+void launch_node_ops_b(int which, const BInst<S>* bi, const BMap& m, int nblocks, int n_inst, int J,
+                       cudaStream_t st);
+// riccati.cu: which = 0 backward chains, 1 backward stage, 2 forward stage,
+// 3 forward chains (direct kernels, warp per chain / node); SL = lane slots
+// for nx + nu.
+template <typename S>
+void launch_riccati_b(int which, const BInst<S>* bi, const BMap& m, int nblocks, int SL, cudaStream_t st);
+// rounds.cu: the four kernels of a round.
+template <typename S>
+void launch_round_decide_b(const BInst<S>* bi, int n_inst, cudaStream_t st);
+template <typename S>
+void launch_round_commit_b(const BInst<S>* bi, const BMap& m, int nblocks, int mem, cudaStream_t st);
+template <typename S>
+void launch_round_aa_solve_b(const BInst<S>* bi, int n_inst, cudaStream_t st);
+template <typename S>
+void launch_round_point_b(const BInst<S>* bi, const BMap& m, int nblocks, int mem, cudaStream_t st);
+
+}  // namespace spock

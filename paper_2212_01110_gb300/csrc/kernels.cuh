@@ -210,9 +210,9 @@ struct NodeAcc {
   }
 };
 
-// Reduces the per-lane statistics of a block and writes one row of partials.
-// Sums for sums, maxima for ST_XIP / ST_XID.
-__device__ __forceinline__ void block_stats_store(StatAcc& a, double* partials) {
+// Reduces the per-lane statistics of a block and writes row `row` of the
+// partials.  Sums for sums, maxima for ST_XIP / ST_XID.
+__device__ __forceinline__ void block_stats_store(StatAcc& a, double* partials, int row) {
   __shared__ double red[kWarpsPerBlock][8];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -227,7 +227,7 @@ __device__ __forceinline__ void block_stats_store(StatAcc& a, double* partials) 
     double v = red[0][i];
     for (int k = 1; k < kWarpsPerBlock; ++k)
       v = (i == ST_XIP || i == ST_XID) ? fmax(v, red[k][i]) : v + red[k][i];
-    partials[(int64_t)blockIdx.x * 8 + i] = v;
+    partials[(int64_t)row * 8 + i] = v;
   }
 }
 

@@ -20,6 +20,7 @@
 // fetched (one word per lane) while the current one is processed.  Cone
 // norms are warp-shuffle reductions over registers: no shared memory and no
 // warp barriers inside the node loop.
+#include "batch.cuh"
 #include "kernels.cuh"
 #include "spock_internal.h"
 
@@ -39,17 +40,19 @@ constexpr int kMaxJ = (kMaxDim + 2 + 31) / 32;   // entries per lane for the lar
 //   tau^c:                (w_nr^c[tau 1] + w_nr^c[tau 2]) / 2
 //   s^c:                  w_nl^c[s - b'y] (c nonleaf) or (w_lf^c[s 1] + w_lf^c[s 2]) / 2
 //   s^0:                  w_nl^0[s - b'y]
+// Body shared by the single-problem and the batched kernels: block `bid` of
+// `nblk` working for problem p.
 template <typename S, int MODE, bool DIR, int J>
-__global__ void __launch_bounds__(128) k_lstar(KP<S> p, const S* __restrict__ eta, const S* __restrict__ etap,
-                                               const S* __restrict__ z, const S* __restrict__ zp,
-                                               S* __restrict__ zo, const S* __restrict__ dir,
-                                               double* __restrict__ partials) {
+__device__ __forceinline__ void lstar_body(const KP<S>& p, int bid, int nblk, const S* __restrict__ eta,
+                                           const S* __restrict__ etap, const S* __restrict__ z,
+                                           const S* __restrict__ zp, S* __restrict__ zo,
+                                           const S* __restrict__ dir, double* __restrict__ partials) {
   if (p.skip && *p.skip) return;
   constexpr bool STATS = MODE == LS_STATS;
   constexpr bool DR = STATS && DIR;
   const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int gw = (bid * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (nblk * blockDim.x) >> 5;
   const int nx = p.nx, nu = p.nu;
   const S al = p.alpha;
   StatAcc acc;
@@ -214,8 +217,16 @@ __global__ void __launch_bounds__(128) k_lstar(KP<S> p, const S* __restrict__ et
   }
   if (STATS) {
     nacc.flush(acc);
-    block_stats_store(acc, partials);
+    block_stats_store(acc, partials, bid);
   }
+}
+
+template <typename S, int MODE, bool DIR, int J>
+__global__ void __launch_bounds__(128) k_lstar(KP<S> p, const S* __restrict__ eta, const S* __restrict__ etap,
+                                               const S* __restrict__ z, const S* __restrict__ zp,
+                                               S* __restrict__ zo, const S* __restrict__ dir,
+                                               double* __restrict__ partials) {
+  lstar_body<S, MODE, DIR, J>(p, blockIdx.x, gridDim.x, eta, etap, z, zp, zo, dir, partials);
 }
 
 // ---------------------------------------------------------------------------
@@ -291,9 +302,10 @@ __device__ __forceinline__ void soc_norm(const S (&w)[J], int dim, S ial, int la
 }
 
 template <typename S, int MODE, bool STATS, bool DIR, int J>
-__global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, const S* __restrict__ zp,
-                                              const S* __restrict__ eta, S* __restrict__ out,
-                                              const S* __restrict__ dir, double* __restrict__ partials) {
+__device__ __forceinline__ void dual_body(const KP<S>& p, int bid, int nblk, const S* __restrict__ z,
+                                          const S* __restrict__ zp, const S* __restrict__ eta,
+                                          S* __restrict__ out, const S* __restrict__ dir,
+                                          double* __restrict__ partials) {
   if (p.skip && *p.skip) return;
   constexpr bool HZ = MODE != DM_PROXG;     // rows of L at z
   constexpr bool HZP = MODE == DM_DUAL;     // ... and at z+
@@ -301,8 +313,8 @@ __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, 
   constexpr bool ST = MODE == DM_DUAL && STATS;
   constexpr bool DR = ST && DIR;
   const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int gw = (bid * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (nblk * blockDim.x) >> 5;
   const S al = p.alpha, ial = p.inv_alpha;
   const int nx = p.nx, nu = p.nu;
   const S* dz = DR ? dir : nullptr;
@@ -477,14 +489,22 @@ __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, 
   }
   if (ST) {
     nacc.flush(acc);
-    block_stats_store(acc, partials);
+    block_stats_store(acc, partials, bid);
   }
+}
+
+template <typename S, int MODE, bool STATS, bool DIR, int J>
+__global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, const S* __restrict__ zp,
+                                              const S* __restrict__ eta, S* __restrict__ out,
+                                              const S* __restrict__ dir, double* __restrict__ partials) {
+  dual_body<S, MODE, STATS, DIR, J>(p, blockIdx.x, gridDim.x, z, zp, eta, out, dir, partials);
 }
 
 // Sums (maxima for xi) of the per-block partial statistics of the dual and
 // primal kernels; one block, fixed order (deterministic).
-__global__ void k_reduce_stats(const double* __restrict__ pd, int nd, const double* __restrict__ pp, int np,
-                               double* __restrict__ out, const int32_t* __restrict__ skip) {
+__device__ __forceinline__ void reduce_stats_body(const double* __restrict__ pd, int nd,
+                                                  const double* __restrict__ pp, int np, double* __restrict__ out,
+                                                  const int32_t* __restrict__ skip) {
   if (skip && *skip) return;
   __shared__ double red[8][32];
   const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;  // 8 warps, one per statistic
@@ -496,6 +516,47 @@ __global__ void k_reduce_stats(const double* __restrict__ pd, int nd, const doub
   if (lane == 0) red[i][0] = v;
   __syncthreads();
   if (threadIdx.x < 8) out[threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void k_reduce_stats(const double* __restrict__ pd, int nd, const double* __restrict__ pp, int np,
+                               double* __restrict__ out, const int32_t* __restrict__ skip) {
+  reduce_stats_body(pd, nd, pp, np, out, skip);
+}
+
+// ---------------------------------------------------------------------------
+// batched kernels: every block looks its instance up in the launch's block
+// map and runs the single-problem body on that instance's buffers (the T
+// evaluation of a round: Vt -> TVt, with the direction d for the
+// line-search statistics)
+// ---------------------------------------------------------------------------
+template <typename S, int J>
+__global__ void __launch_bounds__(128) k_prep_b(const BInst<S>* __restrict__ bi, BMap m) {
+  const int i = m.inst[blockIdx.x];
+  const BInst<S>& b = bi[i];
+  const KP<S> p = b.kp;
+  lstar_body<S, LS_PREP, false, J>(p, blockIdx.x - m.base[i], m.cnt[i], b.Vt + p.n_z, nullptr, b.Vt, nullptr,
+                                   b.TVt, nullptr, nullptr);
+}
+template <typename S, int J>
+__global__ void __launch_bounds__(128) k_dual_b(const BInst<S>* __restrict__ bi, BMap m) {
+  const int i = m.inst[blockIdx.x];
+  const BInst<S>& b = bi[i];
+  const KP<S> p = b.kp;
+  dual_body<S, DM_DUAL, true, true, J>(p, blockIdx.x - m.base[i], m.cnt[i], b.Vt, b.TVt, b.Vt + p.n_z,
+                                       b.TVt + p.n_z, b.d, b.pd);
+}
+template <typename S, int J>
+__global__ void __launch_bounds__(128) k_pstats_b(const BInst<S>* __restrict__ bi, BMap m) {
+  const int i = m.inst[blockIdx.x];
+  const BInst<S>& b = bi[i];
+  const KP<S> p = b.kp;
+  lstar_body<S, LS_STATS, true, J>(p, blockIdx.x - m.base[i], m.cnt[i], b.Vt + p.n_z, b.TVt + p.n_z, b.Vt,
+                                   b.TVt, nullptr, b.d, b.pp);
+}
+template <typename S>
+__global__ void k_reduce_stats_b(const BInst<S>* __restrict__ bi) {
+  const BInst<S>& b = bi[blockIdx.x];
+  reduce_stats_body(b.pd, b.nb_node, b.pp, b.nb_node, b.stats, b.kp.skip);
 }
 
 // ---------------------------------------------------------------------------
@@ -572,6 +633,28 @@ void launch_reduce_stats(const double* pd, int nd, const double* pp, int np, dou
                          const int32_t* skip) {
   k_reduce_stats<<<1, 256, 0, st>>>(pd, nd, pp, np, out, skip);
 }
+
+template <typename S>
+void launch_node_ops_b(int which, const BInst<S>* bi, const BMap& m, int nblocks, int n_inst, int J,
+                       cudaStream_t st) {
+  if (which == 3) {
+    k_reduce_stats_b<S><<<n_inst, 256, 0, st>>>(bi);
+    return;
+  }
+#define SPOCK_NB(JJ)                                                              \
+  case JJ:                                                                        \
+    if (which == 0) k_prep_b<S, JJ><<<nblocks, 128, 0, st>>>(bi, m);              \
+    else if (which == 1) k_dual_b<S, JJ><<<nblocks, 128, 0, st>>>(bi, m);         \
+    else k_pstats_b<S, JJ><<<nblocks, 128, 0, st>>>(bi, m);                       \
+    break;
+  switch (J) {
+    SPOCK_NB(1) SPOCK_NB(2) SPOCK_NB(3) SPOCK_NB(4)
+    default: SPOCK_NB(kMaxJ)
+  }
+#undef SPOCK_NB
+}
+template void launch_node_ops_b<double>(int, const BInst<double>*, const BMap&, int, int, int, cudaStream_t);
+template void launch_node_ops_b<float>(int, const BInst<float>*, const BMap&, int, int, int, cudaStream_t);
 
 template void launch_prep<double>(const KP<double>&, const double*, const double*, double*, int, cudaStream_t);
 template void launch_prep<float>(const KP<float>&, const float*, const float*, float*, int, cudaStream_t);

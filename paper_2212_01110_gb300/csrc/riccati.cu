@@ -26,6 +26,7 @@
 // x^c = [Abar^c | B^c] (x; d) is again lanes-over-outputs.
 #include <cstdlib>
 
+#include "batch.cuh"
 #include "kernels.cuh"
 #include "spock_internal.h"
 
@@ -159,12 +160,12 @@ __device__ __forceinline__ void child_fwd(const S* __restrict__ Gf, const S* w, 
 // backward, chain region: warp per chain, leaves up to the chain stage
 // ---------------------------------------------------------------------------
 template <typename S, int SL>
-__global__ void __launch_bounds__(128) k_bwd_chain(KP<S> p) {
+__device__ __forceinline__ void bwd_chain_body(const KP<S>& p, int bid, int nblk) {
   if (p.skip && *p.skip) return;
   SPOCK_WARP_VECS(S)
   const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int gw = (bid * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (nblk * blockDim.x) >> 5;
   const int nx = p.nx, ncol = p.nx + p.nu;
   for (int ci = gw; ci < p.n_chains; ci += nw) {
     const int leaf = p.stage_begin[p.N] + ci;
@@ -186,16 +187,21 @@ __global__ void __launch_bounds__(128) k_bwd_chain(KP<S> p) {
   }
 }
 
+template <typename S, int SL>
+__global__ void __launch_bounds__(128) k_bwd_chain(KP<S> p) {
+  bwd_chain_body<S, SL>(p, blockIdx.x, gridDim.x);
+}
+
 // ---------------------------------------------------------------------------
 // backward, one branching stage: warp per node
 // ---------------------------------------------------------------------------
 template <typename S, int SL>
-__global__ void __launch_bounds__(128) k_bwd_stage(KP<S> p, int t) {
+__device__ __forceinline__ void bwd_stage_body(const KP<S>& p, int t, int bid, int nblk) {
   if (p.skip && *p.skip) return;
   SPOCK_WARP_VECS(S)
   const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int gw = (bid * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (nblk * blockDim.x) >> 5;
   const int nx = p.nx, ncol = p.nx + p.nu;
   const int b0 = p.stage_begin[t], cnt = p.stage_begin[t + 1] - b0;
   for (int idx = gw; idx < cnt; idx += nw) {
@@ -221,16 +227,21 @@ __global__ void __launch_bounds__(128) k_bwd_stage(KP<S> p, int t) {
   }
 }
 
+template <typename S, int SL>
+__global__ void __launch_bounds__(128) k_bwd_stage(KP<S> p, int t) {
+  bwd_stage_body<S, SL>(p, t, blockIdx.x, gridDim.x);
+}
+
 // ---------------------------------------------------------------------------
 // forward, one branching stage: warp per node
 // ---------------------------------------------------------------------------
 template <typename S, int SL>
-__global__ void __launch_bounds__(128) k_fwd_stage(KP<S> p, int t, S* __restrict__ zo) {
+__device__ __forceinline__ void fwd_stage_body(const KP<S>& p, int t, S* __restrict__ zo, int bid, int nblk) {
   if (p.skip && *p.skip) return;
   SPOCK_WARP_VECS(S)
   const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int gw = (bid * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (nblk * blockDim.x) >> 5;
   const int nx = p.nx, ncol = p.nx + p.nu;
   const int b0 = p.stage_begin[t], cnt = p.stage_begin[t + 1] - b0;
   for (int idx = gw; idx < cnt; idx += nw) {
@@ -262,16 +273,21 @@ __global__ void __launch_bounds__(128) k_fwd_stage(KP<S> p, int t, S* __restrict
   }
 }
 
+template <typename S, int SL>
+__global__ void __launch_bounds__(128) k_fwd_stage(KP<S> p, int t, S* __restrict__ zo) {
+  fwd_stage_body<S, SL>(p, t, zo, blockIdx.x, gridDim.x);
+}
+
 // ---------------------------------------------------------------------------
 // forward, chain region: warp per chain, chain stage down to the leaves
 // ---------------------------------------------------------------------------
 template <typename S, int SL>
-__global__ void __launch_bounds__(128) k_fwd_chain(KP<S> p, S* __restrict__ zo) {
+__device__ __forceinline__ void fwd_chain_body(const KP<S>& p, S* __restrict__ zo, int bid, int nblk) {
   if (p.skip && *p.skip) return;
   SPOCK_WARP_VECS(S)
   const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int gw = (bid * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (nblk * blockDim.x) >> 5;
   const int nx = p.nx, ncol = p.nx + p.nu;
   for (int ci = gw; ci < p.n_chains; ci += nw) {
     const int top = p.stage_begin[p.chain_stage] + ci;
@@ -304,6 +320,11 @@ __global__ void __launch_bounds__(128) k_fwd_chain(KP<S> p, S* __restrict__ zo) 
       __syncwarp();
     }
   }
+}
+
+template <typename S, int SL>
+__global__ void __launch_bounds__(128) k_fwd_chain(KP<S> p, S* __restrict__ zo) {
+  fwd_chain_body<S, SL>(p, zo, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -341,13 +362,7 @@ int launch_fwd_chain_grp(const KP<S>& p, S* zo, cudaStream_t st);
 // SPOCK_RICCATI_KERNELS forces one family everywhere (the tests cover each).
 enum ChainFamily { CF_AUTO = -1, CF_GRP = 0, CF_TMA = 1, CF_DIRECT = 2 };
 constexpr int kStagedMaxNodes = 2048;  // FP64 stages with more nodes use the direct kernels
-// Per-thread override set by the batch autotuner while it times candidates
-// and captures an instance (-2 = none).
-static thread_local int g_family_override = -2;
-void set_riccati_family_override(int fam) { g_family_override = fam; }
-
 static int chain_family() {
-  if (g_family_override != -2) return g_family_override;
   const char* e = getenv("SPOCK_RICCATI_KERNELS");
   if (!e || !e[0]) return CF_AUTO;
   if (e[0] == 'd') return CF_DIRECT;
@@ -432,6 +447,54 @@ int launch_riccati(const KP<S>& p, const std::vector<int32_t>& stage_begin, cons
     default: return riccati_passes_sl<S, 4>(p, stage_begin, stage_maxch, zo, st, ev);
   }
 }
+
+// ---------------------------------------------------------------------------
+// batched: direct kernels over the block map of the launch (chains of every
+// instance, or one stage of every instance: stage[i] from the map)
+// ---------------------------------------------------------------------------
+template <typename S, int SL>
+__global__ void __launch_bounds__(128) k_bwd_chain_b(const BInst<S>* __restrict__ bi, BMap m) {
+  const int i = m.inst[blockIdx.x];
+  const KP<S> p = bi[i].kp;
+  bwd_chain_body<S, SL>(p, blockIdx.x - m.base[i], m.cnt[i]);
+}
+template <typename S, int SL>
+__global__ void __launch_bounds__(128) k_bwd_stage_b(const BInst<S>* __restrict__ bi, BMap m) {
+  const int i = m.inst[blockIdx.x];
+  const KP<S> p = bi[i].kp;
+  bwd_stage_body<S, SL>(p, m.stage[i], blockIdx.x - m.base[i], m.cnt[i]);
+}
+template <typename S, int SL>
+__global__ void __launch_bounds__(128) k_fwd_stage_b(const BInst<S>* __restrict__ bi, BMap m) {
+  const int i = m.inst[blockIdx.x];
+  const KP<S> p = bi[i].kp;
+  fwd_stage_body<S, SL>(p, m.stage[i], bi[i].TVt, blockIdx.x - m.base[i], m.cnt[i]);
+}
+template <typename S, int SL>
+__global__ void __launch_bounds__(128) k_fwd_chain_b(const BInst<S>* __restrict__ bi, BMap m) {
+  const int i = m.inst[blockIdx.x];
+  const KP<S> p = bi[i].kp;
+  fwd_chain_body<S, SL>(p, bi[i].TVt, blockIdx.x - m.base[i], m.cnt[i]);
+}
+
+template <typename S>
+void launch_riccati_b(int which, const BInst<S>* bi, const BMap& m, int nblocks, int SL, cudaStream_t st) {
+  if (nblocks <= 0) return;
+#define SPOCK_RB(L)                                                                    \
+  case L:                                                                              \
+    if (which == 0) k_bwd_chain_b<S, L><<<nblocks, 128, 0, st>>>(bi, m);              \
+    else if (which == 1) k_bwd_stage_b<S, L><<<nblocks, 128, 0, st>>>(bi, m);         \
+    else if (which == 2) k_fwd_stage_b<S, L><<<nblocks, 128, 0, st>>>(bi, m);         \
+    else k_fwd_chain_b<S, L><<<nblocks, 128, 0, st>>>(bi, m);                         \
+    break;
+  switch (SL) {
+    SPOCK_RB(1) SPOCK_RB(2) SPOCK_RB(3)
+    default: SPOCK_RB(4)
+  }
+#undef SPOCK_RB
+}
+template void launch_riccati_b<double>(int, const BInst<double>*, const BMap&, int, int, cudaStream_t);
+template void launch_riccati_b<float>(int, const BInst<float>*, const BMap&, int, int, cudaStream_t);
 
 template int launch_riccati<double>(const KP<double>&, const std::vector<int32_t>&, const std::vector<int32_t>&,
                                     double*, cudaStream_t, cudaEvent_t*);

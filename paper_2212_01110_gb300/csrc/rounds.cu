@@ -14,6 +14,7 @@
 // run of rounds can be captured in a CUDA graph and replayed.
 #include <cmath>
 
+#include "batch.cuh"
 #include "kernels.cuh"
 #include "supermann.cuh"
 
@@ -83,8 +84,7 @@ __device__ void round_after_accept(SmState* st, int32_t* trace) {
   }
 }
 
-__global__ void k_round_decide(SmState* st, const double* __restrict__ stats_t, int32_t* trace) {
-  if (threadIdx.x != 0) return;
+__device__ void round_decide_body(SmState* st, const double* __restrict__ stats_t, int32_t* trace) {
   st->op_accept = 0;
   st->op_aa = 0;
   st->op_point = PT_NONE;
@@ -149,6 +149,11 @@ __global__ void k_round_decide(SmState* st, const double* __restrict__ stats_t, 
   if (!st->done) st->n_T++;  // the T evaluation that follows this round
 }
 
+__global__ void k_round_decide(SmState* st, const double* __restrict__ stats_t, int32_t* trace) {
+  if (threadIdx.x != 0) return;
+  round_decide_body(st, stats_t, trace);
+}
+
 template <typename S>
 struct RPack;
 template <>
@@ -178,11 +183,11 @@ __device__ __forceinline__ void rst(S* p, int64_t q, const typename RPack<S>::T&
 // column (slot st->aa_slot) and the dot products of the stored columns with
 // it and with the new residual (terms in S, FP64 accumulation per pack).
 template <typename S, int MEM>
-__global__ void __launch_bounds__(256, 4) k_round_commit(SmState* st, S* __restrict__ V, S* __restrict__ TV,
-                                                         S* __restrict__ Vp, S* __restrict__ TVp,
-                                                         const S* __restrict__ Vt, const S* __restrict__ TVt,
-                                                         S* __restrict__ MR, S* __restrict__ D, int64_t n,
-                                                         int64_t ld, double* __restrict__ partials) {
+__device__ __forceinline__ void round_commit_body(SmState* st, S* __restrict__ V, S* __restrict__ TV,
+                                                  S* __restrict__ Vp, S* __restrict__ TVp,
+                                                  const S* __restrict__ Vt, const S* __restrict__ TVt,
+                                                  S* __restrict__ MR, S* __restrict__ D, int64_t n, int64_t ld,
+                                                  double* __restrict__ partials, int bid, int nblk) {
   if (!st->op_accept) return;
   const bool aa = st->op_aa != 0;
   const int slot = st->aa_slot, cnt = st->aa_cnt;
@@ -191,8 +196,8 @@ __global__ void __launch_bounds__(256, 4) k_round_commit(SmState* st, S* __restr
   double gr[MEM > 0 ? MEM : 1], rh[MEM > 0 ? MEM : 1];
 #pragma unroll
   for (int j = 0; j < MEM; ++j) gr[j] = rh[j] = 0.0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)nblk * blockDim.x;
+  const int64_t gt = (int64_t)bid * blockDim.x + threadIdx.x;
   const int64_t npack = n / NP;
   for (int64_t q = gt; q < npack; q += stride) {
     PT nv = rld(Vt, q), nt = rld(TVt, q), ov = rld(V, q), ot = rld(TV, q);
@@ -263,14 +268,23 @@ __global__ void __launch_bounds__(256, 4) k_round_commit(SmState* st, S* __restr
     double sum = 0.0;
     if (j < cnt)
       for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) sum += red[ww][threadIdx.x];
-    partials[(int64_t)blockIdx.x * 2 * kMaxMemory + threadIdx.x] = sum;
+    partials[(int64_t)bid * 2 * kMaxMemory + threadIdx.x] = sum;
   }
+}
+
+template <typename S, int MEM>
+__global__ void __launch_bounds__(256, 4) k_round_commit(SmState* st, S* __restrict__ V, S* __restrict__ TV,
+                                                         S* __restrict__ Vp, S* __restrict__ TVp,
+                                                         const S* __restrict__ Vt, const S* __restrict__ TVt,
+                                                         S* __restrict__ MR, S* __restrict__ D, int64_t n,
+                                                         int64_t ld, double* __restrict__ partials) {
+  round_commit_body<S, MEM>(st, V, TV, Vp, TVp, Vt, TVt, MR, D, n, ld, partials, blockIdx.x, gridDim.x);
 }
 
 // Gram update and least squares for gamma (FP64), newest columns first;
 // numerically singular Gram matrices drop their oldest columns from the solve.
-__global__ void __launch_bounds__(256) k_round_aa_solve(SmState* st, const double* __restrict__ partials,
-                                                        int nblocks) {
+__device__ __forceinline__ void round_aa_solve_body(SmState* st, const double* __restrict__ partials,
+                                                    int nblocks) {
   if (!st->op_aa) return;
   __shared__ double part[8][2 * kMaxMemory];
   __shared__ double sums[2 * kMaxMemory];
@@ -339,12 +353,18 @@ __global__ void __launch_bounds__(256) k_round_aa_solve(SmState* st, const doubl
   }
 }
 
+__global__ void __launch_bounds__(256) k_round_aa_solve(SmState* st, const double* __restrict__ partials,
+                                                        int nblocks) {
+  round_aa_solve_body(st, partials, nblocks);
+}
+
 // Next evaluation point in Vt (and the direction d for PT_DIR).
 template <typename S, int MEM>
-__global__ void __launch_bounds__(256) k_round_point(const SmState* __restrict__ st, const S* __restrict__ V,
-                                                     const S* __restrict__ TV, S* __restrict__ Vt,
-                                                     const S* __restrict__ TVt, S* __restrict__ d,
-                                                     const S* __restrict__ D, int64_t n, int64_t ld) {
+__device__ __forceinline__ void round_point_body(const SmState* __restrict__ st, const S* __restrict__ V,
+                                                 const S* __restrict__ TV, S* __restrict__ Vt,
+                                                 const S* __restrict__ TVt, S* __restrict__ d,
+                                                 const S* __restrict__ D, int64_t n, int64_t ld, int bid,
+                                                 int nblk) {
   const int op = st->op_point;
   if (op == PT_NONE) return;
   constexpr int NP = RPack<S>::N;
@@ -410,6 +430,42 @@ __global__ void __launch_bounds__(256) k_round_point(const SmState* __restrict__
   }
 }
 
+template <typename S, int MEM>
+__global__ void __launch_bounds__(256) k_round_point(const SmState* __restrict__ st, const S* __restrict__ V,
+                                                     const S* __restrict__ TV, S* __restrict__ Vt,
+                                                     const S* __restrict__ TVt, S* __restrict__ d,
+                                                     const S* __restrict__ D, int64_t n, int64_t ld) {
+  round_point_body<S, MEM>(st, V, TV, Vt, TVt, d, D, n, ld, blockIdx.x, gridDim.x);
+}
+
+// ---------------------------------------------------------------------------
+// batched rounds
+// ---------------------------------------------------------------------------
+template <typename S>
+__global__ void k_round_decide_b(const BInst<S>* __restrict__ bi, int n_inst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_inst) round_decide_body(bi[i].st, bi[i].stats, nullptr);
+}
+template <typename S, int MEM>
+__global__ void __launch_bounds__(256, 4) k_round_commit_b(const BInst<S>* __restrict__ bi, BMap m) {
+  const int i = m.inst[blockIdx.x];
+  const BInst<S>& b = bi[i];
+  round_commit_body<S, MEM>(b.st, b.V, b.TV, b.Vp, b.TVp, b.Vt, b.TVt, b.MR, b.D, b.n_v, b.ld, b.paa,
+                            blockIdx.x - m.base[i], m.cnt[i]);
+}
+template <typename S>
+__global__ void __launch_bounds__(256) k_round_aa_solve_b(const BInst<S>* __restrict__ bi) {
+  const BInst<S>& b = bi[blockIdx.x];
+  round_aa_solve_body(b.st, b.paa, b.nb_vec);
+}
+template <typename S, int MEM>
+__global__ void __launch_bounds__(256) k_round_point_b(const BInst<S>* __restrict__ bi, BMap m) {
+  const int i = m.inst[blockIdx.x];
+  const BInst<S>& b = bi[i];
+  round_point_body<S, MEM>(b.st, b.V, b.TV, b.Vt, b.TVt, b.d, b.D, b.n_v, b.ld, blockIdx.x - m.base[i],
+                           m.cnt[i]);
+}
+
 void launch_round_decide(SmState* st, const double* stats_t, int32_t* trace, cudaStream_t s) {
   k_round_decide<<<1, 32, 0, s>>>(st, stats_t, trace);
 }
@@ -440,6 +496,43 @@ void launch_round_point(SmState* st, const S* V, const S* TV, S* Vt, const S* TV
     default: break;
   }
 }
+
+template <typename S>
+void launch_round_decide_b(const BInst<S>* bi, int n_inst, cudaStream_t st) {
+  k_round_decide_b<S><<<(n_inst + 63) / 64, 64, 0, st>>>(bi, n_inst);
+}
+template <typename S>
+void launch_round_aa_solve_b(const BInst<S>* bi, int n_inst, cudaStream_t st) {
+  k_round_aa_solve_b<S><<<n_inst, 256, 0, st>>>(bi);
+}
+template <typename S>
+void launch_round_commit_b(const BInst<S>* bi, const BMap& m, int nblocks, int mem, cudaStream_t st) {
+  switch (mem) {
+#define SPOCK_RC(M) case M: k_round_commit_b<S, M><<<nblocks, 256, 0, st>>>(bi, m); break;
+    SPOCK_RC(0) SPOCK_RC(1) SPOCK_RC(2) SPOCK_RC(3) SPOCK_RC(4) SPOCK_RC(5) SPOCK_RC(6) SPOCK_RC(7) SPOCK_RC(8)
+    SPOCK_RC(9) SPOCK_RC(10) SPOCK_RC(11) SPOCK_RC(12) SPOCK_RC(13) SPOCK_RC(14) SPOCK_RC(15) SPOCK_RC(16)
+#undef SPOCK_RC
+    default: break;
+  }
+}
+template <typename S>
+void launch_round_point_b(const BInst<S>* bi, const BMap& m, int nblocks, int mem, cudaStream_t st) {
+  switch (mem) {
+#define SPOCK_RP(M) case M: k_round_point_b<S, M><<<nblocks, 256, 0, st>>>(bi, m); break;
+    SPOCK_RP(0) SPOCK_RP(1) SPOCK_RP(2) SPOCK_RP(3) SPOCK_RP(4) SPOCK_RP(5) SPOCK_RP(6) SPOCK_RP(7) SPOCK_RP(8)
+    SPOCK_RP(9) SPOCK_RP(10) SPOCK_RP(11) SPOCK_RP(12) SPOCK_RP(13) SPOCK_RP(14) SPOCK_RP(15) SPOCK_RP(16)
+#undef SPOCK_RP
+    default: break;
+  }
+}
+#define SPOCK_RB_INST(S)                                                                          \
+  template void launch_round_decide_b<S>(const BInst<S>*, int, cudaStream_t);                     \
+  template void launch_round_aa_solve_b<S>(const BInst<S>*, int, cudaStream_t);                   \
+  template void launch_round_commit_b<S>(const BInst<S>*, const BMap&, int, int, cudaStream_t);   \
+  template void launch_round_point_b<S>(const BInst<S>*, const BMap&, int, int, cudaStream_t);
+SPOCK_RB_INST(double)
+SPOCK_RB_INST(float)
+#undef SPOCK_RB_INST
 
 template void launch_round_commit<double>(SmState*, double*, double*, double*, double*, const double*,
                                           const double*, double*, double*, int64_t, int64_t, int, double*, int,

@@ -3,6 +3,7 @@
 // Algorithm 3 whose decisions are taken on the device (supermann.cu), the
 // vanilla CP loop and the C ABI of include/spock.h.
 #include <chrono>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <exception>
@@ -12,6 +13,7 @@
 #include <thread>
 #include <vector>
 
+#include "batch.cuh"
 #include "kernels.cuh"
 #include "spock_internal.h"
 #include "supermann.cuh"
@@ -34,7 +36,6 @@ int launch_riccati(const KP<S>& p, const std::vector<int32_t>& stage_begin, cons
                    S* zo, cudaStream_t st, cudaEvent_t* ev);
 
 enum { DM_APPLY_L_ = 0, DM_PROXG_ = 1, DM_DUAL_ = 2, PM_APPLY_LT_ = 0, PM_STATS_ = 1 };
-void set_riccati_family_override(int fam);  // riccati.cu
 
 // ---------------------------------------------------------------------------
 // errors
@@ -792,34 +793,85 @@ static int cp_impl(Problem& P, const double* x0_dev, int k, double alpha, double
 }
 
 // ---------------------------------------------------------------------------
-// batches: one graph, one parallel branch of rounds per instance
+// batches: every kernel of a round launched once for all instances
+// (batch.cuh); kBatchRounds rounds captured in one CUDA graph
 // ---------------------------------------------------------------------------
-constexpr int kBatchRounds = 4;
+constexpr int kBatchRounds = 8;
+constexpr int kVecElemsPerThread = 16;   // commit / point kernels of the batch
+
+// Device copy of a block map: inst[nblocks] | base[n] | cnt[n] | stage[n].
+struct DevMap {
+  int32_t* buf = nullptr;
+  int nblocks = 0;
+  BMap view(int n) const { return BMap{buf, buf + nblocks, buf + nblocks + n, buf + nblocks + 2 * n}; }
+};
 
 struct Batch {
   int32_t tag = TAG_BATCH;
   std::vector<Problem*> probs;
-  std::vector<cudaStream_t> streams;
-  std::vector<cudaEvent_t> joins;
-  cudaEvent_t fork = nullptr;
   cudaStream_t main = nullptr;
+  // plan of the batched launches for one precision, node tile and memory
+  int p_prec = -1, p_mem = -1, p_tile = -1;
+  std::vector<void*> p_ws;
+  std::vector<double> p_alpha;
+  void* bi_dev = nullptr;  // BInst<S>[n]
+  DevMap node, vec, chain;
+  std::vector<DevMap> bwd_lv, fwd_lv;  // branching stages, one map per level
+  int J = 1, SL = 1;
+  int launches_per_eval = 0;
+  // graph of kBatchRounds rounds
   cudaGraphExec_t gexec = nullptr;
-  int g_prec = -1, g_mem = -1;
   double g_alpha = -1.0;
   int g_launches = 0;
-  std::vector<void*> g_ws;      // workspaces the graph was captured with
-  SmState** st_ptrs = nullptr;  // device array of the instances' state pointers
+  int tuned_tile[2] = {0, 0};  // node tile (nodes per warp) picked by the autotuner, per precision
+  SmState** st_ptrs = nullptr;
   int32_t* done_dev = nullptr;
   int32_t* done_host = nullptr;  // pinned
-  ~Batch() {
+  std::vector<int32_t*> bufs;
+  void free_plan() {
     if (gexec) cudaGraphExecDestroy(gexec);
-    for (auto s : streams) cudaStreamDestroy(s);
-    for (auto e : joins) cudaEventDestroy(e);
-    if (fork) cudaEventDestroy(fork);
+    gexec = nullptr;
+    for (auto b : bufs) cudaFree(b);
+    bufs.clear();
+    if (bi_dev) cudaFree(bi_dev);
+    bi_dev = nullptr;
+    bwd_lv.clear();
+    fwd_lv.clear();
+    p_prec = p_mem = p_tile = -1;
+    p_ws.clear();
+    p_alpha.clear();
+  }
+  ~Batch() {
+    free_plan();
     if (main) cudaStreamDestroy(main);
     if (st_ptrs) cudaFree(st_ptrs);
     if (done_dev) cudaFree(done_dev);
     if (done_host) cudaFreeHost(done_host);
+  }
+  // uploads one block map from per-instance block counts (and stages)
+  DevMap make_map(const std::vector<int>& cnt, const std::vector<int>& stage) {
+    const int n = (int)cnt.size();
+    DevMap m;
+    std::vector<int32_t> h;
+    std::vector<int32_t> base(n), cn(n), stg(n);
+    int total = 0;
+    for (int i = 0; i < n; ++i) {
+      base[i] = total;
+      cn[i] = cnt[i];
+      stg[i] = stage.empty() ? -1 : stage[i];
+      total += cnt[i];
+    }
+    h.reserve((size_t)total + 3 * n);
+    for (int i = 0; i < n; ++i)
+      for (int b = 0; b < cnt[i]; ++b) h.push_back(i);
+    h.insert(h.end(), base.begin(), base.end());
+    h.insert(h.end(), cn.begin(), cn.end());
+    h.insert(h.end(), stg.begin(), stg.end());
+    CUDA_TRY(cudaMalloc(&m.buf, sizeof(int32_t) * h.size()));
+    bufs.push_back(m.buf);
+    CUDA_TRY(cudaMemcpy(m.buf, h.data(), sizeof(int32_t) * h.size(), cudaMemcpyHostToDevice));
+    m.nblocks = total;
+    return m;
   }
 };
 
@@ -828,36 +880,181 @@ __global__ void k_gather_done(SmState* const* __restrict__ sts, int n, int32_t* 
   if (i < n) out[i] = sts[i]->done;
 }
 
-// Kernel family of an instance: candidate families timed on three T
-// evaluations each (the autotuner of the batch path); cached per problem.
+// Block maps and instance views for the batched launches.  tile = nodes per
+// warp of the node kernels (the autotuned tile shape); the vector kernels
+// take kVecElemsPerThread elements per thread; the Riccati kernels one warp
+// per chain / node.
 template <typename S>
-static int tune_family(Problem& P, Workspace* ws, double alpha, cudaStream_t st) {
-  int& slot = P.tuned_family[sizeof(S) == 8 ? 0 : 1];
-  if (slot != -3) return slot;
-  Ctx c{&P, ws, alpha, st, P.idx.stage_begin};
-  S* v = (S*)ws->v[2];
-  S* Tv = (S*)ws->Tv[2];
-  const int cands[4] = {-1, 1, 2, 0};  // auto, one warp per chain staged, direct, three warps per chain
-  float best = 1e30f;
-  int pick = -1;
+static void batch_plan(Batch& B, const std::vector<Workspace*>& wss, const std::vector<double>& alphas, int mem,
+                       int tile) {
+  std::vector<void*> ws_now(wss.begin(), wss.end());
+  if (B.p_prec == (int)sizeof(S) && B.p_mem == mem && B.p_tile == tile && B.p_ws == ws_now && B.p_alpha == alphas)
+    return;
+  B.free_plan();
+  const int n = (int)B.probs.size();
+  std::vector<BInst<S>> h(n);
+  std::vector<int> cn(n), cv(n), cc(n);
+  int max_cs = 0;
+  B.J = 1;
+  B.SL = 1;
+  for (int i = 0; i < n; ++i) {
+    Problem& P = *B.probs[i];
+    Workspace* ws = wss[i];
+    BInst<S>& b = h[i];
+    b.kp = make_kp<S>(P, alphas[i], P.idx.stage_begin);
+    b.kp.skip = &ws->st->done;
+    b.st = ws->st;
+    b.V = (S*)ws->v[0];
+    b.TV = (S*)ws->Tv[0];
+    b.Vp = (S*)ws->v[1];
+    b.TVp = (S*)ws->Tv[1];
+    b.Vt = (S*)ws->v[2];
+    b.TVt = (S*)ws->Tv[2];
+    b.d = (S*)ws->d;
+    b.MR = (S*)ws->MR;
+    b.D = (S*)ws->D;
+    b.stats = ws->stats;
+    b.pd = ws->pd;
+    b.pp = ws->pp;
+    b.paa = ws->paa;
+    b.n_v = ws->n_v;
+    b.ld = ws->ld;
+    const int nn = P.tree.n;
+    b.nb_node = std::max(1, std::min(ws->grid_d, (nn + kWarpsPerBlock * tile - 1) / (kWarpsPerBlock * tile)));
+    const int64_t per_block = (int64_t)256 * kVecElemsPerThread;
+    b.nb_vec = (int)std::max<int64_t>(1, std::min<int64_t>(ws->grid_v, (ws->n_v + per_block - 1) / per_block));
+    cn[i] = b.nb_node;
+    cv[i] = b.nb_vec;
+    const bool chains = b.kp.n_chains > 0 && b.kp.chain_stage < b.kp.N;
+    cc[i] = chains ? (b.kp.n_chains + kWarpsPerBlock - 1) / kWarpsPerBlock : 0;
+    max_cs = std::max(max_cs, (int)P.tree.chain_stage);
+    B.J = std::max(B.J, (P.nx + P.nu + 2 + 31) / 32);
+    B.SL = std::max(B.SL, (P.nx + P.nu + 31) / 32);
+  }
+  CUDA_TRY(cudaMalloc(&B.bi_dev, sizeof(BInst<S>) * n));
+  CUDA_TRY(cudaMemcpy(B.bi_dev, h.data(), sizeof(BInst<S>) * n, cudaMemcpyHostToDevice));
+  B.node = B.make_map(cn, {});
+  B.vec = B.make_map(cv, {});
+  B.chain = B.make_map(cc, {});
+  for (int L = 0; L < max_cs; ++L) {  // backward: level L is stage cs_i - 1 - L of instance i
+    std::vector<int> cnt(n, 0), stg(n, -1);
+    for (int i = 0; i < n; ++i) {
+      const Tree& t = B.probs[i]->tree;
+      const int st = t.chain_stage - 1 - L;
+      if (st >= 0) {
+        stg[i] = st;
+        cnt[i] = (t.stage_begin[st + 1] - t.stage_begin[st] + kWarpsPerBlock - 1) / kWarpsPerBlock;
+      }
+    }
+    B.bwd_lv.push_back(B.make_map(cnt, stg));
+  }
+  for (int L = 0; L < max_cs; ++L) {  // forward: level L is stage L
+    std::vector<int> cnt(n, 0), stg(n, -1);
+    for (int i = 0; i < n; ++i) {
+      const Tree& t = B.probs[i]->tree;
+      if (L < t.chain_stage) {
+        stg[i] = L;
+        cnt[i] = (t.stage_begin[L + 1] - t.stage_begin[L] + kWarpsPerBlock - 1) / kWarpsPerBlock;
+      }
+    }
+    B.fwd_lv.push_back(B.make_map(cnt, stg));
+  }
+  B.launches_per_eval = 6 + 2 * max_cs;
+  B.p_prec = (int)sizeof(S);
+  B.p_mem = mem;
+  B.p_tile = tile;
+  B.p_ws = ws_now;
+  B.p_alpha = alphas;
+}
+
+// One T evaluation of every instance: Vt -> TVt with statistics (direction d).
+template <typename S>
+static void batch_eval(Batch& B, cudaStream_t st) {
+  const int n = (int)B.probs.size();
+  const BInst<S>* bi = (const BInst<S>*)B.bi_dev;
+  launch_node_ops_b<S>(0, bi, B.node.view(n), B.node.nblocks, n, B.J, st);
+  launch_riccati_b<S>(0, bi, B.chain.view(n), B.chain.nblocks, B.SL, st);
+  for (const DevMap& m : B.bwd_lv) launch_riccati_b<S>(1, bi, m.view(n), m.nblocks, B.SL, st);
+  for (const DevMap& m : B.fwd_lv) launch_riccati_b<S>(2, bi, m.view(n), m.nblocks, B.SL, st);
+  launch_riccati_b<S>(3, bi, B.chain.view(n), B.chain.nblocks, B.SL, st);
+  launch_node_ops_b<S>(1, bi, B.node.view(n), B.node.nblocks, n, B.J, st);
+  launch_node_ops_b<S>(2, bi, B.node.view(n), B.node.nblocks, n, B.J, st);
+  launch_node_ops_b<S>(3, bi, B.node.view(n), 0, n, B.J, st);
+  check_launch();
+}
+
+// Puts every instance at its starting point: Vt = v0 (cold: 0, warm: the
+// caller's (z, eta)), d = 0, fresh SuperMann state.
+template <typename S>
+static void batch_init(Batch& B, const std::vector<Workspace*>& wss, const std::vector<double>& alphas,
+                       const spock_settings& s, int mem, const double* const* x0, double* const* z,
+                       double* const* eta, int warm) {
+  const int n = (int)B.probs.size();
+  cudaStream_t st = B.main;
+  for (int i = 0; i < n; ++i) {
+    Problem& P = *B.probs[i];
+    Workspace* ws = wss[i];
+    const DevFactors<S>& f = factors<S>(P);
+    S* Vt = (S*)ws->v[2];
+    convert<S, double>(x0[i], f.x0, P.nx, st);
+    if (warm) {
+      convert<S, double>(z[i], Vt, P.off.n_z, st);
+      convert<S, double>(eta[i], Vt + P.off.n_z, P.off.n_eta, st);
+    } else {
+      CUDA_TRY(cudaMemsetAsync(Vt, 0, sizeof(S) * ws->n_v, st));
+    }
+    CUDA_TRY(cudaMemsetAsync(ws->d, 0, sizeof(S) * ws->n_v, st));
+    SmState h{};
+    h.alpha = alphas[i];
+    h.eps_abs = s.eps_abs;
+    h.eps_rel = s.eps_rel;
+    h.c0 = s.c0;
+    h.c1 = s.c1;
+    h.c2 = s.c2;
+    h.beta = s.beta;
+    h.sigma = s.sigma;
+    h.lam = s.lambda;
+    h.rho_coef = s.rho_coef;
+    h.max_iter = std::max(0, s.max_iter);
+    h.max_back = std::max(0, s.max_backtracks);
+    h.mem = mem;
+    h.pending = P_INIT;
+    h.n_T = 1;
+    sm_init_state(ws->st, h, st);
+  }
+}
+
+// Autotuner of the batch: the node tile (nodes per warp of the node kernels)
+// with the shortest batched T evaluation, timed over three evaluations per
+// candidate; cached per batch and precision.
+template <typename S>
+static int batch_tune(Batch& B, const std::vector<Workspace*>& wss, const std::vector<double>& alphas, int mem,
+                      const spock_settings& s, const double* const* x0, double* const* z, double* const* eta,
+                      int warm) {
+  const char* env = getenv("SPOCK_BATCH_TILE");  // fixed tile (tests, experiments)
+  if (env && (env[0] == '1' || env[0] == '2' || env[0] == '4') && env[1] == 0) return env[0] - '0';
+  int& slot = B.tuned_tile[sizeof(S) == 8 ? 0 : 1];
+  if (slot > 0) return slot;
   cudaEvent_t a, b;
   CUDA_TRY(cudaEventCreate(&a));
   CUDA_TRY(cudaEventCreate(&b));
-  for (int f : cands) {
-    set_riccati_family_override(f);
-    eval_T<S>(c, v, Tv, nullptr, nullptr);
-    CUDA_TRY(cudaEventRecord(a, st));
-    for (int r = 0; r < 3; ++r) eval_T<S>(c, v, Tv, nullptr, nullptr);
-    CUDA_TRY(cudaEventRecord(b, st));
+  float best = 1e30f;
+  int pick = 1;
+  for (int tile : {1, 2, 4}) {
+    batch_plan<S>(B, wss, alphas, mem, tile);
+    batch_init<S>(B, wss, alphas, s, mem, x0, z, eta, warm);
+    batch_eval<S>(B, B.main);  // warm-up
+    CUDA_TRY(cudaEventRecord(a, B.main));
+    for (int r = 0; r < 3; ++r) batch_eval<S>(B, B.main);
+    CUDA_TRY(cudaEventRecord(b, B.main));
     CUDA_TRY(cudaEventSynchronize(b));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, a, b);
     if (ms < best) {
       best = ms;
-      pick = f;
+      pick = tile;
     }
   }
-  set_riccati_family_override(-2);
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   slot = pick;
@@ -872,101 +1069,32 @@ static int batch_solve(Batch& B, const double* const* x0, const spock_settings& 
   const int max_iter = std::max(0, s.max_iter);
   std::vector<Workspace*> wss(n);
   std::vector<double> alphas(n);
-  std::vector<int> fams(n);
-  std::vector<int64_t> launches(n, 0);
+  CUDA_TRY(cudaSetDevice(B.probs[0]->device));
   for (int i = 0; i < n; ++i) {
     Problem& P = *B.probs[i];
-    CUDA_TRY(cudaSetDevice(P.device));
     wss[i] = get_ws_impl<S>(P, mem);
     alphas[i] = default_alpha(P, s.alpha);
   }
-  // per-instance inputs, state and T(v0) on the instance's stream
-  for (int i = 0; i < n; ++i) {
-    Problem& P = *B.probs[i];
-    Workspace* ws = wss[i];
-    cudaStream_t st = B.streams[i];
-    const DevFactors<S>& f = factors<S>(P);
-    S* Vt = (S*)ws->v[2];
-    convert<S, double>(x0[i], f.x0, P.nx, st);
-    if (warm) {
-      convert<S, double>(z[i], Vt, P.off.n_z, st);
-      convert<S, double>(eta[i], Vt + P.off.n_z, P.off.n_eta, st);
-    } else {
-      CUDA_TRY(cudaMemsetAsync(Vt, 0, sizeof(S) * ws->n_v, st));
-    }
-    CUDA_TRY(cudaMemsetAsync(ws->d, 0, sizeof(S) * ws->n_v, st));
-    fams[i] = tune_family<S>(P, ws, alphas[i], st);
-    if (warm) {  // tuning overwrote the evaluation buffers
-      convert<S, double>(z[i], Vt, P.off.n_z, st);
-      convert<S, double>(eta[i], Vt + P.off.n_z, P.off.n_eta, st);
-    } else {
-      CUDA_TRY(cudaMemsetAsync(Vt, 0, sizeof(S) * ws->n_v, st));
-    }
-    SmState h{};
-    h.alpha = alphas[i];
-    h.eps_abs = s.eps_abs;
-    h.eps_rel = s.eps_rel;
-    h.c0 = s.c0;
-    h.c1 = s.c1;
-    h.c2 = s.c2;
-    h.beta = s.beta;
-    h.sigma = s.sigma;
-    h.lam = s.lambda;
-    h.rho_coef = s.rho_coef;
-    h.max_iter = max_iter;
-    h.max_back = std::max(0, s.max_backtracks);
-    h.mem = mem;
-    h.pending = P_INIT;
-    h.n_T = 1;
-    sm_init_state(ws->st, h, st);
-    Ctx c{&P, ws, alphas[i], st, P.idx.stage_begin};
-    set_riccati_family_override(fams[i]);
-    ws->launches = 0;
-    eval_T<S>(c, Vt, (S*)ws->Tv[2], nullptr, ws->stats, nullptr);
-    launches[i] = ws->launches;
-    set_riccati_family_override(-2);
-  }
-  CUDA_TRY(cudaDeviceSynchronize());
-  // one graph: every instance's kBatchRounds rounds as a parallel branch
-  const bool same_alpha = s.alpha > 0 ? B.g_alpha == s.alpha : B.g_alpha == 0.0;
-  std::vector<void*> ws_now(wss.begin(), wss.end());
-  if (!B.gexec || B.g_prec != (int)sizeof(S) || B.g_mem != mem || !same_alpha || B.g_ws != ws_now) {
+  const int tile = batch_tune<S>(B, wss, alphas, mem, s, x0, z, eta, warm);
+  batch_plan<S>(B, wss, alphas, mem, tile);
+  batch_init<S>(B, wss, alphas, s, mem, x0, z, eta, warm);
+  const BInst<S>* bi = (const BInst<S>*)B.bi_dev;
+  // the graph of kBatchRounds rounds (the plan, hence the graph, is rebuilt
+  // when precision, memory, tile or workspaces change)
+  const double a_key = s.alpha > 0 ? s.alpha : 0.0;
+  if (!B.gexec || B.g_alpha != a_key) {
     if (B.gexec) {
       cudaGraphExecDestroy(B.gexec);
       B.gexec = nullptr;
     }
     cudaGraph_t g = nullptr;
     CUDA_TRY(cudaStreamBeginCapture(B.main, cudaStreamCaptureModeThreadLocal));
-    CUDA_TRY(cudaEventRecord(B.fork, B.main));
-    int total = 0;
-    for (int i = 0; i < n; ++i) {
-      Problem& P = *B.probs[i];
-      Workspace* ws = wss[i];
-      cudaStream_t st = B.streams[i];
-      CUDA_TRY(cudaStreamWaitEvent(st, B.fork, 0));
-      set_riccati_family_override(fams[i]);
-      Ctx c{&P, ws, alphas[i], st, P.idx.stage_begin};
-      S* V = (S*)ws->v[0];
-      S* TV = (S*)ws->Tv[0];
-      S* Vp = (S*)ws->v[1];
-      S* TVp = (S*)ws->Tv[1];
-      S* Vt = (S*)ws->v[2];
-      S* TVt = (S*)ws->Tv[2];
-      S* d = (S*)ws->d;
-      const int32_t* skip = &ws->st->done;
-      for (int r = 0; r < kBatchRounds; ++r) {
-        launch_round_decide(ws->st, ws->stats, nullptr, st);
-        launch_round_commit<S>(ws->st, V, TV, Vp, TVp, Vt, TVt, (S*)ws->MR, (S*)ws->D, ws->n_v, ws->ld, mem,
-                               ws->paa, ws->grid_v, st);
-        launch_round_aa_solve(ws->st, ws->paa, ws->grid_v, st);
-        launch_round_point<S>(ws->st, V, TV, Vt, TVt, d, (S*)ws->D, ws->n_v, ws->ld, mem, ws->grid_v, st);
-        const int64_t before = ws->launches;
-        eval_T<S>(c, Vt, TVt, d, ws->stats, skip);
-        total += 4 + (int)(ws->launches - before);
-      }
-      set_riccati_family_override(-2);
-      CUDA_TRY(cudaEventRecord(B.joins[i], st));
-      CUDA_TRY(cudaStreamWaitEvent(B.main, B.joins[i], 0));
+    for (int r = 0; r < kBatchRounds; ++r) {
+      launch_round_decide_b<S>(bi, n, B.main);
+      launch_round_commit_b<S>(bi, B.vec.view(n), B.vec.nblocks, mem, B.main);
+      launch_round_aa_solve_b<S>(bi, n, B.main);
+      launch_round_point_b<S>(bi, B.vec.view(n), B.vec.nblocks, mem, B.main);
+      batch_eval<S>(B, B.main);
     }
     k_gather_done<<<(n + 127) / 128, 128, 0, B.main>>>(B.st_ptrs, n, B.done_dev);
     check_launch();
@@ -974,13 +1102,9 @@ static int batch_solve(Batch& B, const double* const* x0, const spock_settings& 
     cudaError_t e = cudaGraphInstantiate(&B.gexec, g, 0);
     cudaGraphDestroy(g);
     CUDA_TRY(e);
-    B.g_prec = (int)sizeof(S);
-    B.g_mem = mem;
-    B.g_ws = ws_now;
-    B.g_alpha = s.alpha > 0 ? s.alpha : 0.0;
-    B.g_launches = total + 1;
+    B.g_alpha = a_key;
+    B.g_launches = kBatchRounds * (4 + B.launches_per_eval) + 1;
   }
-  // state pointers for the gather kernel
   {
     std::vector<SmState*> h(n);
     for (int i = 0; i < n; ++i) h[i] = wss[i]->st;
@@ -992,6 +1116,7 @@ static int batch_solve(Batch& B, const double* const* x0, const spock_settings& 
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
   CUDA_TRY(cudaEventRecord(e0, B.main));
+  batch_eval<S>(B, B.main);  // T of the starting points
   for (;;) {
     CUDA_TRY(cudaGraphLaunch(B.gexec, B.main));
     rounds += kBatchRounds;
@@ -1008,17 +1133,20 @@ static int batch_solve(Batch& B, const double* const* x0, const spock_settings& 
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  const int64_t total_launches = B.launches_per_eval + graph_launches * B.g_launches;
   int status = SPOCK_OK;
+  std::vector<SmState> fin(n);
   for (int i = 0; i < n; ++i) {
     Problem& P = *B.probs[i];
     Workspace* ws = wss[i];
-    cudaStream_t st = B.streams[i];
-    convert<double, S>((S*)ws->Tv[0], z[i], P.off.n_z, st);
-    convert<double, S>((S*)ws->Tv[0] + P.off.n_z, eta[i], P.off.n_eta, st);
-    SmState fin;
-    CUDA_TRY(cudaMemcpyAsync(&fin, ws->st, sizeof(SmState), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
-    const int act = fin.done ? fin.action : A_MAXIT;
+    convert<double, S>((S*)ws->Tv[0], z[i], P.off.n_z, B.main);
+    convert<double, S>((S*)ws->Tv[0] + P.off.n_z, eta[i], P.off.n_eta, B.main);
+    CUDA_TRY(cudaMemcpyAsync(&fin[i], ws->st, sizeof(SmState), cudaMemcpyDeviceToHost, B.main));
+  }
+  CUDA_TRY(cudaStreamSynchronize(B.main));
+  for (int i = 0; i < n; ++i) {
+    const SmState& f = fin[i];
+    const int act = f.done ? f.action : A_MAXIT;
     const int si = act == A_DONE ? SPOCK_OK : ((act == A_MAXIT || act == A_STALL) ? SPOCK_MAX_ITER : SPOCK_ERR_NUMERICAL);
     if (si == SPOCK_ERR_NUMERICAL) status = SPOCK_ERR_NUMERICAL;
     else if (si == SPOCK_MAX_ITER && status == SPOCK_OK) status = SPOCK_MAX_ITER;
@@ -1026,24 +1154,23 @@ static int batch_solve(Batch& B, const double* const* x0, const spock_settings& 
       spock_info& I = infos[i];
       std::memset(&I, 0, sizeof(I));
       I.status = si;
-      I.iterations = fin.k;
-      I.n_T = fin.n_T;
-      I.n_K0 = fin.n_k0;
-      I.n_K1 = fin.n_k1;
-      I.n_K2 = fin.n_k2;
-      I.n_cap = fin.n_cap;
-      I.n_backtracks = fin.n_back;
-      I.xi = fin.xi;
-      I.xi0 = fin.xi0;
+      I.iterations = f.k;
+      I.n_T = f.n_T;
+      I.n_K0 = f.n_k0;
+      I.n_K1 = f.n_k1;
+      I.n_K2 = f.n_k2;
+      I.n_cap = f.n_cap;
+      I.n_backtracks = f.n_back;
+      I.xi = f.xi;
+      I.xi0 = f.xi0;
       I.alpha = alphas[i];
-      I.solve_ms = ms;  // wall time of the whole batch
-      I.n_launches = (int32_t)std::min<int64_t>(launches[i] + graph_launches * (B.g_launches / std::max(n, 1)),
-                                                INT32_MAX);
+      I.solve_ms = ms;  // the whole batch
+      I.n_launches = (int32_t)std::min<int64_t>(total_launches, INT32_MAX);  // the whole batch
       I.certified = sizeof(S) == 8 ? 1 : 0;
-      I.fp64_iterations = sizeof(S) == 8 ? fin.k : 0;
-      I.xi_fp32 = sizeof(S) == 8 ? NAN : fin.xi;
+      I.fp64_iterations = sizeof(S) == 8 ? f.k : 0;
+      I.xi_fp32 = sizeof(S) == 8 ? NAN : f.xi;
     }
-    check_device_flag(P, st);
+    check_device_flag(*B.probs[i], B.main);
   }
   if (status == SPOCK_ERR_NUMERICAL) return fail(status, "non-finite residual in a batch instance");
   return status;
@@ -1702,17 +1829,15 @@ int spock_batch_create(int32_t n, spock_problem* const* problems, spock_batch** 
           delete B;
           return fail(SPOCK_ERR_INVALID_ARG, "not a problem handle in the batch");
         }
+        for (Problem* q : B->probs)
+          if (q == P) {
+            delete B;
+            return fail(SPOCK_ERR_INVALID_ARG, "a problem appears twice in the batch (instances need their own problem)");
+          }
         B->probs.push_back(P);
       }
       CUDA_TRY(cudaSetDevice(B->probs[0]->device));
       CUDA_TRY(cudaStreamCreateWithFlags(&B->main, cudaStreamNonBlocking));
-      CUDA_TRY(cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming));
-      B->streams.resize(n);
-      B->joins.resize(n);
-      for (int i = 0; i < n; ++i) {
-        CUDA_TRY(cudaStreamCreateWithFlags(&B->streams[i], cudaStreamNonBlocking));
-        CUDA_TRY(cudaEventCreateWithFlags(&B->joins[i], cudaEventDisableTiming));
-      }
       CUDA_TRY(cudaMalloc(&B->st_ptrs, sizeof(SmState*) * n));
       CUDA_TRY(cudaMalloc(&B->done_dev, sizeof(int32_t) * n));
       CUDA_TRY(cudaMallocHost(&B->done_host, sizeof(int32_t) * n));

@@ -107,9 +107,6 @@ struct Problem {
   // solver workspace, allocated on first use per precision
   struct Workspace* ws64 = nullptr;
   struct Workspace* ws32 = nullptr;
-  // Riccati kernel family picked by the batch autotuner, per precision
-  // (-3 = not tuned yet)
-  int tuned_family[2] = {-3, -3};
   ~Problem();
 };
 

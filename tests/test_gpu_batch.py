@@ -69,3 +69,42 @@ def test_batch_converges():
     infos2 = spock.spock_batch_solve_dev(batch, [b[0] for b in bufs], s, [b[1] for b in bufs], [b[2] for b in bufs], 1)
     assert all(i2.status == spock.SPOCK_OK and i2.iterations < i1.iterations for i1, i2 in zip(infos, infos2))
     spock.spock_free(batch)
+
+
+@pytest.mark.parametrize("precision,tile", [(0, "1"), (0, "4"), (1, "1")])
+def test_batch_heterogeneous_workload_matches_single(precision, tile, monkeypatch):
+    """16 instances of the batched workload (branching 2-4, N 5-15, nx
+    10-30, nu 4-10, scenario cap 64): every instance's fixed-iteration
+    result equals the single-instance solver's (the batched kernels run the
+    same per-node bodies with the largest lane layout of the batch; the
+    single solves use the same direct Riccati kernels; node tile fixed)."""
+    import torch
+    from paper_2212_01110_gb300 import spock
+    monkeypatch.setenv("SPOCK_RICCATI_KERNELS", "direct")
+    monkeypatch.setenv("SPOCK_BATCH_TILE", tile)
+    dev = torch.device("cuda:0")
+    ds = W.batch_instances(seed=3, count=16)
+    assert len({(d["nx"], d["nu"]) for d in ds}) > 4
+    probs = [spock.Problem(d) for d in ds]
+    batch = spock.spock_batch_create([p.handle for p in probs])
+    bufs = [_tensors(P, d, dev) for P, d in zip(probs, ds)]
+    K = 12
+    s = spock.spock_default_settings(max_iter=K, eps_abs=1e-14, eps_rel=1e-14, precision=precision, fp64_tail=0)
+    infos = spock.spock_batch_solve_dev(batch, [b[0] for b in bufs], s, [b[1] for b in bufs], [b[2] for b in bufs], 0)
+    for P, (x0, z, e), inf in zip(probs, bufs, infos):
+        assert inf.iterations == K
+        z1, e1 = torch.zeros_like(z), torch.zeros_like(e)
+        inf1 = spock.spock_solve_dev(P.handle, x0, s, z1, e1, 0)
+        a = torch.cat([z, e]).cpu().numpy()
+        b = torch.cat([z1, e1]).cpu().numpy()
+        err = np.max(np.abs(a - b)) / max(1, np.max(np.abs(b)))
+        assert err < (1e-9 if precision == 0 else 1e-4), err
+        assert inf.n_T == inf1.n_T
+    spock.spock_free(batch)
+
+
+def test_batch_rejects_duplicate_problem():
+    from paper_2212_01110_gb300 import spock
+    P = spock.Problem(W.small_binary(0))
+    with pytest.raises(spock.SpockError):
+        spock.spock_batch_create([P.handle, P.handle])
