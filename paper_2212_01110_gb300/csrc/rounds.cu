@@ -374,8 +374,8 @@ __device__ __forceinline__ void round_point_body(const SmState* __restrict__ st,
 #pragma unroll
   for (int j = 0; j < MEM; ++j) g[j] = (j < cnt) ? (S)st->gamma[j] : S(0);
   const S tau = (S)st->tau, coef = (S)st->coef, lam = (S)st->lam;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)nblk * blockDim.x;
+  const int64_t gt = (int64_t)bid * blockDim.x + threadIdx.x;
   const int64_t npack = n / NP;
   for (int64_t q = gt; q < npack; q += stride) {
     PT v = rld(V, q), out;
