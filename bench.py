@@ -546,6 +546,8 @@ def main():
     ap.add_argument("--paper-max-iter", type=int, default=20000)
     ap.add_argument("--batch", type=int, default=512, help="instances of the batched measurement (0 skips it)")
     ap.add_argument("--batch-iter", type=int, default=50)
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the batched measurement and print it (profiling aid, not a bench line)")
     ap.add_argument("--grad-instances", type=int, default=64,
                     help="instances of the gradient measurement (0 skips it)")
     ap.add_argument("--grad-iter", type=int, default=2000,
@@ -558,6 +560,14 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.batch_only:   # profiling aid: the batched measurement alone
+        import torch
+        from paper_2212_01110_gb300 import build
+        build.build()
+        from paper_2212_01110_gb300 import spock, workloads
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"batch": batch_workload(args, spock, workloads, torch.device("cuda", local_rank))}))
         return
     if world > 1:
         import torch
