@@ -172,13 +172,14 @@ __device__ __forceinline__ S clampv(S v, S lo, S hi) {
   return v < lo ? lo : (v > hi ? hi : v);
 }
 
-// Statistics accumulator of one lane: sums in FP64.  Terms are first summed
-// in the working precision S; FP32 lanes convert and add to FP64 once every
-// kFlushNodes nodes (a few hundred terms at most), FP64 lanes once per node.
-// Each flush costs eight FP64-pipe warp instructions (plus conversions in
-// FP32) whatever the number of active lanes, and that pipe runs at 1/64 of
-// the FP32 rate on this GPU, so flushing per node would dominate the FP32
-// vector kernels.
+// Statistics accumulator: sums in FP64.  Terms are first summed in the
+// working precision S.  FP64: every lane adds its node sums to its own FP64
+// accumulator, and the block store reduces across lanes.  FP32: every
+// kFlushNodesF32 nodes (and at the end) the warp reduces its lanes' FP32
+// sums with shuffles and lane 0 alone adds them in FP64.  Every FP64
+// operation costs a 64-cycle slot of its sub-partition's FP64 pipe per warp
+// instruction on this GPU, whatever the number of active lanes, so the FP32
+// kernels keep FP64 work to ~16 warp instructions per 32 nodes.
 struct StatAcc {
   double s[8];
   __device__ void zero() {
@@ -186,7 +187,12 @@ struct StatAcc {
     for (int i = 0; i < 8; ++i) s[i] = 0.0;
   }
 };
-constexpr int kFlushNodes = 16;
+constexpr int kFlushNodesF32 = 32;
+__device__ __forceinline__ float warp_max_f(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
 template <typename S>
 struct NodeAcc {
   S s[8];
@@ -196,29 +202,42 @@ struct NodeAcc {
     for (int i = 0; i < 8; ++i) s[i] = S(0);
     nodes = 0;
   }
+  // all lanes of the warp call it
   __device__ __forceinline__ void flush(StatAcc& a) {
+    if (sizeof(S) == 4) {
+      const bool lead = (threadIdx.x & 31) == 0;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      if (i == 3 || i == 4) a.s[i] = fmax(a.s[i], (double)s[i]);
-      else a.s[i] += (double)s[i];
+      for (int i = 0; i < 8; ++i) {
+        const bool mx = (i == 3 || i == 4);
+        const float v = mx ? warp_max_f((float)s[i]) : warp_sum((float)s[i]);
+        if (lead) a.s[i] = mx ? fmax(a.s[i], (double)v) : a.s[i] + (double)v;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (i == 3 || i == 4) a.s[i] = fmax(a.s[i], (double)s[i]);
+        else a.s[i] += (double)s[i];
+      }
     }
     zero();
   }
   // end of a node: flush when due
   __device__ __forceinline__ void node_done(StatAcc& a) {
-    if (sizeof(S) == 8 || ++nodes == kFlushNodes) flush(a);
+    if (sizeof(S) == 8 || ++nodes == kFlushNodesF32) flush(a);
   }
 };
 
-// Reduces the per-lane statistics of a block and writes row `row` of the
-// partials.  Sums for sums, maxima for ST_XIP / ST_XID.
+// Reduces the statistics of a block (after the final flush) and writes row
+// `row` of the partials.  Sums for sums, maxima for ST_XIP / ST_XID.  With
+// LEAD (FP32 kernels) lane 0 of every warp already holds its warp's totals.
+template <bool LEAD>
 __device__ __forceinline__ void block_stats_store(StatAcc& a, double* partials, int row) {
   __shared__ double red[kWarpsPerBlock][8];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     double v = a.s[i];
-    v = (i == ST_XIP || i == ST_XID) ? warp_max(v) : warp_sum(v);
+    if (!LEAD) v = (i == ST_XIP || i == ST_XID) ? warp_max(v) : warp_sum(v);
     if (lane == 0) red[w][i] = v;
   }
   __syncthreads();

@@ -217,7 +217,7 @@ __device__ __forceinline__ void lstar_body(const KP<S>& p, int bid, int nblk, co
   }
   if (STATS) {
     nacc.flush(acc);
-    block_stats_store(acc, partials, bid);
+    block_stats_store<sizeof(S) == 4>(acc, partials, bid);
   }
 }
 
@@ -489,7 +489,7 @@ __device__ __forceinline__ void dual_body(const KP<S>& p, int bid, int nblk, con
   }
   if (ST) {
     nacc.flush(acc);
-    block_stats_store(acc, partials, bid);
+    block_stats_store<sizeof(S) == 4>(acc, partials, bid);
   }
 }
 

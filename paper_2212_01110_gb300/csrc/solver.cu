@@ -229,7 +229,10 @@ static Workspace* get_ws_impl(Problem& P, int mem) {
     ws->zero_eta = ws->alloc(sizeof(double) * (size_t)P.off.n_eta);
     CUDA_TRY(cudaMemset(ws->zero_eta, 0, sizeof(double) * (size_t)P.off.n_eta));
     const int sms = sm_count();
-    ws->grid_d = std::min((P.tree.n + kWarpsPerBlock - 1) / kWarpsPerBlock, sms * 16);
+    // one wave of the node kernels (their register counts leave about four
+    // resident 128-thread blocks per SM in FP32, three in FP64): fewer
+    // end-of-block statistics reductions
+    ws->grid_d = std::min((P.tree.n + kWarpsPerBlock - 1) / kWarpsPerBlock, sms * (sizeof(S) == 8 ? 3 : 4));
     ws->grid_d = std::max(ws->grid_d, 1);
     ws->grid_p = ws->grid_d;
     ws->grid_v = sms * 4;
