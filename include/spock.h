@@ -304,7 +304,7 @@ int spock_batch_create(int32_t n, spock_problem* const* problems, spock_batch** 
  * is captured into one CUDA graph; finished instances skip their work; the
  * host only reads the done flags after each graph launch.  Before the first
  * solve in a precision, the node tile of the vector kernels (nodes per
- * warp: 1, 2 or 4) is picked by timing batched evaluations of T
+ * warp: 1, 2, 4, 8 or 16) is picked by timing batched evaluations of T
  * (autotuner).  info.solve_ms and info.n_launches describe the whole batch.
  *   x0_dev, z_dev, eta_dev : host arrays of n device pointers (FP64), per
  *     instance as in spock_solve_dev.

@@ -1027,15 +1027,18 @@ static void batch_init(Batch& B, const std::vector<Workspace*>& wss, const std::
   }
 }
 
-// Autotuner of the batch: the node tile (nodes per warp of the node kernels)
-// with the shortest batched T evaluation, timed over three evaluations per
-// candidate; cached per batch and precision.
+// Autotuner of the batch: the node tile (nodes per warp of the node kernels:
+// 1, 2, 4, 8 or 16) with the shortest batched T evaluation, timed over three
+// evaluations per candidate; cached per batch and precision.
 template <typename S>
 static int batch_tune(Batch& B, const std::vector<Workspace*>& wss, const std::vector<double>& alphas, int mem,
                       const spock_settings& s, const double* const* x0, double* const* z, double* const* eta,
                       int warm) {
   const char* env = getenv("SPOCK_BATCH_TILE");  // fixed tile (tests, experiments)
-  if (env && (env[0] == '1' || env[0] == '2' || env[0] == '4') && env[1] == 0) return env[0] - '0';
+  if (env && env[0]) {
+    const int t = atoi(env);
+    if (t == 1 || t == 2 || t == 4 || t == 8 || t == 16) return t;
+  }
   int& slot = B.tuned_tile[sizeof(S) == 8 ? 0 : 1];
   if (slot > 0) return slot;
   cudaEvent_t a, b;
@@ -1043,7 +1046,7 @@ static int batch_tune(Batch& B, const std::vector<Workspace*>& wss, const std::v
   CUDA_TRY(cudaEventCreate(&b));
   float best = 1e30f;
   int pick = 1;
-  for (int tile : {1, 2, 4}) {
+  for (int tile : {1, 2, 4, 8, 16}) {
     batch_plan<S>(B, wss, alphas, mem, tile);
     batch_init<S>(B, wss, alphas, s, mem, x0, z, eta, warm);
     batch_eval<S>(B, B.main);  // warm-up
