@@ -270,6 +270,7 @@ def run_ours(args, rank, world, local_rank):
                   "call, K iterations from a cold start"}
 
     paper = paper_workload(args, spock, workloads, dev) if (rank == 0 and args.paper_workload) else None
+    small = small_workload(args, spock, workloads, dev) if rank == 0 else None
     batch = batch_workload(args, spock, workloads, dev, seed=rank) if args.batch > 0 else None
     grad = grad_workload(args, spock, workloads, dev) if (rank == 0 and args.grad_instances > 0) else None
 
@@ -311,6 +312,8 @@ def run_ours(args, rank, world, local_rank):
                             if (tt and tf and tt["status"] == "converged" and tf["status"] == "converged") else None}
         if paper:
             line["paper_workload"] = paper
+        if small:
+            line["small_tree"] = small
         if batch:
             line["batch"] = batch
         if grad:
@@ -318,6 +321,48 @@ def run_ours(args, rank, world, local_rank):
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
+
+
+def small_workload(args, spock, workloads, dev):
+    """Config-1 tree (binary, N = 3, 15 nodes, nx = 3, nu = 2): time to the
+    1e-6 residual in FP64 (Anderson m = 3; the captured graph reused, so
+    the second solve is timed), and the FP32 iteration with FP64 factors,
+    residual, Anderson m = 5 and FP64 certification/tail: its optimal cost
+    and trajectory against a tight FP64 solve (1e-11) of the same problem."""
+    import torch
+    d = workloads.small_binary(0)
+    P = spock.Problem(d)
+    x0 = torch.tensor(d["x0"], dtype=torch.float64, device=dev)
+
+    def solve(prec, mem, tol):
+        z = torch.zeros(P.n_z, dtype=torch.float64, device=dev)
+        e = torch.zeros(P.n_eta, dtype=torch.float64, device=dev)
+        st = spock.spock_default_settings(precision=prec, memory=mem, eps_abs=tol, eps_rel=tol, max_iter=100000)
+        inf = spock.spock_solve_dev(P.handle, x0, st, z, e, 0)
+        return z, inf
+
+    solve(spock.SPOCK_FP64, 3, 1e-6)
+    _, inf = solve(spock.SPOCK_FP64, 3, 1e-6)
+    out = {"nodes": len(d["anc"]), "n_z": P.n_z, "n_eta": P.n_eta,
+           "fp64_to_1e-6": {"ms": round(inf.solve_ms, 3), "iterations": inf.iterations, "n_T": inf.n_T,
+                            "T_per_s": round(inf.n_T / (inf.solve_ms * 1e-3), 1),
+                            "status": "converged" if inf.status == 0 else "max_iter"}}
+    zr, _ = solve(spock.SPOCK_FP64, 5, 1e-11)
+    solve(spock.SPOCK_FP32, 5, 1e-6)
+    z32, inf32 = solve(spock.SPOCK_FP32, 5, 1e-6)
+    n, nx, nu = len(d["anc"]), d["nx"], d["nu"]
+    nl = n - int(np.sum(np.bincount(d["anc"][1:], minlength=n) == 0))
+    a, b = z32.cpu().numpy(), zr.cpu().numpy()
+    xs = slice(1, 1 + n * nx)
+    us = slice(1 + n * nx, 1 + n * nx + nl * nu)
+    out["fp32_fp64tail_m5"] = {
+        "ms": round(inf32.solve_ms, 3), "iterations": inf32.iterations, "fp64_iterations": inf32.fp64_iterations,
+        "certified": bool(inf32.certified), "xi": inf32.xi,
+        "cost_abs_err": abs(a[0] - b[0]), "cost_rel_err": abs(a[0] - b[0]) / max(abs(b[0]), 1e-300),
+        "x_max_err": float(np.max(np.abs(a[xs] - b[xs]))), "u_max_err": float(np.max(np.abs(a[us] - b[us]))),
+        "reference": "FP64 solve of the same problem to 1e-11 (the FP64 path is parity-tested against the oracle)"}
+    P.close()
+    return out
 
 
 def paper_workload(args, spock, workloads, dev):
