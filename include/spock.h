@@ -116,7 +116,8 @@ typedef struct spock_info {
      [0] zbar = z - alpha L* eta and proj_S2, [1] Riccati backward, chain
      region, [2] Riccati backward, branching stages, [3] Riccati forward,
      branching stages, [4] Riccati forward, chain region, [5] L and
-     prox_{alpha g*} (dual update), [6] residual statistics */
+     prox_{alpha g*} (dual update, with the residual statistics accumulated
+     in the same pass), [6] reduction of the statistics */
   double t_group_ms[7];
   int32_t fp64_iterations; /* SPOCK_FP32 with fp64_tail: iterations run in FP64 */
   int32_t certified;       /* 1 if the returned pair's xi was computed in FP64 */

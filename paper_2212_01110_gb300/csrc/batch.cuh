@@ -30,7 +30,6 @@ struct BInst {
   S* D;
   double* stats;   // [8] statistics of the last evaluation
   double* pd;      // partial statistics of the dual kernel, nb_node rows
-  double* pp;      // ... of the primal statistics kernel, nb_node rows
   double* paa;     // partial Gram rows of the commit kernel, nb_vec rows
   int64_t n_v, ld;
   int32_t nb_node, nb_vec;
@@ -47,8 +46,9 @@ struct BMap {
 };
 
 // ops.cu: which = 0 prox-f preparation (L* eta, proj_S2), 1 dual update with
-// statistics, 2 primal statistics, 3 reduction of the statistics (one block
-// per instance; m unused).  J = lane slots for blocks of nx + nu + 2.
+// the dual and primal statistics (warp per nonleaf node), 3 reduction of the
+// statistics (one block per instance; m unused).  J = lane slots for blocks
+// of nx + nu + 2.
 template <typename S>
 void launch_node_ops_b(int which, const BInst<S>* bi, const BMap& m, int nblocks, int n_inst, int J,
                        cudaStream_t st);

@@ -4,12 +4,12 @@
 //                      the (x, u) part goes to the Riccati scratch (prox of
 //                      f, Sec. "Proximal operator of f", Sec. "Projection on
 //                      S2");
-//            LS_APPLY  z_out = L* eta (operator-level ABI);
-//            LS_STATS  primal residual statistics (xi_p, ||r_z||^2, r . d).
-//   k_dual   eta+ = prox_{alpha g*}(eta + alpha L (2 z+ - z)) with the cone
-//            projections of Eq. (S3-def); optional residual statistics
-//            (Sec. "The Chambolle-Pock method", Algorithm 3).  Also L z
-//            and prox_{alpha g*}(eta) alone for the operator-level ABI.
+//            LS_APPLY  z_out = L* eta (operator-level ABI).
+//   k_dual_fused  eta+ = prox_{alpha g*}(eta + alpha L (2 z+ - z)) with the
+//            cone projections of Eq. (S3-def) and every residual statistic of
+//            Sec. "The Chambolle-Pock method" / Algorithm 3 in one pass.
+//   k_dual   the same update without statistics, L z, and prox_{alpha g*}(eta)
+//            alone for the operator-level ABI.
 // L and its adjoint are never stored: each entry of eta = L z is a sum over
 // the node's own variables and its ancestor's (definition of L).
 //
@@ -27,7 +27,7 @@
 namespace spock {
 
 enum DualMode : int { DM_APPLY_L = 0, DM_PROXG = 1, DM_DUAL = 2 };
-enum LstarMode : int { LS_APPLY = 0, LS_STATS = 1, LS_PREP = 2 };
+enum LstarMode : int { LS_APPLY = 0, LS_PREP = 2 };
 constexpr int kMaxJ = (kMaxDim + 2 + 31) / 32;   // entries per lane for the largest blocks
 
 // ---------------------------------------------------------------------------
@@ -42,36 +42,17 @@ constexpr int kMaxJ = (kMaxDim + 2 + 31) / 32;   // entries per lane for the lar
 //   s^0:                  w_nl^0[s - b'y]
 // Body shared by the single-problem and the batched kernels: block `bid` of
 // `nblk` working for problem p.
-template <typename S, int MODE, bool DIR, int J>
+template <typename S, int MODE, int J>
 __device__ __forceinline__ void lstar_body(const KP<S>& p, int bid, int nblk, const S* __restrict__ eta,
-                                           const S* __restrict__ etap, const S* __restrict__ z,
-                                           const S* __restrict__ zp, S* __restrict__ zo,
-                                           const S* __restrict__ dir, double* __restrict__ partials) {
+                                           const S* __restrict__ z, S* __restrict__ zo) {
   if (p.skip && *p.skip) return;
-  constexpr bool STATS = MODE == LS_STATS;
-  constexpr bool DR = STATS && DIR;
   const int lane = threadIdx.x & 31;
   const int gw = (bid * blockDim.x + threadIdx.x) >> 5;
   const int nw = (nblk * blockDim.x) >> 5;
   const int nx = p.nx, nu = p.nu;
   const S al = p.alpha;
-  StatAcc acc;
-  acc.zero();
-  NodeAcc<S> nacc;
-  nacc.zero();
-  auto E = [&](int64_t i) -> S { return STATS ? eta[i] - etap[i] : eta[i]; };
-  // one z entry with its value of L* w: write it (APPLY) or accumulate the
-  // primal residual statistics (STATS)
-  auto emit = [&](int64_t zi, S lt) {
-    if (MODE == LS_APPLY) {
-      zo[zi] = lt;
-    } else if (STATS) {
-      const S rz = z[zi] - zp[zi];
-      nacc.s[ST_RZ2] += rz * rz;
-      nacc.s[ST_XIP] = vmax(nacc.s[ST_XIP], vabs(rz * p.inv_alpha - lt));
-      if (DR) nacc.s[ST_RD] += rz * dir[zi];
-    }
-  };
+  auto E = [&](int64_t i) -> S { return eta[i]; };
+  auto emit = [&](int64_t zi, S lt) { zo[zi] = lt; };   // LS_APPLY
   uint32_t wnext = gw < p.n ? desc_word(p.desc, gw, lane) : 0u;
   for (int k = gw; k < p.n; k += nw) {
     const NodeF D = node_fields(wnext);
@@ -81,18 +62,15 @@ __device__ __forceinline__ void lstar_body(const KP<S>& p, int bid, int nblk, co
       const int nxu = nx + nu;
       const int64_t ex = D.enl + 2 * m + 2;
       // ---- (x, u): own rows and the first child's nonroot rows, in registers
-      S lt[J], zv[J], zpv[J], dv[J];
+      S lt[J], zv[J];
 #pragma unroll
       for (int j = 0; j < J; ++j) {
         const int e = lane + 32 * j;
-        lt[j] = zv[j] = zpv[j] = dv[j] = S(0);
+        lt[j] = zv[j] = S(0);
         if (e < nxu) {
           const S coef = e < nx ? p.qs[(int64_t)c0 * nx + e] : p.rs[(int64_t)c0 * nu + (e - nx)];
           lt[j] = E(ex + e) + coef * E(D.enr_c0 + e);
-          const int64_t zi = e < nx ? D.zx + e : D.zu + (e - nx);
-          if (MODE != LS_APPLY) zv[j] = z[zi];
-          if (STATS) zpv[j] = zp[zi];
-          if (DR) dv[j] = dir[zi];
+          if (MODE == LS_PREP) zv[j] = z[e < nx ? D.zx + e : D.zu + (e - nx)];
         }
       }
       for (int c = 1; c < m; ++c) {   // further children (branching stages only)
@@ -113,13 +91,8 @@ __device__ __forceinline__ void lstar_body(const KP<S>& p, int bid, int nblk, co
           if (MODE == LS_PREP) {
             if (e < nx) p.xbar[(int64_t)k * p.xs + e] = zv[j] - al * lt[j];
             else p.ubar[(int64_t)k * p.us + (e - nx)] = zv[j] - al * lt[j];
-          } else if (MODE == LS_APPLY) {
-            zo[e < nx ? D.zx + e : D.zu + (e - nx)] = lt[j];
           } else {
-            const S rz = zv[j] - zpv[j];
-            nacc.s[ST_RZ2] += rz * rz;
-            nacc.s[ST_XIP] = vmax(nacc.s[ST_XIP], vabs(rz * p.inv_alpha - lt[j]));
-            if (DR) nacc.s[ST_RD] += rz * dv[j];
+            zo[e < nx ? D.zx + e : D.zu + (e - nx)] = lt[j];
           }
         }
       }
@@ -213,20 +186,13 @@ __device__ __forceinline__ void lstar_body(const KP<S>& p, int bid, int nblk, co
         }
       }
     }
-    if (STATS) nacc.node_done(acc);
-  }
-  if (STATS) {
-    nacc.flush(acc);
-    block_stats_store<sizeof(S) == 4>(acc, partials, bid);
   }
 }
 
-template <typename S, int MODE, bool DIR, int J>
-__global__ void __launch_bounds__(128) k_lstar(KP<S> p, const S* __restrict__ eta, const S* __restrict__ etap,
-                                               const S* __restrict__ z, const S* __restrict__ zp,
-                                               S* __restrict__ zo, const S* __restrict__ dir,
-                                               double* __restrict__ partials) {
-  lstar_body<S, MODE, DIR, J>(p, blockIdx.x, gridDim.x, eta, etap, z, zp, zo, dir, partials);
+template <typename S, int MODE, int J>
+__global__ void __launch_bounds__(128) k_lstar(KP<S> p, const S* __restrict__ eta, const S* __restrict__ z,
+                                               S* __restrict__ zo) {
+  lstar_body<S, MODE, J>(p, blockIdx.x, gridDim.x, eta, z, zo);
 }
 
 // ---------------------------------------------------------------------------
@@ -500,6 +466,257 @@ __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, 
   dual_body<S, MODE, STATS, DIR, J>(p, blockIdx.x, gridDim.x, z, zp, eta, out, dir, partials);
 }
 
+// ---------------------------------------------------------------------------
+// k_dual_fused: the dual update with all residual statistics in one pass.
+// One warp per NONLEAF node k owns every eta row that involves k's
+// variables: k's nonleaf block, the nonroot block of each child c (rows of
+// Q^c 1/2 x^k, R^c 1/2 u^k, tau^c) and the leaf block of each leaf child.
+// Each z entry's rows of L then lie in one warp, which therefore has the
+// whole of (L* r_eta) there and accumulates the primal statistics as well:
+//   x^k, u^k:  own box rows + sum_c (Q^c or R^c)^1/2 nonroot rows of c
+//   y^k:       y rows - b (s - b'y) row;   s^k (nonleaf): the s - b'y row
+//   tau^c:     the two tau rows of c's nonroot block
+//   x^c, s^c (leaf c): c's leaf block.
+// The nonroot blocks reuse x^k, u^k already in registers.
+// ---------------------------------------------------------------------------
+template <typename S, bool DR>
+__device__ __forceinline__ void primal_stat(NodeAcc<S>& a, S inv_alpha, S zv, S zpv, S dv, S lt) {
+  const S rz = zv - zpv;
+  a.s[ST_RZ2] += rz * rz;
+  a.s[ST_XIP] = vmax(a.s[ST_XIP], vabs(rz * inv_alpha - lt));
+  if (DR) a.s[ST_RD] += rz * dv;
+}
+
+template <typename S, bool DIR, int J>
+__device__ __forceinline__ void dual_fused_body(const KP<S>& p, int bid, int nblk, const S* __restrict__ z,
+                                                const S* __restrict__ zp, const S* __restrict__ eta,
+                                                S* __restrict__ out, const S* __restrict__ dir,
+                                                double* __restrict__ partials) {
+  if (p.skip && *p.skip) return;
+  constexpr bool DR = DIR;
+  const int lane = threadIdx.x & 31;
+  const int gw = (bid * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (nblk * blockDim.x) >> 5;
+  const S al = p.alpha, ial = p.inv_alpha;
+  const int nx = p.nx, nu = p.nu, nxu = nx + nu, nb = nxu + 2;
+  const S* dz = DR ? dir : nullptr;
+  const S* deta = DR ? dir + p.n_z : nullptr;
+  StatAcc acc;
+  acc.zero();
+  NodeAcc<S> nacc;
+  nacc.zero();
+  uint32_t wnext = gw < p.nl ? desc_word(p.desc, gw, lane) : 0u;
+  for (int k = gw; k < p.nl; k += nw) {
+    const NodeF D = node_fields(wnext);
+    if (k + nw < p.nl) wnext = desc_word(p.desc, k + nw, lane);
+    const int m = D.m, c0 = D.c0;
+    const int64_t el = D.enl, ea = el + 2 * m + 2, z2 = D.zz2;
+    // ---- own (x, u) and its box rows
+    S az[J], azp[J], adz[J], lt[J];
+    {
+      S ae[J], ade[J], alo[J], ahi[J];
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const int e = lane + 32 * j;
+        az[j] = azp[j] = adz[j] = lt[j] = ae[j] = ade[j] = alo[j] = ahi[j] = S(0);
+        if (e < nxu) {
+          const int64_t zi = e < nx ? D.zx + e : D.zu + (e - nx);
+          az[j] = z[zi];
+          azp[j] = zp[zi];
+          if (DR) adz[j] = dz[zi];
+          ae[j] = eta[ea + e];
+          if (DR) ade[j] = deta[ea + e];
+          alo[j] = e < nx ? p.xlo[(int64_t)k * nx + e] : p.ulo[(int64_t)k * nu + (e - nx)];
+          ahi[j] = e < nx ? p.xhi[(int64_t)k * nx + e] : p.uhi[(int64_t)k * nu + (e - nx)];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const int e = lane + 32 * j;
+        if (e < nxu) {
+          const S w = dual_w<S, DM_DUAL>(al, ae[j], az[j], azp[j]);
+          const S o = w - al * clampv(w * ial, alo[j], ahi[j]);
+          out[ea + e] = o;
+          dual_stat<S, true, DR>(nacc, ial, ae[j], o, az[j] - azp[j], ade[j], adz[j]);
+          lt[j] = ae[j] - o;
+        }
+      }
+    }
+    // ---- children
+    for (int jc = 0; jc < m; ++jc) {
+      const int c = c0 + jc;
+      const int64_t er = jc == 0 ? D.enr_c0 : __ldg(&p.desc[c].enr);
+      const int64_t ztau = z2 + 2 * m + 1 + jc;
+      const S tz = z[ztau], tzp = zp[ztau], tdz = DR ? dz[ztau] : S(0);
+      {  // nonroot block of c: SOC on (Q^c 1/2 x^k, R^c 1/2 u^k, tau^c / 2, tau^c / 2)
+        S w[J], lrz[J], ld[J], be[J], bde[J], bc[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const int e = lane + 32 * j;
+          w[j] = lrz[j] = ld[j] = be[j] = bde[j] = bc[j] = S(0);
+          if (e < nb) {
+            const S coef = e < nx ? p.qs[(int64_t)c * nx + e]
+                                  : (e < nxu ? p.rs[(int64_t)c * nu + (e - nx)] : S(0.5));
+            const S Lz = coef * (e < nxu ? az[j] : tz);
+            const S Lzp = coef * (e < nxu ? azp[j] : tzp);
+            be[j] = eta[er + e];
+            if (DR) {
+              bde[j] = deta[er + e];
+              ld[j] = coef * (e < nxu ? adz[j] : tdz);
+            }
+            w[j] = dual_w<S, DM_DUAL>(al, be[j], Lz, Lzp);
+            lrz[j] = Lz - Lzp;
+            bc[j] = coef;
+          }
+        }
+        S nv, t, sc;
+        soc_norm<S, J>(w, nb, ial, lane, nv, t, sc);
+        S tau_part = 0;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const int e = lane + 32 * j;
+          if (e < nb) {
+            const S o = soc_entry(w[j], e, nb, al, ial, nv, t, sc);
+            out[er + e] = o;
+            dual_stat<S, true, DR>(nacc, ial, be[j], o, lrz[j], bde[j], ld[j]);
+            const S re = be[j] - o;
+            if (e < nxu) lt[j] += bc[j] * re;
+            else tau_part += re;
+          }
+        }
+        tau_part = warp_sum(tau_part);
+        if (lane == 0) primal_stat<S, DR>(nacc, ial, tz, tzp, tdz, S(0.5) * tau_part);
+      }
+      if (c >= p.nl) {  // leaf block of c: box on x^c, SOC on (Q_N^1/2 x^c, s^c / 2, s^c / 2)
+        const int64_t ef = (jc == 0 ? D.es_c0 : __ldg(&p.desc[c].es)) - 2 * nx;
+        const int64_t zxc = __ldg(&p.desc[c].zx);
+        const int64_t zsc = z2 + 3 * m + 1 + jc;
+        const S sz = z[zsc], szp = zp[zsc], sdz = DR ? dz[zsc] : S(0);
+        S xz[J], xzp[J], xdz[J], ltx[J];
+        {
+          S fe[J], fde[J], flo[J], fhi[J];
+#pragma unroll
+          for (int j = 0; j < J; ++j) {
+            const int e = lane + 32 * j;
+            xz[j] = xzp[j] = xdz[j] = ltx[j] = fe[j] = fde[j] = flo[j] = fhi[j] = S(0);
+            if (e < nx) {
+              xz[j] = z[zxc + e];
+              xzp[j] = zp[zxc + e];
+              if (DR) xdz[j] = dz[zxc + e];
+              fe[j] = eta[ef + e];
+              if (DR) fde[j] = deta[ef + e];
+              flo[j] = p.xlo[(int64_t)c * nx + e];
+              fhi[j] = p.xhi[(int64_t)c * nx + e];
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < J; ++j) {
+            const int e = lane + 32 * j;
+            if (e < nx) {
+              const S w = dual_w<S, DM_DUAL>(al, fe[j], xz[j], xzp[j]);
+              const S o = w - al * clampv(w * ial, flo[j], fhi[j]);
+              out[ef + e] = o;
+              dual_stat<S, true, DR>(nacc, ial, fe[j], o, xz[j] - xzp[j], fde[j], xdz[j]);
+              ltx[j] = fe[j] - o;
+            }
+          }
+        }
+        const int dim = nx + 2;
+        const int64_t es = ef + nx;
+        S w[J], lrz[J], ld[J], ev[J], dev[J], qn[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const int e = lane + 32 * j;
+          w[j] = lrz[j] = ld[j] = ev[j] = dev[j] = qn[j] = S(0);
+          if (e < dim) {
+            const S coef = e < nx ? p.qns[(int64_t)c * nx + e] : S(0.5);
+            const S Lz = coef * (e < nx ? xz[j] : sz);
+            const S Lzp = coef * (e < nx ? xzp[j] : szp);
+            ev[j] = eta[es + e];
+            if (DR) {
+              dev[j] = deta[es + e];
+              ld[j] = coef * (e < nx ? xdz[j] : sdz);
+            }
+            w[j] = dual_w<S, DM_DUAL>(al, ev[j], Lz, Lzp);
+            lrz[j] = Lz - Lzp;
+            qn[j] = coef;
+          }
+        }
+        S nv, t, sc;
+        soc_norm<S, J>(w, dim, ial, lane, nv, t, sc);
+        S s_part = 0;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const int e = lane + 32 * j;
+          if (e < dim) {
+            const S o = soc_entry(w[j], e, dim, al, ial, nv, t, sc);
+            out[es + e] = o;
+            dual_stat<S, true, DR>(nacc, ial, ev[j], o, lrz[j], dev[j], ld[j]);
+            const S re = ev[j] - o;
+            if (e < nx) ltx[j] += qn[j] * re;
+            else s_part += re;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+          if (lane + 32 * j < nx) primal_stat<S, DR>(nacc, ial, xz[j], xzp[j], xdz[j], ltx[j]);
+        s_part = warp_sum(s_part);
+        if (lane == 0) primal_stat<S, DR>(nacc, ial, sz, szp, sdz, S(0.5) * s_part);
+      }
+    }
+    // ---- primal statistics at x^k, u^k
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+      if (lane + 32 * j < nxu) primal_stat<S, DR>(nacc, ial, az[j], azp[j], adz[j], lt[j]);
+    // ---- the s - b'y row of k (b = (p^children, 0, 1)), then the y rows
+    {
+      S bs = 0, bsp = 0, bsd = 0;
+      for (int jj = lane; jj < m; jj += 32) {
+        const S pj = p.prob[c0 + jj];
+        bs += pj * z[z2 + jj];
+        bsp += pj * zp[z2 + jj];
+        if (DR) bsd += pj * dz[z2 + jj];
+      }
+      bs = warp_sum(bs);
+      bsp = warp_sum(bsp);
+      if (DR) bsd = warp_sum(bsd);
+      const int64_t ie = el + 2 * m + 1;
+      const S y3 = z[z2 + 2 * m], y3p = zp[z2 + 2 * m], y3d = DR ? dz[z2 + 2 * m] : S(0);
+      const S sk = z[D.zs], skp = zp[D.zs], skd = DR ? dz[D.zs] : S(0);
+      const S Lz = sk - (bs + y3), Lzp = skp - (bsp + y3p), Ld = DR ? skd - (bsd + y3d) : S(0);
+      const S ev = eta[ie];
+      const S w = dual_w<S, DM_DUAL>(al, ev, Lz, Lzp);
+      const S o = vmin(w, S(0));
+      const S re_sb = ev - o;
+      if (lane == 0) {
+        out[ie] = o;
+        dual_stat<S, true, DR>(nacc, ial, ev, o, Lz - Lzp, DR ? deta[ie] : S(0), Ld);
+        primal_stat<S, DR>(nacc, ial, sk, skp, skd, re_sb);   // s^k (s^0 at the root)
+      }
+      for (int e = lane; e < 2 * m + 1; e += 32) {
+        const S yz = z[z2 + e], yzp = zp[z2 + e], yd = DR ? dz[z2 + e] : S(0);
+        const S ye = eta[el + e];
+        const S yw = dual_w<S, DM_DUAL>(al, ye, yz, yzp);
+        const S yo = e < 2 * m ? vmin(yw, S(0)) : S(0);
+        out[el + e] = yo;
+        dual_stat<S, true, DR>(nacc, ial, ye, yo, yz - yzp, DR ? deta[el + e] : S(0), yd);
+        const S bl = e < m ? p.prob[c0 + e] : (e < 2 * m ? S(0) : S(1));
+        primal_stat<S, DR>(nacc, ial, yz, yzp, yd, (ye - yo) - bl * re_sb);
+      }
+    }
+    nacc.node_done(acc);
+  }
+  nacc.flush(acc);
+  block_stats_store<sizeof(S) == 4>(acc, partials, bid);
+}
+
+template <typename S, bool DIR, int J>
+__global__ void __launch_bounds__(128) k_dual_fused(KP<S> p, const S* __restrict__ z, const S* __restrict__ zp,
+                                                    const S* __restrict__ eta, S* __restrict__ out,
+                                                    const S* __restrict__ dir, double* __restrict__ partials) {
+  dual_fused_body<S, DIR, J>(p, blockIdx.x, gridDim.x, z, zp, eta, out, dir, partials);
+}
+
 // Sums (maxima for xi) of the per-block partial statistics of the dual and
 // primal kernels; one block, fixed order (deterministic).
 __device__ __forceinline__ void reduce_stats_body(const double* __restrict__ pd, int nd,
@@ -534,29 +751,20 @@ __global__ void __launch_bounds__(128) k_prep_b(const BInst<S>* __restrict__ bi,
   const int i = m.inst[blockIdx.x];
   const BInst<S>& b = bi[i];
   const KP<S> p = b.kp;
-  lstar_body<S, LS_PREP, false, J>(p, blockIdx.x - m.base[i], m.cnt[i], b.Vt + p.n_z, nullptr, b.Vt, nullptr,
-                                   b.TVt, nullptr, nullptr);
+  lstar_body<S, LS_PREP, J>(p, blockIdx.x - m.base[i], m.cnt[i], b.Vt + p.n_z, b.Vt, b.TVt);
 }
 template <typename S, int J>
 __global__ void __launch_bounds__(128) k_dual_b(const BInst<S>* __restrict__ bi, BMap m) {
   const int i = m.inst[blockIdx.x];
   const BInst<S>& b = bi[i];
   const KP<S> p = b.kp;
-  dual_body<S, DM_DUAL, true, true, J>(p, blockIdx.x - m.base[i], m.cnt[i], b.Vt, b.TVt, b.Vt + p.n_z,
-                                       b.TVt + p.n_z, b.d, b.pd);
-}
-template <typename S, int J>
-__global__ void __launch_bounds__(128) k_pstats_b(const BInst<S>* __restrict__ bi, BMap m) {
-  const int i = m.inst[blockIdx.x];
-  const BInst<S>& b = bi[i];
-  const KP<S> p = b.kp;
-  lstar_body<S, LS_STATS, true, J>(p, blockIdx.x - m.base[i], m.cnt[i], b.Vt + p.n_z, b.TVt + p.n_z, b.Vt,
-                                   b.TVt, nullptr, b.d, b.pp);
+  dual_fused_body<S, true, J>(p, blockIdx.x - m.base[i], m.cnt[i], b.Vt, b.TVt, b.Vt + p.n_z, b.TVt + p.n_z,
+                              b.d, b.pd);
 }
 template <typename S>
 __global__ void k_reduce_stats_b(const BInst<S>* __restrict__ bi) {
   const BInst<S>& b = bi[blockIdx.x];
-  reduce_stats_body(b.pd, b.nb_node, b.pp, b.nb_node, b.stats, b.kp.skip);
+  reduce_stats_body(b.pd, b.nb_node, nullptr, 0, b.stats, b.kp.skip);
 }
 
 // ---------------------------------------------------------------------------
@@ -570,15 +778,14 @@ inline int warp_grid(int n, int max_blocks) {
 // entries per lane for blocks of nx + nu + 2 entries
 inline int lane_slots(int nx, int nu) { return (nx + nu + 2 + 31) / 32; }
 
-template <typename S, int MODE, bool DIR>
-static void lstar_j(const KP<S>& p, const S* eta, const S* etap, const S* z, const S* zp, S* zo, const S* dir,
-                    double* partials, int grid, cudaStream_t st) {
+template <typename S, int MODE>
+static void lstar_j(const KP<S>& p, const S* eta, const S* z, S* zo, int grid, cudaStream_t st) {
   switch (lane_slots(p.nx, p.nu)) {
-    case 1: k_lstar<S, MODE, DIR, 1><<<grid, 128, 0, st>>>(p, eta, etap, z, zp, zo, dir, partials); break;
-    case 2: k_lstar<S, MODE, DIR, 2><<<grid, 128, 0, st>>>(p, eta, etap, z, zp, zo, dir, partials); break;
-    case 3: k_lstar<S, MODE, DIR, 3><<<grid, 128, 0, st>>>(p, eta, etap, z, zp, zo, dir, partials); break;
-    case 4: k_lstar<S, MODE, DIR, 4><<<grid, 128, 0, st>>>(p, eta, etap, z, zp, zo, dir, partials); break;
-    default: k_lstar<S, MODE, DIR, kMaxJ><<<grid, 128, 0, st>>>(p, eta, etap, z, zp, zo, dir, partials); break;
+    case 1: k_lstar<S, MODE, 1><<<grid, 128, 0, st>>>(p, eta, z, zo); break;
+    case 2: k_lstar<S, MODE, 2><<<grid, 128, 0, st>>>(p, eta, z, zo); break;
+    case 3: k_lstar<S, MODE, 3><<<grid, 128, 0, st>>>(p, eta, z, zo); break;
+    case 4: k_lstar<S, MODE, 4><<<grid, 128, 0, st>>>(p, eta, z, zo); break;
+    default: k_lstar<S, MODE, kMaxJ><<<grid, 128, 0, st>>>(p, eta, z, zo); break;
   }
 }
 
@@ -596,7 +803,7 @@ static void dual_j(const KP<S>& p, const S* z, const S* zp, const S* eta, S* out
 
 template <typename S>
 void launch_prep(const KP<S>& p, const S* z, const S* eta, S* zo, int max_blocks, cudaStream_t st) {
-  lstar_j<S, LS_PREP, false>(p, eta, nullptr, z, nullptr, zo, nullptr, nullptr, warp_grid(p.n, max_blocks), st);
+  lstar_j<S, LS_PREP>(p, eta, z, zo, warp_grid(p.n, max_blocks), st);
 }
 
 template <typename S>
@@ -609,24 +816,26 @@ void launch_dual(const KP<S>& p, int mode, bool stats, const S* z, const S* zp, 
     k_dual<S, DM_PROXG, false, false, kMaxJ><<<grid, 128, 0, st>>>(p, z, zp, eta, out, dir, partials);
   } else if (!stats) {
     dual_j<S, DM_DUAL, false, false>(p, z, zp, eta, out, dir, partials, grid, st);
-  } else if (dir) {
-    dual_j<S, DM_DUAL, true, true>(p, z, zp, eta, out, dir, partials, grid, st);
   } else {
-    dual_j<S, DM_DUAL, true, false>(p, z, zp, eta, out, dir, partials, grid, st);
+    // with statistics: the fused kernel (warp per nonleaf node), which also
+    // accumulates the primal statistics
+    switch (lane_slots(p.nx, p.nu)) {
+#define SPOCK_DF(JJ)                                                                                     \
+  case JJ:                                                                                               \
+    if (dir) k_dual_fused<S, true, JJ><<<grid, 128, 0, st>>>(p, z, zp, eta, out, dir, partials);         \
+    else k_dual_fused<S, false, JJ><<<grid, 128, 0, st>>>(p, z, zp, eta, out, dir, partials);            \
+    break;
+      SPOCK_DF(1) SPOCK_DF(2) SPOCK_DF(3) SPOCK_DF(4)
+      default: SPOCK_DF(kMaxJ)
+#undef SPOCK_DF
+    }
   }
 }
 
-// mode 0: z_out = L* eta; mode 1: primal residual statistics
+// z_out = L* eta
 template <typename S>
-void launch_primal(const KP<S>& p, int mode, const S* eta, const S* etap, const S* z, const S* zp, S* zout,
-                   const S* dir, double* partials, int grid, cudaStream_t st) {
-  if (mode == 0) {
-    k_lstar<S, LS_APPLY, false, kMaxJ><<<grid, 128, 0, st>>>(p, eta, etap, z, zp, zout, dir, partials);
-  } else if (dir) {
-    lstar_j<S, LS_STATS, true>(p, eta, etap, z, zp, zout, dir, partials, grid, st);
-  } else {
-    lstar_j<S, LS_STATS, false>(p, eta, etap, z, zp, zout, dir, partials, grid, st);
-  }
+void launch_lstar(const KP<S>& p, const S* eta, S* zout, int grid, cudaStream_t st) {
+  k_lstar<S, LS_APPLY, kMaxJ><<<grid, 128, 0, st>>>(p, eta, nullptr, zout);
 }
 
 void launch_reduce_stats(const double* pd, int nd, const double* pp, int np, double* out, cudaStream_t st,
@@ -644,8 +853,7 @@ void launch_node_ops_b(int which, const BInst<S>* bi, const BMap& m, int nblocks
 #define SPOCK_NB(JJ)                                                              \
   case JJ:                                                                        \
     if (which == 0) k_prep_b<S, JJ><<<nblocks, 128, 0, st>>>(bi, m);              \
-    else if (which == 1) k_dual_b<S, JJ><<<nblocks, 128, 0, st>>>(bi, m);         \
-    else k_pstats_b<S, JJ><<<nblocks, 128, 0, st>>>(bi, m);                       \
+    else k_dual_b<S, JJ><<<nblocks, 128, 0, st>>>(bi, m);                         \
     break;
   switch (J) {
     SPOCK_NB(1) SPOCK_NB(2) SPOCK_NB(3) SPOCK_NB(4)
@@ -662,9 +870,7 @@ template void launch_dual<double>(const KP<double>&, int, bool, const double*, c
                                   double*, const double*, double*, int, cudaStream_t);
 template void launch_dual<float>(const KP<float>&, int, bool, const float*, const float*, const float*, float*,
                                  const float*, double*, int, cudaStream_t);
-template void launch_primal<double>(const KP<double>&, int, const double*, const double*, const double*,
-                                    const double*, double*, const double*, double*, int, cudaStream_t);
-template void launch_primal<float>(const KP<float>&, int, const float*, const float*, const float*, const float*,
-                                   float*, const float*, double*, int, cudaStream_t);
+template void launch_lstar<double>(const KP<double>&, const double*, double*, int, cudaStream_t);
+template void launch_lstar<float>(const KP<float>&, const float*, float*, int, cudaStream_t);
 
 }  // namespace spock

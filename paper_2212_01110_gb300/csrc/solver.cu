@@ -27,15 +27,14 @@ template <typename S>
 void launch_dual(const KP<S>& p, int mode, bool stats, const S* z, const S* zp, const S* eta, S* out,
                  const S* dir, double* partials, int grid, cudaStream_t st);
 template <typename S>
-void launch_primal(const KP<S>& p, int mode, const S* eta, const S* etap, const S* z, const S* zp, S* zout,
-                   const S* dir, double* partials, int grid, cudaStream_t st);
+void launch_lstar(const KP<S>& p, const S* eta, S* zout, int grid, cudaStream_t st);
 void launch_reduce_stats(const double* pd, int nd, const double* pp, int np, double* out, cudaStream_t st,
                          const int32_t* skip = nullptr);
 template <typename S>
 int launch_riccati(const KP<S>& p, const std::vector<int32_t>& stage_begin, const std::vector<int32_t>& stage_maxch,
                    S* zo, cudaStream_t st, cudaEvent_t* ev);
 
-enum { DM_APPLY_L_ = 0, DM_PROXG_ = 1, DM_DUAL_ = 2, PM_APPLY_LT_ = 0, PM_STATS_ = 1 };
+enum { DM_APPLY_L_ = 0, DM_PROXG_ = 1, DM_DUAL_ = 2 };
 
 // ---------------------------------------------------------------------------
 // errors
@@ -152,9 +151,8 @@ struct Workspace {
   void* D = nullptr;
   void* zero_eta = nullptr;
   double* pd = nullptr;
-  double* pp = nullptr;
   double* paa = nullptr;
-  int grid_d = 0, grid_p = 0, grid_v = 0;
+  int grid_d = 0, grid_v = 0;
   SmState* st = nullptr;
   int32_t* trace = nullptr;
   int trace_cap = 0;
@@ -229,15 +227,13 @@ static Workspace* get_ws_impl(Problem& P, int mem) {
     ws->zero_eta = ws->alloc(sizeof(double) * (size_t)P.off.n_eta);
     CUDA_TRY(cudaMemset(ws->zero_eta, 0, sizeof(double) * (size_t)P.off.n_eta));
     const int sms = sm_count();
-    // one wave of the node kernels (their register counts leave about four
-    // resident 128-thread blocks per SM in FP32, three in FP64): fewer
-    // end-of-block statistics reductions
-    ws->grid_d = std::min((P.tree.n + kWarpsPerBlock - 1) / kWarpsPerBlock, sms * (sizeof(S) == 8 ? 3 : 4));
+    // one wave of the dual kernel (its register count leaves three resident
+    // 128-thread blocks per SM in FP32, two in FP64): fewer end-of-block
+    // statistics reductions
+    ws->grid_d = std::min((P.tree.n + kWarpsPerBlock - 1) / kWarpsPerBlock, sms * (sizeof(S) == 8 ? 2 : 3));
     ws->grid_d = std::max(ws->grid_d, 1);
-    ws->grid_p = ws->grid_d;
     ws->grid_v = sms * 4;
     ws->pd = (double*)ws->alloc(sizeof(double) * 8 * ws->grid_d);
-    ws->pp = (double*)ws->alloc(sizeof(double) * 8 * ws->grid_p);
     ws->paa = (double*)ws->alloc(sizeof(double) * 2 * kMaxMemory * ws->grid_v);
     ws->st = (SmState*)ws->alloc(sizeof(SmState));
     CUDA_TRY(cudaMallocHost(&ws->h_action, sizeof(int32_t) * 4));
@@ -366,10 +362,9 @@ static void eval_T(const Ctx& c, const S* v, S* Tv, const S* dir, double* stats,
   launch_dual<S>(kp, DM_DUAL_, stats != nullptr, v, Tv, v + nz, Tv + nz, dir, ws ? ws->pd : nullptr,
                  ws ? ws->grid_d : std::min((P.tree.n + 3) / 4, maxb), c.st);
   if (ev) record_event(ev[6], c.st);
-  if (stats) {
-    launch_primal<S>(kp, PM_STATS_, v + nz, Tv + nz, v, Tv, nullptr, dir, ws->pp, ws->grid_p, c.st);
-    launch_reduce_stats(ws->pd, ws->grid_d, ws->pp, ws->grid_p, stats, c.st, skip);
-    launches += 2;
+  if (stats) {  // the dual kernel left the dual and primal statistics in pd
+    launch_reduce_stats(ws->pd, ws->grid_d, nullptr, 0, stats, c.st, skip);
+    launches += 1;
   }
   if (ev) record_event(ev[7], c.st);
   if (ws) ws->launches += launches;
@@ -918,7 +913,6 @@ static void batch_plan(Batch& B, const std::vector<Workspace*>& wss, const std::
     b.D = (S*)ws->D;
     b.stats = ws->stats;
     b.pd = ws->pd;
-    b.pp = ws->pp;
     b.paa = ws->paa;
     b.n_v = ws->n_v;
     b.ld = ws->ld;
@@ -962,7 +956,7 @@ static void batch_plan(Batch& B, const std::vector<Workspace*>& wss, const std::
     }
     B.fwd_lv.push_back(B.make_map(cnt, stg));
   }
-  B.launches_per_eval = 6 + 2 * max_cs;
+  B.launches_per_eval = 5 + 2 * max_cs;
   B.p_prec = (int)sizeof(S);
   B.p_mem = mem;
   B.p_tile = tile;
@@ -981,7 +975,6 @@ static void batch_eval(Batch& B, cudaStream_t st) {
   for (const DevMap& m : B.fwd_lv) launch_riccati_b<S>(2, bi, m.view(n), m.nblocks, B.SL, st);
   launch_riccati_b<S>(3, bi, B.chain.view(n), B.chain.nblocks, B.SL, st);
   launch_node_ops_b<S>(1, bi, B.node.view(n), B.node.nblocks, n, B.J, st);
-  launch_node_ops_b<S>(2, bi, B.node.view(n), B.node.nblocks, n, B.J, st);
   launch_node_ops_b<S>(3, bi, B.node.view(n), 0, n, B.J, st);
   check_launch();
 }
@@ -1201,8 +1194,7 @@ static int grad_impl(Problem& P, const double* z, const double* eta, double* gx0
   convert<S, double>(eta, es, ne, st);
   KP<S> kp = make_kp<S>(P, default_alpha(P, 0.0), P.idx.stage_begin);
   const int maxb = sm_count() * 16;
-  launch_primal<S>(kp, PM_APPLY_LT_, es, nullptr, nullptr, nullptr, w, nullptr, nullptr,
-                   std::min((P.tree.n + 3) / 4, maxb), st);  // w = L* eta
+  launch_lstar<S>(kp, es, w, std::min((P.tree.n + 3) / 4, maxb), st);  // w = L* eta
   const int nx = P.nx, nu = P.nu;
   if (gA) CUDA_TRY(cudaMemsetAsync(gA, 0, sizeof(double) * n * nx * nx, st));
   if (gB) CUDA_TRY(cudaMemsetAsync(gB, 0, sizeof(double) * n * nx * nu, st));
@@ -1749,7 +1741,7 @@ int spock_apply_Lt_dev(spock_problem* p, const double* eta, double* z_out, void*
     CUDA_TRY(cudaSetDevice(P->device));
     KP<double> kp = op_kp(P, 0.0);
     const int grid = std::min((P->tree.n + 3) / 4, sm_count() * 16);
-    launch_primal<double>(kp, PM_APPLY_LT_, eta, nullptr, nullptr, nullptr, z_out, nullptr, nullptr, grid,
+    launch_lstar<double>(kp, eta, z_out, grid,
                           (cudaStream_t)stream);
     check_launch();
     CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
