@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
@@ -57,6 +58,19 @@ void launch_node_ops_b(int which, const BInst<S>* bi, const BMap& m, int nblocks
 // for nx + nu.
 template <typename S>
 void launch_riccati_b(int which, const BInst<S>* bi, const BMap& m, int nblocks, int SL, cudaStream_t st);
+// riccati_tma.cu: the same passes with the staged (bulk-copy) kernels: chain
+// blocks of wpb warps, one block per node for the stages.
+struct TmaBatchShape {
+  uint32_t slot_bwd = 0, slot_fwd = 0;   // bytes of shared memory per chain warp
+  int wpb_bwd = 1, wpb_fwd = 1;          // warps per chain block
+  int nw_stage_bwd = 1, nw_stage_fwd = 1;  // warps per stage block
+  uint32_t smem_stage_bwd = 0, smem_stage_fwd = 0;
+};
+template <typename S>
+bool tma_batch_shape(const std::vector<KP<S>>& kps, int max_children, TmaBatchShape& sh);
+template <typename S>
+void launch_riccati_tma_b(int which, const BInst<S>* bi, const BMap& m, int nblocks, int SL, const TmaBatchShape& sh,
+                          cudaStream_t st);
 // rounds.cu: the four kernels of a round.
 template <typename S>
 void launch_round_decide_b(const BInst<S>* bi, int n_inst, cudaStream_t st);

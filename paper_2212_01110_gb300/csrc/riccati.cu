@@ -42,19 +42,10 @@ struct WarpVecs {
   S* w;  // [nx+nu]  forward input (x; d)
 };
 
-// h += [Abar | B]^T q  for one child; G is nx x ncol row-major.  Lanes over
-// columns (slot s holds column 32 s + lane).  When the last slot is at most
-// half full (rem = ncol mod 32 <= 16 columns) it is packed: g = 32 / rem
-// groups of rem lanes each sum every g-th row of those columns, and the
-// groups are added with shuffles -- nx / g row steps instead of nx, which
-// matters where the FP64 pipe is the bound (nx + nu = 70: 110 instead of 150
-// FMA instructions per child).
+// h += [Abar | B]^T q  for one child; G is nx x ncol row-major.
 template <typename S, int SL>
 __device__ __forceinline__ void acc_GTq(const S* __restrict__ G, const S* q, int nx, int ncol, int lane,
                                         S (&h)[SL]) {
-  const int full = ncol >> 5, rem = ncol & 31;
-  const bool pack = rem > 0 && rem <= 16;
-  const int plain = pack ? full : SL;
 #pragma unroll 8
   for (int r = 0; r < nx; ++r) {
     const S qr = q[r];
@@ -62,22 +53,8 @@ __device__ __forceinline__ void acc_GTq(const S* __restrict__ G, const S* q, int
 #pragma unroll
     for (int s = 0; s < SL; ++s) {
       const int col = 32 * s + lane;
-      if (s < plain && col < ncol) h[s] += __ldg(row + col) * qr;
+      if (col < ncol) h[s] += __ldg(row + col) * qr;
     }
-  }
-  if (pack) {
-    const int g = 32 / rem, grp = lane / rem, c = lane - grp * rem;
-    S acc = S(0);
-    if (grp < g) {
-      const S* colp = G + 32 * full + c;
-#pragma unroll 4
-      for (int r = grp; r < nx; r += g) acc += __ldg(colp + (int64_t)r * ncol) * q[r];
-    }
-    S tot = acc;
-    for (int k = 1; k < g; ++k) tot += __shfl_down_sync(kFull, acc, k * rem);
-#pragma unroll
-    for (int s = 0; s < SL; ++s)
-      if (s == full && lane < rem) h[s] += tot;
   }
 }
 

@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "batch.cuh"
 #include "kernels.cuh"
 #include "spock_internal.h"
 #include "tma.cuh"
@@ -163,17 +164,20 @@ __host__ __device__ inline ChainLayout<S> chain_layout_fwd(const KP<S>& p) {
   return L;
 }
 
+// Bodies shared by the single-problem and the batched kernels: block `bid`
+// of `nblk` for problem p; every warp owns `slotB` bytes of shared memory
+// (at least its layout's warpB).
 template <typename S, int SL>
-__global__ void __launch_bounds__(32 * kMaxChainWarps) k_bwd_chain_tma(KP<S> p) {
+__device__ __forceinline__ void bwd_chain_tma_body(const KP<S>& p, int bid, int nblk, uint32_t slotB) {
   if (p.skip && *p.skip) return;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bars[kMaxChainWarps][2];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
-  const int gw = blockIdx.x * wpb + wl, nw = gridDim.x * wpb;
+  const int gw = bid * wpb + wl, nw = nblk * wpb;
   const int nx = p.nx, ncol = p.nx + p.nu;
   const ChainLayout<S> Ly = chain_layout_bwd(p);
-  unsigned char* base = smem + (size_t)wl * Ly.warpB;
+  unsigned char* base = smem + (size_t)wl * slotB;
   S* stg[2] = {reinterpret_cast<S*>(base), reinterpret_cast<S*>(base + Ly.stageB)};
   S* vq = reinterpret_cast<S*>(base + 2 * Ly.stageB);
   S* vh = vq + kVecPad;
@@ -242,16 +246,22 @@ __global__ void __launch_bounds__(32 * kMaxChainWarps) k_bwd_chain_tma(KP<S> p) 
 }
 
 template <typename S, int SL>
-__global__ void __launch_bounds__(32 * kMaxChainWarps) k_fwd_chain_tma(KP<S> p, S* __restrict__ zo) {
+__global__ void __launch_bounds__(32 * kMaxChainWarps) k_bwd_chain_tma(KP<S> p) {
+  bwd_chain_tma_body<S, SL>(p, blockIdx.x, gridDim.x, chain_layout_bwd(p).warpB);
+}
+
+template <typename S, int SL>
+__device__ __forceinline__ void fwd_chain_tma_body(const KP<S>& p, S* __restrict__ zo, int bid, int nblk,
+                                                   uint32_t slotB) {
   if (p.skip && *p.skip) return;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bars[kMaxChainWarps][2];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
-  const int gw = blockIdx.x * wpb + wl, nw = gridDim.x * wpb;
+  const int gw = bid * wpb + wl, nw = nblk * wpb;
   const int nx = p.nx, ncol = p.nx + p.nu;
   const ChainLayout<S> Ly = chain_layout_fwd(p);
-  unsigned char* base = smem + (size_t)wl * Ly.warpB;
+  unsigned char* base = smem + (size_t)wl * slotB;
   S* stg[2] = {reinterpret_cast<S*>(base), reinterpret_cast<S*>(base + Ly.stageB)};
   S* vw = reinterpret_cast<S*>(base + 2 * Ly.stageB);
   uint64_t* bar = bars[wl];
@@ -324,6 +334,11 @@ __global__ void __launch_bounds__(32 * kMaxChainWarps) k_fwd_chain_tma(KP<S> p, 
   }
 }
 
+template <typename S, int SL>
+__global__ void __launch_bounds__(32 * kMaxChainWarps) k_fwd_chain_tma(KP<S> p, S* __restrict__ zo) {
+  fwd_chain_tma_body<S, SL>(p, zo, blockIdx.x, gridDim.x, chain_layout_fwd(p).warpB);
+}
+
 // ---------------------------------------------------------------------------
 // branching-stage kernels: one block per node, warp w takes children w, w+NW..
 // ---------------------------------------------------------------------------
@@ -341,13 +356,13 @@ __host__ __device__ inline uint32_t stage_smem_fwd(const KP<S>& p, int nwarps) {
 }
 
 template <typename S, int SL>
-__global__ void __launch_bounds__(32 * kMaxStageWarps) k_bwd_stage_tma(KP<S> p, int t) {
+__device__ __forceinline__ void bwd_stage_tma_body(const KP<S>& p, int t, int node) {
   if (p.skip && *p.skip) return;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bars[kMaxStageWarps + 1];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5, NW = blockDim.x >> 5;
   const int nx = p.nx, nu = p.nu, ncol = nx + nu;
-  const int k = p.stage_begin[t] + blockIdx.x;
+  const int k = p.stage_begin[t] + node;
   const int c0 = p.ch_begin[k], m = p.ch_count[k];
   S* Gw = reinterpret_cast<S*>(smem) + (size_t)wl * (p.gstride + 2 * kVecPad);
   S* qw = Gw + p.gstride;
@@ -425,13 +440,18 @@ __global__ void __launch_bounds__(32 * kMaxStageWarps) k_bwd_stage_tma(KP<S> p, 
 }
 
 template <typename S, int SL>
-__global__ void __launch_bounds__(32 * kMaxStageWarps) k_fwd_stage_tma(KP<S> p, int t, S* __restrict__ zo) {
+__global__ void __launch_bounds__(32 * kMaxStageWarps) k_bwd_stage_tma(KP<S> p, int t) {
+  bwd_stage_tma_body<S, SL>(p, t, blockIdx.x);
+}
+
+template <typename S, int SL>
+__device__ __forceinline__ void fwd_stage_tma_body(const KP<S>& p, int t, S* __restrict__ zo, int node) {
   if (p.skip && *p.skip) return;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bars[kMaxStageWarps + 1];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5, NW = blockDim.x >> 5;
   const int nx = p.nx, ncol = p.nx + p.nu;
-  const int k = p.stage_begin[t] + blockIdx.x;
+  const int k = p.stage_begin[t] + node;
   const int c0 = p.ch_begin[k], m = p.ch_count[k];
   S* Gw = reinterpret_cast<S*>(smem) + (size_t)wl * p.gstride;
   S* Kt = reinterpret_cast<S*>(smem) + (size_t)NW * p.gstride;
@@ -499,6 +519,43 @@ __global__ void __launch_bounds__(32 * kMaxStageWarps) k_fwd_stage_tma(KP<S> p, 
     __syncwarp();
   }
   (void)ok;
+}
+
+template <typename S, int SL>
+__global__ void __launch_bounds__(32 * kMaxStageWarps) k_fwd_stage_tma(KP<S> p, int t, S* __restrict__ zo) {
+  fwd_stage_tma_body<S, SL>(p, t, zo, blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// batched staged kernels: block -> (instance, block) from the launch's map;
+// chain warps own slotB bytes each (the largest layout of the batch); stage
+// blocks take one node of the instance's stage m.stage[i]
+// ---------------------------------------------------------------------------
+template <typename S, int SL>
+__global__ void __launch_bounds__(32 * kMaxChainWarps) k_bwd_chain_tma_b(const BInst<S>* __restrict__ bi, BMap m,
+                                                                        uint32_t slotB) {
+  const int i = m.inst[blockIdx.x];
+  const KP<S> p = bi[i].kp;
+  bwd_chain_tma_body<S, SL>(p, blockIdx.x - m.base[i], m.cnt[i], slotB);
+}
+template <typename S, int SL>
+__global__ void __launch_bounds__(32 * kMaxChainWarps) k_fwd_chain_tma_b(const BInst<S>* __restrict__ bi, BMap m,
+                                                                        uint32_t slotB) {
+  const int i = m.inst[blockIdx.x];
+  const KP<S> p = bi[i].kp;
+  fwd_chain_tma_body<S, SL>(p, bi[i].TVt, blockIdx.x - m.base[i], m.cnt[i], slotB);
+}
+template <typename S, int SL>
+__global__ void __launch_bounds__(32 * kMaxStageWarps) k_bwd_stage_tma_b(const BInst<S>* __restrict__ bi, BMap m) {
+  const int i = m.inst[blockIdx.x];
+  const KP<S> p = bi[i].kp;
+  bwd_stage_tma_body<S, SL>(p, m.stage[i], blockIdx.x - m.base[i]);
+}
+template <typename S, int SL>
+__global__ void __launch_bounds__(32 * kMaxStageWarps) k_fwd_stage_tma_b(const BInst<S>* __restrict__ bi, BMap m) {
+  const int i = m.inst[blockIdx.x];
+  const KP<S> p = bi[i].kp;
+  fwd_stage_tma_body<S, SL>(p, m.stage[i], bi[i].TVt, blockIdx.x - m.base[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -597,6 +654,83 @@ int launch_fwd_stage_tma(const KP<S>& p, int t, int cnt, int max_children, S* zo
   k_fwd_stage_tma<S, SL><<<cnt, 32 * nwp, bytes, st>>>(p, t, zo);
   return 1;
 }
+
+// Shape of the staged kernels for a batch: warps per chain block and the
+// per-warp slot (largest layout over the instances), warps per stage block
+// and the stage blocks' shared memory.  Returns false if some instance's
+// layout does not fit.
+template <typename S>
+bool tma_batch_shape(const std::vector<KP<S>>& kps, int max_children, TmaBatchShape& sh) {
+  uint32_t wb = 0, wf = 0;
+  for (const KP<S>& p : kps) {
+    wb = std::max(wb, chain_layout_bwd(p).warpB);
+    wf = std::max(wf, chain_layout_fwd(p).warpB);
+  }
+  const size_t avail = max_dyn_smem() - 1024;
+  if (wb == 0 || wf == 0 || wb > avail || wf > avail) return false;
+  sh.slot_bwd = wb;
+  sh.slot_fwd = wf;
+  sh.wpb_bwd = (int)std::min<size_t>(kMaxChainWarps, avail / wb);
+  sh.wpb_fwd = (int)std::min<size_t>(kMaxChainWarps, avail / wf);
+  int nwb = std::max(1, std::min(max_children, kMaxStageWarps)), nwf = nwb;
+  auto smem_b = [&](int nw) {
+    uint32_t v = 0;
+    for (const KP<S>& p : kps) v = std::max(v, stage_smem_bwd(p, nw));
+    return v;
+  };
+  auto smem_f = [&](int nw) {
+    uint32_t v = 0;
+    for (const KP<S>& p : kps) v = std::max(v, stage_smem_fwd(p, nw));
+    return v;
+  };
+  while (nwb > 1 && smem_b(nwb) > avail) --nwb;
+  while (nwf > 1 && smem_f(nwf) > avail) --nwf;
+  if (smem_b(nwb) > avail || smem_f(nwf) > avail) return false;
+  sh.nw_stage_bwd = nwb;
+  sh.nw_stage_fwd = nwf;
+  sh.smem_stage_bwd = smem_b(nwb);
+  sh.smem_stage_fwd = smem_f(nwf);
+  return true;
+}
+
+template <typename S, int SL>
+static void riccati_tma_b_sl(int which, const BInst<S>* bi, const BMap& m, int nblocks, const TmaBatchShape& sh,
+                             cudaStream_t st) {
+  static size_t g0 = 0, g1 = 0, g2 = 0, g3 = 0;
+  if (which == 0) {
+    const size_t bytes = (size_t)sh.wpb_bwd * sh.slot_bwd;
+    allow_smem(k_bwd_chain_tma_b<S, SL>, bytes, g0);
+    k_bwd_chain_tma_b<S, SL><<<nblocks, 32 * sh.wpb_bwd, bytes, st>>>(bi, m, sh.slot_bwd);
+  } else if (which == 1) {
+    allow_smem(k_bwd_stage_tma_b<S, SL>, sh.smem_stage_bwd, g1);
+    k_bwd_stage_tma_b<S, SL><<<nblocks, 32 * sh.nw_stage_bwd, sh.smem_stage_bwd, st>>>(bi, m);
+  } else if (which == 2) {
+    allow_smem(k_fwd_stage_tma_b<S, SL>, sh.smem_stage_fwd, g2);
+    k_fwd_stage_tma_b<S, SL><<<nblocks, 32 * sh.nw_stage_fwd, sh.smem_stage_fwd, st>>>(bi, m);
+  } else {
+    const size_t bytes = (size_t)sh.wpb_fwd * sh.slot_fwd;
+    allow_smem(k_fwd_chain_tma_b<S, SL>, bytes, g3);
+    k_fwd_chain_tma_b<S, SL><<<nblocks, 32 * sh.wpb_fwd, bytes, st>>>(bi, m, sh.slot_fwd);
+  }
+}
+
+template <typename S>
+void launch_riccati_tma_b(int which, const BInst<S>* bi, const BMap& m, int nblocks, int SL, const TmaBatchShape& sh,
+                          cudaStream_t st) {
+  if (nblocks <= 0) return;
+  switch (SL) {
+    case 1: riccati_tma_b_sl<S, 1>(which, bi, m, nblocks, sh, st); break;
+    case 2: riccati_tma_b_sl<S, 2>(which, bi, m, nblocks, sh, st); break;
+    case 3: riccati_tma_b_sl<S, 3>(which, bi, m, nblocks, sh, st); break;
+    default: riccati_tma_b_sl<S, 4>(which, bi, m, nblocks, sh, st); break;
+  }
+}
+template bool tma_batch_shape<double>(const std::vector<KP<double>>&, int, TmaBatchShape&);
+template bool tma_batch_shape<float>(const std::vector<KP<float>>&, int, TmaBatchShape&);
+template void launch_riccati_tma_b<double>(int, const BInst<double>*, const BMap&, int, int, const TmaBatchShape&,
+                                           cudaStream_t);
+template void launch_riccati_tma_b<float>(int, const BInst<float>*, const BMap&, int, int, const TmaBatchShape&,
+                                          cudaStream_t);
 
 #define SPOCK_TMA_INST(S, SL)                                                                    \
   template int launch_bwd_chain_tma<S, SL>(const KP<S>&, cudaStream_t);                          \

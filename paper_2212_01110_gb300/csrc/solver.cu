@@ -809,12 +809,14 @@ struct Batch {
   std::vector<Problem*> probs;
   cudaStream_t main = nullptr;
   // plan of the batched launches for one precision, node tile and memory
-  int p_prec = -1, p_mem = -1, p_tile = -1;
+  int p_prec = -1, p_mem = -1, p_tile = -1, p_fam = -1;
   std::vector<void*> p_ws;
   std::vector<double> p_alpha;
   void* bi_dev = nullptr;  // BInst<S>[n]
-  DevMap node, vec, chain;
+  DevMap node, vec, chain_b, chain_f;
   std::vector<DevMap> bwd_lv, fwd_lv;  // branching stages, one map per level
+  int fam = 0;                         // Riccati kernels: 0 direct, 1 staged (bulk copies)
+  TmaBatchShape tsh;
   int J = 1, SL = 1;
   int launches_per_eval = 0;
   // graph of kBatchRounds rounds
@@ -822,6 +824,7 @@ struct Batch {
   double g_alpha = -1.0;
   int g_launches = 0;
   int tuned_tile[2] = {0, 0};  // node tile (nodes per warp) picked by the autotuner, per precision
+  int tuned_fam[2] = {-1, -1};  // Riccati kernel family picked by the autotuner, per precision
   SmState** st_ptrs = nullptr;
   int32_t* done_dev = nullptr;
   int32_t* done_host = nullptr;  // pinned
@@ -835,7 +838,7 @@ struct Batch {
     bi_dev = nullptr;
     bwd_lv.clear();
     fwd_lv.clear();
-    p_prec = p_mem = p_tile = -1;
+    p_prec = p_mem = p_tile = p_fam = -1;
     p_ws.clear();
     p_alpha.clear();
   }
@@ -880,19 +883,22 @@ __global__ void k_gather_done(SmState* const* __restrict__ sts, int n, int32_t* 
 
 // Block maps and instance views for the batched launches.  tile = nodes per
 // warp of the node kernels (the autotuned tile shape); the vector kernels
-// take kVecElemsPerThread elements per thread; the Riccati kernels one warp
-// per chain / node.
+// take kVecElemsPerThread elements per thread; the Riccati passes use the
+// direct kernels (fam 0: one warp per chain / node) or the staged ones
+// (fam 1: chain blocks of wpb warps, one block per branching node; falls
+// back to direct if a layout does not fit).
 template <typename S>
 static void batch_plan(Batch& B, const std::vector<Workspace*>& wss, const std::vector<double>& alphas, int mem,
-                       int tile) {
+                       int tile, int fam) {
   std::vector<void*> ws_now(wss.begin(), wss.end());
-  if (B.p_prec == (int)sizeof(S) && B.p_mem == mem && B.p_tile == tile && B.p_ws == ws_now && B.p_alpha == alphas)
+  if (B.p_prec == (int)sizeof(S) && B.p_mem == mem && B.p_tile == tile && B.p_fam == fam && B.p_ws == ws_now &&
+      B.p_alpha == alphas)
     return;
   B.free_plan();
   const int n = (int)B.probs.size();
   std::vector<BInst<S>> h(n);
-  std::vector<int> cn(n), cv(n), cc(n);
-  int max_cs = 0;
+  std::vector<int> cn(n), cv(n);
+  int max_cs = 0, max_ch = 1;
   B.J = 1;
   B.SL = 1;
   for (int i = 0; i < n; ++i) {
@@ -922,17 +928,33 @@ static void batch_plan(Batch& B, const std::vector<Workspace*>& wss, const std::
     b.nb_vec = (int)std::max<int64_t>(1, std::min<int64_t>(ws->grid_v, (ws->n_v + per_block - 1) / per_block));
     cn[i] = b.nb_node;
     cv[i] = b.nb_vec;
-    const bool chains = b.kp.n_chains > 0 && b.kp.chain_stage < b.kp.N;
-    cc[i] = chains ? (b.kp.n_chains + kWarpsPerBlock - 1) / kWarpsPerBlock : 0;
     max_cs = std::max(max_cs, (int)P.tree.chain_stage);
+    for (int t = 0; t < P.tree.chain_stage; ++t) max_ch = std::max(max_ch, (int)P.tree.stage_maxch[t]);
     B.J = std::max(B.J, (P.nx + P.nu + 2 + 31) / 32);
     B.SL = std::max(B.SL, (P.nx + P.nu + 31) / 32);
   }
   CUDA_TRY(cudaMalloc(&B.bi_dev, sizeof(BInst<S>) * n));
   CUDA_TRY(cudaMemcpy(B.bi_dev, h.data(), sizeof(BInst<S>) * n, cudaMemcpyHostToDevice));
+  B.fam = fam;
+  if (B.fam == 1) {
+    std::vector<KP<S>> kps(n);
+    for (int i = 0; i < n; ++i) kps[i] = h[i].kp;
+    if (!tma_batch_shape<S>(kps, max_ch, B.tsh)) B.fam = 0;
+  }
+  const int cw_b = B.fam == 1 ? B.tsh.wpb_bwd : kWarpsPerBlock;  // chains per chain block
+  const int cw_f = B.fam == 1 ? B.tsh.wpb_fwd : kWarpsPerBlock;
+  const int npb = B.fam == 1 ? 1 : kWarpsPerBlock;                // branching nodes per stage block
+  std::vector<int> ccb(n), ccf(n);
+  for (int i = 0; i < n; ++i) {
+    const KP<S>& k = h[i].kp;
+    const bool chains = k.n_chains > 0 && k.chain_stage < k.N;
+    ccb[i] = chains ? (k.n_chains + cw_b - 1) / cw_b : 0;
+    ccf[i] = chains ? (k.n_chains + cw_f - 1) / cw_f : 0;
+  }
   B.node = B.make_map(cn, {});
   B.vec = B.make_map(cv, {});
-  B.chain = B.make_map(cc, {});
+  B.chain_b = B.make_map(ccb, {});
+  B.chain_f = B.make_map(ccf, {});
   for (int L = 0; L < max_cs; ++L) {  // backward: level L is stage cs_i - 1 - L of instance i
     std::vector<int> cnt(n, 0), stg(n, -1);
     for (int i = 0; i < n; ++i) {
@@ -940,7 +962,7 @@ static void batch_plan(Batch& B, const std::vector<Workspace*>& wss, const std::
       const int st = t.chain_stage - 1 - L;
       if (st >= 0) {
         stg[i] = st;
-        cnt[i] = (t.stage_begin[st + 1] - t.stage_begin[st] + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        cnt[i] = (t.stage_begin[st + 1] - t.stage_begin[st] + npb - 1) / npb;
       }
     }
     B.bwd_lv.push_back(B.make_map(cnt, stg));
@@ -951,7 +973,7 @@ static void batch_plan(Batch& B, const std::vector<Workspace*>& wss, const std::
       const Tree& t = B.probs[i]->tree;
       if (L < t.chain_stage) {
         stg[i] = L;
-        cnt[i] = (t.stage_begin[L + 1] - t.stage_begin[L] + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        cnt[i] = (t.stage_begin[L + 1] - t.stage_begin[L] + npb - 1) / npb;
       }
     }
     B.fwd_lv.push_back(B.make_map(cnt, stg));
@@ -960,6 +982,7 @@ static void batch_plan(Batch& B, const std::vector<Workspace*>& wss, const std::
   B.p_prec = (int)sizeof(S);
   B.p_mem = mem;
   B.p_tile = tile;
+  B.p_fam = fam;
   B.p_ws = ws_now;
   B.p_alpha = alphas;
 }
@@ -970,10 +993,17 @@ static void batch_eval(Batch& B, cudaStream_t st) {
   const int n = (int)B.probs.size();
   const BInst<S>* bi = (const BInst<S>*)B.bi_dev;
   launch_node_ops_b<S>(0, bi, B.node.view(n), B.node.nblocks, n, B.J, st);
-  launch_riccati_b<S>(0, bi, B.chain.view(n), B.chain.nblocks, B.SL, st);
-  for (const DevMap& m : B.bwd_lv) launch_riccati_b<S>(1, bi, m.view(n), m.nblocks, B.SL, st);
-  for (const DevMap& m : B.fwd_lv) launch_riccati_b<S>(2, bi, m.view(n), m.nblocks, B.SL, st);
-  launch_riccati_b<S>(3, bi, B.chain.view(n), B.chain.nblocks, B.SL, st);
+  if (B.fam == 1) {
+    launch_riccati_tma_b<S>(0, bi, B.chain_b.view(n), B.chain_b.nblocks, B.SL, B.tsh, st);
+    for (const DevMap& m : B.bwd_lv) launch_riccati_tma_b<S>(1, bi, m.view(n), m.nblocks, B.SL, B.tsh, st);
+    for (const DevMap& m : B.fwd_lv) launch_riccati_tma_b<S>(2, bi, m.view(n), m.nblocks, B.SL, B.tsh, st);
+    launch_riccati_tma_b<S>(3, bi, B.chain_f.view(n), B.chain_f.nblocks, B.SL, B.tsh, st);
+  } else {
+    launch_riccati_b<S>(0, bi, B.chain_b.view(n), B.chain_b.nblocks, B.SL, st);
+    for (const DevMap& m : B.bwd_lv) launch_riccati_b<S>(1, bi, m.view(n), m.nblocks, B.SL, st);
+    for (const DevMap& m : B.fwd_lv) launch_riccati_b<S>(2, bi, m.view(n), m.nblocks, B.SL, st);
+    launch_riccati_b<S>(3, bi, B.chain_f.view(n), B.chain_f.nblocks, B.SL, st);
+  }
   launch_node_ops_b<S>(1, bi, B.node.view(n), B.node.nblocks, n, B.J, st);
   launch_node_ops_b<S>(3, bi, B.node.view(n), 0, n, B.J, st);
   check_launch();
@@ -1021,42 +1051,57 @@ static void batch_init(Batch& B, const std::vector<Workspace*>& wss, const std::
 }
 
 // Autotuner of the batch: the node tile (nodes per warp of the node kernels:
-// 1, 2, 4, 8 or 16) with the shortest batched T evaluation, timed over three
-// evaluations per candidate; cached per batch and precision.
+// 1, 2, 4, 8 or 16) and the Riccati kernel family (direct or staged) with the
+// shortest batched T evaluation, timed over three evaluations per candidate;
+// cached per batch and precision.  SPOCK_BATCH_TILE fixes the tile,
+// SPOCK_RICCATI_KERNELS = direct / tma fixes the family.
+struct BatchCfg {
+  int tile, fam;
+};
 template <typename S>
-static int batch_tune(Batch& B, const std::vector<Workspace*>& wss, const std::vector<double>& alphas, int mem,
-                      const spock_settings& s, const double* const* x0, double* const* z, double* const* eta,
-                      int warm) {
-  const char* env = getenv("SPOCK_BATCH_TILE");  // fixed tile (tests, experiments)
+static BatchCfg batch_tune(Batch& B, const std::vector<Workspace*>& wss, const std::vector<double>& alphas, int mem,
+                           const spock_settings& s, const double* const* x0, double* const* z,
+                           double* const* eta, int warm) {
+  std::vector<int> tiles = {1, 2, 4, 8, 16}, fams = {0, 1};
+  const char* env = getenv("SPOCK_BATCH_TILE");
   if (env && env[0]) {
     const int t = atoi(env);
-    if (t == 1 || t == 2 || t == 4 || t == 8 || t == 16) return t;
+    if (t == 1 || t == 2 || t == 4 || t == 8 || t == 16) tiles = {t};
   }
-  int& slot = B.tuned_tile[sizeof(S) == 8 ? 0 : 1];
-  if (slot > 0) return slot;
+  const char* ek = getenv("SPOCK_RICCATI_KERNELS");
+  if (ek && ek[0] == 'd') fams = {0};
+  if (ek && ek[0] == 't') fams = {1};
+  const int pi = sizeof(S) == 8 ? 0 : 1;
+  if (tiles.size() > 1 && fams.size() > 1 && B.tuned_tile[pi] > 0) return {B.tuned_tile[pi], B.tuned_fam[pi]};
   cudaEvent_t a, b;
   CUDA_TRY(cudaEventCreate(&a));
   CUDA_TRY(cudaEventCreate(&b));
   float best = 1e30f;
-  int pick = 1;
-  for (int tile : {1, 2, 4, 8, 16}) {
-    batch_plan<S>(B, wss, alphas, mem, tile);
-    batch_init<S>(B, wss, alphas, s, mem, x0, z, eta, warm);
-    batch_eval<S>(B, B.main);  // warm-up
-    CUDA_TRY(cudaEventRecord(a, B.main));
-    for (int r = 0; r < 3; ++r) batch_eval<S>(B, B.main);
-    CUDA_TRY(cudaEventRecord(b, B.main));
-    CUDA_TRY(cudaEventSynchronize(b));
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, a, b);
-    if (ms < best) {
-      best = ms;
-      pick = tile;
+  BatchCfg pick{tiles[0], fams[0]};
+  for (int fam : fams) {
+    for (int tile : tiles) {
+      batch_plan<S>(B, wss, alphas, mem, tile, fam);
+      if (B.fam != fam) continue;  // staged layout does not fit
+      batch_init<S>(B, wss, alphas, s, mem, x0, z, eta, warm);
+      batch_eval<S>(B, B.main);  // warm-up
+      CUDA_TRY(cudaEventRecord(a, B.main));
+      for (int r = 0; r < 3; ++r) batch_eval<S>(B, B.main);
+      CUDA_TRY(cudaEventRecord(b, B.main));
+      CUDA_TRY(cudaEventSynchronize(b));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (ms < best) {
+        best = ms;
+        pick = {tile, fam};
+      }
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  slot = pick;
+  if (tiles.size() > 1 && fams.size() > 1) {
+    B.tuned_tile[pi] = pick.tile;
+    B.tuned_fam[pi] = pick.fam;
+  }
   return pick;
 }
 
@@ -1074,8 +1119,8 @@ static int batch_solve(Batch& B, const double* const* x0, const spock_settings& 
     wss[i] = get_ws_impl<S>(P, mem);
     alphas[i] = default_alpha(P, s.alpha);
   }
-  const int tile = batch_tune<S>(B, wss, alphas, mem, s, x0, z, eta, warm);
-  batch_plan<S>(B, wss, alphas, mem, tile);
+  const BatchCfg cfg = batch_tune<S>(B, wss, alphas, mem, s, x0, z, eta, warm);
+  batch_plan<S>(B, wss, alphas, mem, cfg.tile, cfg.fam);
   batch_init<S>(B, wss, alphas, s, mem, x0, z, eta, warm);
   const BInst<S>* bi = (const BInst<S>*)B.bi_dev;
   // the graph of kBatchRounds rounds (the plan, hence the graph, is rebuilt

@@ -74,16 +74,18 @@ def test_batch_converges():
     spock.spock_free(batch)
 
 
-@pytest.mark.parametrize("precision,tile", [(0, "1"), (0, "4"), (1, "1")])
-def test_batch_heterogeneous_workload_matches_single(precision, tile, monkeypatch):
+@pytest.mark.parametrize("precision,tile,family", [(0, "1", "direct"), (0, "4", "direct"), (1, "1", "direct"),
+                                                   (0, "1", "tma"), (1, "2", "tma")])
+def test_batch_heterogeneous_workload_matches_single(precision, tile, family, monkeypatch):
     """16 instances of the batched workload (branching 2-4, N 5-15, nx
     10-30, nu 4-10, scenario cap 64): every instance's fixed-iteration
     result equals the single-instance solver's (the batched kernels run the
-    same per-node bodies with the largest lane layout of the batch; the
-    single solves use the same direct Riccati kernels; node tile fixed)."""
+    same per-node bodies with the largest lane layout / shared-memory slot
+    of the batch; the single solves use the same Riccati kernel family;
+    node tile fixed)."""
     import torch
     from paper_2212_01110_gb300 import spock
-    monkeypatch.setenv("SPOCK_RICCATI_KERNELS", "direct")
+    monkeypatch.setenv("SPOCK_RICCATI_KERNELS", family)
     monkeypatch.setenv("SPOCK_BATCH_TILE", tile)
     dev = torch.device("cuda:0")
     ds = W.batch_instances(seed=3, count=16)
