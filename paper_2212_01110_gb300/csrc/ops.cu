@@ -267,28 +267,22 @@ __device__ __forceinline__ void soc_norm(const S (&w)[J], int dim, S ial, int la
   scale = (nv > t && nv > -t) ? S(0.5) * (nv + t) / nv : S(0);
 }
 
-template <typename S, int MODE, bool STATS, bool DIR, int J>
+// Without statistics: the dual update (DM_DUAL), L z (DM_APPLY_L) or
+// prox_{alpha g*}(eta) (DM_PROXG); warp per node, each node's own rows, its
+// nonroot block and (leaves) its leaf block.
+template <typename S, int MODE, int J>
 __device__ __forceinline__ void dual_body(const KP<S>& p, int bid, int nblk, const S* __restrict__ z,
                                           const S* __restrict__ zp, const S* __restrict__ eta,
-                                          S* __restrict__ out, const S* __restrict__ dir,
-                                          double* __restrict__ partials) {
+                                          S* __restrict__ out) {
   if (p.skip && *p.skip) return;
   constexpr bool HZ = MODE != DM_PROXG;     // rows of L at z
   constexpr bool HZP = MODE == DM_DUAL;     // ... and at z+
   constexpr bool HE = MODE != DM_APPLY_L;   // eta is read
-  constexpr bool ST = MODE == DM_DUAL && STATS;
-  constexpr bool DR = ST && DIR;
   const int lane = threadIdx.x & 31;
   const int gw = (bid * blockDim.x + threadIdx.x) >> 5;
   const int nw = (nblk * blockDim.x) >> 5;
   const S al = p.alpha, ial = p.inv_alpha;
   const int nx = p.nx, nu = p.nu;
-  const S* dz = DR ? dir : nullptr;
-  const S* deta = DR ? dir + p.n_z : nullptr;
-  StatAcc acc;
-  acc.zero();
-  NodeAcc<S> nacc;
-  nacc.zero();
   uint32_t wnext = gw < p.n ? desc_word(p.desc, gw, lane) : 0u;
   for (int k = gw; k < p.n; k += nw) {
     const NodeF D = node_fields(wnext);
@@ -298,20 +292,18 @@ __device__ __forceinline__ void dual_body(const KP<S>& p, int bid, int nblk, con
     const int64_t ea = nonleaf ? D.enl + 2 * D.m + 2 : D.elf;   // eta row of the box on x^k
     const int nb = nx + nu + 2;                      // nonroot block
     // ---- loads: own (x, u) with its box rows, the nonroot block, s^k
-    S az[J], azp[J], adz[J], ae[J], ade[J], alo[J], ahi[J];
-    S bz[J], bzp[J], bdz[J], bc[J], be[J], bde[J];
+    S az[J], azp[J], ae[J], alo[J], ahi[J];
+    S bz[J], bzp[J], bc[J], be[J];
 #pragma unroll
     for (int j = 0; j < J; ++j) {
       const int e = lane + 32 * j;
-      az[j] = azp[j] = adz[j] = ae[j] = ade[j] = alo[j] = ahi[j] = S(0);
-      bz[j] = bzp[j] = bdz[j] = bc[j] = be[j] = bde[j] = S(0);
+      az[j] = azp[j] = ae[j] = alo[j] = ahi[j] = S(0);
+      bz[j] = bzp[j] = bc[j] = be[j] = S(0);
       if (e < na) {
         const int64_t zi = e < nx ? D.zx + e : D.zu + (e - nx);
         if (HZ) az[j] = z[zi];
         if (HZP) azp[j] = zp[zi];
-        if (DR) adz[j] = dz[zi];
         if (HE) ae[j] = eta[ea + e];
-        if (DR) ade[j] = deta[ea + e];
         if (MODE != DM_APPLY_L) {
           alo[j] = e < nx ? p.xlo[(int64_t)k * nx + e] : p.ulo[(int64_t)k * nu + (e - nx)];
           ahi[j] = e < nx ? p.xhi[(int64_t)k * nx + e] : p.uhi[(int64_t)k * nu + (e - nx)];
@@ -322,34 +314,24 @@ __device__ __forceinline__ void dual_body(const KP<S>& p, int bid, int nblk, con
         bc[j] = e < nx ? p.qs[(int64_t)k * nx + e] : (e < nx + nu ? p.rs[(int64_t)k * nu + (e - nx)] : S(0.5));
         if (HZ) bz[j] = z[zi];
         if (HZP) bzp[j] = zp[zi];
-        if (DR) bdz[j] = dz[zi];
         if (HE) be[j] = eta[D.enr + e];
-        if (DR) bde[j] = deta[D.enr + e];
       }
     }
-    const S sz = HZ ? z[D.zs] : S(0), szp = HZP ? zp[D.zs] : S(0), sdz = DR ? dz[D.zs] : S(0);
+    const S sz = HZ ? z[D.zs] : S(0), szp = HZP ? zp[D.zs] : S(0);
     // ---- box rows on the node's own x (and u)
 #pragma unroll
     for (int j = 0; j < J; ++j) {
       const int e = lane + 32 * j;
       if (e < na) {
-        const S Lz = az[j], Lzp = azp[j];
-        const S w = dual_w<S, MODE>(al, ae[j], Lz, Lzp);
-        const S o = (MODE == DM_APPLY_L) ? w : w - al * clampv(w * ial, alo[j], ahi[j]);
-        out[ea + e] = o;
-        dual_stat<S, ST, DR>(nacc, ial, ae[j], o, Lz - Lzp, ade[j], adz[j]);
+        const S w = dual_w<S, MODE>(al, ae[j], az[j], azp[j]);
+        out[ea + e] = (MODE == DM_APPLY_L) ? w : w - al * clampv(w * ial, alo[j], ahi[j]);
       }
     }
     // ---- nonroot block: SOC on (Q^1/2 x^anc, R^1/2 u^anc, tau/2, tau/2)
     if (k > 0) {
-      S w[J], lrz[J], ld[J];
+      S w[J];
 #pragma unroll
-      for (int j = 0; j < J; ++j) {
-        const S Lz = bc[j] * bz[j], Lzp = bc[j] * bzp[j];
-        w[j] = dual_w<S, MODE>(al, be[j], Lz, Lzp);
-        lrz[j] = Lz - Lzp;
-        ld[j] = bc[j] * bdz[j];
-      }
+      for (int j = 0; j < J; ++j) w[j] = dual_w<S, MODE>(al, be[j], bc[j] * bz[j], bc[j] * bzp[j]);
       if (MODE == DM_APPLY_L) {
 #pragma unroll
         for (int j = 0; j < J; ++j)
@@ -360,11 +342,7 @@ __device__ __forceinline__ void dual_body(const KP<S>& p, int bid, int nblk, con
 #pragma unroll
         for (int j = 0; j < J; ++j) {
           const int e = lane + 32 * j;
-          if (e < nb) {
-            const S o = soc_entry(w[j], e, nb, al, ial, nv, t, sc);
-            out[D.enr + e] = o;
-            dual_stat<S, ST, DR>(nacc, ial, be[j], o, lrz[j], bde[j], ld[j]);
-          }
+          if (e < nb) out[D.enr + e] = soc_entry(w[j], e, nb, al, ial, nv, t, sc);
         }
       }
     }
@@ -373,65 +351,50 @@ __device__ __forceinline__ void dual_body(const KP<S>& p, int bid, int nblk, con
       // s - b'y row, b = (p^children, 0, 1)
       const int m = D.m, c0 = D.c0;
       const int64_t el = D.enl, z2 = D.zz2;
-      S bs = 0, bsp = 0, bsd = 0;
+      S bs = 0, bsp = 0;
       for (int e = lane; e < 2 * m + 1; e += 32) {
         const S Lz = HZ ? z[z2 + e] : S(0);
         const S Lzp = HZP ? zp[z2 + e] : S(0);
-        const S Ld = DR ? dz[z2 + e] : S(0);
-        const S ev = HE ? eta[el + e] : S(0);
-        const S w = dual_w<S, MODE>(al, ev, Lz, Lzp);
-        const S o = (MODE == DM_APPLY_L) ? w : (e < 2 * m ? vmin(w, S(0)) : S(0));
-        out[el + e] = o;
-        dual_stat<S, ST, DR>(nacc, ial, ev, o, Lz - Lzp, DR ? deta[el + e] : S(0), Ld);
+        const S w = dual_w<S, MODE>(al, HE ? eta[el + e] : S(0), Lz, Lzp);
+        out[el + e] = (MODE == DM_APPLY_L) ? w : (e < 2 * m ? vmin(w, S(0)) : S(0));
         if (e < m) {
           const S pj = p.prob[c0 + e];
           bs += pj * Lz;
           bsp += pj * Lzp;
-          bsd += pj * Ld;
         }
       }
       if (MODE != DM_PROXG) {
         bs = warp_sum(bs);
         if (HZP) bsp = warp_sum(bsp);
-        if (DR) bsd = warp_sum(bsd);
       }
       if (lane == 0) {
         const int64_t ie = el + 2 * m + 1;
-        const S y3 = HZ ? z[z2 + 2 * m] : S(0), y3p = HZP ? zp[z2 + 2 * m] : S(0), y3d = DR ? dz[z2 + 2 * m] : S(0);
-        const S Lz = sz - (bs + y3), Lzp = HZP ? szp - (bsp + y3p) : S(0), Ld = DR ? sdz - (bsd + y3d) : S(0);
-        const S ev = HE ? eta[ie] : S(0);
-        const S w = dual_w<S, MODE>(al, ev, Lz, Lzp);
-        const S o = (MODE == DM_APPLY_L) ? w : vmin(w, S(0));
-        out[ie] = o;
-        dual_stat<S, ST, DR>(nacc, ial, ev, o, Lz - Lzp, DR ? deta[ie] : S(0), Ld);
+        const S y3 = HZ ? z[z2 + 2 * m] : S(0), y3p = HZP ? zp[z2 + 2 * m] : S(0);
+        const S Lz = sz - (bs + y3), Lzp = HZP ? szp - (bsp + y3p) : S(0);
+        const S w = dual_w<S, MODE>(al, HE ? eta[ie] : S(0), Lz, Lzp);
+        out[ie] = (MODE == DM_APPLY_L) ? w : vmin(w, S(0));
       }
     } else {
       // ---- leaf SOC on (Q_N^1/2 x, s/2, s/2)
       const int dim = nx + 2;
       const int64_t es = D.elf + nx;
-      S w[J], lrz[J], ld[J], ev[J], dev[J];
+      S w[J];
 #pragma unroll
       for (int j = 0; j < J; ++j) {
         const int e = lane + 32 * j;
-        S c = S(0), Lz = S(0), Lzp = S(0), Ld = S(0);
-        ev[j] = dev[j] = S(0);
+        S Lz = S(0), Lzp = S(0), ev = S(0);
         if (e < dim) {
           if (e < nx) {
-            c = p.qns[(int64_t)k * nx + e];
+            const S c = p.qns[(int64_t)k * nx + e];
             Lz = c * az[j];
             Lzp = c * azp[j];
-            Ld = c * adz[j];
           } else {
             Lz = S(0.5) * sz;
             Lzp = S(0.5) * szp;
-            Ld = S(0.5) * sdz;
           }
-          if (HE) ev[j] = eta[es + e];
-          if (DR) dev[j] = deta[es + e];
+          if (HE) ev = eta[es + e];
         }
-        w[j] = dual_w<S, MODE>(al, ev[j], Lz, Lzp);
-        lrz[j] = Lz - Lzp;
-        ld[j] = Ld;
+        w[j] = dual_w<S, MODE>(al, ev, Lz, Lzp);
       }
       if (MODE == DM_APPLY_L) {
 #pragma unroll
@@ -443,27 +406,17 @@ __device__ __forceinline__ void dual_body(const KP<S>& p, int bid, int nblk, con
 #pragma unroll
         for (int j = 0; j < J; ++j) {
           const int e = lane + 32 * j;
-          if (e < dim) {
-            const S o = soc_entry(w[j], e, dim, al, ial, nv, t, sc);
-            out[es + e] = o;
-            dual_stat<S, ST, DR>(nacc, ial, ev[j], o, lrz[j], dev[j], ld[j]);
-          }
+          if (e < dim) out[es + e] = soc_entry(w[j], e, dim, al, ial, nv, t, sc);
         }
       }
     }
-    if (ST) nacc.node_done(acc);
-  }
-  if (ST) {
-    nacc.flush(acc);
-    block_stats_store<sizeof(S) == 4>(acc, partials, bid);
   }
 }
 
-template <typename S, int MODE, bool STATS, bool DIR, int J>
+template <typename S, int MODE, int J>
 __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, const S* __restrict__ zp,
-                                              const S* __restrict__ eta, S* __restrict__ out,
-                                              const S* __restrict__ dir, double* __restrict__ partials) {
-  dual_body<S, MODE, STATS, DIR, J>(p, blockIdx.x, gridDim.x, z, zp, eta, out, dir, partials);
+                                              const S* __restrict__ eta, S* __restrict__ out) {
+  dual_body<S, MODE, J>(p, blockIdx.x, gridDim.x, z, zp, eta, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -511,6 +464,34 @@ __device__ __forceinline__ void dual_fused_body(const KP<S>& p, int bid, int nbl
     if (k + nw < p.nl) wnext = desc_word(p.desc, k + nw, lane);
     const int m = D.m, c0 = D.c0;
     const int64_t el = D.enl, ea = el + 2 * m + 2, z2 = D.zz2;
+    // ---- loads issued up front with the node's own rows (one memory round
+    // trip per node on chains): the first child's nonroot rows and tau, the
+    // first 32 y rows and the s - b'y row
+    S pbe[J], pbde[J], pbc[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int e = lane + 32 * j;
+      pbe[j] = pbde[j] = pbc[j] = S(0);
+      if (e < nb) {
+        pbc[j] = e < nx ? p.qs[(int64_t)c0 * nx + e] : (e < nxu ? p.rs[(int64_t)c0 * nu + (e - nx)] : S(0.5));
+        pbe[j] = eta[D.enr_c0 + e];
+        if (DR) pbde[j] = deta[D.enr_c0 + e];
+      }
+    }
+    const S ptz = z[z2 + 2 * m + 1], ptzp = zp[z2 + 2 * m + 1], ptdz = DR ? dz[z2 + 2 * m + 1] : S(0);
+    S yz0 = 0, yzp0 = 0, yd0 = 0, ye0 = 0, yde0 = 0, pr0 = 0;
+    if (lane < 2 * m + 1) {
+      yz0 = z[z2 + lane];
+      yzp0 = zp[z2 + lane];
+      if (DR) yd0 = dz[z2 + lane];
+      ye0 = eta[el + lane];
+      if (DR) yde0 = deta[el + lane];
+      if (lane < m) pr0 = p.prob[c0 + lane];
+    }
+    const int64_t ie_sb = el + 2 * m + 1;
+    const S sk = z[D.zs], skp = zp[D.zs], skd = DR ? dz[D.zs] : S(0);
+    const S y3 = z[z2 + 2 * m], y3p = zp[z2 + 2 * m], y3d = DR ? dz[z2 + 2 * m] : S(0);
+    const S esb = eta[ie_sb], desb = DR ? deta[ie_sb] : S(0);
     // ---- own (x, u) and its box rows
     S az[J], azp[J], adz[J], lt[J];
     {
@@ -545,28 +526,43 @@ __device__ __forceinline__ void dual_fused_body(const KP<S>& p, int bid, int nbl
     // ---- children
     for (int jc = 0; jc < m; ++jc) {
       const int c = c0 + jc;
-      const int64_t er = jc == 0 ? D.enr_c0 : __ldg(&p.desc[c].enr);
       const int64_t ztau = z2 + 2 * m + 1 + jc;
-      const S tz = z[ztau], tzp = zp[ztau], tdz = DR ? dz[ztau] : S(0);
-      {  // nonroot block of c: SOC on (Q^c 1/2 x^k, R^c 1/2 u^k, tau^c / 2, tau^c / 2)
-        S w[J], lrz[J], ld[J], be[J], bde[J], bc[J];
+      const int64_t er = jc == 0 ? D.enr_c0 : __ldg(&p.desc[c].enr);
+      S tz = ptz, tzp = ptzp, tdz = ptdz;
+      S be[J], bde[J], bc[J];
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        be[j] = pbe[j];
+        bde[j] = pbde[j];
+        bc[j] = pbc[j];
+      }
+      if (jc > 0) {  // further children (branching stages only)
+        tz = z[ztau];
+        tzp = zp[ztau];
+        if (DR) tdz = dz[ztau];
 #pragma unroll
         for (int j = 0; j < J; ++j) {
           const int e = lane + 32 * j;
-          w[j] = lrz[j] = ld[j] = be[j] = bde[j] = bc[j] = S(0);
           if (e < nb) {
-            const S coef = e < nx ? p.qs[(int64_t)c * nx + e]
-                                  : (e < nxu ? p.rs[(int64_t)c * nu + (e - nx)] : S(0.5));
+            bc[j] = e < nx ? p.qs[(int64_t)c * nx + e] : (e < nxu ? p.rs[(int64_t)c * nu + (e - nx)] : S(0.5));
+            be[j] = eta[er + e];
+            if (DR) bde[j] = deta[er + e];
+          }
+        }
+      }
+      {  // nonroot block of c: SOC on (Q^c 1/2 x^k, R^c 1/2 u^k, tau^c / 2, tau^c / 2)
+        S w[J], lrz[J], ld[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const int e = lane + 32 * j;
+          w[j] = lrz[j] = ld[j] = S(0);
+          if (e < nb) {
+            const S coef = bc[j];
             const S Lz = coef * (e < nxu ? az[j] : tz);
             const S Lzp = coef * (e < nxu ? azp[j] : tzp);
-            be[j] = eta[er + e];
-            if (DR) {
-              bde[j] = deta[er + e];
-              ld[j] = coef * (e < nxu ? adz[j] : tdz);
-            }
+            if (DR) ld[j] = coef * (e < nxu ? adz[j] : tdz);
             w[j] = dual_w<S, DM_DUAL>(al, be[j], Lz, Lzp);
             lrz[j] = Lz - Lzp;
-            bc[j] = coef;
           }
         }
         S nv, t, sc;
@@ -670,8 +666,8 @@ __device__ __forceinline__ void dual_fused_body(const KP<S>& p, int bid, int nbl
       if (lane + 32 * j < nxu) primal_stat<S, DR>(nacc, ial, az[j], azp[j], adz[j], lt[j]);
     // ---- the s - b'y row of k (b = (p^children, 0, 1)), then the y rows
     {
-      S bs = 0, bsp = 0, bsd = 0;
-      for (int jj = lane; jj < m; jj += 32) {
+      S bs = pr0 * yz0, bsp = pr0 * yzp0, bsd = DR ? pr0 * yd0 : S(0);
+      for (int jj = lane + 32; jj < m; jj += 32) {  // nodes with more than 32 children
         const S pj = p.prob[c0 + jj];
         bs += pj * z[z2 + jj];
         bsp += pj * zp[z2 + jj];
@@ -680,29 +676,26 @@ __device__ __forceinline__ void dual_fused_body(const KP<S>& p, int bid, int nbl
       bs = warp_sum(bs);
       bsp = warp_sum(bsp);
       if (DR) bsd = warp_sum(bsd);
-      const int64_t ie = el + 2 * m + 1;
-      const S y3 = z[z2 + 2 * m], y3p = zp[z2 + 2 * m], y3d = DR ? dz[z2 + 2 * m] : S(0);
-      const S sk = z[D.zs], skp = zp[D.zs], skd = DR ? dz[D.zs] : S(0);
       const S Lz = sk - (bs + y3), Lzp = skp - (bsp + y3p), Ld = DR ? skd - (bsd + y3d) : S(0);
-      const S ev = eta[ie];
-      const S w = dual_w<S, DM_DUAL>(al, ev, Lz, Lzp);
+      const S w = dual_w<S, DM_DUAL>(al, esb, Lz, Lzp);
       const S o = vmin(w, S(0));
-      const S re_sb = ev - o;
+      const S re_sb = esb - o;
       if (lane == 0) {
-        out[ie] = o;
-        dual_stat<S, true, DR>(nacc, ial, ev, o, Lz - Lzp, DR ? deta[ie] : S(0), Ld);
+        out[ie_sb] = o;
+        dual_stat<S, true, DR>(nacc, ial, esb, o, Lz - Lzp, desb, Ld);
         primal_stat<S, DR>(nacc, ial, sk, skp, skd, re_sb);   // s^k (s^0 at the root)
       }
-      for (int e = lane; e < 2 * m + 1; e += 32) {
-        const S yz = z[z2 + e], yzp = zp[z2 + e], yd = DR ? dz[z2 + e] : S(0);
-        const S ye = eta[el + e];
+      auto yrow = [&](int e, S yz, S yzp, S yd, S ye, S yde) {
         const S yw = dual_w<S, DM_DUAL>(al, ye, yz, yzp);
         const S yo = e < 2 * m ? vmin(yw, S(0)) : S(0);
         out[el + e] = yo;
-        dual_stat<S, true, DR>(nacc, ial, ye, yo, yz - yzp, DR ? deta[el + e] : S(0), yd);
+        dual_stat<S, true, DR>(nacc, ial, ye, yo, yz - yzp, yde, yd);
         const S bl = e < m ? p.prob[c0 + e] : (e < 2 * m ? S(0) : S(1));
         primal_stat<S, DR>(nacc, ial, yz, yzp, yd, (ye - yo) - bl * re_sb);
-      }
+      };
+      if (lane < 2 * m + 1) yrow(lane, yz0, yzp0, yd0, ye0, yde0);
+      for (int e = lane + 32; e < 2 * m + 1; e += 32)
+        yrow(e, z[z2 + e], zp[z2 + e], DR ? dz[z2 + e] : S(0), eta[el + e], DR ? deta[el + e] : S(0));
     }
     nacc.node_done(acc);
   }
@@ -789,15 +782,14 @@ static void lstar_j(const KP<S>& p, const S* eta, const S* z, S* zo, int grid, c
   }
 }
 
-template <typename S, int MODE, bool STATS, bool DIR>
-static void dual_j(const KP<S>& p, const S* z, const S* zp, const S* eta, S* out, const S* dir, double* partials,
-                   int grid, cudaStream_t st) {
+template <typename S, int MODE>
+static void dual_j(const KP<S>& p, const S* z, const S* zp, const S* eta, S* out, int grid, cudaStream_t st) {
   switch (lane_slots(p.nx, p.nu)) {
-    case 1: k_dual<S, MODE, STATS, DIR, 1><<<grid, 128, 0, st>>>(p, z, zp, eta, out, dir, partials); break;
-    case 2: k_dual<S, MODE, STATS, DIR, 2><<<grid, 128, 0, st>>>(p, z, zp, eta, out, dir, partials); break;
-    case 3: k_dual<S, MODE, STATS, DIR, 3><<<grid, 128, 0, st>>>(p, z, zp, eta, out, dir, partials); break;
-    case 4: k_dual<S, MODE, STATS, DIR, 4><<<grid, 128, 0, st>>>(p, z, zp, eta, out, dir, partials); break;
-    default: k_dual<S, MODE, STATS, DIR, kMaxJ><<<grid, 128, 0, st>>>(p, z, zp, eta, out, dir, partials); break;
+    case 1: k_dual<S, MODE, 1><<<grid, 128, 0, st>>>(p, z, zp, eta, out); break;
+    case 2: k_dual<S, MODE, 2><<<grid, 128, 0, st>>>(p, z, zp, eta, out); break;
+    case 3: k_dual<S, MODE, 3><<<grid, 128, 0, st>>>(p, z, zp, eta, out); break;
+    case 4: k_dual<S, MODE, 4><<<grid, 128, 0, st>>>(p, z, zp, eta, out); break;
+    default: k_dual<S, MODE, kMaxJ><<<grid, 128, 0, st>>>(p, z, zp, eta, out); break;
   }
 }
 
@@ -811,11 +803,11 @@ void launch_dual(const KP<S>& p, int mode, bool stats, const S* z, const S* zp, 
                  const S* dir, double* partials, int grid, cudaStream_t st) {
   // operator-level modes (not on the solve path) use the widest lane layout
   if (mode == DM_APPLY_L) {
-    k_dual<S, DM_APPLY_L, false, false, kMaxJ><<<grid, 128, 0, st>>>(p, z, zp, eta, out, dir, partials);
+    k_dual<S, DM_APPLY_L, kMaxJ><<<grid, 128, 0, st>>>(p, z, zp, eta, out);
   } else if (mode == DM_PROXG) {
-    k_dual<S, DM_PROXG, false, false, kMaxJ><<<grid, 128, 0, st>>>(p, z, zp, eta, out, dir, partials);
+    k_dual<S, DM_PROXG, kMaxJ><<<grid, 128, 0, st>>>(p, z, zp, eta, out);
   } else if (!stats) {
-    dual_j<S, DM_DUAL, false, false>(p, z, zp, eta, out, dir, partials, grid, st);
+    dual_j<S, DM_DUAL>(p, z, zp, eta, out, grid, st);
   } else {
     // with statistics: the fused kernel (warp per nonleaf node), which also
     // accumulates the primal statistics
