@@ -404,10 +404,11 @@ def paper_workload(args, spock, workloads, dev):
 def batch_workload(args, spock, workloads, dev, seed=0):
     """Batched SPOCK: args.batch heterogeneous instances (branching 2-4,
     N 5-15, nx 10-30, nu 4-10, scenario cap 64; data as the large tree) in
-    one spock_batch_solve_dev call -- one CUDA graph with a parallel branch
-    of rounds per instance.  A warm-up solve (autotuning, capture) is
-    excluded; the timed solve runs args.batch_iter SPOCK iterations per
-    instance from a cold start, FP32 (FP64 residual/Anderson) and FP64."""
+    one spock_batch_solve_dev call -- every kernel of a round launched once
+    for the whole batch, rounds replayed from a CUDA graph.  A warm-up solve
+    (autotuning, capture) is excluded; the timed solve runs args.batch_iter
+    SPOCK iterations per instance from a cold start, FP32 (FP64
+    residual/Anderson) and FP64."""
     import torch
     t0 = time.time()
     ds = workloads.batch_instances(seed=seed, count=args.batch)
