@@ -275,11 +275,15 @@ class Problem:
     ``workloads``); frees both on close / garbage collection."""
 
     def __init__(self, d):
+        self.handle = None
         self.tree = spock_tree_create(d["anc"], d["prob"])
         try:
             self.handle = spock_problem_create(self.tree, d)
         except Exception:
+            # free the tree once: close() / __del__ must not free it again (the
+            # address may already belong to another handle by then)
             spock_free(self.tree)
+            self.tree = None
             raise
         self.nx, self.nu = int(d["nx"]), int(d["nu"])
         self.n_nodes = len(d["anc"])

@@ -196,3 +196,23 @@ def test_profiled_solve_times_kernel_groups(drv, monkeypatch):
     info = spock.spock_solve_dev(pair.gp.handle, pair.x0, s, z, e, 0)
     assert info.n_timed >= info.n_T - 1 > 0
     assert all(t >= 0 for t in info.t_group_ms) and sum(info.t_group_ms) > 0
+
+
+def test_failed_problem_create_frees_its_tree_once():
+    """A problem that fails validation releases its tree handle exactly once:
+    later problems (which may reuse the address) stay valid after garbage
+    collection of the failed attempts."""
+    import gc
+    from paper_2212_01110_gb300 import spock, workloads as W
+    bad = W.small_binary(0)
+    bad["A"] = bad["A"].copy()
+    bad["A"][1, 0, 0] = np.nan
+    for _ in range(10):
+        with pytest.raises(spock.SpockError):
+            spock.Problem(bad)
+    good = [spock.Problem(W.small_binary(s)) for s in range(10)]
+    gc.collect()
+    for p in good:
+        assert spock.spock_problem_info(p.handle)[0] == p.n_z
+    for p in good:
+        p.close()
