@@ -146,12 +146,8 @@ __host__ __device__ inline ChainLayout<S> chain_layout_bwd(const KP<S>& p) {
   L.xB = p.xs * sizeof(S);
   L.uB = p.us * sizeof(S);
   L.ktB = p.ktstride * sizeof(S);
-  // ring of two steps of G | xbar_k | ubar_k | xbar_leaf, one node block NB
-  // (fetched after the previous node update, while the next step's GEMV
-  // runs), then the vectors: 40.7 KB per warp at nx = 50, nu = 20 in FP32,
-  // five warps per SM instead of four with NB in the ring as well
-  L.stageB = L.gB + 2 * L.xB + L.uB;
-  L.warpB = 2 * L.stageB + L.nbB + 4 * kVecPad * sizeof(S);
+  L.stageB = L.gB + L.nbB + 2 * L.xB + L.uB;  // G | NB | xbar_k | ubar_k | xbar_leaf
+  L.warpB = 2 * L.stageB + 4 * kVecPad * sizeof(S);
   return L;
 }
 
@@ -175,7 +171,7 @@ template <typename S, int SL>
 __device__ __forceinline__ void bwd_chain_tma_body(const KP<S>& p, int bid, int nblk, uint32_t slotB) {
   if (p.skip && *p.skip) return;
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ uint64_t bars[kMaxChainWarps][3];
+  __shared__ uint64_t bars[kMaxChainWarps][2];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
   const int gw = bid * wpb + wl, nw = nblk * wpb;
@@ -183,56 +179,41 @@ __device__ __forceinline__ void bwd_chain_tma_body(const KP<S>& p, int bid, int 
   const ChainLayout<S> Ly = chain_layout_bwd(p);
   unsigned char* base = smem + (size_t)wl * slotB;
   S* stg[2] = {reinterpret_cast<S*>(base), reinterpret_cast<S*>(base + Ly.stageB)};
-  S* nbs = reinterpret_cast<S*>(base + 2 * Ly.stageB);
-  S* vq = reinterpret_cast<S*>(base + 2 * Ly.stageB + Ly.nbB);
+  S* vq = reinterpret_cast<S*>(base + 2 * Ly.stageB);
   S* vh = vq + kVecPad;
   S* vg = vh + kVecPad;
   S* vd = vg + kVecPad;
-  uint64_t* bar = bars[wl];  // [0], [1]: the ring of steps; [2]: the node block
+  uint64_t* bar = bars[wl];
   if (lane == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
-    mbar_init(&bar[2], 1);
     fence_mbar_init();
   }
   __syncwarp();
   const int Lc = p.N - p.chain_stage;  // steps per chain
   const int ldim = p.n_chains > 0 ? (p.n_chains - gw + nw - 1) / nw : 0;
   const int nsteps = gw < p.n_chains ? ldim * Lc : 0;
-  auto node_of = [&](int j, int& k, int& c, int& t) {
+  auto issue = [&](int j) {
     const int ci = gw + (j / Lc) * nw;
-    t = p.N - 1 - (j % Lc);
-    k = p.stage_begin[t] + ci;
-    c = p.stage_begin[t + 1] + ci;
-  };
-  auto issue_step = [&](int j) {  // G of the child, xbar / ubar of the node (and the leaf's xbar)
-    int k, c, t;
-    node_of(j, k, c, t);
+    const int t = p.N - 1 - (j % Lc);
+    const int k = p.stage_begin[t] + ci, c = p.stage_begin[t + 1] + ci;
     S* dst = stg[j & 1];
     const bool first = (t == p.N - 1);
     fence_proxy_async();
-    mbar_expect_tx(&bar[j & 1], Ly.gB + Ly.xB + Ly.uB + (first ? Ly.xB : 0u));
+    mbar_expect_tx(&bar[j & 1], Ly.gB + Ly.nbB + Ly.xB + Ly.uB + (first ? Ly.xB : 0u));
     bulk_g2s(dst, p.Gb + (int64_t)(c - 1) * p.gstride, Ly.gB, &bar[j & 1]);
-    bulk_g2s(dst + p.gstride, p.xbar + (int64_t)k * p.xs, Ly.xB, &bar[j & 1]);
-    bulk_g2s(dst + p.gstride + p.xs, p.ubar + (int64_t)k * p.us, Ly.uB, &bar[j & 1]);
-    if (first) bulk_g2s(dst + p.gstride + p.xs + p.us, p.xbar + (int64_t)c * p.xs, Ly.xB, &bar[j & 1]);
+    bulk_g2s(dst + p.gstride, p.NB + (int64_t)k * p.nbstride, Ly.nbB, &bar[j & 1]);
+    bulk_g2s(dst + p.gstride + p.nbstride, p.xbar + (int64_t)k * p.xs, Ly.xB, &bar[j & 1]);
+    bulk_g2s(dst + p.gstride + p.nbstride + p.xs, p.ubar + (int64_t)k * p.us, Ly.uB, &bar[j & 1]);
+    if (first) bulk_g2s(dst + p.gstride + p.nbstride + p.xs + p.us, p.xbar + (int64_t)c * p.xs, Ly.xB, &bar[j & 1]);
   };
-  auto issue_node = [&](int j) {  // [K | W^T | Rt^-1] of the node
-    int k, c, t;
-    node_of(j, k, c, t);
-    fence_proxy_async();
-    mbar_expect_tx(&bar[2], Ly.nbB);
-    bulk_g2s(nbs, p.NB + (int64_t)k * p.nbstride, Ly.nbB, &bar[2]);
-  };
-  uint32_t phase0 = 0, phase1 = 0, phaseN = 0;
-  if (nsteps > 0 && lane == 0) {
-    issue_step(0);
-    issue_node(0);
-  }
+  uint32_t phase0 = 0, phase1 = 0;
+  if (nsteps > 0 && lane == 0) issue(0);
   for (int j = 0; j < nsteps; ++j) {
-    int k, c, t;
-    node_of(j, k, c, t);
-    if (j + 1 < nsteps && lane == 0) issue_step(j + 1);
+    const int ci = gw + (j / Lc) * nw;
+    const int t = p.N - 1 - (j % Lc);
+    const int k = p.stage_begin[t] + ci;
+    if (j + 1 < nsteps && lane == 0) issue(j + 1);
     uint32_t& ph = (j & 1) ? phase1 : phase0;
     const uint32_t par = ph;
     const bool ok = __all_sync(kFull, mbar_wait(&bar[j & 1], par));
@@ -241,11 +222,11 @@ __device__ __forceinline__ void bwd_chain_tma_body(const KP<S>& p, int bid, int 
       flag_timeout(p.err, lane);
       mbar_wait(&bar[j & 1], par);
       if (j + 1 < nsteps) mbar_wait(&bar[(j + 1) & 1], (j & 1) ? phase0 : phase1);
-      mbar_wait(&bar[2], phaseN);
       return;
     }
     const S* G = stg[j & 1];
-    const S* xb = G + p.gstride;
+    const S* NBk = G + p.gstride;
+    const S* xb = NBk + p.nbstride;
     const S* ub = xb + p.xs;
     if (t == p.N - 1) {
       const S* xl = ub + p.us;
@@ -257,20 +238,10 @@ __device__ __forceinline__ void bwd_chain_tma_body(const KP<S>& p, int bid, int 
     for (int s = 0; s < SL; ++s) h[s] = S(0);
     sm_GTq<S, SL>(G, vq, nx, ncol, lane, h);
     __syncwarp();
-    const uint32_t parN = phaseN;
-    const bool okn = __all_sync(kFull, mbar_wait(&bar[2], parN));
-    phaseN ^= 1u;
-    if (!okn) {
-      flag_timeout(p.err, lane);
-      mbar_wait(&bar[2], parN);
-      if (j + 1 < nsteps) mbar_wait(&bar[(j + 1) & 1], (j & 1) ? phase0 : phase1);
-      return;
-    }
-    sm_node_bwd<S, SL>(p, k, h, nbs, xb, ub, vh, vg, vd, vq, lane);
+    sm_node_bwd<S, SL>(p, k, h, NBk, xb, ub, vh, vg, vd, vq, lane);
     if (t == p.chain_stage)
       for (int r = lane; r < nx; r += 32) p.q[(int64_t)k * p.xs + r] = vq[r];
     __syncwarp();
-    if (j + 1 < nsteps && lane == 0) issue_node(j + 1);  // the node block was read by all lanes above
   }
 }
 
