@@ -26,6 +26,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -45,9 +46,9 @@ def measured_peaks():
         return {}
 
 
-# Measured FP64 FMA throughput of this GB300 pool (microbenchmark of 8
-# independent FMA chains per thread, 152 x 8 blocks of 256 threads): about
-# 2 FP64 FMA per clock per SM.  Used as the ALU roofline of the FP64 path.
+# Measured FP64 FMA throughput of a GB300 (microbenchmark of 8 independent
+# FMA chains per thread, 152 x 8 blocks of 256 threads): about 2 FP64 FMA per
+# clock per SM.  Used as the ALU roofline of the FP64 path.
 FP64_PEAK_TFLOPS = 1.193
 
 # DRAM bytes (read + write) per chain of one launch of the backward chain
@@ -86,8 +87,8 @@ class Clocks:
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-        os.makedirs(os.path.join(HERE, "gpurun_out"), exist_ok=True)
-        self.path = os.path.join(HERE, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="spock_clocks_", suffix=".csv")
+        os.close(fd)
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
@@ -213,7 +214,7 @@ def run_ours(args, rank, world, local_rank):
             ach = fl / (t_bwd * 1e-3) / 1e12
             r = {"kernel": "k_bwd_chain<double>", "bound": "alu", "achieved": round(ach, 4),
                  "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(ach / FP64_PEAK_TFLOPS, 4),
-                 "peak_source": "measured FP64 FMA microbenchmark on this pool",
+                 "peak_source": "measured FP64 FMA microbenchmark on a GB300 (8 independent FMA chains per thread)",
                  "traffic": traffic(prec), "algorithmic_bytes": bb, "algorithmic_flops": fl,
                  "hbm_achieved_gbs": round(bb / (t_bwd * 1e-3) / 1e9, 1),
                  "hbm_frac_of_measured": round(bb / (t_bwd * 1e-3) / 1e9 / hbm, 4),
@@ -324,7 +325,7 @@ def run_ours(args, rank, world, local_rank):
 
 
 def small_workload(args, spock, workloads, dev):
-    """Config-1 tree (binary, N = 3, 15 nodes, nx = 3, nu = 2): time to the
+    """The 15-node binary tree (N = 3, nx = 3, nu = 2): time to the
     1e-6 residual in FP64 (Anderson m = 3; the captured graph reused, so
     the second solve is timed), and the FP32 iteration with FP64 factors,
     residual, Anderson m = 5 and FP64 certification/tail: its optimal cost

@@ -178,7 +178,7 @@ __device__ __forceinline__ S clampv(S v, S lo, S hi) {
 // kFlushNodesF32 nodes (and at the end) the warp reduces its lanes' FP32
 // sums with shuffles and lane 0 alone adds them in FP64.  Every FP64
 // operation costs a 64-cycle slot of its sub-partition's FP64 pipe per warp
-// instruction on this GPU, whatever the number of active lanes, so the FP32
+// instruction on GB300, whatever the number of active lanes, so the FP32
 // kernels keep FP64 work to ~16 warp instructions per 32 nodes.
 struct StatAcc {
   double s[8];
