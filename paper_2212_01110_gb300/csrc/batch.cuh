@@ -71,6 +71,13 @@ bool tma_batch_shape(const std::vector<KP<S>>& kps, int max_children, TmaBatchSh
 template <typename S>
 void launch_riccati_tma_b(int which, const BInst<S>* bi, const BMap& m, int nblocks, int SL, const TmaBatchShape& sh,
                           cudaStream_t st);
+// cta.cu: whole solves, one 128-thread block per instance (instances with
+// nx + nu <= max_nxu <= 62, Anderson memory 0, 3 or 5), at most max_rounds
+// rounds each; trace (or NULL) for a single instance.
+bool cta_supported(int nx, int nu, int mem);
+template <typename S>
+void launch_solve_cta(const BInst<S>* bi, int n_inst, int max_nxu, int mem, int64_t max_rounds, int32_t* trace,
+                      cudaStream_t st);
 // rounds.cu: the four kernels of a round.
 template <typename S>
 void launch_round_decide_b(const BInst<S>* bi, int n_inst, cudaStream_t st);

@@ -22,395 +22,15 @@
 // warp barriers inside the node loop.
 #include "batch.cuh"
 #include "kernels.cuh"
+#include "ops_body.cuh"
 #include "spock_internal.h"
 
 namespace spock {
-
-enum DualMode : int { DM_APPLY_L = 0, DM_PROXG = 1, DM_DUAL = 2 };
-enum LstarMode : int { LS_APPLY = 0, LS_PREP = 2 };
-constexpr int kMaxJ = (kMaxDim + 2 + 31) / 32;   // entries per lane for the largest blocks
-
-// ---------------------------------------------------------------------------
-// k_lstar
-// ---------------------------------------------------------------------------
-// (L* w) at the entries of node k, from the rows of L that involve them:
-//   x^k, u^k  (nonleaf):  w_nl[x, u] + sum_c (Q^c or R^c)^1/2 w_nr^c[x, u]
-//   x^k       (leaf):     w_lf[x] + Q_N^1/2 w_lf[soc x]
-//   y^k_l:                w_nl[y_l] - b_l w_nl[s - b'y],   b = (p^children, 0, 1)
-//   tau^c:                (w_nr^c[tau 1] + w_nr^c[tau 2]) / 2
-//   s^c:                  w_nl^c[s - b'y] (c nonleaf) or (w_lf^c[s 1] + w_lf^c[s 2]) / 2
-//   s^0:                  w_nl^0[s - b'y]
-// Body shared by the single-problem and the batched kernels: block `bid` of
-// `nblk` working for problem p.
-template <typename S, int MODE, int J>
-__device__ __forceinline__ void lstar_body(const KP<S>& p, int bid, int nblk, const S* __restrict__ eta,
-                                           const S* __restrict__ z, S* __restrict__ zo) {
-  if (p.skip && *p.skip) return;
-  const int lane = threadIdx.x & 31;
-  const int gw = (bid * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (nblk * blockDim.x) >> 5;
-  const int nx = p.nx, nu = p.nu;
-  const S al = p.alpha;
-  auto E = [&](int64_t i) -> S { return eta[i]; };
-  auto emit = [&](int64_t zi, S lt) { zo[zi] = lt; };   // LS_APPLY
-  uint32_t wnext = gw < p.n ? desc_word(p.desc, gw, lane) : 0u;
-  for (int k = gw; k < p.n; k += nw) {
-    const NodeF D = node_fields(wnext);
-    if (k + nw < p.n) wnext = desc_word(p.desc, k + nw, lane);
-    if (k < p.nl) {
-      const int m = D.m, c0 = D.c0;
-      const int nxu = nx + nu;
-      const int64_t ex = D.enl + 2 * m + 2;
-      // ---- (x, u): own rows and the first child's nonroot rows, in registers
-      S lt[J], zv[J];
-#pragma unroll
-      for (int j = 0; j < J; ++j) {
-        const int e = lane + 32 * j;
-        lt[j] = zv[j] = S(0);
-        if (e < nxu) {
-          const S coef = e < nx ? p.qs[(int64_t)c0 * nx + e] : p.rs[(int64_t)c0 * nu + (e - nx)];
-          lt[j] = E(ex + e) + coef * E(D.enr_c0 + e);
-          if (MODE == LS_PREP) zv[j] = z[e < nx ? D.zx + e : D.zu + (e - nx)];
-        }
-      }
-      for (int c = 1; c < m; ++c) {   // further children (branching stages only)
-        const int64_t er = __ldg(&p.desc[c0 + c].enr);
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-          const int e = lane + 32 * j;
-          if (e < nxu) {
-            const S coef = e < nx ? p.qs[(int64_t)(c0 + c) * nx + e] : p.rs[(int64_t)(c0 + c) * nu + (e - nx)];
-            lt[j] += coef * E(er + e);
-          }
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < J; ++j) {
-        const int e = lane + 32 * j;
-        if (e < nxu) {
-          if (MODE == LS_PREP) {
-            if (e < nx) p.xbar[(int64_t)k * p.xs + e] = zv[j] - al * lt[j];
-            else p.ubar[(int64_t)k * p.us + (e - nx)] = zv[j] - al * lt[j];
-          } else {
-            zo[e < nx ? D.zx + e : D.zu + (e - nx)] = lt[j];
-          }
-        }
-      }
-      // ---- z_2 block
-      const int64_t el = D.enl, z2 = D.zz2;
-      const S sb = E(el + 2 * m + 1);
-      // child j's tau and s rows of L* w
-      auto child_rows = [&](int jc, S& tau_l, S& s_l) {
-        const int c = c0 + jc;
-        const int64_t er = jc == 0 ? D.enr_c0 : __ldg(&p.desc[c].enr);
-        const int64_t es = jc == 0 ? D.es_c0 : __ldg(&p.desc[c].es);
-        tau_l = S(0.5) * (E(er + nxu) + E(er + nxu + 1));
-        s_l = (c < p.nl) ? E(es) : S(0.5) * (E(es) + E(es + 1));
-      };
-      if (MODE != LS_PREP) {
-        for (int l = lane; l < 2 * m + 1; l += 32) {
-          const S bl = l < m ? p.prob[c0 + l] : (l < 2 * m ? S(0) : S(1));
-          emit(z2 + l, E(el + l) - bl * sb);
-        }
-        for (int jc = lane; jc < m; jc += 32) {
-          S tl, sl;
-          child_rows(jc, tl, sl);
-          emit(z2 + 2 * m + 1 + jc, tl);
-          emit(z2 + 3 * m + 1 + jc, sl);
-        }
-        if (k == 0 && lane == 0) emit(0, sb);
-      } else {
-        // zbar = z - alpha L* eta on z_2, then the projection on
-        // ker [E^T, -I, -I] with (M M^T)^-1 = (I - 11^T / (c + m)) / c,
-        // c = a^2 + 3 (Sherman-Morrison); M w = a y1 - y2 + y3 - tau - s per child.
-        const S a = p.av[k];
-        const S cc = a * a + S(3);
-        const S y3 = z[z2 + 2 * m] - al * (E(el + 2 * m) - sb);
-        auto bars = [&](int jc, S& y1, S& y2, S& ta, S& sv) {
-          S tl, sl;
-          child_rows(jc, tl, sl);
-          y1 = z[z2 + jc] - al * (E(el + jc) - p.prob[c0 + jc] * sb);
-          y2 = z[z2 + m + jc] - al * E(el + m + jc);
-          ta = z[z2 + 2 * m + 1 + jc] - al * tl;
-          sv = z[z2 + 3 * m + 1 + jc] - al * sl;
-        };
-        // children 0..31 kept in registers; further ones recomputed
-        S y1 = 0, y2 = 0, ta = 0, sv = 0, sumMw = 0;
-        if (lane < m) {
-          bars(lane, y1, y2, ta, sv);
-          sumMw = a * y1 - y2 + y3 - ta - sv;
-        }
-        for (int jc = lane + 32; jc < m; jc += 32) {
-          S b1, b2, bt, bs;
-          bars(jc, b1, b2, bt, bs);
-          sumMw += a * b1 - b2 + y3 - bt - bs;
-        }
-        sumMw = warp_sum(sumMw);
-        const S inv_cc = S(1) / cc;
-        const S shift = sumMw / (cc + S(m));
-        S sumlam = 0;
-        if (lane < m) {
-          const S lam = (a * y1 - y2 + y3 - ta - sv - shift) * inv_cc;
-          zo[z2 + lane] = y1 - a * lam;
-          zo[z2 + m + lane] = y2 + lam;
-          zo[z2 + 2 * m + 1 + lane] = ta + lam;
-          zo[z2 + 3 * m + 1 + lane] = sv + lam;
-          sumlam = lam;
-        }
-        for (int jc = lane + 32; jc < m; jc += 32) {
-          S b1, b2, bt, bs;
-          bars(jc, b1, b2, bt, bs);
-          const S lam = (a * b1 - b2 + y3 - bt - bs - shift) * inv_cc;
-          zo[z2 + jc] = b1 - a * lam;
-          zo[z2 + m + jc] = b2 + lam;
-          zo[z2 + 2 * m + 1 + jc] = bt + lam;
-          zo[z2 + 3 * m + 1 + jc] = bs + lam;
-          sumlam += lam;
-        }
-        sumlam = warp_sum(sumlam);
-        if (lane == 0) {
-          zo[z2 + 2 * m] = y3 - sumlam;
-          if (k == 0) zo[0] = (z[0] - al * sb) - al;   // prox of alpha * s^0
-        }
-      }
-    } else {
-      // ---- leaf: x^k
-      const int64_t ef = D.elf;
-#pragma unroll
-      for (int j = 0; j < J; ++j) {
-        const int e = lane + 32 * j;
-        if (e < nx) {
-          const S lt = E(ef + e) + p.qns[(int64_t)k * nx + e] * E(ef + nx + e);
-          if (MODE == LS_PREP) p.xbar[(int64_t)k * p.xs + e] = z[D.zx + e] - al * lt;
-          else emit(D.zx + e, lt);
-        }
-      }
-    }
-  }
-}
 
 template <typename S, int MODE, int J>
 __global__ void __launch_bounds__(128) k_lstar(KP<S> p, const S* __restrict__ eta, const S* __restrict__ z,
                                                S* __restrict__ zo) {
   lstar_body<S, MODE, J>(p, blockIdx.x, gridDim.x, eta, z, zo);
-}
-
-// ---------------------------------------------------------------------------
-// k_dual
-// ---------------------------------------------------------------------------
-// Per entry of eta: the value of the L row at z (Lz), at z+ (Lzp) and at the
-// direction (Ld).  For DM_DUAL, w = eta + alpha (2 Lzp - Lz) and the
-// residual row of L is L r_z = Lz - Lzp.
-
-template <typename S, int MODE>
-__device__ __forceinline__ S dual_w(S alpha, S e, S Lz, S Lzp) {
-  if (MODE == DM_APPLY_L) return Lz;
-  if (MODE == DM_PROXG) return e;
-  return e + alpha * (S(2) * Lzp - Lz);
-}
-
-// Residual statistics of one eta row: r_eta = eta - eta+ against L r_z, and
-// with a direction d the inner products of the line search.
-template <typename S, bool ST, bool DR>
-__device__ __forceinline__ void dual_stat(NodeAcc<S>& a, S inv_alpha, S e_old, S e_new, S lrz, S de, S ld) {
-  if (!ST) return;
-  const S re = e_old - e_new;
-  a.s[ST_RE2] += re * re;
-  a.s[ST_RE_LRZ] += re * lrz;
-  a.s[ST_XID] = vmax(a.s[ST_XID], vabs(re * inv_alpha - lrz));
-  if (DR) {
-    a.s[ST_RD] += re * de;
-    a.s[ST_LRZ_DE] += lrz * de;
-    a.s[ST_RE_LDZ] += re * ld;
-  }
-}
-
-// Translated second-order cone: the block w (entries 0..dim-1, t = entry
-// dim-1) maps to w - alpha P(w / alpha - sh) - alpha sh with
-// sh = (0, .., 1/2, -1/2) and P the projection on SOC = {(v, t): ||v|| <= t}.
-// nv = ||v||, t the cone coordinate, scale = (nv + t) / (2 nv) on the
-// boundary case (one division per block).
-template <typename S>
-__device__ __forceinline__ S soc_entry(S wv, int e, int dim, S al, S ial, S nv, S t, S scale) {
-  S v = wv * ial;
-  if (e == dim - 2) v -= S(0.5);
-  if (e == dim - 1) v = t;
-  S pr;
-  if (nv <= t) pr = v;
-  else if (nv <= -t) pr = S(0);
-  else pr = (e == dim - 1) ? S(0.5) * (nv + t) : scale * v;
-  if (e == dim - 2) pr += S(0.5);
-  if (e == dim - 1) pr -= S(0.5);
-  return wv - al * pr;
-}
-
-// Norm data of the translated SOC block held in registers w[j] (entry
-// lane + 32 j; entries >= dim are ignored).
-template <typename S, int J>
-__device__ __forceinline__ void soc_norm(const S (&w)[J], int dim, S ial, int lane, S& nv, S& t, S& scale) {
-  S s2 = 0, wt = 0;
-#pragma unroll
-  for (int j = 0; j < J; ++j) {
-    const int e = lane + 32 * j;
-    if (e < dim - 1) {
-      S v = w[j] * ial;
-      if (e == dim - 2) v -= S(0.5);
-      s2 += v * v;
-    } else if (e == dim - 1) {
-      wt = w[j];
-    }
-  }
-  s2 = warp_sum(s2);
-  wt = __shfl_sync(kFull, wt, (dim - 1) & 31);
-  nv = vsqrt(s2);
-  t = wt * ial + S(0.5);
-  scale = (nv > t && nv > -t) ? S(0.5) * (nv + t) / nv : S(0);
-}
-
-// Without statistics: the dual update (DM_DUAL), L z (DM_APPLY_L) or
-// prox_{alpha g*}(eta) (DM_PROXG); warp per node, each node's own rows, its
-// nonroot block and (leaves) its leaf block.
-template <typename S, int MODE, int J>
-__device__ __forceinline__ void dual_body(const KP<S>& p, int bid, int nblk, const S* __restrict__ z,
-                                          const S* __restrict__ zp, const S* __restrict__ eta,
-                                          S* __restrict__ out) {
-  if (p.skip && *p.skip) return;
-  constexpr bool HZ = MODE != DM_PROXG;     // rows of L at z
-  constexpr bool HZP = MODE == DM_DUAL;     // ... and at z+
-  constexpr bool HE = MODE != DM_APPLY_L;   // eta is read
-  const int lane = threadIdx.x & 31;
-  const int gw = (bid * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (nblk * blockDim.x) >> 5;
-  const S al = p.alpha, ial = p.inv_alpha;
-  const int nx = p.nx, nu = p.nu;
-  uint32_t wnext = gw < p.n ? desc_word(p.desc, gw, lane) : 0u;
-  for (int k = gw; k < p.n; k += nw) {
-    const NodeF D = node_fields(wnext);
-    if (k + nw < p.n) wnext = desc_word(p.desc, k + nw, lane);
-    const bool nonleaf = k < p.nl;
-    const int na = nonleaf ? nx + nu : nx;          // own (x, u) or x entries
-    const int64_t ea = nonleaf ? D.enl + 2 * D.m + 2 : D.elf;   // eta row of the box on x^k
-    const int nb = nx + nu + 2;                      // nonroot block
-    // ---- loads: own (x, u) with its box rows, the nonroot block, s^k
-    S az[J], azp[J], ae[J], alo[J], ahi[J];
-    S bz[J], bzp[J], bc[J], be[J];
-#pragma unroll
-    for (int j = 0; j < J; ++j) {
-      const int e = lane + 32 * j;
-      az[j] = azp[j] = ae[j] = alo[j] = ahi[j] = S(0);
-      bz[j] = bzp[j] = bc[j] = be[j] = S(0);
-      if (e < na) {
-        const int64_t zi = e < nx ? D.zx + e : D.zu + (e - nx);
-        if (HZ) az[j] = z[zi];
-        if (HZP) azp[j] = zp[zi];
-        if (HE) ae[j] = eta[ea + e];
-        if (MODE != DM_APPLY_L) {
-          alo[j] = e < nx ? p.xlo[(int64_t)k * nx + e] : p.ulo[(int64_t)k * nu + (e - nx)];
-          ahi[j] = e < nx ? p.xhi[(int64_t)k * nx + e] : p.uhi[(int64_t)k * nu + (e - nx)];
-        }
-      }
-      if (k > 0 && e < nb) {
-        const int64_t zi = e < nx ? D.zxp + e : (e < nx + nu ? D.zup + (e - nx) : D.ztau);
-        bc[j] = e < nx ? p.qs[(int64_t)k * nx + e] : (e < nx + nu ? p.rs[(int64_t)k * nu + (e - nx)] : S(0.5));
-        if (HZ) bz[j] = z[zi];
-        if (HZP) bzp[j] = zp[zi];
-        if (HE) be[j] = eta[D.enr + e];
-      }
-    }
-    const S sz = HZ ? z[D.zs] : S(0), szp = HZP ? zp[D.zs] : S(0);
-    // ---- box rows on the node's own x (and u)
-#pragma unroll
-    for (int j = 0; j < J; ++j) {
-      const int e = lane + 32 * j;
-      if (e < na) {
-        const S w = dual_w<S, MODE>(al, ae[j], az[j], azp[j]);
-        out[ea + e] = (MODE == DM_APPLY_L) ? w : w - al * clampv(w * ial, alo[j], ahi[j]);
-      }
-    }
-    // ---- nonroot block: SOC on (Q^1/2 x^anc, R^1/2 u^anc, tau/2, tau/2)
-    if (k > 0) {
-      S w[J];
-#pragma unroll
-      for (int j = 0; j < J; ++j) w[j] = dual_w<S, MODE>(al, be[j], bc[j] * bz[j], bc[j] * bzp[j]);
-      if (MODE == DM_APPLY_L) {
-#pragma unroll
-        for (int j = 0; j < J; ++j)
-          if (lane + 32 * j < nb) out[D.enr + lane + 32 * j] = w[j];
-      } else {
-        S nv, t, sc;
-        soc_norm<S, J>(w, nb, ial, lane, nv, t, sc);
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-          const int e = lane + 32 * j;
-          if (e < nb) out[D.enr + e] = soc_entry(w[j], e, nb, al, ial, nv, t, sc);
-        }
-      }
-    }
-    if (nonleaf) {
-      // ---- y rows (K* cone: y1, y2 <= 0 after the prox, y3 free) and the
-      // s - b'y row, b = (p^children, 0, 1)
-      const int m = D.m, c0 = D.c0;
-      const int64_t el = D.enl, z2 = D.zz2;
-      S bs = 0, bsp = 0;
-      for (int e = lane; e < 2 * m + 1; e += 32) {
-        const S Lz = HZ ? z[z2 + e] : S(0);
-        const S Lzp = HZP ? zp[z2 + e] : S(0);
-        const S w = dual_w<S, MODE>(al, HE ? eta[el + e] : S(0), Lz, Lzp);
-        out[el + e] = (MODE == DM_APPLY_L) ? w : (e < 2 * m ? vmin(w, S(0)) : S(0));
-        if (e < m) {
-          const S pj = p.prob[c0 + e];
-          bs += pj * Lz;
-          bsp += pj * Lzp;
-        }
-      }
-      if (MODE != DM_PROXG) {
-        bs = warp_sum(bs);
-        if (HZP) bsp = warp_sum(bsp);
-      }
-      if (lane == 0) {
-        const int64_t ie = el + 2 * m + 1;
-        const S y3 = HZ ? z[z2 + 2 * m] : S(0), y3p = HZP ? zp[z2 + 2 * m] : S(0);
-        const S Lz = sz - (bs + y3), Lzp = HZP ? szp - (bsp + y3p) : S(0);
-        const S w = dual_w<S, MODE>(al, HE ? eta[ie] : S(0), Lz, Lzp);
-        out[ie] = (MODE == DM_APPLY_L) ? w : vmin(w, S(0));
-      }
-    } else {
-      // ---- leaf SOC on (Q_N^1/2 x, s/2, s/2)
-      const int dim = nx + 2;
-      const int64_t es = D.elf + nx;
-      S w[J];
-#pragma unroll
-      for (int j = 0; j < J; ++j) {
-        const int e = lane + 32 * j;
-        S Lz = S(0), Lzp = S(0), ev = S(0);
-        if (e < dim) {
-          if (e < nx) {
-            const S c = p.qns[(int64_t)k * nx + e];
-            Lz = c * az[j];
-            Lzp = c * azp[j];
-          } else {
-            Lz = S(0.5) * sz;
-            Lzp = S(0.5) * szp;
-          }
-          if (HE) ev = eta[es + e];
-        }
-        w[j] = dual_w<S, MODE>(al, ev, Lz, Lzp);
-      }
-      if (MODE == DM_APPLY_L) {
-#pragma unroll
-        for (int j = 0; j < J; ++j)
-          if (lane + 32 * j < dim) out[es + lane + 32 * j] = w[j];
-      } else {
-        S nv, t, sc;
-        soc_norm<S, J>(w, dim, ial, lane, nv, t, sc);
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-          const int e = lane + 32 * j;
-          if (e < dim) out[es + e] = soc_entry(w[j], e, dim, al, ial, nv, t, sc);
-        }
-      }
-    }
-  }
 }
 
 template <typename S, int MODE, int J>
@@ -419,313 +39,11 @@ __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, 
   dual_body<S, MODE, J>(p, blockIdx.x, gridDim.x, z, zp, eta, out);
 }
 
-// ---------------------------------------------------------------------------
-// k_dual_fused: the dual update with all residual statistics in one pass.
-// One warp per NONLEAF node k owns every eta row that involves k's
-// variables: k's nonleaf block, the nonroot block of each child c (rows of
-// Q^c 1/2 x^k, R^c 1/2 u^k, tau^c) and the leaf block of each leaf child.
-// Each z entry's rows of L then lie in one warp, which therefore has the
-// whole of (L* r_eta) there and accumulates the primal statistics as well:
-//   x^k, u^k:  own box rows + sum_c (Q^c or R^c)^1/2 nonroot rows of c
-//   y^k:       y rows - b (s - b'y) row;   s^k (nonleaf): the s - b'y row
-//   tau^c:     the two tau rows of c's nonroot block
-//   x^c, s^c (leaf c): c's leaf block.
-// The nonroot blocks reuse x^k, u^k already in registers.
-// ---------------------------------------------------------------------------
-template <typename S, bool DR>
-__device__ __forceinline__ void primal_stat(NodeAcc<S>& a, S inv_alpha, S zv, S zpv, S dv, S lt) {
-  const S rz = zv - zpv;
-  a.s[ST_RZ2] += rz * rz;
-  a.s[ST_XIP] = vmax(a.s[ST_XIP], vabs(rz * inv_alpha - lt));
-  if (DR) a.s[ST_RD] += rz * dv;
-}
-
-template <typename S, bool DIR, int J>
-__device__ __forceinline__ void dual_fused_body(const KP<S>& p, int bid, int nblk, const S* __restrict__ z,
-                                                const S* __restrict__ zp, const S* __restrict__ eta,
-                                                S* __restrict__ out, const S* __restrict__ dir,
-                                                double* __restrict__ partials) {
-  if (p.skip && *p.skip) return;
-  constexpr bool DR = DIR;
-  const int lane = threadIdx.x & 31;
-  const int gw = (bid * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (nblk * blockDim.x) >> 5;
-  const S al = p.alpha, ial = p.inv_alpha;
-  const int nx = p.nx, nu = p.nu, nxu = nx + nu, nb = nxu + 2;
-  const S* dz = DR ? dir : nullptr;
-  const S* deta = DR ? dir + p.n_z : nullptr;
-  StatAcc acc;
-  acc.zero();
-  NodeAcc<S> nacc;
-  nacc.zero();
-  uint32_t wnext = gw < p.nl ? desc_word(p.desc, gw, lane) : 0u;
-  for (int k = gw; k < p.nl; k += nw) {
-    const NodeF D = node_fields(wnext);
-    if (k + nw < p.nl) wnext = desc_word(p.desc, k + nw, lane);
-    const int m = D.m, c0 = D.c0;
-    const int64_t el = D.enl, ea = el + 2 * m + 2, z2 = D.zz2;
-    // ---- loads issued up front with the node's own rows (one memory round
-    // trip per node on chains): the first child's nonroot rows and tau, the
-    // first 32 y rows and the s - b'y row
-    S pbe[J], pbde[J], pbc[J];
-#pragma unroll
-    for (int j = 0; j < J; ++j) {
-      const int e = lane + 32 * j;
-      pbe[j] = pbde[j] = pbc[j] = S(0);
-      if (e < nb) {
-        pbc[j] = e < nx ? p.qs[(int64_t)c0 * nx + e] : (e < nxu ? p.rs[(int64_t)c0 * nu + (e - nx)] : S(0.5));
-        pbe[j] = eta[D.enr_c0 + e];
-        if (DR) pbde[j] = deta[D.enr_c0 + e];
-      }
-    }
-    const S ptz = z[z2 + 2 * m + 1], ptzp = zp[z2 + 2 * m + 1], ptdz = DR ? dz[z2 + 2 * m + 1] : S(0);
-    S yz0 = 0, yzp0 = 0, yd0 = 0, ye0 = 0, yde0 = 0, pr0 = 0;
-    if (lane < 2 * m + 1) {
-      yz0 = z[z2 + lane];
-      yzp0 = zp[z2 + lane];
-      if (DR) yd0 = dz[z2 + lane];
-      ye0 = eta[el + lane];
-      if (DR) yde0 = deta[el + lane];
-      if (lane < m) pr0 = p.prob[c0 + lane];
-    }
-    const int64_t ie_sb = el + 2 * m + 1;
-    const S sk = z[D.zs], skp = zp[D.zs], skd = DR ? dz[D.zs] : S(0);
-    const S y3 = z[z2 + 2 * m], y3p = zp[z2 + 2 * m], y3d = DR ? dz[z2 + 2 * m] : S(0);
-    const S esb = eta[ie_sb], desb = DR ? deta[ie_sb] : S(0);
-    // ---- own (x, u) and its box rows
-    S az[J], azp[J], adz[J], lt[J];
-    {
-      S ae[J], ade[J], alo[J], ahi[J];
-#pragma unroll
-      for (int j = 0; j < J; ++j) {
-        const int e = lane + 32 * j;
-        az[j] = azp[j] = adz[j] = lt[j] = ae[j] = ade[j] = alo[j] = ahi[j] = S(0);
-        if (e < nxu) {
-          const int64_t zi = e < nx ? D.zx + e : D.zu + (e - nx);
-          az[j] = z[zi];
-          azp[j] = zp[zi];
-          if (DR) adz[j] = dz[zi];
-          ae[j] = eta[ea + e];
-          if (DR) ade[j] = deta[ea + e];
-          alo[j] = e < nx ? p.xlo[(int64_t)k * nx + e] : p.ulo[(int64_t)k * nu + (e - nx)];
-          ahi[j] = e < nx ? p.xhi[(int64_t)k * nx + e] : p.uhi[(int64_t)k * nu + (e - nx)];
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < J; ++j) {
-        const int e = lane + 32 * j;
-        if (e < nxu) {
-          const S w = dual_w<S, DM_DUAL>(al, ae[j], az[j], azp[j]);
-          const S o = w - al * clampv(w * ial, alo[j], ahi[j]);
-          out[ea + e] = o;
-          dual_stat<S, true, DR>(nacc, ial, ae[j], o, az[j] - azp[j], ade[j], adz[j]);
-          lt[j] = ae[j] - o;
-        }
-      }
-    }
-    // ---- children
-    for (int jc = 0; jc < m; ++jc) {
-      const int c = c0 + jc;
-      const int64_t ztau = z2 + 2 * m + 1 + jc;
-      const int64_t er = jc == 0 ? D.enr_c0 : __ldg(&p.desc[c].enr);
-      S tz = ptz, tzp = ptzp, tdz = ptdz;
-      S be[J], bde[J], bc[J];
-#pragma unroll
-      for (int j = 0; j < J; ++j) {
-        be[j] = pbe[j];
-        bde[j] = pbde[j];
-        bc[j] = pbc[j];
-      }
-      if (jc > 0) {  // further children (branching stages only)
-        tz = z[ztau];
-        tzp = zp[ztau];
-        if (DR) tdz = dz[ztau];
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-          const int e = lane + 32 * j;
-          if (e < nb) {
-            bc[j] = e < nx ? p.qs[(int64_t)c * nx + e] : (e < nxu ? p.rs[(int64_t)c * nu + (e - nx)] : S(0.5));
-            be[j] = eta[er + e];
-            if (DR) bde[j] = deta[er + e];
-          }
-        }
-      }
-      {  // nonroot block of c: SOC on (Q^c 1/2 x^k, R^c 1/2 u^k, tau^c / 2, tau^c / 2)
-        S w[J], lrz[J], ld[J];
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-          const int e = lane + 32 * j;
-          w[j] = lrz[j] = ld[j] = S(0);
-          if (e < nb) {
-            const S coef = bc[j];
-            const S Lz = coef * (e < nxu ? az[j] : tz);
-            const S Lzp = coef * (e < nxu ? azp[j] : tzp);
-            if (DR) ld[j] = coef * (e < nxu ? adz[j] : tdz);
-            w[j] = dual_w<S, DM_DUAL>(al, be[j], Lz, Lzp);
-            lrz[j] = Lz - Lzp;
-          }
-        }
-        S nv, t, sc;
-        soc_norm<S, J>(w, nb, ial, lane, nv, t, sc);
-        S tau_part = 0;
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-          const int e = lane + 32 * j;
-          if (e < nb) {
-            const S o = soc_entry(w[j], e, nb, al, ial, nv, t, sc);
-            out[er + e] = o;
-            dual_stat<S, true, DR>(nacc, ial, be[j], o, lrz[j], bde[j], ld[j]);
-            const S re = be[j] - o;
-            if (e < nxu) lt[j] += bc[j] * re;
-            else tau_part += re;
-          }
-        }
-        tau_part = warp_sum(tau_part);
-        if (lane == 0) primal_stat<S, DR>(nacc, ial, tz, tzp, tdz, S(0.5) * tau_part);
-      }
-      if (c >= p.nl) {  // leaf block of c: box on x^c, SOC on (Q_N^1/2 x^c, s^c / 2, s^c / 2)
-        const int64_t ef = (jc == 0 ? D.es_c0 : __ldg(&p.desc[c].es)) - 2 * nx;
-        const int64_t zxc = __ldg(&p.desc[c].zx);
-        const int64_t zsc = z2 + 3 * m + 1 + jc;
-        const S sz = z[zsc], szp = zp[zsc], sdz = DR ? dz[zsc] : S(0);
-        S xz[J], xzp[J], xdz[J], ltx[J];
-        {
-          S fe[J], fde[J], flo[J], fhi[J];
-#pragma unroll
-          for (int j = 0; j < J; ++j) {
-            const int e = lane + 32 * j;
-            xz[j] = xzp[j] = xdz[j] = ltx[j] = fe[j] = fde[j] = flo[j] = fhi[j] = S(0);
-            if (e < nx) {
-              xz[j] = z[zxc + e];
-              xzp[j] = zp[zxc + e];
-              if (DR) xdz[j] = dz[zxc + e];
-              fe[j] = eta[ef + e];
-              if (DR) fde[j] = deta[ef + e];
-              flo[j] = p.xlo[(int64_t)c * nx + e];
-              fhi[j] = p.xhi[(int64_t)c * nx + e];
-            }
-          }
-#pragma unroll
-          for (int j = 0; j < J; ++j) {
-            const int e = lane + 32 * j;
-            if (e < nx) {
-              const S w = dual_w<S, DM_DUAL>(al, fe[j], xz[j], xzp[j]);
-              const S o = w - al * clampv(w * ial, flo[j], fhi[j]);
-              out[ef + e] = o;
-              dual_stat<S, true, DR>(nacc, ial, fe[j], o, xz[j] - xzp[j], fde[j], xdz[j]);
-              ltx[j] = fe[j] - o;
-            }
-          }
-        }
-        const int dim = nx + 2;
-        const int64_t es = ef + nx;
-        S w[J], lrz[J], ld[J], ev[J], dev[J], qn[J];
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-          const int e = lane + 32 * j;
-          w[j] = lrz[j] = ld[j] = ev[j] = dev[j] = qn[j] = S(0);
-          if (e < dim) {
-            const S coef = e < nx ? p.qns[(int64_t)c * nx + e] : S(0.5);
-            const S Lz = coef * (e < nx ? xz[j] : sz);
-            const S Lzp = coef * (e < nx ? xzp[j] : szp);
-            ev[j] = eta[es + e];
-            if (DR) {
-              dev[j] = deta[es + e];
-              ld[j] = coef * (e < nx ? xdz[j] : sdz);
-            }
-            w[j] = dual_w<S, DM_DUAL>(al, ev[j], Lz, Lzp);
-            lrz[j] = Lz - Lzp;
-            qn[j] = coef;
-          }
-        }
-        S nv, t, sc;
-        soc_norm<S, J>(w, dim, ial, lane, nv, t, sc);
-        S s_part = 0;
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-          const int e = lane + 32 * j;
-          if (e < dim) {
-            const S o = soc_entry(w[j], e, dim, al, ial, nv, t, sc);
-            out[es + e] = o;
-            dual_stat<S, true, DR>(nacc, ial, ev[j], o, lrz[j], dev[j], ld[j]);
-            const S re = ev[j] - o;
-            if (e < nx) ltx[j] += qn[j] * re;
-            else s_part += re;
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < J; ++j)
-          if (lane + 32 * j < nx) primal_stat<S, DR>(nacc, ial, xz[j], xzp[j], xdz[j], ltx[j]);
-        s_part = warp_sum(s_part);
-        if (lane == 0) primal_stat<S, DR>(nacc, ial, sz, szp, sdz, S(0.5) * s_part);
-      }
-    }
-    // ---- primal statistics at x^k, u^k
-#pragma unroll
-    for (int j = 0; j < J; ++j)
-      if (lane + 32 * j < nxu) primal_stat<S, DR>(nacc, ial, az[j], azp[j], adz[j], lt[j]);
-    // ---- the s - b'y row of k (b = (p^children, 0, 1)), then the y rows
-    {
-      S bs = pr0 * yz0, bsp = pr0 * yzp0, bsd = DR ? pr0 * yd0 : S(0);
-      for (int jj = lane + 32; jj < m; jj += 32) {  // nodes with more than 32 children
-        const S pj = p.prob[c0 + jj];
-        bs += pj * z[z2 + jj];
-        bsp += pj * zp[z2 + jj];
-        if (DR) bsd += pj * dz[z2 + jj];
-      }
-      bs = warp_sum(bs);
-      bsp = warp_sum(bsp);
-      if (DR) bsd = warp_sum(bsd);
-      const S Lz = sk - (bs + y3), Lzp = skp - (bsp + y3p), Ld = DR ? skd - (bsd + y3d) : S(0);
-      const S w = dual_w<S, DM_DUAL>(al, esb, Lz, Lzp);
-      const S o = vmin(w, S(0));
-      const S re_sb = esb - o;
-      if (lane == 0) {
-        out[ie_sb] = o;
-        dual_stat<S, true, DR>(nacc, ial, esb, o, Lz - Lzp, desb, Ld);
-        primal_stat<S, DR>(nacc, ial, sk, skp, skd, re_sb);   // s^k (s^0 at the root)
-      }
-      auto yrow = [&](int e, S yz, S yzp, S yd, S ye, S yde) {
-        const S yw = dual_w<S, DM_DUAL>(al, ye, yz, yzp);
-        const S yo = e < 2 * m ? vmin(yw, S(0)) : S(0);
-        out[el + e] = yo;
-        dual_stat<S, true, DR>(nacc, ial, ye, yo, yz - yzp, yde, yd);
-        const S bl = e < m ? p.prob[c0 + e] : (e < 2 * m ? S(0) : S(1));
-        primal_stat<S, DR>(nacc, ial, yz, yzp, yd, (ye - yo) - bl * re_sb);
-      };
-      if (lane < 2 * m + 1) yrow(lane, yz0, yzp0, yd0, ye0, yde0);
-      for (int e = lane + 32; e < 2 * m + 1; e += 32)
-        yrow(e, z[z2 + e], zp[z2 + e], DR ? dz[z2 + e] : S(0), eta[el + e], DR ? deta[el + e] : S(0));
-    }
-    nacc.node_done(acc);
-  }
-  nacc.flush(acc);
-  block_stats_store<sizeof(S) == 4>(acc, partials, bid);
-}
-
 template <typename S, bool DIR, int J>
 __global__ void __launch_bounds__(128) k_dual_fused(KP<S> p, const S* __restrict__ z, const S* __restrict__ zp,
                                                     const S* __restrict__ eta, S* __restrict__ out,
                                                     const S* __restrict__ dir, double* __restrict__ partials) {
   dual_fused_body<S, DIR, J>(p, blockIdx.x, gridDim.x, z, zp, eta, out, dir, partials);
-}
-
-// Sums (maxima for xi) of the per-block partial statistics of the dual and
-// primal kernels; one block, fixed order (deterministic).
-__device__ __forceinline__ void reduce_stats_body(const double* __restrict__ pd, int nd,
-                                                  const double* __restrict__ pp, int np, double* __restrict__ out,
-                                                  const int32_t* __restrict__ skip) {
-  if (skip && *skip) return;
-  __shared__ double red[8][32];
-  const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;  // 8 warps, one per statistic
-  const bool mx = (i == ST_XIP || i == ST_XID);
-  double v = 0.0;
-  for (int b = lane; b < nd; b += 32) v = mx ? fmax(v, pd[(int64_t)b * 8 + i]) : v + pd[(int64_t)b * 8 + i];
-  for (int b = lane; b < np; b += 32) v = mx ? fmax(v, pp[(int64_t)b * 8 + i]) : v + pp[(int64_t)b * 8 + i];
-  v = mx ? warp_max(v) : warp_sum(v);
-  if (lane == 0) red[i][0] = v;
-  __syncthreads();
-  if (threadIdx.x < 8) out[threadIdx.x] = red[threadIdx.x][0];
 }
 
 __global__ void k_reduce_stats(const double* __restrict__ pd, int nd, const double* __restrict__ pp, int np,
@@ -746,6 +64,7 @@ __global__ void __launch_bounds__(128) k_prep_b(const BInst<S>* __restrict__ bi,
   const KP<S> p = b.kp;
   lstar_body<S, LS_PREP, J>(p, blockIdx.x - m.base[i], m.cnt[i], b.Vt + p.n_z, b.Vt, b.TVt);
 }
+
 template <typename S, int J>
 __global__ void __launch_bounds__(128) k_dual_b(const BInst<S>* __restrict__ bi, BMap m) {
   const int i = m.inst[blockIdx.x];
@@ -754,6 +73,7 @@ __global__ void __launch_bounds__(128) k_dual_b(const BInst<S>* __restrict__ bi,
   dual_fused_body<S, true, J>(p, blockIdx.x - m.base[i], m.cnt[i], b.Vt, b.TVt, b.Vt + p.n_z, b.TVt + p.n_z,
                               b.d, b.pd);
 }
+
 template <typename S>
 __global__ void k_reduce_stats_b(const BInst<S>* __restrict__ bi) {
   const BInst<S>& b = bi[blockIdx.x];

@@ -166,6 +166,7 @@ struct Workspace {
   double g_alpha = 0.0;
   int g_trace = -1, g_launches_per_round = 0;
   int32_t* h_done = nullptr;  // pinned
+  void* cta_bi = nullptr;      // instance view of the single-block solve (device)
   std::vector<void*> allocs;
   ~Workspace() {
     if (gexec) cudaGraphExecDestroy(gexec);
@@ -316,6 +317,33 @@ static KP<S> make_kp(const Problem& P, double alpha, const int32_t* stage_begin_
   k.skip = nullptr;
   return k;
 }
+
+// One instance's view for the batched and single-block kernels.
+template <typename S>
+static BInst<S> make_binst(Problem& P, Workspace* ws, double alpha) {
+  BInst<S> b;
+  b.kp = make_kp<S>(P, alpha, P.idx.stage_begin);
+  b.kp.skip = &ws->st->done;
+  b.st = ws->st;
+  b.V = (S*)ws->v[0];
+  b.TV = (S*)ws->Tv[0];
+  b.Vp = (S*)ws->v[1];
+  b.TVp = (S*)ws->Tv[1];
+  b.Vt = (S*)ws->v[2];
+  b.TVt = (S*)ws->Tv[2];
+  b.d = (S*)ws->d;
+  b.MR = (S*)ws->MR;
+  b.D = (S*)ws->D;
+  b.stats = ws->stats;
+  b.pd = ws->pd;
+  b.paa = ws->paa;
+  b.n_v = ws->n_v;
+  b.ld = ws->ld;
+  b.nb_node = 1;
+  b.nb_vec = 1;
+  return b;
+}
+
 
 static double default_alpha(const Problem& P, double alpha) { return alpha > 0.0 ? alpha : 0.99 / P.normL; }
 
@@ -580,7 +608,7 @@ constexpr int kRounds = 8;  // rounds per graph launch (one host check per launc
 template <typename S>
 static int solve_graph(Problem& P, const double* x0_dev, const spock_settings& s, double* z_dev, double* eta_dev,
                        int warm, spock_info* info, cudaStream_t user_st, double tol_given, int stall_window,
-                       int* final_action_out) {
+                       int* final_action_out, bool cta = false) {
   const int mem = std::max(0, std::min<int>(s.memory, kMaxMemory));
   Workspace* ws = get_ws_impl<S>(P, mem);
   const DevFactors<S>& f = factors<S>(P);
@@ -656,49 +684,62 @@ static int solve_graph(Problem& P, const double* x0_dev, const spock_settings& s
     return 4 + (int)(ws->launches - before);
   };
   ws->launches = 0;
-  CUDA_TRY(cudaEventRecord(ws->e0, st));
-  eval_T<S>(c, Vt, TVt, nullptr, stats_t, nullptr);  // T(v0); also sets kernel attributes outside capture
-  const int64_t launches0 = ws->launches;
-  const char* fam = getenv("SPOCK_RICCATI_KERNELS");
-  const int trace_key = (trace_dev ? 1 : 0) + 2 * (s.profile ? 1 : 0) +
-                        4 * (fam && fam[0] ? (int)(unsigned char)fam[0] : 0);
-  if (s.profile) ws->prof.start();  // event slot r is recorded by round r of every replay
-  if (!ws->gexec || ws->g_alpha != alpha || ws->g_trace != trace_key) {
-    if (ws->gexec) {
-      cudaGraphExecDestroy(ws->gexec);
-      ws->gexec = nullptr;
-    }
-    cudaGraph_t g = nullptr;
-    CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    int per = 0;
-    for (int r = 0; r < kRounds; ++r) per = round(st);
-    CUDA_TRY(cudaStreamEndCapture(st, &g));
-    cudaError_t e = cudaGraphInstantiate(&ws->gexec, g, 0);
-    cudaGraphDestroy(g);
-    CUDA_TRY(e);
-    ws->g_alpha = alpha;
-    ws->g_trace = trace_key;
-    ws->g_launches_per_round = per;
-  }
-  int64_t launches = launches0;
   const int64_t max_rounds = (int64_t)(max_iter + 1) * (h.max_back + 3) + 2;
-  int64_t rounds = 0;
-  int32_t rounds_done = 0;
-  for (;;) {
-    CUDA_TRY(cudaGraphLaunch(ws->gexec, st));
-    rounds += kRounds;
-    launches += (int64_t)kRounds * ws->g_launches_per_round;
-    CUDA_TRY(cudaMemcpyAsync(ws->h_done, &ws->st->done, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaMemcpyAsync(ws->h_done + 1, &ws->st->rounds, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
-    if (s.profile) {  // rounds that evaluated T in this replay: the first (rounds now - rounds before)
-      const int ran = ws->h_done[1] - rounds_done - (ws->h_done[0] ? 1 : 0);
-      ws->prof.used = kRounds;
-      ws->prof.harvest_first(std::max(0, std::min(ran, kRounds)));
+  if (cta) {  // the whole solve in one block (cta.cu): one launch
+    const BInst<S> hb = make_binst<S>(P, ws, alpha);
+    if (!ws->cta_bi) ws->cta_bi = ws->alloc(sizeof(BInst<S>));
+    CUDA_TRY(cudaMemcpyAsync(ws->cta_bi, &hb, sizeof(hb), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));  // hb lives on this stack frame
+    CUDA_TRY(cudaEventRecord(ws->e0, st));
+    launch_solve_cta<S>((const BInst<S>*)ws->cta_bi, 1, P.nx + P.nu, mem, max_rounds, trace_dev, st);
+    check_launch();
+    ws->launches = 1;
+  } else {
+    CUDA_TRY(cudaEventRecord(ws->e0, st));
+    eval_T<S>(c, Vt, TVt, nullptr, stats_t, nullptr);  // T(v0); also sets kernel attributes outside capture
+    const int64_t launches0 = ws->launches;
+    const char* fam = getenv("SPOCK_RICCATI_KERNELS");
+    const int trace_key = (trace_dev ? 1 : 0) + 2 * (s.profile ? 1 : 0) +
+                          4 * (fam && fam[0] ? (int)(unsigned char)fam[0] : 0);
+    if (s.profile) ws->prof.start();  // event slot r is recorded by round r of every replay
+    if (!ws->gexec || ws->g_alpha != alpha || ws->g_trace != trace_key) {
+      if (ws->gexec) {
+        cudaGraphExecDestroy(ws->gexec);
+        ws->gexec = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      int per = 0;
+      for (int r = 0; r < kRounds; ++r) per = round(st);
+      CUDA_TRY(cudaStreamEndCapture(st, &g));
+      cudaError_t e = cudaGraphInstantiate(&ws->gexec, g, 0);
+      cudaGraphDestroy(g);
+      CUDA_TRY(e);
+      ws->g_alpha = alpha;
+      ws->g_trace = trace_key;
+      ws->g_launches_per_round = per;
     }
-    rounds_done = ws->h_done[1];
-    if (ws->h_done[0] || rounds > max_rounds) break;
+    int64_t launches = launches0;
+    int64_t rounds = 0;
+    int32_t rounds_done = 0;
+    for (;;) {
+      CUDA_TRY(cudaGraphLaunch(ws->gexec, st));
+      rounds += kRounds;
+      launches += (int64_t)kRounds * ws->g_launches_per_round;
+      CUDA_TRY(cudaMemcpyAsync(ws->h_done, &ws->st->done, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(cudaMemcpyAsync(ws->h_done + 1, &ws->st->rounds, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(cudaStreamSynchronize(st));
+      if (s.profile) {  // rounds that evaluated T in this replay: the first (rounds now - rounds before)
+        const int ran = ws->h_done[1] - rounds_done - (ws->h_done[0] ? 1 : 0);
+        ws->prof.used = kRounds;
+        ws->prof.harvest_first(std::max(0, std::min(ran, kRounds)));
+      }
+      rounds_done = ws->h_done[1];
+      if (ws->h_done[0] || rounds > max_rounds) break;
+    }
+    ws->launches = launches;
   }
+  const int64_t launches = ws->launches;
   CUDA_TRY(cudaEventRecord(ws->e1, st));
   convert<double, S>(TV, z_dev, nz, st);
   convert<double, S>(TV + nz, eta_dev, P.off.n_eta, st);
@@ -744,8 +785,12 @@ static int solve_graph(Problem& P, const double* x0_dev, const spock_settings& s
   return status;
 }
 
-// Device-driven rounds replayed from a CUDA graph; SPOCK_DRIVER=host selects
-// the host-driven loop (one host decision per SuperMann step) instead.
+// Device-driven rounds replayed from a CUDA graph, or -- for small problems
+// (at most kCtaAutoNodes nodes, nx + nu <= 62, Anderson memory 0, 3 or 5, no
+// profiling) -- the whole solve in one single-block launch (cta.cu).
+// SPOCK_DRIVER = host / graph / cta selects the host-driven loop (one host
+// decision per SuperMann step), the graph or the single block.
+constexpr int kCtaAutoNodes = 64;
 template <typename S>
 static int solve_impl(Problem& P, const double* x0_dev, const spock_settings& s, double* z_dev, double* eta_dev,
                       int warm, spock_info* info, cudaStream_t st, double tol_given = 0.0, int stall_window = 0,
@@ -753,7 +798,11 @@ static int solve_impl(Problem& P, const double* x0_dev, const spock_settings& s,
   const char* drv = getenv("SPOCK_DRIVER");
   if (drv && drv[0] == 'h')
     return solve_host<S>(P, x0_dev, s, z_dev, eta_dev, warm, info, st, tol_given, stall_window, final_action_out);
-  return solve_graph<S>(P, x0_dev, s, z_dev, eta_dev, warm, info, st, tol_given, stall_window, final_action_out);
+  const int mem = std::max(0, std::min<int>(s.memory, kMaxMemory));
+  const bool cta_ok = cta_supported(P.nx, P.nu, mem) && !s.profile;
+  const bool cta = cta_ok && (drv && drv[0] == 'c' ? true : (!(drv && drv[0]) && P.tree.n <= kCtaAutoNodes));
+  return solve_graph<S>(P, x0_dev, s, z_dev, eta_dev, warm, info, st, tol_given, stall_window, final_action_out,
+                        cta);
 }
 
 template <typename S>
@@ -825,6 +874,7 @@ struct Batch {
   int g_launches = 0;
   int tuned_tile[2] = {0, 0};  // node tile (nodes per warp) picked by the autotuner, per precision
   int tuned_fam[2] = {-1, -1};  // Riccati kernel family picked by the autotuner, per precision
+  int tuned_cta[2] = {0, 0};     // 1: the single-block persistent solve was faster
   SmState** st_ptrs = nullptr;
   int32_t* done_dev = nullptr;
   int32_t* done_host = nullptr;  // pinned
@@ -905,23 +955,7 @@ static void batch_plan(Batch& B, const std::vector<Workspace*>& wss, const std::
     Problem& P = *B.probs[i];
     Workspace* ws = wss[i];
     BInst<S>& b = h[i];
-    b.kp = make_kp<S>(P, alphas[i], P.idx.stage_begin);
-    b.kp.skip = &ws->st->done;
-    b.st = ws->st;
-    b.V = (S*)ws->v[0];
-    b.TV = (S*)ws->Tv[0];
-    b.Vp = (S*)ws->v[1];
-    b.TVp = (S*)ws->Tv[1];
-    b.Vt = (S*)ws->v[2];
-    b.TVt = (S*)ws->Tv[2];
-    b.d = (S*)ws->d;
-    b.MR = (S*)ws->MR;
-    b.D = (S*)ws->D;
-    b.stats = ws->stats;
-    b.pd = ws->pd;
-    b.paa = ws->paa;
-    b.n_v = ws->n_v;
-    b.ld = ws->ld;
+    b = make_binst<S>(P, ws, alphas[i]);
     const int nn = P.tree.n;
     b.nb_node = std::max(1, std::min(ws->grid_d, (nn + kWarpsPerBlock * tile - 1) / (kWarpsPerBlock * tile)));
     const int64_t per_block = (int64_t)256 * kVecElemsPerThread;
@@ -1050,14 +1084,40 @@ static void batch_init(Batch& B, const std::vector<Workspace*>& wss, const std::
   }
 }
 
-// Autotuner of the batch: the node tile (nodes per warp of the node kernels:
-// 1, 2, 4, 8 or 16) and the Riccati kernel family (direct or staged) with the
-// shortest batched T evaluation, timed over three evaluations per candidate;
-// cached per batch and precision.  SPOCK_BATCH_TILE fixes the tile,
-// SPOCK_RICCATI_KERNELS = direct / tma fixes the family.
+// Autotuner of the batch.  Candidates: the work-list kernels with node tile
+// 1, 2, 4, 8 or 16 (nodes per warp of the node kernels) and the direct or
+// staged Riccati family, and -- when every instance fits it -- the
+// single-block persistent solve (cta.cu).  Each candidate runs the
+// evaluation of T at the starting points and kTuneRounds rounds from the
+// same state; the fastest is cached per batch and precision.
+// SPOCK_BATCH_TILE fixes the tile, SPOCK_RICCATI_KERNELS = direct / tma the
+// family, SPOCK_BATCH_MODE = list / cta the mode.
+constexpr int kTuneRounds = 4;
 struct BatchCfg {
   int tile, fam;
+  bool cta;
 };
+
+template <typename S>
+static void batch_rounds_direct(Batch& B, int mem, int rounds) {
+  const int n = (int)B.probs.size();
+  const BInst<S>* bi = (const BInst<S>*)B.bi_dev;
+  batch_eval<S>(B, B.main);
+  for (int r = 0; r < rounds; ++r) {
+    launch_round_decide_b<S>(bi, n, B.main);
+    launch_round_commit_b<S>(bi, B.vec.view(n), B.vec.nblocks, mem, B.main);
+    launch_round_aa_solve_b<S>(bi, n, B.main);
+    launch_round_point_b<S>(bi, B.vec.view(n), B.vec.nblocks, mem, B.main);
+    batch_eval<S>(B, B.main);
+  }
+}
+
+static int batch_max_nxu(const Batch& B) {
+  int v = 0;
+  for (const Problem* P : B.probs) v = std::max(v, P->nx + P->nu);
+  return v;
+}
+
 template <typename S>
 static BatchCfg batch_tune(Batch& B, const std::vector<Workspace*>& wss, const std::vector<double>& alphas, int mem,
                            const spock_settings& s, const double* const* x0, double* const* z,
@@ -1071,36 +1131,62 @@ static BatchCfg batch_tune(Batch& B, const std::vector<Workspace*>& wss, const s
   const char* ek = getenv("SPOCK_RICCATI_KERNELS");
   if (ek && ek[0] == 'd') fams = {0};
   if (ek && ek[0] == 't') fams = {1};
+  bool cta_ok = true;
+  for (const Problem* P : B.probs) cta_ok = cta_ok && cta_supported(P->nx, P->nu, mem);
+  bool try_list = true;
+  const char* em = getenv("SPOCK_BATCH_MODE");
+  if (em && em[0] == 'l') cta_ok = false;
+  if (em && em[0] == 'c' && cta_ok) try_list = false;
+  const bool cacheable = tiles.size() > 1 && fams.size() > 1 && !(em && em[0]);
   const int pi = sizeof(S) == 8 ? 0 : 1;
-  if (tiles.size() > 1 && fams.size() > 1 && B.tuned_tile[pi] > 0) return {B.tuned_tile[pi], B.tuned_fam[pi]};
+  if (cacheable && B.tuned_tile[pi] > 0) return {B.tuned_tile[pi], B.tuned_fam[pi], B.tuned_cta[pi] != 0};
   cudaEvent_t a, b;
   CUDA_TRY(cudaEventCreate(&a));
   CUDA_TRY(cudaEventCreate(&b));
   float best = 1e30f;
-  BatchCfg pick{tiles[0], fams[0]};
-  for (int fam : fams) {
-    for (int tile : tiles) {
-      batch_plan<S>(B, wss, alphas, mem, tile, fam);
-      if (B.fam != fam) continue;  // staged layout does not fit
-      batch_init<S>(B, wss, alphas, s, mem, x0, z, eta, warm);
-      batch_eval<S>(B, B.main);  // warm-up
-      CUDA_TRY(cudaEventRecord(a, B.main));
-      for (int r = 0; r < 3; ++r) batch_eval<S>(B, B.main);
-      CUDA_TRY(cudaEventRecord(b, B.main));
-      CUDA_TRY(cudaEventSynchronize(b));
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, a, b);
-      if (ms < best) {
-        best = ms;
-        pick = {tile, fam};
+  BatchCfg pick{tiles[0], fams[0], false};
+  auto timed = [&](auto&& run) {
+    batch_init<S>(B, wss, alphas, s, mem, x0, z, eta, warm);
+    CUDA_TRY(cudaEventRecord(a, B.main));
+    run();
+    CUDA_TRY(cudaEventRecord(b, B.main));
+    CUDA_TRY(cudaEventSynchronize(b));
+    check_launch();
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+  };
+  if (try_list) {
+    for (int fam : fams) {
+      for (int tile : tiles) {
+        batch_plan<S>(B, wss, alphas, mem, tile, fam);
+        if (B.fam != fam) continue;  // staged layout does not fit
+        timed([&] { batch_rounds_direct<S>(B, mem, 1); });  // warm-up
+        const float ms = timed([&] { batch_rounds_direct<S>(B, mem, kTuneRounds); });
+        if (ms < best) {
+          best = ms;
+          pick = {tile, fam, false};
+        }
       }
+    }
+  }
+  if (cta_ok) {
+    batch_plan<S>(B, wss, alphas, mem, pick.tile, pick.fam);
+    const int n = (int)B.probs.size(), nxu = batch_max_nxu(B);
+    const BInst<S>* bi = (const BInst<S>*)B.bi_dev;
+    timed([&] { launch_solve_cta<S>(bi, n, nxu, mem, 1, nullptr, B.main); });  // warm-up
+    const float ms = timed([&] { launch_solve_cta<S>(bi, n, nxu, mem, kTuneRounds, nullptr, B.main); });
+    if (ms < best) {
+      best = ms;
+      pick.cta = true;
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  if (tiles.size() > 1 && fams.size() > 1) {
+  if (cacheable) {
     B.tuned_tile[pi] = pick.tile;
     B.tuned_fam[pi] = pick.fam;
+    B.tuned_cta[pi] = pick.cta ? 1 : 0;
   }
   return pick;
 }
@@ -1123,10 +1209,11 @@ static int batch_solve(Batch& B, const double* const* x0, const spock_settings& 
   batch_plan<S>(B, wss, alphas, mem, cfg.tile, cfg.fam);
   batch_init<S>(B, wss, alphas, s, mem, x0, z, eta, warm);
   const BInst<S>* bi = (const BInst<S>*)B.bi_dev;
+  const int64_t max_rounds = (int64_t)(max_iter + 1) * (std::max(0, s.max_backtracks) + 3) + 2;
   // the graph of kBatchRounds rounds (the plan, hence the graph, is rebuilt
   // when precision, memory, tile or workspaces change)
   const double a_key = s.alpha > 0 ? s.alpha : 0.0;
-  if (!B.gexec || B.g_alpha != a_key) {
+  if (!cfg.cta && (!B.gexec || B.g_alpha != a_key)) {
     if (B.gexec) {
       cudaGraphExecDestroy(B.gexec);
       B.gexec = nullptr;
@@ -1154,14 +1241,18 @@ static int batch_solve(Batch& B, const double* const* x0, const spock_settings& 
     for (int i = 0; i < n; ++i) h[i] = wss[i]->st;
     CUDA_TRY(cudaMemcpy(B.st_ptrs, h.data(), sizeof(SmState*) * n, cudaMemcpyHostToDevice));
   }
-  const int64_t max_rounds = (int64_t)(max_iter + 1) * (std::max(0, s.max_backtracks) + 3) + 2;
   int64_t rounds = 0, graph_launches = 0;
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
   CUDA_TRY(cudaEventRecord(e0, B.main));
-  batch_eval<S>(B, B.main);  // T of the starting points
-  for (;;) {
+  if (cfg.cta) {  // one persistent launch: every instance solved by its own block
+    launch_solve_cta<S>(bi, n, batch_max_nxu(B), mem, max_rounds, nullptr, B.main);
+    check_launch();
+  } else {
+    batch_eval<S>(B, B.main);  // T of the starting points
+  }
+  for (; !cfg.cta;) {
     CUDA_TRY(cudaGraphLaunch(B.gexec, B.main));
     rounds += kBatchRounds;
     ++graph_launches;
@@ -1177,7 +1268,7 @@ static int batch_solve(Batch& B, const double* const* x0, const spock_settings& 
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  const int64_t total_launches = B.launches_per_eval + graph_launches * B.g_launches;
+  const int64_t total_launches = cfg.cta ? 1 : B.launches_per_eval + graph_launches * B.g_launches;
   int status = SPOCK_OK;
   std::vector<SmState> fin(n);
   for (int i = 0; i < n; ++i) {

@@ -113,3 +113,33 @@ def test_batch_rejects_duplicate_problem():
     P = spock.Problem(W.small_binary(0))
     with pytest.raises(spock.SpockError):
         spock.spock_batch_create([P.handle, P.handle])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_single_block_mode_matches_single_block_solves(precision, monkeypatch):
+    """The persistent mode (one launch, one block per instance) on 16
+    instances of the batched workload equals, instance by instance, the
+    single-block solve of that instance (same bodies, same block shape)."""
+    import torch
+    from paper_2212_01110_gb300 import spock
+    monkeypatch.setenv("SPOCK_BATCH_MODE", "cta")
+    monkeypatch.setenv("SPOCK_DRIVER", "cta")
+    dev = torch.device("cuda:0")
+    ds = W.batch_instances(seed=5, count=16)
+    probs = [spock.Problem(d) for d in ds]
+    batch = spock.spock_batch_create([p.handle for p in probs])
+    bufs = [_tensors(P, d, dev) for P, d in zip(probs, ds)]
+    K = 12
+    s = spock.spock_default_settings(max_iter=K, eps_abs=1e-14, eps_rel=1e-14, precision=precision, fp64_tail=0)
+    infos = spock.spock_batch_solve_dev(batch, [b[0] for b in bufs], s, [b[1] for b in bufs], [b[2] for b in bufs], 0)
+    assert all(i.n_launches == 1 for i in infos)
+    for P, (x0, z, e), inf in zip(probs, bufs, infos):
+        assert inf.iterations == K
+        z1, e1 = torch.zeros_like(z), torch.zeros_like(e)
+        inf1 = spock.spock_solve_dev(P.handle, x0, s, z1, e1, 0)
+        a = torch.cat([z, e]).cpu().numpy()
+        b = torch.cat([z1, e1]).cpu().numpy()
+        err = np.max(np.abs(a - b)) / max(1, np.max(np.abs(b)))
+        assert err < (1e-12 if precision == 0 else 1e-4), err
+        assert inf.n_T == inf1.n_T
+    spock.spock_free(batch)

@@ -161,15 +161,16 @@ def test_errors():
         spock.spock_solve(pair.gp.handle, d["x0"], s, z, e, 0)
 
 
-def test_graph_and_host_drivers_agree(monkeypatch):
-    """The device-driven rounds (CUDA graph) and the host-driven loop take
-    the same decisions and return the same iterate."""
+def test_drivers_agree(monkeypatch):
+    """The device-driven rounds (CUDA graph), the host-driven loop and the
+    single-block solve (one launch) take the same decisions and return the
+    same iterate."""
     import ctypes as C
     from paper_2212_01110_gb300 import spock
     pair = Pair(CASES["ragged"])
     K = 40
     out = {}
-    for drv in ("graph", "host"):
+    for drv in ("graph", "host", "cta"):
         monkeypatch.setenv("SPOCK_DRIVER", drv)
         trace = (C.c_int32 * (2 * K))()
         s = spock.spock_default_settings(max_iter=K, alpha=pair.alpha, eps_abs=1e-14, eps_rel=1e-14)
@@ -178,9 +179,27 @@ def test_graph_and_host_drivers_agree(monkeypatch):
         e = pair.t(np.zeros(pair.gp.n_eta))
         info = spock.spock_solve_dev(pair.gp.handle, pair.x0, s, z, e, 0)
         out[drv] = (np.concatenate([z.cpu().numpy(), e.cpu().numpy()]), list(trace), info.n_T)
-    assert out["graph"][1] == out["host"][1]
-    assert out["graph"][2] == out["host"][2]
+    assert out["graph"][1] == out["host"][1] == out["cta"][1]
+    assert out["graph"][2] == out["host"][2] == out["cta"][2]
     assert rel_err(out["graph"][0], out["host"][0]) < 1e-13
+    # one block sums the statistics in another order: rounding-level differences
+    assert rel_err(out["cta"][0], out["graph"][0]) < 1e-11
+
+
+@pytest.mark.parametrize("name", ["binary_N3", "chains", "a0_a1"])
+def test_single_block_solve_converges_to_oracle(name, monkeypatch):
+    """The single-block driver (forced) reaches the oracle's solution."""
+    from paper_2212_01110_gb300 import spock
+    monkeypatch.setenv("SPOCK_DRIVER", "cta")
+    pair = Pair(CASES[name])
+    s = spock.spock_default_settings(alpha=pair.alpha, memory=5)
+    z = np.zeros(pair.gp.n_z)
+    e = np.zeros(pair.gp.n_eta)
+    info = spock.spock_solve(pair.gp.handle, pair.d["x0"], s, z, e, 0)
+    assert info.status == spock.SPOCK_OK and info.n_launches == 1
+    ref = ospock(pair.cp, pair.d["x0"], s=OSettings(memory=5))
+    assert ref.status == "converged"
+    assert abs(z[0] - ref.v[0]) < 1e-4 * max(1, abs(ref.v[0]))
 
 
 @pytest.mark.parametrize("drv", ["graph", "host"])
