@@ -193,6 +193,13 @@ int spock_problem_info(const spock_problem* p, int64_t* n_z, int64_t* n_eta,
  * Copies inputs to the device and results back inside the call.  Returns
  * SPOCK_OK on convergence, SPOCK_MAX_ITER at the iteration cap (outputs
  * written in both cases), or an error.
+ * Execution: the SuperMann decisions are taken on the device; rounds of
+ * (decision, Anderson update, next point, evaluation of T) are replayed from
+ * a CUDA graph, or -- for problems of at most 64 nodes with nx + nu <= 62,
+ * memory 0, 3 or 5 and no profiling -- the whole solve runs in one
+ * single-block launch.  The environment variable SPOCK_DRIVER = graph /
+ * cta / host forces the graph, the single block (if the problem fits) or a
+ * host-driven loop.
  */
 int spock_solve(spock_problem* p, const double* x0, const spock_settings* settings,
                 double* z_io, double* eta_io, int32_t warm, spock_info* info);
@@ -303,10 +310,15 @@ int spock_batch_create(int32_t n, spock_problem* const* problems, spock_batch** 
  * instance) by tables built once per batch, so a round costs the same
  * number of launches for 1 or 10,000 instances.  A fixed number of rounds
  * is captured into one CUDA graph; finished instances skip their work; the
- * host only reads the done flags after each graph launch.  Before the first
- * solve in a precision, the node tile of the vector kernels (nodes per
- * warp: 1, 2, 4, 8 or 16) is picked by timing batched evaluations of T
- * (autotuner).  info.solve_ms and info.n_launches describe the whole batch.
+ * host only reads the done flags after each graph launch.  When every
+ * instance has nx + nu <= 62 (memory 0, 3 or 5), a second mode solves the
+ * whole batch in one persistent launch, one thread block per instance; the
+ * autotuner times both (SPOCK_BATCH_MODE = list / cta forces one).
+ * Autotuner (before the first solve in a precision): the node tile of the
+ * vector kernels (nodes per warp: 1, 2, 4, 8 or 16), the Riccati kernel
+ * family (direct or staged) and the mode, each candidate timed over the
+ * first evaluation of T and four rounds.  info.solve_ms and info.n_launches
+ * describe the whole batch.
  *   x0_dev, z_dev, eta_dev : host arrays of n device pointers (FP64), per
  *     instance as in spock_solve_dev.
  *   settings : shared by all instances (alpha <= 0: each instance's own
