@@ -434,7 +434,9 @@ def batch_workload(args, spock, workloads, dev, seed=0):
         out[nm] = {"value": round(nT / infos[0].solve_ms * 1e3, 1), "unit": "instance CP iters/s",
                    "device_ms": round(infos[0].solve_ms, 2), "wall_ms": round(wall * 1e3, 2), "n_T_total": nT,
                    "converged": sum(1 for i in infos if i.status == 0),
-                   "median_xi": float(np.median([i.xi for i in infos]))}
+                   "median_xi": float(np.median([i.xi for i in infos])),
+                   "mode": "persistent (one launch, one block per instance)" if infos[0].n_launches == 1
+                           else "work-list kernels, %d launches" % infos[0].n_launches}
     spock.spock_free(b)
     for p in probs:
         p.close()
@@ -470,7 +472,9 @@ def grad_workload(args, spock, workloads, dev):
            "solve": {"tol": 1e-6, "max_iter": args.grad_iter, "batch_ms": round(batch_ms, 2),
                      "ms_per_instance": round(batch_ms / cnt, 3),
                      "converged": sum(1 for i in infos if i.status == 0),
-                     "median_xi": float(np.median([i.xi for i in infos]))}}
+                     "median_xi": float(np.median([i.xi for i in infos])),
+                     "mode": "persistent (one launch, one block per instance)" if infos[0].n_launches == 1
+                             else "work-list kernels, %d launches" % infos[0].n_launches}}
 
     def grads(p, n, nx, nu):
         return [torch.zeros(nx, dtype=torch.float64, device=dev),
