@@ -878,6 +878,11 @@ struct Batch {
   SmState** st_ptrs = nullptr;
   int32_t* done_dev = nullptr;
   int32_t* done_host = nullptr;  // pinned
+  void* tab_dev = nullptr;       // pointer / length tables of the batched copies
+  void* tab_host = nullptr;      // pinned
+  size_t tab_bytes = 0;
+  SmState* st_stage = nullptr;   // staging of the instances' states
+  int st_stage_n = 0;
   std::vector<int32_t*> bufs;
   void free_plan() {
     if (gexec) cudaGraphExecDestroy(gexec);
@@ -898,6 +903,9 @@ struct Batch {
     if (st_ptrs) cudaFree(st_ptrs);
     if (done_dev) cudaFree(done_dev);
     if (done_host) cudaFreeHost(done_host);
+    if (tab_dev) cudaFree(tab_dev);
+    if (tab_host) cudaFreeHost(tab_host);
+    if (st_stage) cudaFree(st_stage);
   }
   // uploads one block map from per-instance block counts (and stages)
   DevMap make_map(const std::vector<int>& cnt, const std::vector<int>& stage) {
@@ -1043,28 +1051,127 @@ static void batch_eval(Batch& B, cudaStream_t st) {
   check_launch();
 }
 
+// Per-instance copies of a batch in one launch each: pointer tables on the
+// device, blockIdx.y over instances, x-blocks and threads over the entries.
+template <typename D, typename S>
+__global__ void k_convert_many(const D* const* __restrict__ in, S* const* __restrict__ out,
+                               const int64_t* __restrict__ len, int count) {
+  for (int i = blockIdx.y; i < count; i += gridDim.y) {
+    const D* a = in[i];
+    S* b = out[i];
+    const int64_t m = len[i];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+      b[e] = a ? (S)a[e] : S(0);   // a NULL source zero-fills
+  }
+}
+// SmState scatter / gather between per-instance states and a staging array.
+__global__ void k_states_many(SmState* const* __restrict__ per, SmState* __restrict__ staging, int count,
+                              int to_instances) {
+  constexpr int W = (int)(sizeof(SmState) / sizeof(int32_t));
+  const int64_t total = (int64_t)count * W;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / W), w = (int)(t % W);
+    int32_t* a = reinterpret_cast<int32_t*>(per[i]) + w;
+    int32_t* b = reinterpret_cast<int32_t*>(staging + i) + w;
+    if (to_instances) *a = *b;
+    else *b = *a;
+  }
+}
+static_assert(sizeof(SmState) % sizeof(int32_t) == 0, "SmState is copied as 32-bit words");
+
+// Uploads the pointer/length tables of one batched copy (device scratch of
+// the batch, grown on demand) and launches it.
+template <typename D, typename S>
+static void copy_many(Batch& B, const std::vector<const D*>& in, const std::vector<S*>& out,
+                      const std::vector<int64_t>& len, cudaStream_t st) {
+  const int n = (int)in.size();
+  if (n == 0) return;
+  const size_t bytes = (size_t)n * (2 * sizeof(void*) + sizeof(int64_t));
+  if (B.tab_bytes < bytes) {
+    if (B.tab_dev) cudaFree(B.tab_dev);
+    if (B.tab_host) cudaFreeHost(B.tab_host);
+    B.tab_dev = nullptr;
+    B.tab_host = nullptr;
+    CUDA_TRY(cudaMalloc(&B.tab_dev, bytes));
+    CUDA_TRY(cudaMallocHost(&B.tab_host, bytes));
+    B.tab_bytes = bytes;
+  }
+  CUDA_TRY(cudaStreamSynchronize(st));  // the pinned table of the previous copy is free again
+  char* h = (char*)B.tab_host;
+  std::memcpy(h, in.data(), n * sizeof(void*));
+  std::memcpy(h + n * sizeof(void*), out.data(), n * sizeof(void*));
+  std::memcpy(h + 2 * n * sizeof(void*), len.data(), n * sizeof(int64_t));
+  CUDA_TRY(cudaMemcpyAsync(B.tab_dev, h, bytes, cudaMemcpyHostToDevice, st));
+  char* d = (char*)B.tab_dev;
+  int64_t mx = 1;
+  for (int64_t l : len) mx = std::max(mx, l);
+  const dim3 grid((unsigned)std::min<int64_t>((mx + 255) / 256, 64), (unsigned)std::min(n, 65535));
+  k_convert_many<D, S><<<grid, 256, 0, st>>>((const D* const*)d, (S* const*)(d + n * sizeof(void*)),
+                                             (const int64_t*)(d + 2 * n * sizeof(void*)), n);
+  check_launch();
+}
+
+// Host states -> every instance's device state (to_instances) or back, with
+// one staging copy and one scatter / gather launch.
+static void batch_states(Batch& B, const std::vector<Workspace*>& wss, SmState* host, bool to_instances,
+                         cudaStream_t st) {
+  const int n = (int)wss.size();
+  if (B.st_stage_n < n) {
+    if (B.st_stage) cudaFree(B.st_stage);
+    B.st_stage = nullptr;
+    CUDA_TRY(cudaMalloc(&B.st_stage, sizeof(SmState) * n));
+    B.st_stage_n = n;
+  }
+  std::vector<SmState*> ptrs(n);
+  for (int i = 0; i < n; ++i) ptrs[i] = wss[i]->st;
+  CUDA_TRY(cudaMemcpyAsync(B.st_ptrs, ptrs.data(), sizeof(SmState*) * n, cudaMemcpyHostToDevice, st));
+  constexpr int W = (int)(sizeof(SmState) / sizeof(int32_t));
+  const int blocks = (int)std::min<int64_t>(((int64_t)n * W + 255) / 256, 1024);
+  if (to_instances) {
+    CUDA_TRY(cudaMemcpyAsync(B.st_stage, host, sizeof(SmState) * n, cudaMemcpyHostToDevice, st));
+    k_states_many<<<blocks, 256, 0, st>>>(B.st_ptrs, B.st_stage, n, 1);
+  } else {
+    k_states_many<<<blocks, 256, 0, st>>>(B.st_ptrs, B.st_stage, n, 0);
+    CUDA_TRY(cudaMemcpyAsync(host, B.st_stage, sizeof(SmState) * n, cudaMemcpyDeviceToHost, st));
+  }
+  check_launch();
+  CUDA_TRY(cudaStreamSynchronize(st));  // host buffer and pointer table in use until here
+}
+
 // Puts every instance at its starting point: Vt = v0 (cold: 0, warm: the
-// caller's (z, eta)), d = 0, fresh SuperMann state.
+// caller's (z, eta)), d = 0, fresh SuperMann state -- a handful of launches
+// for the whole batch.
 template <typename S>
 static void batch_init(Batch& B, const std::vector<Workspace*>& wss, const std::vector<double>& alphas,
                        const spock_settings& s, int mem, const double* const* x0, double* const* z,
                        double* const* eta, int warm) {
   const int n = (int)B.probs.size();
   cudaStream_t st = B.main;
-  for (int i = 0; i < n; ++i) {
+  std::vector<const double*> src;
+  std::vector<S*> dst;
+  std::vector<int64_t> len;
+  for (int i = 0; i < n; ++i) {  // x0 and the starting points (NULL source: zeros)
     Problem& P = *B.probs[i];
     Workspace* ws = wss[i];
-    const DevFactors<S>& f = factors<S>(P);
     S* Vt = (S*)ws->v[2];
-    convert<S, double>(x0[i], f.x0, P.nx, st);
-    if (warm) {
-      convert<S, double>(z[i], Vt, P.off.n_z, st);
-      convert<S, double>(eta[i], Vt + P.off.n_z, P.off.n_eta, st);
-    } else {
-      CUDA_TRY(cudaMemsetAsync(Vt, 0, sizeof(S) * ws->n_v, st));
-    }
-    CUDA_TRY(cudaMemsetAsync(ws->d, 0, sizeof(S) * ws->n_v, st));
-    SmState h{};
+    src.push_back(x0[i]);
+    dst.push_back(factors<S>(P).x0);
+    len.push_back(P.nx);
+    src.push_back(warm ? z[i] : nullptr);
+    dst.push_back(Vt);
+    len.push_back(P.off.n_z);
+    src.push_back(warm ? eta[i] : nullptr);
+    dst.push_back(Vt + P.off.n_z);
+    len.push_back(P.off.n_eta);
+    src.push_back(nullptr);
+    dst.push_back((S*)ws->d);
+    len.push_back(ws->n_v);
+  }
+  copy_many<double, S>(B, src, dst, len, st);
+  std::vector<SmState> hs(n);
+  for (int i = 0; i < n; ++i) {
+    SmState& h = hs[i];
+    h = SmState{};
     h.alpha = alphas[i];
     h.eps_abs = s.eps_abs;
     h.eps_rel = s.eps_rel;
@@ -1080,8 +1187,8 @@ static void batch_init(Batch& B, const std::vector<Workspace*>& wss, const std::
     h.mem = mem;
     h.pending = P_INIT;
     h.n_T = 1;
-    sm_init_state(ws->st, h, st);
   }
+  batch_states(B, wss, hs.data(), true, st);
 }
 
 // Autotuner of the batch.  Candidates: the work-list kernels with node tile
@@ -1271,14 +1378,23 @@ static int batch_solve(Batch& B, const double* const* x0, const spock_settings& 
   const int64_t total_launches = cfg.cta ? 1 : B.launches_per_eval + graph_launches * B.g_launches;
   int status = SPOCK_OK;
   std::vector<SmState> fin(n);
-  for (int i = 0; i < n; ++i) {
-    Problem& P = *B.probs[i];
-    Workspace* ws = wss[i];
-    convert<double, S>((S*)ws->Tv[0], z[i], P.off.n_z, B.main);
-    convert<double, S>((S*)ws->Tv[0] + P.off.n_z, eta[i], P.off.n_eta, B.main);
-    CUDA_TRY(cudaMemcpyAsync(&fin[i], ws->st, sizeof(SmState), cudaMemcpyDeviceToHost, B.main));
+  {
+    std::vector<const S*> src;
+    std::vector<double*> dst;
+    std::vector<int64_t> len;
+    for (int i = 0; i < n; ++i) {
+      Problem& P = *B.probs[i];
+      const S* TV = (const S*)wss[i]->Tv[0];
+      src.push_back(TV);
+      dst.push_back(z[i]);
+      len.push_back(P.off.n_z);
+      src.push_back(TV + P.off.n_z);
+      dst.push_back(eta[i]);
+      len.push_back(P.off.n_eta);
+    }
+    copy_many<S, double>(B, src, dst, len, B.main);
+    batch_states(B, wss, fin.data(), false, B.main);
   }
-  CUDA_TRY(cudaStreamSynchronize(B.main));
   for (int i = 0; i < n; ++i) {
     const SmState& f = fin[i];
     const int act = f.done ? f.action : A_MAXIT;
