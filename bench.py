@@ -53,9 +53,9 @@ FP64_PEAK_TFLOPS = 1.193
 
 # DRAM bytes (read + write) per chain of one launch of the backward chain
 # kernels, from ncu captures on the 15,701-node tree (1,024 chains of 14
-# nonleaf nodes, nx = 50, nu = 20; profiles/k_bwd_chain_f64_f32_15701node_tree.md),
-# scaled by the chains of the measured tree (each chain reads its own factors
-# once).  Valid for these kernels as captured; remeasure after changing them.
+# nonleaf nodes, nx = 50, nu = 20), scaled by the chains of the measured tree
+# (each chain reads its own factors once).  Valid for these kernels as
+# captured; remeasure after changing them.
 NCU_TRAFFIC_PER_CHAIN = {"fp64": 739.954688e6 / 1024, "fp32": 372.118272e6 / 1024}
 NCU_CHAIN_SHAPE = (14, 50, 20)   # chain length, nx, nu of the capture
 

@@ -122,6 +122,10 @@ typedef struct spock_info {
   int32_t fp64_iterations; /* SPOCK_FP32 with fp64_tail: iterations run in FP64 */
   int32_t certified;       /* 1 if the returned pair's xi was computed in FP64 */
   double xi_fp32;          /* xi reported by the FP32 iteration when it stopped */
+  int32_t n_L;             /* applications of L (the x-axis of Fig. 1): two per
+                              evaluation of T -- L z and L z+, from which the
+                              dual update L(2 z+ - z) and the residual's L r_z
+                              are formed in the same pass */
 } spock_info;
 
 /* Fills *s with the defaults listed above.  Returns SPOCK_ERR_INVALID_ARG
@@ -143,6 +147,17 @@ int spock_default_settings(spock_settings* s);
  */
 int spock_tree_create(int32_t n_nodes, const int32_t* anc, const double* prob,
                       spock_tree** out);
+
+/*
+ * spock_tree_create_abs -- as spock_tree_create, with the absolute
+ * probability pi^i of every node (Sec. "Scenario trees": pi^i is the
+ * probability of reaching node i; pi[0] is the root's, normally 1).  The
+ * conditional probabilities p^i = pi^i / pi^anc(i) are formed here, so the
+ * children of every node must carry their parent's probability in total
+ * (within 1e-9 relative).  Errors as spock_tree_create; non-positive or
+ * non-finite pi is SPOCK_ERR_INVALID_ARG.  Host only; no GPU work.
+ */
+int spock_tree_create_abs(int32_t n_nodes, const int32_t* anc, const double* pi, spock_tree** out);
 
 /* Number of nodes, horizon N and number of nonleaf nodes of a tree. */
 int spock_tree_info(const spock_tree* tree, int32_t* n_nodes, int32_t* horizon,
@@ -255,15 +270,20 @@ int spock_T_dev(spock_problem* p, const double* x0_dev, double alpha, const doub
  * allocator).  It computes exactly what spock_prox_f_dev computes, but the
  * scratch vectors of the Riccati passes and the zero dual vector live in a
  * fixed, file-scope device array of 2^20 doubles (8 MiB) that every GPU which
- * loads the library holds until the process exits.  It calls no cudaMalloc
- * or cudaFree.
+ * loads the library holds until the process exits; x0_dev is read in place.
+ * It calls no cudaMalloc or cudaFree.  The array's device address is looked
+ * up by spock_problem_create (which allocates anyway), so the array is
+ * brought onto the device there, before the first call of this function.
  *   Limit: 2 (n nx' + n_nonleaf nu') + n_eta <= 2^20 with nx', nu' the
  *   dimensions rounded up to even numbers; larger problems are
  *   rejected with SPOCK_ERR_INVALID_ARG and a message giving both sizes.
- *   The first call on a device looks up the array's device address; make
- *   that first call before capturing the stream into a CUDA graph.
  *   All calls share the one array: calls that overlap on the GPU (other
  *   streams, other host threads) race and must be serialised by the caller.
+ *   No buffer owned by the problem is written (except its error flag when a
+ *   kernel reports a failure), so calls on one problem from other entry
+ *   points do not race with it through the problem's buffers.
+ *   The call synchronises `stream` before it returns (to read the kernels'
+ *   error flag), so it cannot be captured into a CUDA graph.
  * Arguments, layout and other errors as spock_prox_f_dev.
  */
 int spock_prox_f_noalloc_dev(spock_problem* p, const double* x0_dev, double alpha, const double* z,
@@ -292,6 +312,16 @@ int spock_prox_f_noalloc_dev(spock_problem* p, const double* x0_dev, double alph
  */
 int spock_grad_dev(spock_problem* p, const double* z, const double* eta, int32_t precision, double* g_x0,
                    double* g_A, double* g_B, double* g_Q, double* g_R, double* g_QN, void* stream);
+
+/*
+ * spock_grad -- spock_grad_dev with host buffers: z [n_z] and eta [n_eta]
+ * are copied to the device, the gradients (same layout as spock_grad_dev)
+ * copied back into the non-NULL host outputs.  Device buffers for the
+ * outputs are allocated on the first call and kept by the problem.
+ * Blocking; errors as spock_grad_dev.
+ */
+int spock_grad(spock_problem* p, const double* z, const double* eta, int32_t precision, double* g_x0,
+               double* g_A, double* g_B, double* g_Q, double* g_R, double* g_QN);
 
 /*
  * spock_batch_create -- a batch of independent problems (any trees, depths,
@@ -329,6 +359,16 @@ int spock_batch_create(int32_t n, spock_problem* const* problems, spock_batch** 
  */
 int spock_batch_solve_dev(spock_batch* batch, const double* const* x0_dev, const spock_settings* settings,
                           double* const* z_dev, double* const* eta_dev, int32_t warm, spock_info* infos);
+
+/*
+ * spock_batch_solve -- spock_batch_solve_dev with host buffers: x0[i] [nx_i],
+ * z_io[i] [n_z,i], eta_io[i] [n_eta,i] (host arrays of n host pointers, FP64).
+ * The inputs are copied into each problem's device staging buffers (the
+ * ones spock_solve uses; allocated on first use and kept by the problem),
+ * the solutions copied back on SPOCK_OK and SPOCK_MAX_ITER.  Blocking.
+ */
+int spock_batch_solve(spock_batch* batch, const double* const* x0, const spock_settings* settings,
+                      double* const* z_io, double* const* eta_io, int32_t warm, spock_info* infos);
 
 /* Frees a handle returned by any *_create call; NULL is a no-op. */
 void spock_free(void* handle);

@@ -1533,6 +1533,8 @@ static bool all_finite(const double* a, size_t n) {
   return true;
 }
 
+static int noalloc_scratch(int dev, double** out);
+
 static int problem_create(const Tree& tree, int32_t nx, int32_t nu, const double* A, const double* B,
                           const double* Q, const double* R, const double* QN, const double* a, const double* xmin,
                           const double* xmax, const double* umin, const double* umax, spock_problem** out) {
@@ -1704,6 +1706,15 @@ static int problem_create(const Tree& tree, int32_t nx, int32_t nu, const double
     }
     P->err = upload(*P, std::vector<int32_t>(1, 0));
     CUDA_TRY(cudaDeviceSynchronize());
+    // device address of the fixed scratch array of spock_prox_f_noalloc_dev,
+    // looked up here (where allocating is allowed) so that the lookup, and
+    // any module loading it triggers, never happens inside that entry point
+    double* scratch = nullptr;
+    const int rc = noalloc_scratch(P->device, &scratch);
+    if (rc != SPOCK_OK) {
+      delete P;
+      return rc;
+    }
   } catch (const SpockError& e) {
     delete P;
     return fail(e.code, e.what());
@@ -1756,6 +1767,31 @@ int spock_tree_create(int32_t n_nodes, const int32_t* anc, const double* prob, s
     if (!out) return fail(SPOCK_ERR_INVALID_ARG, "out is NULL");
     auto* t = new Tree();
     int rc = build_tree(n_nodes, anc, prob, *t);
+    if (rc != SPOCK_OK) {
+      delete t;
+      return rc;
+    }
+    *out = reinterpret_cast<spock_tree*>(t);
+    return SPOCK_OK;
+  });
+}
+
+int spock_tree_create_abs(int32_t n_nodes, const int32_t* anc, const double* pi, spock_tree** out) {
+  return guarded([&]() -> int {
+    if (!out || !anc || !pi) return fail(SPOCK_ERR_INVALID_ARG, "NULL argument");
+    if (n_nodes < 2) return fail(SPOCK_ERR_INVALID_ARG, "tree needs at least 2 nodes");
+    if (anc[0] != -1) return fail(SPOCK_ERR_BAD_TREE, "anc[0] must be -1 (node 0 is the root)");
+    std::vector<double> p((size_t)n_nodes, 1.0);
+    for (int32_t i = 0; i < n_nodes; ++i)
+      if (!(pi[i] > 0.0) || !std::isfinite(pi[i]))
+        return fail(SPOCK_ERR_INVALID_ARG, "absolute probabilities must be positive and finite");
+    for (int32_t i = 1; i < n_nodes; ++i) {
+      if (anc[i] < 0 || anc[i] >= n_nodes || anc[i] == i)
+        return fail(SPOCK_ERR_BAD_TREE, "anc[" + std::to_string(i) + "] out of range");
+      p[(size_t)i] = pi[i] / pi[anc[i]];   // p^i = pi^i / pi^anc(i)
+    }
+    auto* t = new Tree();
+    int rc = build_tree(n_nodes, anc, p.data(), *t);
     if (rc != SPOCK_OK) {
       delete t;
       return rc;
@@ -1849,9 +1885,12 @@ static int solve_dev_impl(Problem* P, const double* x0_dev, const spock_settings
   if (s.max_iter < 0 || s.max_backtracks < 0) return fail(SPOCK_ERR_INVALID_ARG, "negative cap");
   if (s.alpha > 0 && s.alpha * P->normL >= 1.0) return fail(SPOCK_ERR_INVALID_ARG, "alpha ||L|| must be < 1");
   CUDA_TRY(cudaSetDevice(P->device));
-  if (s.precision == SPOCK_FP64) return solve_impl<double>(*P, x0_dev, s, z_dev, eta_dev, warm, info, st);
-  if (s.precision == SPOCK_FP32) return solve_mixed(*P, x0_dev, s, z_dev, eta_dev, warm, info, st);
-  return fail(SPOCK_ERR_INVALID_ARG, "unknown precision");
+  int rc;
+  if (s.precision == SPOCK_FP64) rc = solve_impl<double>(*P, x0_dev, s, z_dev, eta_dev, warm, info, st);
+  else if (s.precision == SPOCK_FP32) rc = solve_mixed(*P, x0_dev, s, z_dev, eta_dev, warm, info, st);
+  else return fail(SPOCK_ERR_INVALID_ARG, "unknown precision");
+  if (info && rc >= 0) info->n_L = 2 * info->n_T;   // L z and L z+ in every evaluation of T
+  return rc;
 }
 
 // Root box check on a host copy of x0.
@@ -2068,6 +2107,41 @@ int spock_grad_dev(spock_problem* p, const double* z, const double* eta, int32_t
   });
 }
 
+int spock_grad(spock_problem* p, const double* z, const double* eta, int32_t precision, double* g_x0, double* g_A,
+               double* g_B, double* g_Q, double* g_R, double* g_QN) {
+  return guarded([&]() -> int {
+    Problem* P = as_problem(p);
+    if (!P || !z || !eta) return fail(SPOCK_ERR_INVALID_ARG, "NULL argument");
+    CUDA_TRY(cudaSetDevice(P->device));
+    const size_t n = (size_t)P->tree.n, nx = (size_t)P->nx, nu = (size_t)P->nu;
+    double *dx0 = nullptr, *dz = nullptr, *de = nullptr;
+    host_io_buffers(*P, &dx0, &dz, &de);
+    if (!P->io_grad) {   // gradient outputs, allocated once per problem
+      const size_t len = nx + n * nx * nx + n * nx * nu + 2 * n * nx + n * nu;
+      CUDA_TRY(cudaMalloc(&P->io_grad, sizeof(double) * len));
+      P->allocations.push_back(P->io_grad);
+    }
+    double* gx0 = P->io_grad;
+    double* gA = gx0 + nx;
+    double* gB = gA + n * nx * nx;
+    double* gQ = gB + n * nx * nu;
+    double* gR = gQ + n * nx;
+    double* gQN = gR + n * nu;
+    CUDA_TRY(cudaMemcpy(dz, z, sizeof(double) * P->off.n_z, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(de, eta, sizeof(double) * P->off.n_eta, cudaMemcpyHostToDevice));
+    const int rc = spock_grad_dev(p, dz, de, precision, g_x0 ? gx0 : nullptr, g_A ? gA : nullptr,
+                                  g_B ? gB : nullptr, g_Q ? gQ : nullptr, g_R ? gR : nullptr,
+                                  g_QN ? gQN : nullptr, nullptr);
+    if (rc != SPOCK_OK) return rc;
+    const struct { double* host; const double* dev; size_t len; } outs[] = {
+        {g_x0, gx0, nx}, {g_A, gA, n * nx * nx}, {g_B, gB, n * nx * nu},
+        {g_Q, gQ, n * nx}, {g_R, gR, n * nu}, {g_QN, gQN, n * nx}};
+    for (const auto& o : outs)
+      if (o.host) CUDA_TRY(cudaMemcpy(o.host, o.dev, sizeof(double) * o.len, cudaMemcpyDeviceToHost));
+    return SPOCK_OK;
+  });
+}
+
 int spock_batch_create(int32_t n, spock_problem* const* problems, spock_batch** out) {
   return guarded([&]() -> int {
     if (n < 1 || !problems || !out) return fail(SPOCK_ERR_INVALID_ARG, "need n >= 1 problems and an out pointer");
@@ -2119,9 +2193,54 @@ int spock_batch_solve_dev(spock_batch* batch, const double* const* x0_dev, const
       if (rc != SPOCK_OK) return rc;
     }
     CUDA_TRY(cudaSetDevice(B->probs[0]->device));
-    if (s.precision == SPOCK_FP64) return batch_solve<double>(*B, x0_dev, s, z_dev, eta_dev, warm, infos);
-    if (s.precision == SPOCK_FP32) return batch_solve<float>(*B, x0_dev, s, z_dev, eta_dev, warm, infos);
-    return fail(SPOCK_ERR_INVALID_ARG, "unknown precision");
+    int rc;
+    if (s.precision == SPOCK_FP64) rc = batch_solve<double>(*B, x0_dev, s, z_dev, eta_dev, warm, infos);
+    else if (s.precision == SPOCK_FP32) rc = batch_solve<float>(*B, x0_dev, s, z_dev, eta_dev, warm, infos);
+    else return fail(SPOCK_ERR_INVALID_ARG, "unknown precision");
+    if (infos && rc >= 0)
+      for (size_t i = 0; i < B->probs.size(); ++i) infos[i].n_L = 2 * infos[i].n_T;
+    return rc;
+  });
+}
+
+int spock_batch_solve(spock_batch* batch, const double* const* x0, const spock_settings* settings,
+                      double* const* z_io, double* const* eta_io, int32_t warm, spock_info* infos) {
+  return guarded([&]() -> int {
+    Batch* B = reinterpret_cast<Batch*>(batch);
+    if (!B || B->tag != TAG_BATCH || !x0 || !z_io || !eta_io)
+      return fail(SPOCK_ERR_INVALID_ARG, "NULL argument or not a batch handle");
+    const size_t n = B->probs.size();
+    for (size_t i = 0; i < n; ++i)
+      if (!x0[i] || !z_io[i] || !eta_io[i]) return fail(SPOCK_ERR_INVALID_ARG, "NULL instance buffer");
+    CUDA_TRY(cudaSetDevice(B->probs[0]->device));
+    // every instance is a distinct problem: its own staging buffers serve
+    std::vector<const double*> dx0(n);
+    std::vector<double*> dz(n), de(n);
+    for (size_t i = 0; i < n; ++i) {
+      Problem& P = *B->probs[i];
+      double *a = nullptr, *b = nullptr, *c = nullptr;
+      host_io_buffers(P, &a, &b, &c);
+      CUDA_TRY(cudaMemcpyAsync(a, x0[i], sizeof(double) * P.nx, cudaMemcpyHostToDevice, B->main));
+      if (warm) {
+        CUDA_TRY(cudaMemcpyAsync(b, z_io[i], sizeof(double) * P.off.n_z, cudaMemcpyHostToDevice, B->main));
+        CUDA_TRY(cudaMemcpyAsync(c, eta_io[i], sizeof(double) * P.off.n_eta, cudaMemcpyHostToDevice, B->main));
+      }
+      dx0[i] = a;
+      dz[i] = b;
+      de[i] = c;
+    }
+    CUDA_TRY(cudaStreamSynchronize(B->main));
+    const int rc = spock_batch_solve_dev(batch, dx0.data(), settings, dz.data(), de.data(), warm, infos);
+    if (rc == SPOCK_OK || rc == SPOCK_MAX_ITER) {
+      for (size_t i = 0; i < n; ++i) {
+        const Problem& P = *B->probs[i];
+        CUDA_TRY(cudaMemcpyAsync(z_io[i], dz[i], sizeof(double) * P.off.n_z, cudaMemcpyDeviceToHost, B->main));
+        CUDA_TRY(cudaMemcpyAsync(eta_io[i], de[i], sizeof(double) * P.off.n_eta, cudaMemcpyDeviceToHost,
+                                 B->main));
+      }
+      CUDA_TRY(cudaStreamSynchronize(B->main));
+    }
+    return rc;
   });
 }
 
@@ -2159,7 +2278,8 @@ static double* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
 
 // Device address of g_noalloc_scratch on `dev` (the current device).  Host
 // code must not use the symbol itself: on the host it names a stand-in, not
-// device memory.  Looked up once per device, on the first call there.
+// device memory.  Looked up once per device, by the first spock_problem_create
+// on that device.
 static int noalloc_scratch(int dev, double** out) {
   if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(SPOCK_ERR_INVALID_ARG, "device ordinal out of range");
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
@@ -2190,10 +2310,11 @@ extern "C" int spock_prox_f_noalloc_dev(spock_problem* p, const double* x0_dev, 
                                              std::to_string(kNoAllocScratchDoubles));
     CUDA_TRY(cudaSetDevice(P->device));
     double* scratch = nullptr;
-    int rc = noalloc_scratch(P->device, &scratch);
+    int rc = noalloc_scratch(P->device, &scratch);   // cached at problem creation
     if (rc != SPOCK_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     KP<double> kp = op_kp(P, alpha);
+    kp.x0 = x0_dev;   // read in place: no buffer owned by the problem is written
     kp.xbar = scratch;
     kp.q = scratch + nxb;
     kp.ubar = scratch + 2 * nxb;
@@ -2201,7 +2322,6 @@ extern "C" int spock_prox_f_noalloc_dev(spock_problem* p, const double* x0_dev, 
     double* zero_eta = scratch + 2 * nxb + 2 * nub;
     // the array keeps the previous call's contents: the dual input must be zero
     CUDA_TRY(cudaMemsetAsync(zero_eta, 0, sizeof(double) * (size_t)P->off.n_eta, st));
-    CUDA_TRY(cudaMemcpyAsync(P->f64.x0, x0_dev, sizeof(double) * P->nx, cudaMemcpyDeviceToDevice, st));
     launch_prep<double>(kp, z, zero_eta, z_out, sm_count() * 16, st);
     launch_riccati<double>(kp, P->tree.stage_begin, P->tree.stage_maxch, z_out, st, nullptr);
     check_launch();

@@ -104,6 +104,7 @@ struct Problem {
   double* io_x0 = nullptr;
   double* io_z = nullptr;
   double* io_eta = nullptr;
+  double* io_grad = nullptr;   // outputs of spock_grad (host-buffer variant)
   // solver workspace, allocated on first use per precision
   struct Workspace* ws64 = nullptr;
   struct Workspace* ws32 = nullptr;

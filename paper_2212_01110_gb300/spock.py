@@ -50,7 +50,7 @@ class Info(C.Structure):
                 ("n_backtracks", C.c_int32), ("xi", C.c_double), ("xi0", C.c_double),
                 ("alpha", C.c_double), ("solve_ms", C.c_double), ("n_launches", C.c_int32),
                 ("n_timed", C.c_int32), ("t_group_ms", C.c_double * 7), ("fp64_iterations", C.c_int32),
-                ("certified", C.c_int32), ("xi_fp32", C.c_double)]
+                ("certified", C.c_int32), ("xi_fp32", C.c_double), ("n_L", C.c_int32)]
 
     GROUPS = ("prep", "bwd_chain", "bwd_stages", "fwd_stages", "fwd_chain", "dual", "stats")
 
@@ -68,6 +68,7 @@ _I64 = C.POINTER(C.c_int64)
 _sig = {
     "spock_default_settings": ([C.POINTER(Settings)], C.c_int),
     "spock_tree_create": ([C.c_int32, _I32, _D, C.POINTER(_P)], C.c_int),
+    "spock_tree_create_abs": ([C.c_int32, _I32, _D, C.POINTER(_P)], C.c_int),
     "spock_tree_info": ([_P, _I32, _I32, _I32], C.c_int),
     "spock_problem_create": ([_P, C.c_int32, C.c_int32] + [_D] * 10 + [C.c_int32, C.POINTER(_P)], C.c_int),
     "spock_problem_info": ([_P, _I64, _I64, _D, _D], C.c_int),
@@ -82,9 +83,12 @@ _sig = {
     "spock_prox_gconj_dev": ([_P, C.c_double, _P, _P, _P], C.c_int),
     "spock_T_dev": ([_P, _P, C.c_double, _P, _P, _P, _P, _P], C.c_int),
     "spock_grad_dev": ([_P, _P, _P, C.c_int32, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "spock_grad": ([_P, _D, _D, C.c_int32, _D, _D, _D, _D, _D, _D], C.c_int),
     "spock_batch_create": ([C.c_int32, C.POINTER(_P), C.POINTER(_P)], C.c_int),
     "spock_batch_solve_dev": ([_P, C.POINTER(_P), C.POINTER(Settings), C.POINTER(_P), C.POINTER(_P), C.c_int32,
                                C.POINTER(Info)], C.c_int),
+    "spock_batch_solve": ([_P, C.POINTER(_D), C.POINTER(Settings), C.POINTER(_D), C.POINTER(_D), C.c_int32,
+                           C.POINTER(Info)], C.c_int),
     "spock_free": ([_P], None),
     "spock_last_error": ([], C.c_char_p),
 }
@@ -142,6 +146,15 @@ def spock_tree_create(anc, prob):
     prob, pp = _dptr(prob)
     h = _P()
     _check(_lib.spock_tree_create(len(anc), anc.ctypes.data_as(_I32), pp, C.byref(h)))
+    return h
+
+
+def spock_tree_create_abs(anc, pi):
+    """Tree from absolute node probabilities pi^i."""
+    anc = np.ascontiguousarray(anc, dtype=np.int32)
+    pi, pp = _dptr(pi)
+    h = _P()
+    _check(_lib.spock_tree_create_abs(len(anc), anc.ctypes.data_as(_I32), pp, C.byref(h)))
     return h
 
 
@@ -237,6 +250,20 @@ def spock_grad_dev(problem, z, eta, precision, g_x0=None, g_A=None, g_B=None, g_
                                _stream(stream)))
 
 
+def spock_grad(problem, z, eta, precision, g_x0=None, g_A=None, g_B=None, g_Q=None, g_R=None, g_QN=None):
+    """Host-buffer gradient: z, eta and the outputs are float64 numpy arrays
+    (outputs written in place, any may be None)."""
+    def hp(a):
+        if a is None:
+            return None
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+        return a.ctypes.data_as(_D)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    eta = np.ascontiguousarray(eta, dtype=np.float64)
+    _check(_lib.spock_grad(problem, hp(z), hp(eta), int(precision), hp(g_x0), hp(g_A), hp(g_B), hp(g_Q), hp(g_R),
+                           hp(g_QN)))
+
+
 def spock_batch_create(problems):
     """problems: list of problem handles (c_void_p)."""
     arr = (_P * len(problems))(*[p.value if isinstance(p, _P) else p for p in problems])
@@ -254,6 +281,21 @@ def spock_batch_solve_dev(batch, x0s, settings, zs, etas, warm):
     infos = (Info * n)()
     rc = _lib.spock_batch_solve_dev(batch, ptrs(x0s), C.byref(settings) if settings is not None else None,
                                     ptrs(zs), ptrs(etas), int(warm), infos)
+    _check(rc, (SPOCK_OK, SPOCK_MAX_ITER))
+    return list(infos)
+
+
+def spock_batch_solve(batch, x0s, settings, zs, etas, warm):
+    """Host buffers: x0s, zs, etas are lists of float64 numpy arrays (zs and
+    etas modified in place).  Returns the list of per-instance Info."""
+    n = len(x0s)
+    x0s = [np.ascontiguousarray(a, dtype=np.float64) for a in x0s]
+    for a in list(zs) + list(etas):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    ptrs = lambda arrs: (_D * n)(*[a.ctypes.data_as(_D) for a in arrs])
+    infos = (Info * n)()
+    rc = _lib.spock_batch_solve(batch, ptrs(x0s), C.byref(settings) if settings is not None else None,
+                                ptrs(zs), ptrs(etas), int(warm), infos)
     _check(rc, (SPOCK_OK, SPOCK_MAX_ITER))
     return list(infos)
 

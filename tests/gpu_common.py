@@ -52,4 +52,12 @@ def cases():
         # (2m + 1 entries) and the children of a node span several warp chunks
         "root_40": W.with_tree(W.tree_from_branching([40, 1])[0], seed=9, nx=3, nu=2),
         "root_17_2": W.with_tree(W.tree_from_branching([17, 2])[0], seed=10, nx=4, nu=2, a=0.3),
+        # the paper's system on a 127-node tree: above the single-block size,
+        # so solves run the graph-driven kernels
+        "datacenter_N6": W.datacenter(N=6, nx=3),
+        # the large tree's launch shapes: 1,024 chains of 3 nonleaf nodes below
+        # 5 stages with 4 children (4,437 nodes), nx = 50, nu = 20 -- many blocks
+        # per SM for the direct kernels, several chains per block in the
+        # persistent loops of the staged kernels
+        "chains_1024_50_20": W.large_tree(3, branching_stages=5, branch=4, N=8, nx=50, nu=20),
     }

@@ -46,6 +46,20 @@ def test_host_only_calls(lib):
     assert (n.value, N.value, nl.value) == (15, 3, 7)
     spock.spock_free(t)
     spock.spock_free(None)
+    # absolute probabilities: pi^c must add up to the parent's pi
+    pi = np.ones(15)
+    for i in range(1, 15):
+        pi[i] = pi[d["anc"][i]] * d["prob"][i]
+    t = spock.spock_tree_create_abs(d["anc"], pi)
+    assert lib.spock_tree_info(t, C.byref(n), C.byref(N), C.byref(nl)) == 0
+    assert (n.value, N.value, nl.value) == (15, 3, 7)
+    spock.spock_free(t)
+    pi[3] *= 2.0
+    with pytest.raises(spock.SpockError):
+        spock.spock_tree_create_abs(d["anc"], pi)
+    pi[3] = -1.0
+    with pytest.raises(spock.SpockError):
+        spock.spock_tree_create_abs(d["anc"], pi)
 
 
 @pytest.mark.parametrize("anc,code", [([-1], -1), ([0, 0], -2), ([-1, 0, 0, 1], -2), ([-1, 2, 1], -2),

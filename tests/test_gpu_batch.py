@@ -62,10 +62,11 @@ def test_batch_converges():
         assert inf.status == spock.SPOCK_OK and inf.xi <= max(1e-6, 1e-6 * inf.xi0) * (1 + 1e-9)
         z1, e1 = torch.zeros_like(z), torch.zeros_like(e)
         spock.spock_solve_dev(P.handle, x0, s, z1, e1, 0)
-        # two independent 1e-6-accurate solutions (their SuperMann decisions may
-        # part after many iterations: the statistics are summed in a different
-        # block order): costs agree to the tolerance scale, as against the oracle
-        assert abs(float(z[0]) - float(z1[0])) < 1e-4 * max(1, abs(float(z1[0])))
+        # two independent pairs certified at xi <= 1e-6 (their SuperMann
+        # decisions may part after many iterations: the statistics are summed in
+        # a different block order): costs agree within 10 x the solve tolerance,
+        # as against the oracle
+        assert abs(float(z[0]) - float(z1[0])) < 1e-5 * max(1, abs(float(z1[0])))
     # a second solve reuses the captured graph; warm-started from the solution
     # it converges in fewer iterations (the relative tolerance is re-based on
     # the warm point's xi_0, so it still iterates)

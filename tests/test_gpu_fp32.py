@@ -1,0 +1,82 @@
+"""The FP32 operator path against the FP64 oracle.
+
+spock_cp_step_dev with precision SPOCK_FP32 runs the kernels of the
+graph-driven solves (the staged and direct Riccati families in single
+precision, the FP32 vector kernels) on every tree size, so k = 1 compares
+the FP32 evaluation of T (Eq. (chambolle-pock-operator)) element by element
+with the oracle's, and k = 25 compares 25 vanilla CP iterations.
+
+Tolerance (relative to max(1, |reference|_inf)): one FP32 evaluation of T
+rounds its inputs and factors to single precision (unit roundoff
+u = 2^-24 = 6e-8) and accumulates dot products of at most nx + nu = 128
+terms along Riccati recursions of a few stages; with errors adding in
+quadrature over those terms, 2e-5 = 330 u bounds one evaluation.  T is
+nonexpansive in the M-metric, so k iterations add at most k such errors
+(in M-norm); with random signs they add in quadrature, sqrt(25) x 2e-5 =
+1e-4 for k = 25.  Solves in FP32 (FP64 residual, Anderson and certification
+tail) are compared with the FP64 oracle's converged solution through the
+graph driver."""
+import numpy as np
+import pytest
+
+from oracle.cp import vanilla_cp
+from oracle.spock import Settings as OSettings, spock as ospock
+from tests.gpu_common import Pair, cases, rel_err
+
+pytestmark = pytest.mark.gpu
+CASES = cases()
+TOL_FP32_T = 2e-5
+
+
+@pytest.fixture(scope="module", params=["chains", "wide_50_20", "root_40", "datacenter_N6", "chains_1024_50_20"])
+def pair(request):
+    return Pair(CASES[request.param])
+
+
+@pytest.mark.parametrize("k", [1, 25])
+def test_cp_step_fp32_matches_oracle(pair, k):
+    from paper_2212_01110_gb300 import spock
+    rng = np.random.default_rng(40 + k)
+    z0 = rng.standard_normal(pair.gp.n_z)
+    e0 = rng.standard_normal(pair.gp.n_eta)
+    z, e = pair.t(z0), pair.t(e0)
+    xi = spock.spock_cp_step_dev(pair.gp.handle, pair.x0, k, pair.alpha, spock.SPOCK_FP32, z, e)
+    ref, xi_ref = vanilla_cp(pair.cp, np.concatenate([z0, e0]), pair.d["x0"], k)
+    got = np.concatenate([z.cpu().numpy(), e.cpu().numpy()])
+    err = rel_err(got, ref)
+    tol = TOL_FP32_T * np.sqrt(k)
+    print(f"FP32 CP k={k}: max rel. error {err:.2e} (tolerance {tol:.1e}), xi {xi:.4e} vs {xi_ref:.4e}")
+    assert err < tol
+    # xi = max(|r_z/alpha - L* r_eta|, |r_eta/alpha - L r_z|): the FP32 error
+    # of the pair enters divided by alpha
+    # (and through L, whose rows have at most a few entries of size <= ||L||)
+    assert abs(xi - xi_ref) <= 2 * tol * max(1.0, np.max(np.abs(ref))) * (1 / pair.alpha + 4 * pair.cp.normL)
+
+
+@pytest.mark.parametrize("name,driver", [("binary_N3", "graph"), ("chains", "graph"), ("datacenter_N6", "auto")])
+def test_fp32_solve_graph_driver_against_oracle(name, driver, monkeypatch):
+    """FP32 iteration (FP64 residual, Anderson m = 5, FP64 certification and
+    tail) through the graph-driven rounds; the certified pair is compared
+    with the oracle's FP64 solution to 1e-10.  Bounds: the cost of a pair
+    certified at xi <= 1e-6 differs from the optimum by O(1e-6) relative,
+    and the trajectory by the solution's sensitivity to that residual
+    (measured below 2e-4 on these trees; asserted at 1e-3)."""
+    from paper_2212_01110_gb300 import spock
+    if driver != "auto":
+        monkeypatch.setenv("SPOCK_DRIVER", driver)
+    pair = Pair(CASES[name])
+    s = spock.spock_default_settings(alpha=pair.alpha, precision=spock.SPOCK_FP32, memory=5, max_iter=50000)
+    z = np.zeros(pair.gp.n_z)
+    e = np.zeros(pair.gp.n_eta)
+    info = spock.spock_solve(pair.gp.handle, pair.d["x0"], s, z, e, 0)
+    assert info.status == spock.SPOCK_OK and info.certified == 1
+    assert info.n_launches > 1   # not the single-block solve
+    assert info.xi <= max(1e-6, 1e-6 * info.xi0) * (1 + 1e-9)
+    ref = ospock(pair.cp, pair.d["x0"], s=OSettings(eps_abs=1e-10, eps_rel=1e-10, memory=5, max_iter=50000))
+    assert ref.status == "converged"
+    cost_err = abs(z[0] - ref.v[0]) / max(1, abs(ref.v[0]))
+    x_idx = slice(1, 1 + pair.op.tree.n * pair.op.nx)
+    traj_err = np.max(np.abs(z[x_idx] - ref.v[x_idx]))
+    print(f"{name}/{driver}: FP32 solve cost rel. error {cost_err:.2e}, trajectory {traj_err:.2e}, "
+          f"{info.iterations} iterations ({info.fp64_iterations} in FP64)")
+    assert cost_err < 1e-5 and traj_err < 1e-3

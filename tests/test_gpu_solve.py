@@ -77,10 +77,17 @@ def test_spock_converged(name):
     assert info.xi <= max(1e-6, 1e-6 * info.xi0) * 1.0000001
     ref = ospock(pair.cp, pair.d["x0"], s=OSettings())
     assert ref.status == "converged"
-    # both are 1e-6-accurate solutions: the optimal cost and the trajectory agree to the tolerance scale
-    assert abs(z[0] - ref.v[0]) < 1e-4 * max(1, abs(ref.v[0]))
+    # both pairs are certified at xi <= eps = 1e-6: their optimal costs lie
+    # within O(eps) of the optimum (measured on the oracle: 2.4e-6 absolute
+    # between eps = 1e-6 and 1e-10 on these trees), asserted at 10 eps
+    # relative; trajectories at 1e-3 (deep nodes of small probability weigh
+    # little in the cost, so their states are determined less sharply)
+    cost_err = abs(z[0] - ref.v[0]) / max(1, abs(ref.v[0]))
     x_idx = slice(1, 1 + pair.op.tree.n * pair.op.nx)
-    assert np.max(np.abs(z[x_idx] - ref.v[x_idx])) < 1e-3
+    traj_err = np.max(np.abs(z[x_idx] - ref.v[x_idx]))
+    print(f"{name}: cost rel. error {cost_err:.2e}, trajectory {traj_err:.2e}")
+    assert cost_err < 1e-5
+    assert traj_err < 1e-3
 
 
 def test_warm_start_converges_immediately():
@@ -115,7 +122,7 @@ def test_fp32_mode_certified_against_fp64_oracle(name):
     traj_err = np.max(np.abs(z[x_idx] - ref.v[x_idx]))
     print(f"{name}: FP32+FP64-tail cost rel. error {cost_err:.2e}, trajectory max error {traj_err:.2e}, "
           f"FP64 iterations {info.fp64_iterations} of {info.iterations}, FP32 xi at hand-over {info.xi_fp32:.2e}")
-    assert cost_err < 1e-4 and traj_err < 1e-3
+    assert cost_err < 1e-5 and traj_err < 1e-3   # 10 x the solve tolerance; trajectory as above
 
 
 def test_fp32_mode_without_tail():
@@ -199,7 +206,7 @@ def test_single_block_solve_converges_to_oracle(name, monkeypatch):
     assert info.status == spock.SPOCK_OK and info.n_launches == 1
     ref = ospock(pair.cp, pair.d["x0"], s=OSettings(memory=5))
     assert ref.status == "converged"
-    assert abs(z[0] - ref.v[0]) < 1e-4 * max(1, abs(ref.v[0]))
+    assert abs(z[0] - ref.v[0]) < 1e-5 * max(1, abs(ref.v[0]))   # 10 x the solve tolerance
 
 
 @pytest.mark.parametrize("drv", ["graph", "host"])

@@ -38,6 +38,37 @@ def test_noalloc_matches_prox_f_on_consecutive_calls():
         P.close()
 
 
+def test_noalloc_allocates_nothing():
+    """On a fresh problem, after one warm-up call (which loads the kernels'
+    code), further calls leave the device's free memory unchanged; only then
+    is the result compared with spock_prox_f_dev."""
+    import torch
+    from paper_2212_01110_gb300 import build
+    build.build()
+    from paper_2212_01110_gb300 import spock, workloads
+    dev = torch.device("cuda:0")
+    d = workloads.large_tree(2, branching_stages=2, branch=3, N=5, nx=50, nu=20)
+    P = spock.Problem(d)
+    x0 = torch.tensor(d["x0"], dtype=torch.float64, device=dev)
+    alpha = 0.99 / P.norm_L
+    z = torch.tensor(np.random.default_rng(12).standard_normal(P.n_z), dtype=torch.float64, device=dev)
+    out = torch.empty_like(z)
+    ref = torch.empty_like(z)
+    torch.cuda.synchronize()
+    spock.spock_prox_f_noalloc_dev(P.handle, x0, alpha, z, out)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(5):
+        spock.spock_prox_f_noalloc_dev(P.handle, x0, alpha, z, out)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0, (free0, free1)
+    spock.spock_prox_f_dev(P.handle, x0, alpha, z, ref)
+    torch.cuda.synchronize()
+    assert _rel(out.cpu().numpy(), ref.cpu().numpy()) < RTOL
+    P.close()
+
+
 def test_noalloc_rejects_problems_beyond_the_fixed_scratch():
     import torch
     from paper_2212_01110_gb300 import build
