@@ -36,7 +36,6 @@ sys.path.insert(0, HERE)
 
 METRIC = "time-to-1e-6 residual and CP iters/s (FP64 vs FP32/batched); % HBM peak"
 WORKLOAD = dict(branching_stages=6, branch=4, N=20, nx=50, nu=20)
-SAMPLE = dict(branching_stages=2, branch=4, N=20, nx=50, nu=20)   # oracle sample (309 nodes)
 
 
 def measured_peaks():
@@ -271,13 +270,14 @@ def run_ours(args, rank, world, local_rank):
                   "call, K iterations from a cold start"}
 
     paper = paper_workload(args, spock, workloads, dev) if (rank == 0 and args.paper_workload) else None
+    mpc_res = closed_loop_workload(args, spock, workloads, dev) if (rank == 0 and args.mpc_realisations > 0) else None
     small = small_workload(args, spock, workloads, dev) if rank == 0 else None
     batch = batch_workload(args, spock, workloads, dev, seed=rank) if args.batch > 0 else None
     grad = grad_workload(args, spock, workloads, dev) if (rank == 0 and args.grad_instances > 0) else None
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(n, seconds=args.cpu_seconds)
+        cpu = cpu_baseline(d, seconds=args.cpu_seconds)
 
     if rank == 0:
         h = out[head]
@@ -315,6 +315,8 @@ def run_ours(args, rank, world, local_rank):
             line["paper_workload"] = paper
         if small:
             line["small_tree"] = small
+        if mpc_res:
+            line["closed_loop_mpc"] = mpc_res
         if batch:
             line["batch"] = batch
         if grad:
@@ -374,7 +376,7 @@ def paper_workload(args, spock, workloads, dev):
     hardware not stated -- context only), and horizon 12 at 1e-6 in FP64 and
     in FP32 with FP64 certification/tail.  Cold starts, Anderson memory m."""
     import torch
-    out = {}
+    out = {"fig1": fig1_comparison(args, spock, workloads, dev), "table1": table1_iterations(args, spock, workloads, dev)}
     for N, tol, key in ((15, 1e-3, "fig2_N15_tol1e-3"), (12, 1e-6, "N12_tol1e-6")):
         d = workloads.datacenter(N=N, nx=50)
         P = spock.Problem(d)
@@ -400,6 +402,92 @@ def paper_workload(args, spock, workloads, dev):
         del P, z, e
         torch.cuda.empty_cache()
     return out
+
+
+def fig1_comparison(args, spock, workloads, dev):
+    """Fig. 1 of the paper: the data-center system with N = 7, nx = nu = 5,
+    x0 = 0.1, tolerances 1e-5: applications of L until termination for
+    vanilla CP and for SPOCK (Anderson m = 3).  Vanilla CP runs as
+    spock_cp_step_dev calls of 10 iterations, its residual read after each
+    call (so its count is exact to 10 iterations)."""
+    import torch
+    d = workloads.datacenter(N=7, nx=5)
+    P = spock.Problem(d)
+    x0 = torch.tensor(d["x0"], dtype=torch.float64, device=dev)
+    z = torch.zeros(P.n_z, dtype=torch.float64, device=dev)
+    e = torch.zeros(P.n_eta, dtype=torch.float64, device=dev)
+    tol = 1e-5
+    st = spock.spock_default_settings(eps_abs=tol, eps_rel=tol, memory=3)
+    inf = spock.spock_solve_dev(P.handle, x0, st, z, e, 0)
+    out = {"nodes": len(d["anc"]), "tol": tol,
+           "spock": {"iterations": inf.iterations, "n_T": inf.n_T, "n_L": inf.n_L,
+                     "status": "converged" if inf.status == 0 else "max_iter",
+                     "K0_K1_K2": [inf.n_K0, inf.n_K1, inf.n_K2]}}
+    z.zero_()
+    e.zero_()
+    xi0 = spock.spock_cp_step_dev(P.handle, x0, 1, 0.0, spock.SPOCK_FP64, z, e)
+    target = max(tol, tol * xi0)
+    k, xi = 1, xi0
+    while xi > target and k < 200000:
+        xi = spock.spock_cp_step_dev(P.handle, x0, 10, 0.0, spock.SPOCK_FP64, z, e)
+        k += 10
+    out["vanilla_cp"] = {"iterations": k, "n_L": 2 * k, "xi": xi,
+                         "status": "converged" if xi <= target else "max_iter"}
+    out["ratio_L_calls"] = round(out["vanilla_cp"]["n_L"] / max(inf.n_L, 1), 2)
+    out["paper"] = {"spock_L_calls": 571, "cp_L_calls": 3159, "ratio": round(3159 / 571, 2),
+                    "note": "the paper does not say how it counts calls of L; here two per evaluation of T (L z "
+                            "and L z+), for both methods"}
+    P.close()
+    return out
+
+
+def table1_iterations(args, spock, workloads, dev):
+    """Table 1 of the paper: SPOCK iterations to tolerance 1e-3 on the
+    data-center system with nx = nu = 50, x0 = 0.1, horizons 3..15 (FP64,
+    Anderson m = 3, cold starts)."""
+    import torch
+    rows = {}
+    for N in (3, 6, 9, 12, 15):
+        d = workloads.datacenter(N=N, nx=50)
+        P = spock.Problem(d)
+        x0 = torch.tensor(d["x0"], dtype=torch.float64, device=dev)
+        z = torch.zeros(P.n_z, dtype=torch.float64, device=dev)
+        e = torch.zeros(P.n_eta, dtype=torch.float64, device=dev)
+        st = spock.spock_default_settings(eps_abs=1e-3, eps_rel=1e-3, memory=3, max_iter=args.paper_max_iter)
+        inf = spock.spock_solve_dev(P.handle, x0, st, z, e, 0)
+        rows[str(N)] = {"nodes": len(d["anc"]), "iterations": inf.iterations, "n_T": inf.n_T,
+                        "seconds": round(inf.solve_ms * 1e-3, 4),
+                        "status": "converged" if inf.status == 0 else "max_iter"}
+        P.close()
+        del P, z, e
+        torch.cuda.empty_cache()
+    return {"rows": rows, "paper_iterations": {"3": 105, "6": 128, "9": 110, "12": 109, "15": 105}}
+
+
+def closed_loop_workload(args, spock, workloads, dev):
+    """The paper's closed-loop simulation: data-center system, N = 10,
+    nx = nu = 20 (2,047 nodes), tolerance 1e-3, 20 MPC steps from
+    x0 = 0.1, each solve warm-started from the previous step's primal and
+    dual vectors; args.mpc_realisations random disturbance sequences (the
+    paper uses 15).  Per step: mean device time and iterations over the
+    realisations, warm and cold."""
+    from paper_2212_01110_gb300 import mpc
+    d = workloads.datacenter(N=10, nx=20)
+    res = {}
+    for mode in ("warm", "cold"):
+        runs = [mpc.closed_loop(spock, d, steps=20, seed=s, tol=1e-3, warm=(mode == "warm"), device=dev)
+                for s in range(args.mpc_realisations)]
+        ms = np.array([[r["ms"] for r in run] for run in runs])
+        it = np.array([[r["iterations"] for r in run] for run in runs])
+        res[mode] = {"mean_ms_per_step": [round(float(v), 3) for v in ms.mean(axis=0)],
+                     "mean_iterations_per_step": [round(float(v), 1) for v in it.mean(axis=0)],
+                     "converged": int(sum(r["status"] == 0 for run in runs for r in run)),
+                     "solves": int(ms.size)}
+    w, c = res["warm"], res["cold"]
+    res.update({"nodes": len(d["anc"]), "realisations": args.mpc_realisations, "steps": 20, "tol": 1e-3,
+                "mean_ms_steps_2_20": {"warm": round(float(np.mean(w["mean_ms_per_step"][1:])), 3),
+                                       "cold": round(float(np.mean(c["mean_ms_per_step"][1:])), 3)}})
+    return res
 
 
 def batch_workload(args, spock, workloads, dev, seed=0):
@@ -534,49 +622,99 @@ def grad_workload(args, spock, workloads, dev):
     return out
 
 
-def cpu_baseline(n_full, seconds=15.0):
-    """The oracle (FP64 numpy/scipy, dense-structure KKT solve for S1) timed on
-    a bounded sample: T evaluations on a 309-node tree of the same family,
-    scaled to the full tree by the node count."""
-    from oracle.cp import CP
-    from oracle.problem import Problem as OP
-    from paper_2212_01110_gb300 import workloads
-    d = workloads.large_tree(seed=0, **SAMPLE)
-    cp = CP(OP(d))
-    v = np.zeros(cp.n_z + cp.n_eta)
-    cp.T(v, d["x0"])
-    k, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < seconds:
-        v = cp.T(v, d["x0"])
-        k += 1
-    dt = time.perf_counter() - t0
-    n_s = len(d["anc"])
-    rate = k / dt * n_s / n_full
-    return {"value": rate, "unit": "CP iters/s", "cores": 1, "kind": "oracle",
-            "sample": f"{k} oracle T evaluations in {dt:.1f} s on a {n_s}-node tree of the same family "
-                      f"(branching 4 for 2 stages, N=20, nx=50, nu=20), scaled by nodes {n_s}/{n_full}; "
-                      "scipy sparse LU solve + sparse matvecs, single-threaded"}
+def host_cpu():
+    """Cores this process may use and the CPU model of the host."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+        for key in ("model name", "Model name", "CPU part"):
+            hits = [ln.split(":", 1)[1].strip() for ln in info if ln.startswith(key)]
+            if hits:
+                model = hits[0] if key != "CPU part" else f"Arm CPU part {hits[0]}"
+                break
+    except Exception:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return cores, model or "unknown"
+
+
+def cpu_baseline(d, seconds=10.0, threads=None):
+    """The oracle's C++ CP operator (riccati_cpu: plain FP64, Algorithms 1-2
+    as printed, OpenMP over the nodes of a stage) timed on the same
+    62,805-node tree: evaluations of T from v = 0 for about ``seconds`` at
+    one thread and at all host cores (Algorithm 1 excluded, as for the GPU)."""
+    from oracle.riccati_cpu import RiccatiCPU
+    cores, model = host_cpu()
+    threads = threads or cores
+    t0 = time.perf_counter()
+    rc = RiccatiCPU(d, threads=threads)
+    setup_s = time.perf_counter() - t0
+    alpha = 0.3   # any step: the cost of T does not depend on it
+    z, e = np.zeros(rc.n_z), np.zeros(rc.n_eta)
+    out = (np.empty(rc.n_z), np.empty(rc.n_eta))
+    rates = {}
+    for th in sorted({1, threads}):
+        rc.set_threads(th)
+        rc.T(z, e, alpha, out=out)
+        k, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < seconds / 2 or k < 2:
+            rc.T(z, e, alpha, out=out)
+            k += 1
+        rates[th] = (k, time.perf_counter() - t0)
+    rc.close()
+    k, dt = rates[threads]
+    k1, dt1 = rates[1]
+    return {"value": k / dt, "unit": "CP iters/s", "cores": threads, "kind": "oracle",
+            "cpu_model": model, "nproc": cores,
+            "one_thread": {"value": k1 / dt1, "evaluations": k1, "seconds": round(dt1, 2)},
+            "sample": f"{k} evaluations of T in {dt:.1f} s on the full {len(d['anc']):,}-node tree (the "
+                      f"timed workload itself), riccati_cpu (C++ FP64, Algorithms 1-2 as printed, OpenMP "
+                      f"over the nodes of a stage) on {threads} threads; Algorithm 1 ({setup_s:.1f} s) "
+                      "not timed"}
 
 
 def run_reference(args, rank, world):
+    """The oracle's C++ CP operator on the host cores, one evaluation of T of
+    the full tree per step."""
     if rank != 0:
         return
+    from oracle.riccati_cpu import RiccatiCPU
     from paper_2212_01110_gb300 import workloads
     d = workloads.large_tree(seed=0, **WORKLOAD)
-    n_full = len(d["anc"])
-    del d
-    samples = []
-    cpu_baseline(n_full, seconds=min(args.cpu_seconds, 3.0))
-    samples.append(cpu_baseline(n_full, seconds=args.cpu_seconds))
-    v = statistics.mean(s["value"] for s in samples)
+    cores, model = host_cpu()
+    rc = RiccatiCPU(d, threads=cores)
+    z, e = np.zeros(rc.n_z), np.zeros(rc.n_eta)
+    out = (np.empty(rc.n_z), np.empty(rc.n_eta))
+    for _ in range(args.warmup):
+        rc.T(z, e, 0.3, out=out)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rc.T(z, e, 0.3, out=out)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "CP iters/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
-            "config": {"workload": "large scenario tree: branching 4 for 6 stages then 1, N=20 (62,805 nodes), nx=50, nu=20",
-                       "step": "oracle T evaluations on a bounded sample, scaled to the full tree"},
-            "cpu_baseline": {"value": v, "unit": "CP iters/s", "cores": 1, "kind": "oracle",
-                             "sample": samples[0]["sample"]},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)",
+            "config": {"workload": "large scenario tree: branching 4 for 6 stages then 1, N=20 (62,805 nodes), "
+                                   "nx=50, nu=20",
+                       "step": "one evaluation of the CP operator T on the host cores"},
+            "cpu_baseline": {"value": v, "unit": "CP iters/s", "cores": cores, "kind": "oracle", "cpu_model": model,
+                             "sample": f"{args.steps} evaluations of T on the full tree, riccati_cpu (C++ FP64, "
+                                       f"Algorithms 1-2 as printed, OpenMP over the nodes of a stage), {cores} threads"},
             "e2e": {"value": v, "unit": "CP iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    rc.close()
     print(json.dumps(line), flush=True)
 
 
@@ -595,6 +733,8 @@ def main():
     ap.add_argument("--paper-workload", type=int, default=1,
                     help="also time SPOCK to tolerance on the paper's data-center system (1) or not (0)")
     ap.add_argument("--paper-max-iter", type=int, default=20000)
+    ap.add_argument("--mpc-realisations", type=int, default=5,
+                    help="disturbance sequences of the closed-loop MPC measurement (0 skips it; the paper uses 15)")
     ap.add_argument("--batch", type=int, default=512, help="instances of the batched measurement (0 skips it)")
     ap.add_argument("--batch-iter", type=int, default=50)
     ap.add_argument("--batch-only", action="store_true",

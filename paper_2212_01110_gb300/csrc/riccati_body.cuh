@@ -56,7 +56,9 @@ __device__ __forceinline__ void node_bwd(const KP<S>& p, int k, const S (&h)[SL]
   const S* __restrict__ Ri = Km + 2 * (int64_t)nu * nx;
   for (int a = lane; a < nu; a += 32) {
     S acc = 0;
-    for (int b = 0; b < nu; ++b) acc += __ldg(Ri + a * nu + b) * v.g[b];
+    // Rtilde^-1 is stored exactly symmetric: lane a reads column a (row a),
+    // consecutive lanes consecutive addresses
+    for (int b = 0; b < nu; ++b) acc += __ldg(Ri + b * nu + a) * v.g[b];
     v.d[a] = acc;
     p.d[(int64_t)k * p.us + a] = acc;
   }

@@ -9,13 +9,13 @@ with the oracle's, and k = 25 compares 25 vanilla CP iterations.
 Tolerance (relative to max(1, |reference|_inf)): one FP32 evaluation of T
 rounds its inputs and factors to single precision (unit roundoff
 u = 2^-24 = 6e-8) and accumulates dot products of at most nx + nu = 128
-terms along Riccati recursions of a few stages; with errors adding in
-quadrature over those terms, 2e-5 = 330 u bounds one evaluation.  T is
-nonexpansive in the M-metric, so k iterations add at most k such errors
-(in M-norm); with random signs they add in quadrature, sqrt(25) x 2e-5 =
-1e-4 for k = 25.  Solves in FP32 (FP64 residual, Anderson and certification
-tail) are compared with the FP64 oracle's converged solution through the
-graph driver."""
+terms in registers along Riccati recursions of a few stages; measured
+errors are 1.5-4 u (0.9-2.3e-7) on every tree here, asserted at
+2e-6 = 33 u.  T is nonexpansive in the M-metric, so iterating it does not
+amplify earlier errors (measured 1.1-2.2e-7 after 25 iterations, asserted at
+5e-6).  Solves in FP32 (FP64 residual, Anderson and certification tail) are
+compared with the FP64 oracle's converged solution through the graph
+driver."""
 import numpy as np
 import pytest
 
@@ -25,7 +25,7 @@ from tests.gpu_common import Pair, cases, rel_err
 
 pytestmark = pytest.mark.gpu
 CASES = cases()
-TOL_FP32_T = 2e-5
+TOL_FP32_T = {1: 2e-6, 25: 5e-6}
 
 
 @pytest.fixture(scope="module", params=["chains", "wide_50_20", "root_40", "datacenter_N6", "chains_1024_50_20"])
@@ -44,7 +44,7 @@ def test_cp_step_fp32_matches_oracle(pair, k):
     ref, xi_ref = vanilla_cp(pair.cp, np.concatenate([z0, e0]), pair.d["x0"], k)
     got = np.concatenate([z.cpu().numpy(), e.cpu().numpy()])
     err = rel_err(got, ref)
-    tol = TOL_FP32_T * np.sqrt(k)
+    tol = TOL_FP32_T[k]
     print(f"FP32 CP k={k}: max rel. error {err:.2e} (tolerance {tol:.1e}), xi {xi:.4e} vs {xi_ref:.4e}")
     assert err < tol
     # xi = max(|r_z/alpha - L* r_eta|, |r_eta/alpha - L r_z|): the FP32 error
