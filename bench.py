@@ -492,12 +492,14 @@ def closed_loop_workload(args, spock, workloads, dev):
 
 def batch_workload(args, spock, workloads, dev, seed=0):
     """Batched SPOCK: args.batch heterogeneous instances (branching 2-4,
-    N 5-15, nx 10-30, nu 4-10, scenario cap 64; data as the large tree) in
+    N 5-15, nx 10-30, nu 4-10, scenario cap 64; data as the large tree with
+    uniform child probabilities) in
     one spock_batch_solve_dev call -- every kernel of a round launched once
     for the whole batch, rounds replayed from a CUDA graph.  A warm-up solve
     (autotuning, capture) is excluded; the timed solve runs args.batch_iter
     SPOCK iterations per instance from a cold start, FP32 (FP64
-    residual/Anderson) and FP64."""
+    residual/Anderson) and FP64; then every instance from a cold start to the
+    1e-6 residual (time for all to reach it)."""
     import torch
     t0 = time.time()
     ds = workloads.batch_instances(seed=seed, count=args.batch)
@@ -525,6 +527,22 @@ def batch_workload(args, spock, workloads, dev, seed=0):
                    "median_xi": float(np.median([i.xi for i in infos])),
                    "mode": "persistent (one launch, one block per instance)" if infos[0].n_launches == 1
                            else "work-list kernels, %d launches" % infos[0].n_launches}
+        if args.batch_tol_iter > 0:
+            # every instance from a cold start to xi <= 1e-6 (iteration cap per instance)
+            st = spock.spock_default_settings(precision=prec, max_iter=args.batch_tol_iter, memory=args.memory,
+                                              fp64_tail=0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            infos = spock.spock_batch_solve_dev(b, x0s, st, zs, es, 0)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            its = [i.iterations for i in infos]
+            out[nm]["to_tol_1e-6"] = {
+                "device_ms": round(infos[0].solve_ms, 2), "wall_ms": round(wall * 1e3, 2),
+                "converged": sum(1 for i in infos if i.status == 0), "instances": len(infos),
+                "iterations_median_max": [int(np.median(its)), int(max(its))],
+                "n_T_total": int(sum(i.n_T for i in infos)), "max_iter": args.batch_tol_iter,
+                "xi_over_tol_max": float(max(i.xi / max(1e-6, 1e-6 * i.xi0) for i in infos))}
     spock.spock_free(b)
     for p in probs:
         p.close()
@@ -535,16 +553,17 @@ def batch_workload(args, spock, workloads, dev, seed=0):
 def grad_workload(args, spock, workloads, dev):
     """Gradients of the optimal cost (envelope theorem at the converged pair)
     on 64 instances of the tree with branching 3 for 4 stages, N = 10
-    (607 nodes), nx = 20, nu = 8: one batched FP64 solve (tolerance 1e-6,
-    at most args.grad_iter iterations per instance), then spock_grad_dev per
-    instance in FP64 and FP32 (CUDA events), compared with the solve time
-    per instance.  This family converges slowly under the scalar CP step
-    (the oracle needs ~3,600 iterations for 1e-8 on a 13-node member), so
-    the finite-difference check of dV/dx0 (random direction, h = 1e-6,
-    solves to 1e-11) runs on the 13-node member of the same family."""
+    (607 nodes), nx = 20, nu = 8, data as the large tree with uniform child
+    probabilities (the workload does not state them): one batched FP64 solve
+    (tolerance 1e-6, at most args.grad_iter iterations per instance), then
+    spock_grad_dev per instance in FP64 and FP32 (CUDA events), compared with
+    the solve time per instance.  Finite-difference check on instance 0 of
+    the same workload: central differences with h = 1e-6 along random
+    directions of x0 and of diag Q, from solves to xi <= 1e-12."""
     import torch
     cnt = args.grad_instances
-    ds = [workloads.large_tree(seed=s, branching_stages=4, branch=3, N=10, nx=20, nu=8) for s in range(cnt)]
+    ds = [workloads.large_tree(seed=s, branching_stages=4, branch=3, N=10, nx=20, nu=8, probs="uniform")
+          for s in range(cnt)]
     probs = [spock.Problem(d) for d in ds]
     b = spock.spock_batch_create([p.handle for p in probs])
     x0s = [torch.tensor(d["x0"], dtype=torch.float64, device=dev) for d in ds]
@@ -590,63 +609,52 @@ def grad_workload(args, spock, workloads, dev):
     spock.spock_free(b)
     for p in probs:
         p.close()
-    # finite-difference check of dV/dx0 on the 13-node member of the family
-    d = workloads.large_tree(seed=0, branching_stages=1, branch=3, N=4, nx=20, nu=8)
+    # finite-difference checks on instance 0 of the workload (solves to 1e-12)
+    d = ds[0]
     P = spock.Problem(d)
-    tight = spock.spock_default_settings(precision=spock.SPOCK_FP64, eps_abs=1e-11, eps_rel=1e-11, memory=5,
+    tight = spock.spock_default_settings(precision=spock.SPOCK_FP64, eps_abs=1e-12, eps_rel=1e-12, memory=5,
                                          max_iter=200000)
 
-    def solve(x0):
-        z = torch.zeros(P.n_z, dtype=torch.float64, device=dev)
-        e = torch.zeros(P.n_eta, dtype=torch.float64, device=dev)
-        inf = spock.spock_solve_dev(P.handle, torch.tensor(x0, dtype=torch.float64, device=dev), tight, z, e, 0)
+    def solve(PP, x0):
+        z = torch.zeros(PP.n_z, dtype=torch.float64, device=dev)
+        e = torch.zeros(PP.n_eta, dtype=torch.float64, device=dev)
+        inf = spock.spock_solve_dev(PP.handle, torch.tensor(x0, dtype=torch.float64, device=dev), tight, z, e, 0)
         return z, e, inf
 
-    z, e, inf0 = solve(d["x0"])
+    z, e, inf0 = solve(P, d["x0"])
     g = grads(None, len(d["anc"]), d["nx"], d["nu"])
     spock.spock_grad_dev(P.handle, z, e, spock.SPOCK_FP64, *g)
     rng = np.random.default_rng(7)
+    h = 1e-6
     dirv = rng.standard_normal(d["nx"])
     dirv /= np.linalg.norm(dirv)
-    h = 1e-6
-    zp_, _, infp = solve(d["x0"] + h * dirv)
-    zm_, _, infm = solve(d["x0"] - h * dirv)
+    zp_, _, infp = solve(P, d["x0"] + h * dirv)
+    zm_, _, infm = solve(P, d["x0"] - h * dirv)
     fd = (float(zp_[0].item()) - float(zm_[0].item())) / (2 * h)
     an = float(g[0].cpu().numpy() @ dirv)
-    out["fd_check_x0"] = {"tree": "branching 3 for 1 stage, N=4 (13 nodes), nx=20, nu=8", "analytic": an,
-                          "central_fd": fd, "rel_err": abs(an - fd) / max(abs(fd), 1e-12), "h": h,
-                          "solve_tol": 1e-11, "iterations": [inf0.iterations, infp.iterations, infm.iterations],
+    out["fd_check_x0"] = {"tree": "instance 0 of the workload (607 nodes)", "analytic": an, "central_fd": fd,
+                          "rel_err": abs(an - fd) / max(abs(fd), 1e-12), "h": h, "solve_tol": 1e-12,
+                          "iterations": [inf0.iterations, infp.iterations, infm.iterations],
                           "converged": all(i.status == 0 for i in (inf0, infp, infm))}
+    # diag Q along a random direction over all nonroot nodes (relative step h per entry)
+    dq = rng.standard_normal(d["Q"].shape)
+    dq[0] = 0.0
+    an_q = float(np.sum(g[3].cpu().numpy() * dq * d["Q"]))
+    vals = []
+    for sgn in (1.0, -1.0):
+        dd = dict(d)
+        dd["Q"] = d["Q"] * (1.0 + sgn * h * dq)
+        PP = spock.Problem(dd)
+        zz, _, inf_ = solve(PP, d["x0"])
+        vals.append((float(zz[0].item()), inf_.status == 0))
+        PP.close()
+    fd_q = (vals[0][0] - vals[1][0]) / (2 * h)
+    out["fd_check_Q"] = {"analytic": an_q, "central_fd": fd_q, "rel_err": abs(an_q - fd_q) / max(abs(fd_q), 1e-12),
+                         "h": h, "direction": "Q <- Q (1 + h dQ), dQ ~ N(0, 1) per entry",
+                         "converged": all(v[1] for v in vals)}
     P.close()
     torch.cuda.empty_cache()
     return out
-
-
-def host_cpu():
-    """Cores this process may use and the CPU model of the host."""
-    try:
-        cores = len(os.sched_getaffinity(0))
-    except Exception:
-        cores = os.cpu_count() or 1
-    model = None
-    try:
-        info = open("/proc/cpuinfo").read().splitlines()
-        for key in ("model name", "Model name", "CPU part"):
-            hits = [ln.split(":", 1)[1].strip() for ln in info if ln.startswith(key)]
-            if hits:
-                model = hits[0] if key != "CPU part" else f"Arm CPU part {hits[0]}"
-                break
-    except Exception:
-        pass
-    try:
-        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
-        for ln in out.splitlines():
-            if ln.strip().startswith("Model name:"):
-                model = ln.split(":", 1)[1].strip()
-                break
-    except Exception:
-        pass
-    return cores, model or "unknown"
 
 
 def cpu_baseline(d, seconds=10.0, threads=None):
@@ -737,6 +745,8 @@ def main():
                     help="disturbance sequences of the closed-loop MPC measurement (0 skips it; the paper uses 15)")
     ap.add_argument("--batch", type=int, default=512, help="instances of the batched measurement (0 skips it)")
     ap.add_argument("--batch-iter", type=int, default=50)
+    ap.add_argument("--batch-tol-iter", type=int, default=20000,
+                    help="iteration cap of the batched time-to-1e-6 solve (0 skips it)")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batched measurement and print it (profiling aid, not a bench line)")
     ap.add_argument("--grad-instances", type=int, default=64,

@@ -22,8 +22,6 @@ struct BInst {
   SmState* st;
   S* V;     // accepted iterate and T of it
   S* TV;
-  S* Vp;    // previously accepted pair (Anderson differences)
-  S* TVp;
   S* Vt;    // evaluation point and T of it
   S* TVt;
   S* d;     // direction

@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(128) k_solve_cta(const BInst<S>* __restrict__ 
     __syncthreads();
     // an accepted point is committed even when the decision ends the solve:
     // the returned pair is the last accepted (v, T(v))
-    round_commit_body<S, MEM>(st, b.V, b.TV, b.Vp, b.TVp, b.Vt, b.TVt, b.MR, b.D, b.n_v, b.ld, b.paa, 0, 1);
+    round_commit_body<S, MEM>(st, b.V, b.TV, b.Vt, b.TVt, b.MR, b.D, b.n_v, b.ld, b.paa, 0, 1);
     __syncthreads();
     if (*reinterpret_cast<volatile int32_t*>(&st->done)) break;
     round_aa_solve_body(st, b.paa, 1);

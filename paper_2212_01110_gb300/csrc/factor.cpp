@@ -178,7 +178,9 @@ bool riccati_factor(const Tree& t, int nx, int nu, const std::vector<double>& A,
         for (int r = 0; r < nu; ++r)
           for (int q = 0; q < nx; ++q) {
             nb[r * nx + q] = K[r * nx + q];                       // K   (nu x nx)
-            nb[(size_t)nu * nx + r * nx + q] = W[q * nu + r];     // W^T (nu x nx)
+            // C = K + W^T (nu x nx): the backward step forms K^T (d - ubar) + W d
+            // as C^T d - K^T ubar, without the difference d - ubar
+            nb[(size_t)nu * nx + r * nx + q] = K[r * nx + q] + W[q * nu + r];
           }
         for (int e = 0; e < nu * nu; ++e) nb[2 * (size_t)nu * nx + e] = Rinv[e];
       }

@@ -166,6 +166,8 @@ __device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
 __device__ __forceinline__ float vsqrt(float v) { return sqrtf(v); }
 __device__ __forceinline__ double vsqrt(double v) { return sqrt(v); }
+__device__ __forceinline__ float vrsqrt(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double vrsqrt(double v) { return rsqrt(v); }
 
 template <typename S>
 __device__ __forceinline__ S clampv(S v, S lo, S hi) {
@@ -223,7 +225,9 @@ struct NodeAcc {
   }
   // end of a node: flush when due
   __device__ __forceinline__ void node_done(StatAcc& a) {
-    if (sizeof(S) == 8 || ++nodes == kFlushNodesF32) flush(a);
+    // FP64 terms are summed in FP64 already: one flush at the end of the
+    // kernel; FP32 terms are flushed into FP64 every kFlushNodesF32 nodes
+    if (sizeof(S) == 4 && ++nodes == kFlushNodesF32) flush(a);
   }
 };
 

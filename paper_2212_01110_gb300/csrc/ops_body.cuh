@@ -204,46 +204,48 @@ __device__ __forceinline__ void dual_stat(NodeAcc<S>& a, S inv_alpha, S e_old, S
   }
 }
 
-// Translated second-order cone: the block w (entries 0..dim-1, t = entry
-// dim-1) maps to w - alpha P(w / alpha - sh) - alpha sh with
-// sh = (0, .., 1/2, -1/2) and P the projection on SOC = {(v, t): ||v|| <= t}.
-// nv = ||v||, t the cone coordinate, scale = (nv + t) / (2 nv) on the
-// boundary case (one division per block).
-template <typename S>
-__device__ __forceinline__ S soc_entry(S wv, int e, int dim, S al, S ial, S nv, S t, S scale) {
-  S v = wv * ial;
-  if (e == dim - 2) v -= S(0.5);
-  if (e == dim - 1) v = t;
-  S pr;
-  if (nv <= t) pr = v;
-  else if (nv <= -t) pr = S(0);
-  else pr = (e == dim - 1) ? S(0.5) * (nv + t) : scale * v;
-  if (e == dim - 2) pr += S(0.5);
-  if (e == dim - 1) pr -= S(0.5);
-  return wv - al * pr;
-}
-
-// Norm data of the translated SOC block held in registers w[j] (entry
-// lane + 32 j; entries >= dim are ignored).
+// Translated second-order cone of S3, SOC + sh with SOC = {(v, t): ||v|| <= t}
+// (t the last entry) and sh = (0, .., 1/2, -1/2).  The caller holds in y[j]
+// (entry lane + 32 j of a block of `dim` entries) the point y = w / alpha - sh
+// of the Moreau decomposition w - alpha proj(w / alpha) = alpha (y - P(y)),
+// P the projection on SOC.  o[j] receives alpha (y - P(y)):
+//   ||v|| <= t:  0;   ||v|| <= -t:  alpha y;
+//   otherwise:   v-part alpha (1 - s) v, t-part alpha (t - s ||v||),
+//                s = (||v|| + t) / (2 ||v||),
+// with one reciprocal square root per block (the case tests use ||v||^2).
 template <typename S, int J>
-__device__ __forceinline__ void soc_norm(const S (&w)[J], int dim, S ial, int lane, S& nv, S& t, S& scale) {
-  S s2 = 0, wt = 0;
+__device__ __forceinline__ void soc_moreau(const S (&y)[J], int dim, S al, int lane, S (&o)[J]) {
+  S s2 = 0, tl = 0;
 #pragma unroll
   for (int j = 0; j < J; ++j) {
     const int e = lane + 32 * j;
-    if (e < dim - 1) {
-      S v = w[j] * ial;
-      if (e == dim - 2) v -= S(0.5);
-      s2 += v * v;
-    } else if (e == dim - 1) {
-      wt = w[j];
-    }
+    if (e < dim - 1) s2 += y[j] * y[j];
+    else if (e == dim - 1) tl = y[j];
   }
   s2 = warp_sum(s2);
-  wt = __shfl_sync(kFull, wt, (dim - 1) & 31);
-  nv = vsqrt(s2);
-  t = wt * ial + S(0.5);
-  scale = (nv > t && nv > -t) ? S(0.5) * (nv + t) / nv : S(0);
+  const S t = __shfl_sync(kFull, tl, (dim - 1) & 31);
+  const bool in_cone = s2 <= t * t;
+  if (in_cone && t >= S(0)) {
+#pragma unroll
+    for (int j = 0; j < J; ++j) o[j] = S(0);
+  } else if (in_cone) {
+#pragma unroll
+    for (int j = 0; j < J; ++j) o[j] = al * y[j];
+  } else {
+    const S rs = vrsqrt(s2);
+    const S c = S(0.5) * al * (S(1) - t * rs);
+    const S ot = S(0.5) * al * (t - s2 * rs);
+#pragma unroll
+    for (int j = 0; j < J; ++j) o[j] = (lane + 32 * j == dim - 1) ? ot : c * y[j];
+  }
+}
+
+// y = w / alpha - sh of the translated SOC block (entries e < dim).
+template <typename S>
+__device__ __forceinline__ S soc_shift(S y, int e, int dim) {
+  if (e == dim - 2) return y - S(0.5);
+  if (e == dim - 1) return y + S(0.5);
+  return y;
 }
 
 // Without statistics: the dual update (DM_DUAL), L z (DM_APPLY_L) or
@@ -316,12 +318,14 @@ __device__ __forceinline__ void dual_body(const KP<S>& p, int bid, int nblk, con
         for (int j = 0; j < J; ++j)
           if (lane + 32 * j < nb) out[D.enr + lane + 32 * j] = w[j];
       } else {
-        S nv, t, sc;
-        soc_norm<S, J>(w, nb, ial, lane, nv, t, sc);
+        S y[J], o[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) y[j] = lane + 32 * j < nb ? soc_shift(w[j] * ial, lane + 32 * j, nb) : S(0);
+        soc_moreau<S, J>(y, nb, al, lane, o);
 #pragma unroll
         for (int j = 0; j < J; ++j) {
           const int e = lane + 32 * j;
-          if (e < nb) out[D.enr + e] = soc_entry(w[j], e, nb, al, ial, nv, t, sc);
+          if (e < nb) out[D.enr + e] = o[j];
         }
       }
     }
@@ -380,12 +384,14 @@ __device__ __forceinline__ void dual_body(const KP<S>& p, int bid, int nblk, con
         for (int j = 0; j < J; ++j)
           if (lane + 32 * j < dim) out[es + lane + 32 * j] = w[j];
       } else {
-        S nv, t, sc;
-        soc_norm<S, J>(w, dim, ial, lane, nv, t, sc);
+        S y[J], o[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) y[j] = lane + 32 * j < dim ? soc_shift(w[j] * ial, lane + 32 * j, dim) : S(0);
+        soc_moreau<S, J>(y, dim, al, lane, o);
 #pragma unroll
         for (int j = 0; j < J; ++j) {
           const int e = lane + 32 * j;
-          if (e < dim) out[es + e] = soc_entry(w[j], e, dim, al, ial, nv, t, sc);
+          if (e < dim) out[es + e] = o[j];
         }
       }
     }
@@ -406,9 +412,9 @@ __device__ __forceinline__ void dual_body(const KP<S>& p, int bid, int nblk, con
 //   x^c, s^c (leaf c): c's leaf block.
 // The nonroot blocks reuse x^k, u^k already in registers.
 // ---------------------------------------------------------------------------
+// rz = z - z+ of one entry, lt = (L* r_eta) there, dv the direction
 template <typename S, bool DR>
-__device__ __forceinline__ void primal_stat(NodeAcc<S>& a, S inv_alpha, S zv, S zpv, S dv, S lt) {
-  const S rz = zv - zpv;
+__device__ __forceinline__ void primal_stat(NodeAcc<S>& a, S inv_alpha, S rz, S dv, S lt) {
   a.s[ST_RZ2] += rz * rz;
   a.s[ST_XIP] = vmax(a.s[ST_XIP], vabs(rz * inv_alpha - lt));
   if (DR) a.s[ST_RD] += rz * dv;
@@ -466,10 +472,13 @@ __device__ __forceinline__ void dual_fused_body(const KP<S>& p, int bid, int nbl
     const S sk = z[D.zs], skp = zp[D.zs], skd = DR ? dz[D.zs] : S(0);
     const S y3 = z[z2 + 2 * m], y3p = zp[z2 + 2 * m], y3d = DR ? dz[z2 + 2 * m] : S(0);
     const S esb = eta[ie_sb], desb = DR ? deta[ie_sb] : S(0);
-    // ---- own (x, u) and its box rows
-    S az[J], azp[J], adz[J], lt[J];
+    // ---- own (x, u) and its box rows.  Per entry the differences r_z = z - z+
+    // (the residual, also L r_z of every row of L that reads it, scaled) and
+    // q_z = z+ - r_z = 2 z+ - z (the point L is applied to in the dual update)
+    // are formed once and reused by every row of L that reads the entry.
+    S rzv[J], qzv[J], adz[J], lt[J];
     {
-      S ae[J], ade[J], alo[J], ahi[J];
+      S az[J], azp[J], ae[J], ade[J], alo[J], ahi[J];
 #pragma unroll
       for (int j = 0; j < J; ++j) {
         const int e = lane + 32 * j;
@@ -488,11 +497,13 @@ __device__ __forceinline__ void dual_fused_body(const KP<S>& p, int bid, int nbl
 #pragma unroll
       for (int j = 0; j < J; ++j) {
         const int e = lane + 32 * j;
+        rzv[j] = az[j] - azp[j];
+        qzv[j] = azp[j] - rzv[j];
         if (e < nxu) {
-          const S w = dual_w<S, DM_DUAL>(al, ae[j], az[j], azp[j]);
+          const S w = ae[j] + al * qzv[j];
           const S o = w - al * clampv(w * ial, alo[j], ahi[j]);
           out[ea + e] = o;
-          dual_stat<S, true, DR>(nacc, ial, ae[j], o, az[j] - azp[j], ade[j], adz[j]);
+          dual_stat<S, true, DR>(nacc, ial, ae[j], o, rzv[j], ade[j], adz[j]);
           lt[j] = ae[j] - o;
         }
       }
@@ -525,46 +536,46 @@ __device__ __forceinline__ void dual_fused_body(const KP<S>& p, int bid, int nbl
         }
       }
       {  // nonroot block of c: SOC on (Q^c 1/2 x^k, R^c 1/2 u^k, tau^c / 2, tau^c / 2)
-        S w[J], lrz[J], ld[J];
+        const S rt = tz - tzp, qt = tzp - rt;
+        S y[J], lrz[J], ld[J], o[J];
 #pragma unroll
         for (int j = 0; j < J; ++j) {
           const int e = lane + 32 * j;
-          w[j] = lrz[j] = ld[j] = S(0);
+          y[j] = lrz[j] = ld[j] = S(0);
           if (e < nb) {
             const S coef = bc[j];
-            const S Lz = coef * (e < nxu ? az[j] : tz);
-            const S Lzp = coef * (e < nxu ? azp[j] : tzp);
-            if (DR) ld[j] = coef * (e < nxu ? adz[j] : tdz);
-            w[j] = dual_w<S, DM_DUAL>(al, be[j], Lz, Lzp);
-            lrz[j] = Lz - Lzp;
+            const bool xu = e < nxu;
+            lrz[j] = coef * (xu ? rzv[j] : rt);
+            if (DR) ld[j] = coef * (xu ? adz[j] : tdz);
+            // w / alpha = eta / alpha + (L (2 z+ - z))_e
+            y[j] = soc_shift(be[j] * ial + coef * (xu ? qzv[j] : qt), e, nb);
           }
         }
-        S nv, t, sc;
-        soc_norm<S, J>(w, nb, ial, lane, nv, t, sc);
+        soc_moreau<S, J>(y, nb, al, lane, o);
         S tau_part = 0;
 #pragma unroll
         for (int j = 0; j < J; ++j) {
           const int e = lane + 32 * j;
           if (e < nb) {
-            const S o = soc_entry(w[j], e, nb, al, ial, nv, t, sc);
-            out[er + e] = o;
-            dual_stat<S, true, DR>(nacc, ial, be[j], o, lrz[j], bde[j], ld[j]);
-            const S re = be[j] - o;
+            out[er + e] = o[j];
+            dual_stat<S, true, DR>(nacc, ial, be[j], o[j], lrz[j], bde[j], ld[j]);
+            const S re = be[j] - o[j];
             if (e < nxu) lt[j] += bc[j] * re;
             else tau_part += re;
           }
         }
         tau_part = warp_sum(tau_part);
-        if (lane == 0) primal_stat<S, DR>(nacc, ial, tz, tzp, tdz, S(0.5) * tau_part);
+        if (lane == 0) primal_stat<S, DR>(nacc, ial, rt, tdz, S(0.5) * tau_part);
       }
       if (c >= p.nl) {  // leaf block of c: box on x^c, SOC on (Q_N^1/2 x^c, s^c / 2, s^c / 2)
         const int64_t ef = (jc == 0 ? D.es_c0 : __ldg(&p.desc[c].es)) - 2 * nx;
         const int64_t zxc = __ldg(&p.desc[c].zx);
         const int64_t zsc = z2 + 3 * m + 1 + jc;
         const S sz = z[zsc], szp = zp[zsc], sdz = DR ? dz[zsc] : S(0);
-        S xz[J], xzp[J], xdz[J], ltx[J];
+        const S rs_ = sz - szp, qs_ = szp - rs_;
+        S rx[J], qx[J], xdz[J], ltx[J];
         {
-          S fe[J], fde[J], flo[J], fhi[J];
+          S xz[J], xzp[J], fe[J], fde[J], flo[J], fhi[J];
 #pragma unroll
           for (int j = 0; j < J; ++j) {
             const int e = lane + 32 * j;
@@ -582,62 +593,61 @@ __device__ __forceinline__ void dual_fused_body(const KP<S>& p, int bid, int nbl
 #pragma unroll
           for (int j = 0; j < J; ++j) {
             const int e = lane + 32 * j;
+            rx[j] = xz[j] - xzp[j];
+            qx[j] = xzp[j] - rx[j];
             if (e < nx) {
-              const S w = dual_w<S, DM_DUAL>(al, fe[j], xz[j], xzp[j]);
+              const S w = fe[j] + al * qx[j];
               const S o = w - al * clampv(w * ial, flo[j], fhi[j]);
               out[ef + e] = o;
-              dual_stat<S, true, DR>(nacc, ial, fe[j], o, xz[j] - xzp[j], fde[j], xdz[j]);
+              dual_stat<S, true, DR>(nacc, ial, fe[j], o, rx[j], fde[j], xdz[j]);
               ltx[j] = fe[j] - o;
             }
           }
         }
         const int dim = nx + 2;
         const int64_t es = ef + nx;
-        S w[J], lrz[J], ld[J], ev[J], dev[J], qn[J];
+        S y[J], lrz[J], ld[J], ev[J], dev[J], qn[J], o[J];
 #pragma unroll
         for (int j = 0; j < J; ++j) {
           const int e = lane + 32 * j;
-          w[j] = lrz[j] = ld[j] = ev[j] = dev[j] = qn[j] = S(0);
+          y[j] = lrz[j] = ld[j] = ev[j] = dev[j] = qn[j] = S(0);
           if (e < dim) {
-            const S coef = e < nx ? p.qns[(int64_t)c * nx + e] : S(0.5);
-            const S Lz = coef * (e < nx ? xz[j] : sz);
-            const S Lzp = coef * (e < nx ? xzp[j] : szp);
+            const bool xr = e < nx;
+            const S coef = xr ? p.qns[(int64_t)c * nx + e] : S(0.5);
             ev[j] = eta[es + e];
+            lrz[j] = coef * (xr ? rx[j] : rs_);
             if (DR) {
               dev[j] = deta[es + e];
-              ld[j] = coef * (e < nx ? xdz[j] : sdz);
+              ld[j] = coef * (xr ? xdz[j] : sdz);
             }
-            w[j] = dual_w<S, DM_DUAL>(al, ev[j], Lz, Lzp);
-            lrz[j] = Lz - Lzp;
+            y[j] = soc_shift(ev[j] * ial + coef * (xr ? qx[j] : qs_), e, dim);
             qn[j] = coef;
           }
         }
-        S nv, t, sc;
-        soc_norm<S, J>(w, dim, ial, lane, nv, t, sc);
+        soc_moreau<S, J>(y, dim, al, lane, o);
         S s_part = 0;
 #pragma unroll
         for (int j = 0; j < J; ++j) {
           const int e = lane + 32 * j;
           if (e < dim) {
-            const S o = soc_entry(w[j], e, dim, al, ial, nv, t, sc);
-            out[es + e] = o;
-            dual_stat<S, true, DR>(nacc, ial, ev[j], o, lrz[j], dev[j], ld[j]);
-            const S re = ev[j] - o;
+            out[es + e] = o[j];
+            dual_stat<S, true, DR>(nacc, ial, ev[j], o[j], lrz[j], dev[j], ld[j]);
+            const S re = ev[j] - o[j];
             if (e < nx) ltx[j] += qn[j] * re;
             else s_part += re;
           }
         }
 #pragma unroll
         for (int j = 0; j < J; ++j)
-          if (lane + 32 * j < nx) primal_stat<S, DR>(nacc, ial, xz[j], xzp[j], xdz[j], ltx[j]);
+          if (lane + 32 * j < nx) primal_stat<S, DR>(nacc, ial, rx[j], xdz[j], ltx[j]);
         s_part = warp_sum(s_part);
-        if (lane == 0) primal_stat<S, DR>(nacc, ial, sz, szp, sdz, S(0.5) * s_part);
+        if (lane == 0) primal_stat<S, DR>(nacc, ial, rs_, sdz, S(0.5) * s_part);
       }
     }
     // ---- primal statistics at x^k, u^k
 #pragma unroll
     for (int j = 0; j < J; ++j)
-      if (lane + 32 * j < nxu) primal_stat<S, DR>(nacc, ial, az[j], azp[j], adz[j], lt[j]);
+      if (lane + 32 * j < nxu) primal_stat<S, DR>(nacc, ial, rzv[j], adz[j], lt[j]);
     // ---- the s - b'y row of k (b = (p^children, 0, 1)), then the y rows
     {
       S bs = pr0 * yz0, bsp = pr0 * yzp0, bsd = DR ? pr0 * yd0 : S(0);
@@ -657,7 +667,7 @@ __device__ __forceinline__ void dual_fused_body(const KP<S>& p, int bid, int nbl
       if (lane == 0) {
         out[ie_sb] = o;
         dual_stat<S, true, DR>(nacc, ial, esb, o, Lz - Lzp, desb, Ld);
-        primal_stat<S, DR>(nacc, ial, sk, skp, skd, re_sb);   // s^k (s^0 at the root)
+        primal_stat<S, DR>(nacc, ial, sk - skp, skd, re_sb);   // s^k (s^0 at the root)
       }
       auto yrow = [&](int e, S yz, S yzp, S yd, S ye, S yde) {
         const S yw = dual_w<S, DM_DUAL>(al, ye, yz, yzp);
@@ -665,7 +675,7 @@ __device__ __forceinline__ void dual_fused_body(const KP<S>& p, int bid, int nbl
         out[el + e] = yo;
         dual_stat<S, true, DR>(nacc, ial, ye, yo, yz - yzp, yde, yd);
         const S bl = e < m ? p.prob[c0 + e] : (e < 2 * m ? S(0) : S(1));
-        primal_stat<S, DR>(nacc, ial, yz, yzp, yd, (ye - yo) - bl * re_sb);
+        primal_stat<S, DR>(nacc, ial, yz - yzp, yd, (ye - yo) - bl * re_sb);
       };
       if (lane < 2 * m + 1) yrow(lane, yz0, yzp0, yd0, ye0, yde0);
       for (int e = lane + 32; e < 2 * m + 1; e += 32)

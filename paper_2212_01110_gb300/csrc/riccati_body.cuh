@@ -52,7 +52,7 @@ __device__ __forceinline__ void node_bwd(const KP<S>& p, int k, const S (&h)[SL]
   for (int b = lane; b < nu; b += 32) v.g[b] = v.u[b] - v.h[nx + b];
   __syncwarp();
   const S* __restrict__ Km = p.NB + (int64_t)k * p.nbstride;
-  const S* __restrict__ Wt = Km + (int64_t)nu * nx;
+  const S* __restrict__ Cm = Km + (int64_t)nu * nx;   // K + W^T
   const S* __restrict__ Ri = Km + 2 * (int64_t)nu * nx;
   for (int a = lane; a < nu; a += 32) {
     S acc = 0;
@@ -70,16 +70,17 @@ __device__ __forceinline__ void node_bwd(const KP<S>& p, int k, const S (&h)[SL]
     const int r = 32 * s + lane;
     qn[s] = (r < nx) ? v.h[r] - xb[r] : S(0);
   }
+  // q += K^T (d - ubar) + W d = C^T d - K^T ubar
 #pragma unroll 4
   for (int b = 0; b < nu; ++b) {
     const S db = v.d[b];
-    const S dmu = db - v.u[b];
+    const S ub = v.u[b];
     const S* kr = Km + (int64_t)b * nx;
-    const S* wr = Wt + (int64_t)b * nx;
+    const S* cr = Cm + (int64_t)b * nx;
 #pragma unroll
     for (int s = 0; s < SL; ++s) {
       const int r = 32 * s + lane;
-      if (r < nx) qn[s] += __ldg(kr + r) * dmu + __ldg(wr + r) * db;
+      if (r < nx) qn[s] += __ldg(cr + r) * db - __ldg(kr + r) * ub;
     }
   }
   __syncwarp();

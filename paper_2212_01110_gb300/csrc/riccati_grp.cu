@@ -167,10 +167,11 @@ __global__ void __launch_bounds__(kGrpThreads* kMaxGroups) k_bwd_chain_grp(KP<S>
       }
     }
     named_bar(bar_id, kGrpThreads);
-    // phase C: q = K^T (d - ubar) + W d - xbar + Abar^T q, rows split over the warps
+    // phase C: q = K^T (d - ubar) + W d - xbar + Abar^T q = C^T d - K^T ubar - xbar
+    // + Abar^T q (C = K + W^T), rows split over the warps
     {
       const S* Km = NBk;
-      const S* Wt = NBk + nu * nx;
+      const S* Cm = NBk + nu * nx;
       S qn[SLG];
 #pragma unroll
       for (int s = 0; s < SLG; ++s) {
@@ -180,13 +181,13 @@ __global__ void __launch_bounds__(kGrpThreads* kMaxGroups) k_bwd_chain_grp(KP<S>
 #pragma unroll 4
       for (int b = 0; b < nu; ++b) {
         const S db = vd[b];
-        const S dmu = db - ub[b];
+        const S u = ub[b];
         const S* kr = Km + b * nx;
-        const S* wr = Wt + b * nx;
+        const S* cr = Cm + b * nx;
 #pragma unroll
         for (int s = 0; s < SLG; ++s) {
           const int r = sub * 32 + lane + s * kGrpThreads;
-          if (r < nx) qn[s] += kr[r] * dmu + wr[r] * db;
+          if (r < nx) qn[s] += cr[r] * db - kr[r] * u;
         }
       }
       // every warp has finished reading vq in phase A (barrier above)

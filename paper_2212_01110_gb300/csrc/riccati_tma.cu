@@ -4,7 +4,7 @@
 // Chain region (one warp per chain, persistent grid, double-buffered):
 //   while the warp computes chain step j from stage buffer j&1, the copy of
 //   step j+1 -- [Abar^c | B^c] (or its transpose for the forward pass), the
-//   node block [K | W^T | Rt^-1] (or K^T) and the node's vectors -- is in
+//   node block [K | K + W^T | Rt^-1] (or K^T) and the node's vectors -- is in
 //   flight into the other buffer, so the GEMVs never wait on DRAM; the
 //   costate q (backward) or state x (forward) of the chain stays in shared
 //   memory from step to step.
@@ -57,7 +57,7 @@ __device__ __forceinline__ void sm_node_bwd(const KP<S>& p, int k, const S (&h)[
   for (int b = lane; b < nu; b += 32) vg[b] = ub[b] - vh[nx + b];
   __syncwarp();
   const S* Km = NBk;
-  const S* Wt = NBk + nu * nx;
+  const S* Cm = NBk + nu * nx;      // K + W^T
   const S* Ri = NBk + 2 * nu * nx;  // symmetric: read column-wise for conflict-free lanes
   for (int a = lane; a < nu; a += 32) {
     S acc = 0;
@@ -72,16 +72,17 @@ __device__ __forceinline__ void sm_node_bwd(const KP<S>& p, int k, const S (&h)[
     const int r = 32 * s + lane;
     qn[s] = (r < nx) ? vh[r] - xb[r] : S(0);
   }
+  // q += K^T (d - ubar) + W d = C^T d - K^T ubar
 #pragma unroll 4
   for (int b = 0; b < nu; ++b) {
     const S db = vd[b];
-    const S dmu = db - ub[b];
+    const S u = ub[b];
     const S* kr = Km + b * nx;
-    const S* wr = Wt + b * nx;
+    const S* cr = Cm + b * nx;
 #pragma unroll
     for (int s = 0; s < SL; ++s) {
       const int r = 32 * s + lane;
-      if (r < nx) qn[s] += kr[r] * dmu + wr[r] * db;
+      if (r < nx) qn[s] += cr[r] * db - kr[r] * u;
     }
   }
   __syncwarp();

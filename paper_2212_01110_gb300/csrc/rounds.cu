@@ -1,12 +1,11 @@
 // Device-driven iteration of Algorithm 3 (SPOCK).
 //
-// The buffers are fixed: (V, TV) the accepted iterate and T of it, (Vp, TVp)
-// the previously accepted one (for the Anderson differences), (Vt, TVt) the
-// point being evaluated and T of it, d the direction, the Anderson columns.
+// The buffers are fixed: (V, TV) the accepted iterate and T of it, (Vt, TVt)
+// the point being evaluated and T of it, d the direction, the Anderson columns.
 // Each round: k_round_decide reads the statistics of the last evaluation and
 // the state, takes the SuperMann decision of Algorithm 3 (same readings as
 // supermann.cu) and writes this round's orders; k_round_commit copies an
-// accepted (Vt, TVt) into (V, TV) -- the old pair into (Vp, TVp) -- and in the
+// accepted (Vt, TVt) into (V, TV) and in the
 // same pass writes the new Anderson column and its Gram row; k_round_aa_solve
 // solves for gamma; k_round_point forms the next evaluation point in Vt
 // (v + d with the Anderson direction, v + tau d, the K2 point, or the relaxed
@@ -28,11 +27,10 @@ __global__ void k_round_decide(SmState* st, const double* __restrict__ stats_t, 
 
 template <typename S, int MEM>
 __global__ void __launch_bounds__(256, 4) k_round_commit(SmState* st, S* __restrict__ V, S* __restrict__ TV,
-                                                         S* __restrict__ Vp, S* __restrict__ TVp,
                                                          const S* __restrict__ Vt, const S* __restrict__ TVt,
                                                          S* __restrict__ MR, S* __restrict__ D, int64_t n,
                                                          int64_t ld, double* __restrict__ partials) {
-  round_commit_body<S, MEM>(st, V, TV, Vp, TVp, Vt, TVt, MR, D, n, ld, partials, blockIdx.x, gridDim.x);
+  round_commit_body<S, MEM>(st, V, TV, Vt, TVt, MR, D, n, ld, partials, blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(256) k_round_aa_solve(SmState* st, const double* __restrict__ partials,
@@ -60,7 +58,7 @@ template <typename S, int MEM>
 __global__ void __launch_bounds__(256, 4) k_round_commit_b(const BInst<S>* __restrict__ bi, BMap m) {
   const int i = m.inst[blockIdx.x];
   const BInst<S>& b = bi[i];
-  round_commit_body<S, MEM>(b.st, b.V, b.TV, b.Vp, b.TVp, b.Vt, b.TVt, b.MR, b.D, b.n_v, b.ld, b.paa,
+  round_commit_body<S, MEM>(b.st, b.V, b.TV, b.Vt, b.TVt, b.MR, b.D, b.n_v, b.ld, b.paa,
                             blockIdx.x - m.base[i], m.cnt[i]);
 }
 template <typename S>
@@ -84,11 +82,11 @@ void launch_round_aa_solve(SmState* st, const double* partials, int nblocks, cud
 }
 
 template <typename S>
-void launch_round_commit(SmState* st, S* V, S* TV, S* Vp, S* TVp, const S* Vt, const S* TVt, S* MR, S* D,
+void launch_round_commit(SmState* st, S* V, S* TV, const S* Vt, const S* TVt, S* MR, S* D,
                          int64_t n, int64_t ld, int mem, double* partials, int grid, cudaStream_t s) {
   switch (mem) {
 #define SPOCK_RC(M) \
-  case M: k_round_commit<S, M><<<grid, 256, 0, s>>>(st, V, TV, Vp, TVp, Vt, TVt, MR, D, n, ld, partials); break;
+  case M: k_round_commit<S, M><<<grid, 256, 0, s>>>(st, V, TV, Vt, TVt, MR, D, n, ld, partials); break;
     SPOCK_RC(0) SPOCK_RC(1) SPOCK_RC(2) SPOCK_RC(3) SPOCK_RC(4) SPOCK_RC(5) SPOCK_RC(6) SPOCK_RC(7) SPOCK_RC(8)
     SPOCK_RC(9) SPOCK_RC(10) SPOCK_RC(11) SPOCK_RC(12) SPOCK_RC(13) SPOCK_RC(14) SPOCK_RC(15) SPOCK_RC(16)
 #undef SPOCK_RC
@@ -144,11 +142,10 @@ SPOCK_RB_INST(double)
 SPOCK_RB_INST(float)
 #undef SPOCK_RB_INST
 
-template void launch_round_commit<double>(SmState*, double*, double*, double*, double*, const double*,
-                                          const double*, double*, double*, int64_t, int64_t, int, double*, int,
-                                          cudaStream_t);
-template void launch_round_commit<float>(SmState*, float*, float*, float*, float*, const float*, const float*,
-                                         float*, float*, int64_t, int64_t, int, double*, int, cudaStream_t);
+template void launch_round_commit<double>(SmState*, double*, double*, const double*, const double*, double*,
+                                          double*, int64_t, int64_t, int, double*, int, cudaStream_t);
+template void launch_round_commit<float>(SmState*, float*, float*, const float*, const float*, float*, float*,
+                                         int64_t, int64_t, int, double*, int, cudaStream_t);
 template void launch_round_point<double>(SmState*, const double*, const double*, double*, const double*, double*,
                                          const double*, int64_t, int64_t, int, int, cudaStream_t);
 template void launch_round_point<float>(SmState*, const float*, const float*, float*, const float*, float*,

@@ -169,9 +169,10 @@ __device__ __forceinline__ void rst(S* p, int64_t q, const typename RPack<S>::T&
 // Commit an accepted (Vt, TVt) and, with op_aa, write the new Anderson
 // column (slot st->aa_slot) and the dot products of the stored columns with
 // it and with the new residual (terms in S, FP64 accumulation per pack).
+// The Anderson differences are formed from the old (V, TV) as it is read, so
+// the previous pair is not kept.
 template <typename S, int MEM>
 __device__ __forceinline__ void round_commit_body(SmState* st, S* __restrict__ V, S* __restrict__ TV,
-                                                  S* __restrict__ Vp, S* __restrict__ TVp,
                                                   const S* __restrict__ Vt, const S* __restrict__ TVt,
                                                   S* __restrict__ MR, S* __restrict__ D, int64_t n, int64_t ld,
                                                   double* __restrict__ partials, int bid, int nblk) {
@@ -188,8 +189,6 @@ __device__ __forceinline__ void round_commit_body(SmState* st, S* __restrict__ V
   const int64_t npack = n / NP;
   for (int64_t q = gt; q < npack; q += stride) {
     PT nv = rld(Vt, q), nt = rld(TVt, q), ov = rld(V, q), ot = rld(TV, q);
-    rst(Vp, q, ov);
-    rst(TVp, q, ot);
     rst(V, q, nv);
     rst(TV, q, nt);
     if (MEM > 0 && aa) {
@@ -220,8 +219,6 @@ __device__ __forceinline__ void round_commit_body(SmState* st, S* __restrict__ V
   }
   for (int64_t i = npack * NP + gt; i < n; i += stride) {  // tail
     const S nv = Vt[i], nt = TVt[i], ov = V[i], ot = TV[i];
-    Vp[i] = ov;
-    TVp[i] = ot;
     V[i] = nv;
     TV[i] = nt;
     if (MEM > 0 && aa) {

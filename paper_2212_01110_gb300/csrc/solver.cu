@@ -327,8 +327,6 @@ static BInst<S> make_binst(Problem& P, Workspace* ws, double alpha) {
   b.st = ws->st;
   b.V = (S*)ws->v[0];
   b.TV = (S*)ws->Tv[0];
-  b.Vp = (S*)ws->v[1];
-  b.TVp = (S*)ws->Tv[1];
   b.Vt = (S*)ws->v[2];
   b.TVt = (S*)ws->Tv[2];
   b.d = (S*)ws->d;
@@ -619,8 +617,6 @@ static int solve_graph(Problem& P, const double* x0_dev, const spock_settings& s
   Ctx c{&P, ws, alpha, st, P.idx.stage_begin};
   S* V = (S*)ws->v[0];
   S* TV = (S*)ws->Tv[0];
-  S* Vp = (S*)ws->v[1];
-  S* TVp = (S*)ws->Tv[1];
   S* Vt = (S*)ws->v[2];
   S* TVt = (S*)ws->Tv[2];
   S* d = (S*)ws->d;
@@ -676,7 +672,7 @@ static int solve_graph(Problem& P, const double* x0_dev, const spock_settings& s
     Ctx c2 = c;
     c2.st = s2;
     launch_round_decide(ws->st, stats_t, trace_dev, s2);
-    launch_round_commit<S>(ws->st, V, TV, Vp, TVp, Vt, TVt, MR, Dm, nv, ws->ld, mem, ws->paa, grid_v, s2);
+    launch_round_commit<S>(ws->st, V, TV, Vt, TVt, MR, Dm, nv, ws->ld, mem, ws->paa, grid_v, s2);
     launch_round_aa_solve(ws->st, ws->paa, grid_v, s2);
     launch_round_point<S>(ws->st, V, TV, Vt, TVt, d, Dm, nv, ws->ld, mem, grid_v, s2);
     const int64_t before = ws->launches;

@@ -57,7 +57,7 @@ template <typename S>
 struct DevFactors {
   S* Gb = nullptr;   // [n-1][nx][nx+nu]  rows of [Abar^c | B^c], nonroot c
   S* Gf = nullptr;   // [n-1][nx+nu][nx]  transpose of the above
-  S* NB = nullptr;   // [nl][K (nu x nx) | W^T (nu x nx) | Rtilde^-1 (nu x nu)]
+  S* NB = nullptr;   // [nl][K (nu x nx) | K + W^T (nu x nx) | Rtilde^-1 (nu x nu)]
   S* Kt = nullptr;   // [nl][nx][nu]      K^T
   S* qs = nullptr;   // [n][nx]  sqrt(Q) of the edge into the node
   S* rs = nullptr;   // [n][nu]  sqrt(R)
@@ -119,7 +119,7 @@ void build_offsets(const Tree& t, int nx, int nu, Offsets& o);
 // Inputs in internal numbering: A [n][nx][nx], B [n][nx][nu].
 // Outputs (internal numbering):
 //   Gb  [n-1][nx][nx+nu]  [Abar^c | B^c]     (c = 1..n-1)
-//   NB  [nl][K | W^T | Rtilde^-1]
+//   NB  [nl][K | K + W^T | Rtilde^-1]
 // Returns false if some Rtilde is numerically singular (cannot happen for
 // finite data since Rtilde >= I).
 bool riccati_factor(const Tree& t, int nx, int nu, const std::vector<double>& A,

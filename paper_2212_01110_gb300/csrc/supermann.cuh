@@ -49,7 +49,7 @@ enum SmPoint : int32_t { PT_NONE = 0, PT_DIR = 1, PT_LS = 2, PT_K2 = 3, PT_KM = 
 // its orders from the state, so the sequence can be captured in a graph.
 void launch_round_decide(SmState* st, const double* stats_t, int32_t* trace, cudaStream_t s);
 template <typename S>
-void launch_round_commit(SmState* st, S* V, S* TV, S* Vp, S* TVp, const S* Vt, const S* TVt, S* MR, S* D,
+void launch_round_commit(SmState* st, S* V, S* TV, const S* Vt, const S* TVt, S* MR, S* D,
                          int64_t n, int64_t ld, int mem, double* partials, int grid, cudaStream_t s);
 void launch_round_aa_solve(SmState* st, const double* partials, int nblocks, cudaStream_t s);
 template <typename S>

@@ -140,18 +140,22 @@ def small_binary(seed=0, N=3, nx=3, nu=2, a=0.5):
 
 
 def large_tree(seed=0, branching_stages=6, branch=4, N=20, nx=50, nu=20,
-               xlim=5.0, ulim=1.0):
+               xlim=5.0, ulim=1.0, probs="dirichlet"):
     """Branching ``branch`` for the first ``branching_stages`` stages, then one
     child per node, horizon N (defaults: 62,805 nodes, 58,709 nonleaf, 4,096
     scenarios, about 4.3 M state/input variables).  A = 0.95 U with U
     Haar-orthogonal (spectral radius 0.95), B ~ N(0, 1/nx), Q = diag U(0.5, 2),
     R = 0.1 I, Q_N = I, AV@R parameter U(0.1, 0.9) per nonleaf node,
-    Dirichlet(1) child probabilities, |x| <= xlim, |u| <= ulim, x0 ~ N(0,1)."""
+    Dirichlet(1) child probabilities (``probs="uniform"``: 1/branch; the draws
+    of the other data do not change), |x| <= xlim, |u| <= ulim,
+    x0 ~ N(0,1)."""
     rng = np.random.default_rng(seed)
     branching = [branch] * branching_stages + [1] * (N - branching_stages)
     anc, _ = tree_from_branching(branching)
     n = len(anc)
     prob = _conditional_probs(rng, anc, "dirichlet")
+    if probs == "uniform":
+        prob = _conditional_probs(None, anc, "uniform")
     A = 0.95 * _haar_orthogonal(rng, n, nx)
     B = rng.standard_normal((n, nx, nu)) / np.sqrt(nx)
     A[0] = 0.0
@@ -275,14 +279,16 @@ def random_vectors(n_z, n_eta, seed=0, scale=1.0):
     return scale * rng.standard_normal(n_z), scale * rng.standard_normal(n_eta)
 
 
-def batch_instances(seed=0, count=512, max_scenarios=64):
+def batch_instances(seed=0, count=512, max_scenarios=64, probs="uniform"):
     """Heterogeneous batch: per instance a branching factor b ~ U{2,3,4},
     horizon N ~ U{5..15}, nx ~ U{10..30}, nu ~ U{4..10}; the tree branches
     for the first floor(log_b max_scenarios) stages and then has one child
     per node (scenario cap: full trees of branching 4 and horizon 15 would
     have 1.4e9 nodes).  Data as ``large_tree`` (A = 0.95 x Haar-orthogonal,
     B ~ N(0, 1/nx), Q = diag U(0.5, 2), R = 0.1 I, Q_N = I, AV@R a ~ U(0.1, 0.9),
-    Dirichlet child probabilities, |x| <= 5, |u| <= 1, x0 ~ N(0, 1))."""
+    |x| <= 5, |u| <= 1, x0 ~ N(0, 1)) with uniform child probabilities by
+    default (the batched workload states the cost, AV@R and box distributions
+    but not the probabilities)."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
@@ -294,5 +300,6 @@ def batch_instances(seed=0, count=512, max_scenarios=64):
         while b ** (stages + 1) <= max_scenarios:
             stages += 1
         stages = min(stages, N)
-        out.append(large_tree(seed=1000 * seed + i, branching_stages=stages, branch=b, N=N, nx=nx, nu=nu))
+        out.append(large_tree(seed=1000 * seed + i, branching_stages=stages, branch=b, N=N, nx=nx, nu=nu,
+                              probs=probs))
     return out
