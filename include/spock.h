@@ -314,6 +314,42 @@ int spock_grad_dev(spock_problem* p, const double* z, const double* eta, int32_t
                    double* g_A, double* g_B, double* g_Q, double* g_R, double* g_QN, void* stream);
 
 /*
+ * spock_adjoint_dev -- gradient of phi(z*) = <g, z*> for any linear function
+ * of the solution (g_z = NULL: phi = s^0, the optimal cost V*) with respect
+ * to the problem data, by implicit differentiation of the CP fixed point
+ * v* = T(v*) of Eq. (chambolle-pock-operator): the adjoint w = J^T w + (g, 0)
+ * is iterated from w = 0 with J the Jacobian of T at the converged pair
+ * (z, eta) (device buffers, FP64, e.g. the output of spock_solve_dev).  J^T
+ * is applied with the library's kernels: the Jacobians of the cone
+ * projections of S3 at eta + alpha L z, L*, the Jacobian of prox_{alpha f}
+ * (the homogeneous Riccati pass of Algorithm 2 and proj_S2) and L.  Then
+ *   d phi/d x0    = mu^0,
+ *   d phi/d A^c   = nu^c p_x^anc(c)T + mu^c x*^anc(c)T,  B^c likewise with u,
+ *   d phi/d Q^c_kk = alpha (q_{c,Qx,k} x*^anc_k - eta_{c,Qx,k} p_{x^anc,k})
+ *                    / (2 sqrt Q^c_kk),  R^c and Q_N^j likewise,
+ * with q = B w_eta, r = w_z + 2 alpha L* q, p = (Jacobian of prox_f) r, mu and
+ * nu the multipliers of the dynamics for r - p and for -alpha L* eta (tree
+ * recursions on the stored factors).  For phi = s^0 the result equals
+ * spock_grad_dev's (envelope theorem); for other phi (a component of the
+ * first input u^0, say) it is the derivative of the solution map.
+ *   g_z        : [n_z] device, the gradient of phi in z (NULL: e_{s^0}).
+ *   max_iter, tol : the iteration stops when max|w_new - w| <=
+ *                tol max(1, max|w|) (checked every 20 iterations).
+ *   outputs    : as spock_grad_dev (device, FP64, caller's numbering, any
+ *                may be NULL); iterations, residual (optional host pointers)
+ *                receive the iterations run and the final relative change.
+ * Returns SPOCK_OK when the tolerance is met, SPOCK_MAX_ITER at the cap
+ * (gradients written), SPOCK_ERR_NUMERICAL if the iteration diverges (the
+ * fixed point must be one where T is differentiable and I - J^T invertible
+ * on the data's directions).  Uses the problem's Riccati scratch: not
+ * concurrent with solves on the same problem.  Device vectors are allocated
+ * on the first call and kept by the problem.  Blocking.
+ */
+int spock_adjoint_dev(spock_problem* p, const double* z, const double* eta, const double* g_z, int32_t max_iter,
+                      double tol, double* g_x0, double* g_A, double* g_B, double* g_Q, double* g_R, double* g_QN,
+                      int32_t* iterations, double* residual, void* stream);
+
+/*
  * spock_grad -- spock_grad_dev with host buffers: z [n_z] and eta [n_eta]
  * are copied to the device, the gradients (same layout as spock_grad_dev)
  * copied back into the non-NULL host outputs.  Device buffers for the

@@ -118,10 +118,12 @@ __global__ void __launch_bounds__(128) k_gradients(KP<S> p, const S* __restrict_
   }
 }
 
+// Multipliers of the dynamics for a right-hand side -w_1: the solution of
+// G^T lambda = -w_{z_1} by the tree recursion above (leaves lambda = -w_x,
+// not stored); lam [nonleaf][xs].
 template <typename S>
-int launch_gradient(const KP<S>& p, const std::vector<int32_t>& stage_begin, const S* z, const S* eta, const S* w,
-                    S* lam, double* gx0, double* gA, double* gB, double* gQ, double* gR, double* gQN, int max_blocks,
-                    cudaStream_t st) {
+int launch_lambda(const KP<S>& p, const std::vector<int32_t>& stage_begin, const S* w, S* lam, int max_blocks,
+                  cudaStream_t st) {
   const int sl = (p.nx + p.nu + 31) / 32;
   int launches = 0;
   for (int t = p.N - 1; t >= 0; --t) {
@@ -135,6 +137,18 @@ int launch_gradient(const KP<S>& p, const std::vector<int32_t>& stage_begin, con
     }
     ++launches;
   }
+  return launches;
+}
+template int launch_lambda<double>(const KP<double>&, const std::vector<int32_t>&, const double*, double*, int,
+                                   cudaStream_t);
+template int launch_lambda<float>(const KP<float>&, const std::vector<int32_t>&, const float*, float*, int,
+                                  cudaStream_t);
+
+template <typename S>
+int launch_gradient(const KP<S>& p, const std::vector<int32_t>& stage_begin, const S* z, const S* eta, const S* w,
+                    S* lam, double* gx0, double* gA, double* gB, double* gQ, double* gR, double* gQN, int max_blocks,
+                    cudaStream_t st) {
+  const int launches = launch_lambda<S>(p, stage_begin, w, lam, max_blocks, st);
   const int grid = std::max(1, std::min((p.n + kWarpsPerBlock - 1) / kWarpsPerBlock, max_blocks));
   k_gradients<S><<<grid, 128, 0, st>>>(p, z, eta, w, lam, gx0, gA, gB, gQ, gR, gQN);
   return launches + 1;

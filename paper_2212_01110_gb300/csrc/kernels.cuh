@@ -123,6 +123,7 @@ struct KP {
   const S* __restrict__ uhi;
   const S* __restrict__ av;
   const S* __restrict__ prob;
+  const S* __restrict__ s2inv;   // per nonleaf node: 1 / (a^2 + 3), 1 / (a^2 + 3 + m)
   S* __restrict__ xbar;
   S* __restrict__ ubar;
   S* __restrict__ q;

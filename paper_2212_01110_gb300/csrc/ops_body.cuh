@@ -108,7 +108,6 @@ __device__ __forceinline__ void lstar_body(const KP<S>& p, int bid, int nblk, co
         // ker [E^T, -I, -I] with (M M^T)^-1 = (I - 11^T / (c + m)) / c,
         // c = a^2 + 3 (Sherman-Morrison); M w = a y1 - y2 + y3 - tau - s per child.
         const S a = p.av[k];
-        const S cc = a * a + S(3);
         const S y3 = z[z2 + 2 * m] - al * (E(el + 2 * m) - sb);
         auto bars = [&](int jc, S& y1, S& y2, S& ta, S& sv) {
           S tl, sl;
@@ -130,8 +129,8 @@ __device__ __forceinline__ void lstar_body(const KP<S>& p, int bid, int nblk, co
           sumMw += a * b1 - b2 + y3 - bt - bs;
         }
         sumMw = warp_sum(sumMw);
-        const S inv_cc = S(1) / cc;
-        const S shift = sumMw / (cc + S(m));
+        const S inv_cc = p.s2inv[2 * (int64_t)k];                // 1 / cc, precomputed
+        const S shift = sumMw * p.s2inv[2 * (int64_t)k + 1];     // sumMw / (cc + m)
         S sumlam = 0;
         if (lane < m) {
           const S lam = (a * y1 - y2 + y3 - ta - sv - shift) * inv_cc;

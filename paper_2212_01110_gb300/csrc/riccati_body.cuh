@@ -80,7 +80,7 @@ __device__ __forceinline__ void node_bwd(const KP<S>& p, int k, const S (&h)[SL]
 #pragma unroll
     for (int s = 0; s < SL; ++s) {
       const int r = 32 * s + lane;
-      if (r < nx) qn[s] += __ldg(cr + r) * db - __ldg(kr + r) * ub;
+      if (r < nx) qn[s] = fma(-__ldg(kr + r), ub, fma(__ldg(cr + r), db, qn[s]));   // two FMAs, no add
     }
   }
   __syncwarp();

@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(kGrpThreads* kMaxGroups) k_bwd_chain_grp(KP<S>
 #pragma unroll
         for (int s = 0; s < SLG; ++s) {
           const int r = sub * 32 + lane + s * kGrpThreads;
-          if (r < nx) qn[s] += cr[r] * db - kr[r] * u;
+          if (r < nx) qn[s] = fma(-kr[r], u, fma(cr[r], db, qn[s]));   // two FMAs, no add
         }
       }
       // every warp has finished reading vq in phase A (barrier above)

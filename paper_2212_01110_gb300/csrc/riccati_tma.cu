@@ -82,7 +82,7 @@ __device__ __forceinline__ void sm_node_bwd(const KP<S>& p, int k, const S (&h)[
 #pragma unroll
     for (int s = 0; s < SL; ++s) {
       const int r = 32 * s + lane;
-      if (r < nx) qn[s] += cr[r] * db - kr[r] * u;
+      if (r < nx) qn[s] = fma(-kr[r], u, fma(cr[r], db, qn[s]));   // two FMAs, no add
     }
   }
   __syncwarp();

@@ -303,6 +303,7 @@ static KP<S> make_kp(const Problem& P, double alpha, const int32_t* stage_begin_
   k.uhi = f.uhi;
   k.av = f.av;
   k.prob = f.prob;
+  k.s2inv = f.s2inv;
   k.xbar = f.xbar;
   k.ubar = f.ubar;
   k.q = f.q;
@@ -1424,6 +1425,20 @@ static int batch_solve(Batch& B, const double* const* x0, const spock_settings& 
 }
 
 template <typename S>
+int launch_lambda(const KP<S>& p, const std::vector<int32_t>& stage_begin, const S* w, S* lam, int max_blocks,
+                  cudaStream_t st);
+void launch_cone_jac(const KP<double>& p, const double* wbar, const double* x, double* out, int grid,
+                     cudaStream_t st);
+void launch_axpy(int64_t n, double a, const double* x, const double* y, double* out, int grid, cudaStream_t st);
+void launch_adj_update(int64_t nz, int64_t ne, double alpha, const double* pz, const double* t, const double* g,
+                       const double* q, const double* Lp, double* w, unsigned long long* red, int grid,
+                       cudaStream_t st);
+void launch_adj_gradients(const KP<double>& p, const double* z, const double* eta, const double* q,
+                          const double* pv, const double* lam_mu, const double* negy, const double* lam_env,
+                          const double* wenv, double* gx0, double* gA, double* gB, double* gQ, double* gR,
+                          double* gQN, int grid, cudaStream_t st);
+
+template <typename S>
 int launch_gradient(const KP<S>& p, const std::vector<int32_t>& stage_begin, const S* z, const S* eta, const S* w,
                     S* lam, double* gx0, double* gA, double* gB, double* gQ, double* gR, double* gQN, int max_blocks,
                     cudaStream_t st);
@@ -1453,6 +1468,108 @@ static int grad_impl(Problem& P, const double* z, const double* eta, double* gx0
   check_launch();
   CUDA_TRY(cudaStreamSynchronize(st));
   return SPOCK_OK;
+}
+
+// Adjoint of the CP fixed point (implicit differentiation of v* = T(v*)):
+// w = J^T w + (g, 0) iterated from w = 0, J the Jacobian of T at the
+// converged pair (z, eta); then the gradient of <g, z*> in x0, A, B and the
+// diagonals of Q, R, Q_N (adjoint.cu).  One iteration: q = B w_eta (cone
+// Jacobians), t = L* q, r = w_z + 2 alpha t, p = A r (the prox-of-f kernels
+// with alpha = 0 and x0 = 0: the homogeneous Riccati pass and proj_S2),
+// L p, then w = (p - alpha t + g, q - alpha L p).
+static int adjoint_impl(Problem& P, const double* z, const double* eta, const double* gz, int max_iter, double tol,
+                        double* gx0, double* gA, double* gB, double* gQ, double* gR, double* gQN,
+                        int32_t* iters_out, double* res_out, cudaStream_t st) {
+  Workspace* ws = get_ws_impl<double>(P, 0);
+  const int64_t nz = P.off.n_z, ne = P.off.n_eta;
+  const size_t n = (size_t)P.tree.n, nx = (size_t)P.nx, nu = (size_t)P.nu;
+  const size_t xs = (size_t)P.f64.xs;
+  const size_t len = (size_t)(nz + ne) + 3 * (size_t)ne + 6 * (size_t)nz + 2 * n * xs + xs + 2;
+  if (!P.adj) {
+    CUDA_TRY(cudaMalloc(&P.adj, sizeof(double) * len));
+    P.allocations.push_back(P.adj);
+  }
+  double* w = P.adj;
+  double* wbar = w + nz + ne;
+  double* q = wbar + ne;
+  double* Lp = q + ne;
+  double* t = Lp + ne;
+  double* r = t + nz;
+  double* pv = r + nz;
+  double* g = pv + nz;
+  double* negy = g + nz;
+  double* wenv = negy + nz;
+  double* lam_mu = wenv + nz;
+  double* lam_env = lam_mu + n * xs;
+  double* zero_x0 = lam_env + n * xs;
+  unsigned long long* red = reinterpret_cast<unsigned long long*>(zero_x0 + xs);
+  const double alpha = default_alpha(P, 0.0);
+  KP<double> kp = make_kp<double>(P, alpha, P.idx.stage_begin);
+  KP<double> kA = kp;   // Jacobian of prox_{alpha f}: no shift of s^0, x0 = 0
+  kA.alpha = 0.0;
+  kA.inv_alpha = 0.0;
+  kA.x0 = zero_x0;
+  const int maxb = sm_count() * 16;
+  const int gnode = std::min((P.tree.n + 3) / 4, maxb);
+  const int gvec = sm_count() * 4;
+  CUDA_TRY(cudaMemsetAsync(zero_x0, 0, sizeof(double) * xs, st));
+  // wbar = eta + alpha L z (the point of prox_{alpha g*} at the fixed point)
+  launch_dual<double>(kp, DM_APPLY_L_, false, z, nullptr, nullptr, Lp, nullptr, nullptr, gnode, st);
+  launch_axpy(ne, alpha, Lp, eta, wbar, gvec, st);
+  if (gz) {
+    CUDA_TRY(cudaMemcpyAsync(g, gz, sizeof(double) * nz, cudaMemcpyDeviceToDevice, st));
+  } else {
+    const double one = 1.0;
+    CUDA_TRY(cudaMemsetAsync(g, 0, sizeof(double) * nz, st));
+    CUDA_TRY(cudaMemcpyAsync(g, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  CUDA_TRY(cudaMemsetAsync(w, 0, sizeof(double) * (nz + ne), st));
+  const double* zero_eta = (const double*)ws->zero_eta;
+  auto jt_parts = [&]() {   // q, t, r, p, L p from the current w
+    launch_cone_jac(kp, wbar, w + nz, q, gnode, st);
+    launch_lstar<double>(kp, q, t, gnode, st);
+    launch_axpy(nz, 2.0 * alpha, t, w, r, gvec, st);
+    launch_prep<double>(kA, r, zero_eta, pv, maxb, st);
+    launch_riccati<double>(kA, P.tree.stage_begin, P.tree.stage_maxch, pv, st, nullptr);
+    launch_dual<double>(kp, DM_APPLY_L_, false, pv, nullptr, nullptr, Lp, nullptr, nullptr, gnode, st);
+  };
+  constexpr int kCheckEvery = 20;
+  int it = 0;
+  double diff = INFINITY, mag = 0.0;
+  for (; it < max_iter;) {
+    const bool check = (it + 1) % kCheckEvery == 0 || it + 1 == max_iter;
+    jt_parts();
+    if (check) CUDA_TRY(cudaMemsetAsync(red, 0, 2 * sizeof(unsigned long long), st));
+    launch_adj_update(nz, ne, alpha, pv, t, g, q, Lp, w, check ? red : nullptr, gvec, st);
+    ++it;
+    if (check) {
+      unsigned long long h[2];
+      CUDA_TRY(cudaMemcpyAsync(h, red, sizeof(h), cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(cudaStreamSynchronize(st));
+      std::memcpy(&diff, &h[0], sizeof(double));
+      std::memcpy(&mag, &h[1], sizeof(double));
+      if (!std::isfinite(diff)) return fail(SPOCK_ERR_NUMERICAL, "the adjoint iteration diverged");
+      if (diff <= tol * std::max(1.0, mag)) break;
+    }
+  }
+  // data derivatives from the final w
+  jt_parts();
+  launch_axpy(nz, -1.0, r, pv, negy, gvec, st);                    // negy = p - r
+  launch_lambda<double>(kp, P.tree.stage_begin, negy, lam_mu, maxb, st);
+  launch_lstar<double>(kp, eta, wenv, gnode, st);                  // wenv = L* eta
+  launch_lambda<double>(kp, P.tree.stage_begin, wenv, lam_env, maxb, st);
+  if (gA) CUDA_TRY(cudaMemsetAsync(gA, 0, sizeof(double) * n * nx * nx, st));
+  if (gB) CUDA_TRY(cudaMemsetAsync(gB, 0, sizeof(double) * n * nx * nu, st));
+  if (gQ) CUDA_TRY(cudaMemsetAsync(gQ, 0, sizeof(double) * n * nx, st));
+  if (gR) CUDA_TRY(cudaMemsetAsync(gR, 0, sizeof(double) * n * nu, st));
+  if (gQN) CUDA_TRY(cudaMemsetAsync(gQN, 0, sizeof(double) * n * nx, st));
+  launch_adj_gradients(kp, z, eta, q, pv, lam_mu, negy, lam_env, wenv, gx0, gA, gB, gQ, gR, gQN, gnode, st);
+  check_launch();
+  CUDA_TRY(cudaStreamSynchronize(st));
+  check_device_flag(P, st);
+  if (iters_out) *iters_out = it;
+  if (res_out) *res_out = diff / std::max(1.0, mag);
+  return diff <= tol * std::max(1.0, mag) ? SPOCK_OK : SPOCK_MAX_ITER;
 }
 
 // ---------------------------------------------------------------------------
@@ -1516,6 +1633,15 @@ static void upload_factors(Problem& P, DevFactors<S>& f, const std::vector<doubl
   f.av = upload(P, cast(par[7]));
   f.prob = upload(P, cast(par[8]));
   const Tree& t = P.tree;
+  {  // reciprocals of the Sherman-Morrison closed form of proj_S2 (one pair per node)
+    std::vector<S> inv(2 * (size_t)t.n, S(0));
+    for (int32_t k = 0; k < t.n_nonleaf; ++k) {
+      const double a = par[7][k], c = a * a + 3.0;
+      inv[2 * (size_t)k] = (S)(1.0 / c);
+      inv[2 * (size_t)k + 1] = (S)(1.0 / (c + t.ch_count[k]));
+    }
+    f.s2inv = upload(P, inv);
+  }
   f.xbar = dalloc<S>(P, (size_t)t.n * f.xs);
   f.ubar = dalloc<S>(P, (size_t)t.n_nonleaf * f.us);
   f.q = dalloc<S>(P, (size_t)t.n * f.xs);
@@ -2135,6 +2261,19 @@ int spock_grad(spock_problem* p, const double* z, const double* eta, int32_t pre
     for (const auto& o : outs)
       if (o.host) CUDA_TRY(cudaMemcpy(o.host, o.dev, sizeof(double) * o.len, cudaMemcpyDeviceToHost));
     return SPOCK_OK;
+  });
+}
+
+int spock_adjoint_dev(spock_problem* p, const double* z, const double* eta, const double* g_z, int32_t max_iter,
+                      double tol, double* g_x0, double* g_A, double* g_B, double* g_Q, double* g_R, double* g_QN,
+                      int32_t* iterations, double* residual, void* stream) {
+  return guarded([&]() -> int {
+    Problem* P = as_problem(p);
+    if (!P || !z || !eta) return fail(SPOCK_ERR_INVALID_ARG, "NULL argument");
+    if (max_iter < 1 || !(tol > 0.0)) return fail(SPOCK_ERR_INVALID_ARG, "need max_iter >= 1 and tol > 0");
+    CUDA_TRY(cudaSetDevice(P->device));
+    return adjoint_impl(*P, z, eta, g_z, max_iter, tol, g_x0, g_A, g_B, g_Q, g_R, g_QN, iterations, residual,
+                        (cudaStream_t)stream);
   });
 }
 

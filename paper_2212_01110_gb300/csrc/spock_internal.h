@@ -66,6 +66,7 @@ struct DevFactors {
   S* ulo = nullptr; S* uhi = nullptr;   // [n][nu]
   S* av = nullptr;   // [n] AV@R parameter
   S* prob = nullptr; // [n] conditional probability
+  S* s2inv = nullptr; // [n][2] 1 / c and 1 / (c + m_i), c = a_i^2 + 3 (closed form of proj_S2^i)
   // scratch of the Riccati passes
   S* xbar = nullptr;  // [n][nx]
   S* ubar = nullptr;  // [nl][nu]
@@ -105,6 +106,7 @@ struct Problem {
   double* io_z = nullptr;
   double* io_eta = nullptr;
   double* io_grad = nullptr;   // outputs of spock_grad (host-buffer variant)
+  double* adj = nullptr;       // vectors of the adjoint iteration (spock_adjoint_dev)
   // solver workspace, allocated on first use per precision
   struct Workspace* ws64 = nullptr;
   struct Workspace* ws32 = nullptr;

@@ -84,6 +84,7 @@ _sig = {
     "spock_T_dev": ([_P, _P, C.c_double, _P, _P, _P, _P, _P], C.c_int),
     "spock_grad_dev": ([_P, _P, _P, C.c_int32, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "spock_grad": ([_P, _D, _D, C.c_int32, _D, _D, _D, _D, _D, _D], C.c_int),
+    "spock_adjoint_dev": ([_P, _P, _P, _P, C.c_int32, C.c_double] + [_P] * 6 + [_I32, _D, _P], C.c_int),
     "spock_batch_create": ([C.c_int32, C.POINTER(_P), C.POINTER(_P)], C.c_int),
     "spock_batch_solve_dev": ([_P, C.POINTER(_P), C.POINTER(Settings), C.POINTER(_P), C.POINTER(_P), C.c_int32,
                                C.POINTER(Info)], C.c_int),
@@ -248,6 +249,21 @@ def spock_grad_dev(problem, z, eta, precision, g_x0=None, g_A=None, g_B=None, g_
     _check(_lib.spock_grad_dev(problem, _tptr(z, dtype=torch.float64), _tptr(eta, dtype=torch.float64),
                                int(precision), ptr(g_x0), ptr(g_A), ptr(g_B), ptr(g_Q), ptr(g_R), ptr(g_QN),
                                _stream(stream)))
+
+
+def spock_adjoint_dev(problem, z, eta, g_z=None, max_iter=20000, tol=1e-10, g_x0=None, g_A=None, g_B=None,
+                      g_Q=None, g_R=None, g_QN=None, stream=None):
+    """Gradient of <g_z, z*> (default: the optimal cost) by the adjoint of the
+    CP fixed point; device float64 tensors.  Returns (status, iterations,
+    final relative change of the adjoint)."""
+    import torch
+    ptr = lambda t: None if t is None else _tptr(t, dtype=torch.float64)
+    its, res = C.c_int32(), C.c_double()
+    rc = _lib.spock_adjoint_dev(problem, _tptr(z, dtype=torch.float64), _tptr(eta, dtype=torch.float64), ptr(g_z),
+                                int(max_iter), float(tol), ptr(g_x0), ptr(g_A), ptr(g_B), ptr(g_Q), ptr(g_R),
+                                ptr(g_QN), C.byref(its), C.byref(res), _stream(stream))
+    _check(rc, (SPOCK_OK, SPOCK_MAX_ITER))
+    return rc, its.value, res.value
 
 
 def spock_grad(problem, z, eta, precision, g_x0=None, g_A=None, g_B=None, g_Q=None, g_R=None, g_QN=None):
