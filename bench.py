@@ -269,15 +269,24 @@ def run_ours(args, rank, world, local_rank):
            "api": "spock_solve: host buffers (pinned), x0 copied in and (z, eta) copied out inside the timed "
                   "call, K iterations from a cold start"}
 
-    paper = paper_workload(args, spock, workloads, dev) if (rank == 0 and args.paper_workload) else None
-    mpc_res = closed_loop_workload(args, spock, workloads, dev) if (rank == 0 and args.mpc_realisations > 0) else None
-    small = small_workload(args, spock, workloads, dev) if rank == 0 else None
-    batch = batch_workload(args, spock, workloads, dev, seed=rank) if args.batch > 0 else None
-    grad = grad_workload(args, spock, workloads, dev) if (rank == 0 and args.grad_instances > 0) else None
+    def section(name, fn):
+        t_s = time.time()
+        res = fn()
+        print(f"[bench] {name}: {time.time() - t_s:.1f} s", file=sys.stderr, flush=True)
+        return res
+
+    paper = section("paper workload", lambda: paper_workload(args, spock, workloads, dev)) \
+        if (rank == 0 and args.paper_workload) else None
+    mpc_res = section("closed loop", lambda: closed_loop_workload(args, spock, workloads, dev)) \
+        if (rank == 0 and args.mpc_realisations > 0) else None
+    small = section("small tree", lambda: small_workload(args, spock, workloads, dev)) if rank == 0 else None
+    batch = section("batch", lambda: batch_workload(args, spock, workloads, dev, seed=rank)) if args.batch > 0 else None
+    grad = section("gradient", lambda: grad_workload(args, spock, workloads, dev)) \
+        if (rank == 0 and args.grad_instances > 0) else None
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(d, seconds=args.cpu_seconds)
+        cpu = section("cpu baseline", lambda: cpu_baseline(d, seconds=args.cpu_seconds))
 
     if rank == 0:
         h = out[head]
@@ -527,8 +536,9 @@ def batch_workload(args, spock, workloads, dev, seed=0):
                    "median_xi": float(np.median([i.xi for i in infos])),
                    "mode": "persistent (one launch, one block per instance)" if infos[0].n_launches == 1
                            else "work-list kernels, %d launches" % infos[0].n_launches}
-        if args.batch_tol_iter > 0:
-            # every instance from a cold start to xi <= 1e-6 (iteration cap per instance)
+        if args.batch_tol_iter > 0 and prec == spock.SPOCK_FP32:
+            # every instance from a cold start to xi <= 1e-6 (iteration cap per
+            # instance); the batched form is the FP32 one
             st = spock.spock_default_settings(precision=prec, max_iter=args.batch_tol_iter, memory=args.memory,
                                               fp64_tail=0)
             torch.cuda.synchronize()
@@ -613,7 +623,7 @@ def grad_workload(args, spock, workloads, dev):
     d = ds[0]
     P = spock.Problem(d)
     tight = spock.spock_default_settings(precision=spock.SPOCK_FP64, eps_abs=1e-12, eps_rel=1e-12, memory=5,
-                                         max_iter=200000)
+                                         max_iter=50000)
 
     def solve(PP, x0):
         z = torch.zeros(PP.n_z, dtype=torch.float64, device=dev)
@@ -655,6 +665,33 @@ def grad_workload(args, spock, workloads, dev):
     P.close()
     torch.cuda.empty_cache()
     return out
+
+
+def host_cpu():
+    """Cores this process may use and the CPU model of the host."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+        for key in ("model name", "Model name", "CPU part"):
+            hits = [ln.split(":", 1)[1].strip() for ln in info if ln.startswith(key)]
+            if hits:
+                model = hits[0] if key != "CPU part" else f"Arm CPU part {hits[0]}"
+                break
+    except Exception:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return cores, model or "unknown"
 
 
 def cpu_baseline(d, seconds=10.0, threads=None):
@@ -741,11 +778,11 @@ def main():
     ap.add_argument("--paper-workload", type=int, default=1,
                     help="also time SPOCK to tolerance on the paper's data-center system (1) or not (0)")
     ap.add_argument("--paper-max-iter", type=int, default=20000)
-    ap.add_argument("--mpc-realisations", type=int, default=5,
+    ap.add_argument("--mpc-realisations", type=int, default=3,
                     help="disturbance sequences of the closed-loop MPC measurement (0 skips it; the paper uses 15)")
     ap.add_argument("--batch", type=int, default=512, help="instances of the batched measurement (0 skips it)")
     ap.add_argument("--batch-iter", type=int, default=50)
-    ap.add_argument("--batch-tol-iter", type=int, default=20000,
+    ap.add_argument("--batch-tol-iter", type=int, default=10000,
                     help="iteration cap of the batched time-to-1e-6 solve (0 skips it)")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batched measurement and print it (profiling aid, not a bench line)")

@@ -53,3 +53,16 @@ def test_replica_reduce_world2():
 def test_replica_reduce_single_process():
     import bench
     assert bench.replica_reduce(3.5, 7, None) == (3.5, 7.0)
+
+
+def test_cpu_baseline_leg_runs_on_the_host():
+    """bench.py's CPU baseline (the oracle's C++ operator) on a small tree of
+    the benchmark family: the fields the bench line reports."""
+    import bench
+    from paper_2212_01110_gb300 import workloads
+    cores, model = bench.host_cpu()
+    assert cores >= 1 and isinstance(model, str)
+    d = workloads.large_tree(seed=0, branching_stages=1, branch=4, N=6, nx=5, nu=2)
+    out = bench.cpu_baseline(d, seconds=0.2, threads=2)
+    assert out["kind"] == "oracle" and out["value"] > 0 and out["cores"] == 2
+    assert out["one_thread"]["value"] > 0 and out["nproc"] == cores
