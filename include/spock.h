@@ -406,6 +406,17 @@ int spock_batch_solve_dev(spock_batch* batch, const double* const* x0_dev, const
 int spock_batch_solve(spock_batch* batch, const double* const* x0, const spock_settings* settings,
                       double* const* z_io, double* const* eta_io, int32_t warm, spock_info* infos);
 
+/*
+ * spock_fp64_fma_rate -- measures the FP64 fused multiply-add throughput of
+ * the current device (TFLOP/s, two flops per FMA): the ALU roofline of the
+ * SPOCK_FP64 path.  The paper has no counterpart; it is a measurement
+ * utility.  A kernel of 8 blocks of 256 threads per SM, each thread running
+ * 8 independent FMA chains for `iters` iterations, timed with CUDA events on
+ * `stream` after a warm-up launch.  Blocking.  Errors: INVALID_ARG (iters < 1
+ * or NULL output), CUDA, OOM.
+ */
+int spock_fp64_fma_rate(int32_t iters, double* tflops, void* stream);
+
 /* Frees a handle returned by any *_create call; NULL is a no-op. */
 void spock_free(void* handle);
 

@@ -1424,6 +1424,7 @@ static int batch_solve(Batch& B, const double* const* x0, const spock_settings& 
   return status;
 }
 
+int fp64_fma_rate(int iters, double* tflops, cudaStream_t st);
 template <typename S>
 int launch_lambda(const KP<S>& p, const std::vector<int32_t>& stage_begin, const S* w, S* lam, int max_blocks,
                   cudaStream_t st);
@@ -2261,6 +2262,13 @@ int spock_grad(spock_problem* p, const double* z, const double* eta, int32_t pre
     for (const auto& o : outs)
       if (o.host) CUDA_TRY(cudaMemcpy(o.host, o.dev, sizeof(double) * o.len, cudaMemcpyDeviceToHost));
     return SPOCK_OK;
+  });
+}
+
+int spock_fp64_fma_rate(int32_t iters, double* tflops, void* stream) {
+  return guarded([&]() -> int {
+    if (iters < 1 || !tflops) return fail(SPOCK_ERR_INVALID_ARG, "need iters >= 1 and an output");
+    return fp64_fma_rate(iters, tflops, (cudaStream_t)stream);
   });
 }
 

@@ -90,6 +90,7 @@ _sig = {
                                C.POINTER(Info)], C.c_int),
     "spock_batch_solve": ([_P, C.POINTER(_D), C.POINTER(Settings), C.POINTER(_D), C.POINTER(_D), C.c_int32,
                            C.POINTER(Info)], C.c_int),
+    "spock_fp64_fma_rate": ([C.c_int32, _D, _P], C.c_int),
     "spock_free": ([_P], None),
     "spock_last_error": ([], C.c_char_p),
 }
@@ -314,6 +315,13 @@ def spock_batch_solve(batch, x0s, settings, zs, etas, warm):
                                 ptrs(zs), ptrs(etas), int(warm), infos)
     _check(rc, (SPOCK_OK, SPOCK_MAX_ITER))
     return list(infos)
+
+
+def spock_fp64_fma_rate(iters=20000, stream=None):
+    """Measured FP64 FMA throughput of the current device in TFLOP/s."""
+    v = C.c_double()
+    _check(_lib.spock_fp64_fma_rate(int(iters), C.byref(v), _stream(stream)))
+    return v.value
 
 
 def spock_free(handle):

@@ -111,3 +111,13 @@ def test_cp_counts_of_L_match_between_cp_and_spock():
     e = torch.zeros(P.n_eta, dtype=torch.float64, device=dev)
     info = spock.spock_solve_dev(P.handle, x0, spock.spock_default_settings(eps_abs=1e-5, eps_rel=1e-5), z, e, 0)
     assert info.status == spock.SPOCK_OK and info.n_L == 2 * info.n_T > 0
+
+
+def test_fp64_fma_rate_is_plausible():
+    """The measured FP64 FMA throughput (the ALU roofline of the FP64 path):
+    positive and within the range of current GPUs (0.1 to 100 TFLOP/s)."""
+    from paper_2212_01110_gb300 import spock
+    v = spock.spock_fp64_fma_rate(2000)
+    assert 0.1 < v < 100.0
+    with pytest.raises(spock.SpockError):
+        spock.spock_fp64_fma_rate(0)
