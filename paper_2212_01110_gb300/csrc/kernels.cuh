@@ -151,6 +151,19 @@ __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
   return v;
 }
+// Sum over lanes [0, n) of v (zero on the other lanes), returned to every
+// lane: ceil(log2 n) adds instead of five (n = 1 is a broadcast of lane 0).
+template <typename S>
+__device__ __forceinline__ S lanes_sum(S v, int n) {
+  for (int o = 1; o < n && o < 32; o <<= 1) v += __shfl_xor_sync(kFull, v, o);
+  return __shfl_sync(kFull, v, 0);
+}
+// Sum of the values held by lanes a and b (different lanes), to every lane.
+template <typename S>
+__device__ __forceinline__ S two_lanes_sum(S v, int a, int b) {
+  return __shfl_sync(kFull, v, a) + __shfl_sync(kFull, v, b);
+}
+
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));

@@ -128,7 +128,7 @@ __device__ __forceinline__ void lstar_body(const KP<S>& p, int bid, int nblk, co
           bars(jc, b1, b2, bt, bs);
           sumMw += a * b1 - b2 + y3 - bt - bs;
         }
-        sumMw = warp_sum(sumMw);
+        sumMw = lanes_sum(sumMw, m);
         const S inv_cc = p.s2inv[2 * (int64_t)k];                // 1 / cc, precomputed
         const S shift = sumMw * p.s2inv[2 * (int64_t)k + 1];     // sumMw / (cc + m)
         S sumlam = 0;
@@ -150,7 +150,7 @@ __device__ __forceinline__ void lstar_body(const KP<S>& p, int bid, int nblk, co
           zo[z2 + 3 * m + 1 + jc] = bs + lam;
           sumlam += lam;
         }
-        sumlam = warp_sum(sumlam);
+        sumlam = lanes_sum(sumlam, m);
         if (lane == 0) {
           zo[z2 + 2 * m] = y3 - sumlam;
           if (k == 0) zo[0] = (z[0] - al * sb) - al;   // prox of alpha * s^0
@@ -346,8 +346,8 @@ __device__ __forceinline__ void dual_body(const KP<S>& p, int bid, int nblk, con
         }
       }
       if (MODE != DM_PROXG) {
-        bs = warp_sum(bs);
-        if (HZP) bsp = warp_sum(bsp);
+        bs = lanes_sum(bs, m);   // lanes < m hold the children's terms
+        if (HZP) bsp = lanes_sum(bsp, m);
       }
       if (lane == 0) {
         const int64_t ie = el + 2 * m + 1;
@@ -563,7 +563,7 @@ __device__ __forceinline__ void dual_fused_body(const KP<S>& p, int bid, int nbl
             else tau_part += re;
           }
         }
-        tau_part = warp_sum(tau_part);
+        tau_part = two_lanes_sum(tau_part, nxu & 31, (nxu + 1) & 31);   // the two tau rows
         if (lane == 0) primal_stat<S, DR>(nacc, ial, rt, tdz, S(0.5) * tau_part);
       }
       if (c >= p.nl) {  // leaf block of c: box on x^c, SOC on (Q_N^1/2 x^c, s^c / 2, s^c / 2)
@@ -639,7 +639,7 @@ __device__ __forceinline__ void dual_fused_body(const KP<S>& p, int bid, int nbl
 #pragma unroll
         for (int j = 0; j < J; ++j)
           if (lane + 32 * j < nx) primal_stat<S, DR>(nacc, ial, rx[j], xdz[j], ltx[j]);
-        s_part = warp_sum(s_part);
+        s_part = two_lanes_sum(s_part, nx & 31, (nx + 1) & 31);   // the two s rows
         if (lane == 0) primal_stat<S, DR>(nacc, ial, rs_, sdz, S(0.5) * s_part);
       }
     }
@@ -656,9 +656,9 @@ __device__ __forceinline__ void dual_fused_body(const KP<S>& p, int bid, int nbl
         bsp += pj * zp[z2 + jj];
         if (DR) bsd += pj * dz[z2 + jj];
       }
-      bs = warp_sum(bs);
-      bsp = warp_sum(bsp);
-      if (DR) bsd = warp_sum(bsd);
+      bs = lanes_sum(bs, m);   // lanes < m hold the children's terms
+      bsp = lanes_sum(bsp, m);
+      if (DR) bsd = lanes_sum(bsd, m);
       const S Lz = sk - (bs + y3), Lzp = skp - (bsp + y3p), Ld = DR ? skd - (bsd + y3d) : S(0);
       const S w = dual_w<S, DM_DUAL>(al, esb, Lz, Lzp);
       const S o = vmin(w, S(0));

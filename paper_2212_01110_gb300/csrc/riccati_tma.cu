@@ -14,7 +14,6 @@
 // Bounded waits: a wait that exceeds kWaitLimit polls sets *p.err, drains the
 // copies the warp has in flight (again bounded) and returns.
 #include <algorithm>
-#include <cstdlib>
 #include <vector>
 
 #include "batch.cuh"
@@ -140,21 +139,8 @@ struct ChainLayout {
   uint32_t gB, nbB, xB, uB, ktB, stageB, warpB;
 };
 
-// Stage buffers per warp of the staged backward chain kernel: 2 (the next
-// step in flight while one is used) or 3 (two steps in flight, fewer warps
-// per SM); SPOCK_CHAIN_STAGES = 2 / 3 selects, default 2.
-constexpr int kMaxChainStages = 3;
-inline int chain_stages_env() {
-  static int ns = [] {
-    const char* e = getenv("SPOCK_CHAIN_STAGES");
-    const int v = e ? atoi(e) : 2;
-    return v == 3 ? 3 : 2;
-  }();
-  return ns;
-}
-
 template <typename S>
-__host__ __device__ inline ChainLayout<S> chain_layout_bwd(const KP<S>& p, int ns = 2) {
+__host__ __device__ inline ChainLayout<S> chain_layout_bwd(const KP<S>& p) {
   ChainLayout<S> L;
   L.gB = p.gstride * sizeof(S);
   L.nbB = p.nbstride * sizeof(S);
@@ -162,7 +148,7 @@ __host__ __device__ inline ChainLayout<S> chain_layout_bwd(const KP<S>& p, int n
   L.uB = p.us * sizeof(S);
   L.ktB = p.ktstride * sizeof(S);
   L.stageB = L.gB + L.nbB + 2 * L.xB + L.uB;  // G | NB | xbar_k | ubar_k | xbar_leaf
-  L.warpB = ns * L.stageB + 4 * kVecPad * sizeof(S);
+  L.warpB = 2 * L.stageB + 4 * kVecPad * sizeof(S);
   return L;
 }
 
@@ -183,25 +169,25 @@ __host__ __device__ inline ChainLayout<S> chain_layout_fwd(const KP<S>& p) {
 // of `nblk` for problem p; every warp owns `slotB` bytes of shared memory
 // (at least its layout's warpB).
 template <typename S, int SL>
-__device__ __forceinline__ void bwd_chain_tma_body(const KP<S>& p, int bid, int nblk, uint32_t slotB, int ns = 2) {
+__device__ __forceinline__ void bwd_chain_tma_body(const KP<S>& p, int bid, int nblk, uint32_t slotB) {
   if (p.skip && *p.skip) return;
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ uint64_t bars[kMaxChainWarps][kMaxChainStages];
+  __shared__ uint64_t bars[kMaxChainWarps][2];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
   const int gw = bid * wpb + wl, nw = nblk * wpb;
   const int nx = p.nx, ncol = p.nx + p.nu;
-  const ChainLayout<S> Ly = chain_layout_bwd(p, ns);
+  const ChainLayout<S> Ly = chain_layout_bwd(p);
   unsigned char* base = smem + (size_t)wl * slotB;
-  S* stg[kMaxChainStages];
-  for (int b = 0; b < kMaxChainStages; ++b) stg[b] = reinterpret_cast<S*>(base + (size_t)b * Ly.stageB);
-  S* vq = reinterpret_cast<S*>(base + (size_t)ns * Ly.stageB);
+  S* stg[2] = {reinterpret_cast<S*>(base), reinterpret_cast<S*>(base + Ly.stageB)};
+  S* vq = reinterpret_cast<S*>(base + 2 * Ly.stageB);
   S* vh = vq + kVecPad;
   S* vg = vh + kVecPad;
   S* vd = vg + kVecPad;
   uint64_t* bar = bars[wl];
   if (lane == 0) {
-    for (int b = 0; b < ns; ++b) mbar_init(&bar[b], 1);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     fence_mbar_init();
   }
   __syncwarp();
@@ -212,40 +198,34 @@ __device__ __forceinline__ void bwd_chain_tma_body(const KP<S>& p, int bid, int 
     const int ci = gw + (j / Lc) * nw;
     const int t = p.N - 1 - (j % Lc);
     const int k = p.stage_begin[t] + ci, c = p.stage_begin[t + 1] + ci;
-    const int b = j % ns;
-    S* dst = stg[b];
+    S* dst = stg[j & 1];
     const bool first = (t == p.N - 1);
     fence_proxy_async();
-    mbar_expect_tx(&bar[b], Ly.gB + Ly.nbB + Ly.xB + Ly.uB + (first ? Ly.xB : 0u));
-    bulk_g2s(dst, p.Gb + (int64_t)(c - 1) * p.gstride, Ly.gB, &bar[b]);
-    bulk_g2s(dst + p.gstride, p.NB + (int64_t)k * p.nbstride, Ly.nbB, &bar[b]);
-    bulk_g2s(dst + p.gstride + p.nbstride, p.xbar + (int64_t)k * p.xs, Ly.xB, &bar[b]);
-    bulk_g2s(dst + p.gstride + p.nbstride + p.xs, p.ubar + (int64_t)k * p.us, Ly.uB, &bar[b]);
-    if (first) bulk_g2s(dst + p.gstride + p.nbstride + p.xs + p.us, p.xbar + (int64_t)c * p.xs, Ly.xB, &bar[b]);
+    mbar_expect_tx(&bar[j & 1], Ly.gB + Ly.nbB + Ly.xB + Ly.uB + (first ? Ly.xB : 0u));
+    bulk_g2s(dst, p.Gb + (int64_t)(c - 1) * p.gstride, Ly.gB, &bar[j & 1]);
+    bulk_g2s(dst + p.gstride, p.NB + (int64_t)k * p.nbstride, Ly.nbB, &bar[j & 1]);
+    bulk_g2s(dst + p.gstride + p.nbstride, p.xbar + (int64_t)k * p.xs, Ly.xB, &bar[j & 1]);
+    bulk_g2s(dst + p.gstride + p.nbstride + p.xs, p.ubar + (int64_t)k * p.us, Ly.uB, &bar[j & 1]);
+    if (first) bulk_g2s(dst + p.gstride + p.nbstride + p.xs + p.us, p.xbar + (int64_t)c * p.xs, Ly.xB, &bar[j & 1]);
   };
-  uint32_t phases = 0;   // bit b: parity of the next completion of buffer b
-  if (lane == 0)
-    for (int j = 0; j < ns - 1 && j < nsteps; ++j) issue(j);
+  uint32_t phase0 = 0, phase1 = 0;
+  if (nsteps > 0 && lane == 0) issue(0);
   for (int j = 0; j < nsteps; ++j) {
     const int ci = gw + (j / Lc) * nw;
     const int t = p.N - 1 - (j % Lc);
     const int k = p.stage_begin[t] + ci;
-    // the buffer of step j + ns - 1 was last read in step j - 1 (warp-synchronised)
-    if (j + ns - 1 < nsteps && lane == 0) issue(j + ns - 1);
-    const int b = j % ns;
-    const uint32_t par = (phases >> b) & 1u;
-    const bool ok = __all_sync(kFull, mbar_wait(&bar[b], par));
-    phases ^= 1u << b;
+    if (j + 1 < nsteps && lane == 0) issue(j + 1);
+    uint32_t& ph = (j & 1) ? phase1 : phase0;
+    const uint32_t par = ph;
+    const bool ok = __all_sync(kFull, mbar_wait(&bar[j & 1], par));
+    ph ^= 1u;
     if (!ok) {  // flag, then drain this warp's copies in flight (bounded) and leave
       flag_timeout(p.err, lane);
-      mbar_wait(&bar[b], par);
-      for (int jj = j + 1; jj < j + ns && jj < nsteps; ++jj) {
-        const int bb = jj % ns;
-        mbar_wait(&bar[bb], (phases >> bb) & 1u);
-      }
+      mbar_wait(&bar[j & 1], par);
+      if (j + 1 < nsteps) mbar_wait(&bar[(j + 1) & 1], (j & 1) ? phase0 : phase1);
       return;
     }
-    const S* G = stg[b];
+    const S* G = stg[j & 1];
     const S* NBk = G + p.gstride;
     const S* xb = NBk + p.nbstride;
     const S* ub = xb + p.xs;
@@ -267,8 +247,8 @@ __device__ __forceinline__ void bwd_chain_tma_body(const KP<S>& p, int bid, int 
 }
 
 template <typename S, int SL>
-__global__ void __launch_bounds__(32 * kMaxChainWarps) k_bwd_chain_tma(KP<S> p, int ns) {
-  bwd_chain_tma_body<S, SL>(p, blockIdx.x, gridDim.x, chain_layout_bwd(p, ns).warpB, ns);
+__global__ void __launch_bounds__(32 * kMaxChainWarps) k_bwd_chain_tma(KP<S> p) {
+  bwd_chain_tma_body<S, SL>(p, blockIdx.x, gridDim.x, chain_layout_bwd(p).warpB);
 }
 
 template <typename S, int SL>
@@ -630,16 +610,14 @@ bool tma_stage_fits(const KP<S>& p) {
 
 template <typename S, int SL>
 int launch_bwd_chain_tma(const KP<S>& p, cudaStream_t st) {
-  int ns = chain_stages_env();
-  if (chain_layout_bwd(p, ns).warpB + 1024 > max_dyn_smem()) ns = 2;
-  const ChainLayout<S> Ly = chain_layout_bwd(p, ns);
+  const ChainLayout<S> Ly = chain_layout_bwd(p);
   int wpb = (int)std::min<size_t>(kMaxChainWarps, (max_dyn_smem() - 1024) / Ly.warpB);
   wpb = std::max(1, wpb);
   const size_t bytes = (size_t)wpb * Ly.warpB;
   static size_t granted = 0;
   allow_smem(k_bwd_chain_tma<S, SL>, bytes, granted);
   int grid = std::min(num_sms(), (p.n_chains + wpb - 1) / wpb);
-  k_bwd_chain_tma<S, SL><<<grid, 32 * wpb, bytes, st>>>(p, ns);
+  k_bwd_chain_tma<S, SL><<<grid, 32 * wpb, bytes, st>>>(p);
   return 1;
 }
 
