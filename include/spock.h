@@ -410,10 +410,11 @@ int spock_batch_solve(spock_batch* batch, const double* const* x0, const spock_s
  * spock_fp64_fma_rate -- measures the FP64 fused multiply-add throughput of
  * the current device (TFLOP/s, two flops per FMA): the ALU roofline of the
  * SPOCK_FP64 path.  The paper has no counterpart; it is a measurement
- * utility.  A kernel of 8 blocks of 256 threads per SM, each thread running
- * 8 independent FMA chains for `iters` iterations, timed with CUDA events on
- * `stream` after a warm-up launch.  Blocking.  Errors: INVALID_ARG (iters < 1
- * or NULL output), CUDA, OOM.
+ * utility.  Kernels of 4 or 8 blocks of 256 threads per SM, each thread
+ * running 8 or 16 independent FMA chains (8 `iters` FMAs per thread), timed
+ * with CUDA events on `stream` after a warm-up launch each; the best of the
+ * four is returned.  Blocking.  Errors: INVALID_ARG (iters < 1 or NULL
+ * output), CUDA, OOM.
  */
 int spock_fp64_fma_rate(int32_t iters, double* tflops, void* stream);
 

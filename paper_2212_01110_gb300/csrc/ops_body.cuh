@@ -26,6 +26,36 @@ constexpr int kMaxJ = (kMaxDim + 2 + 31) / 32;   // entries per lane for the lar
 //   s^0:                  w_nl^0[s - b'y]
 // Body shared by the single-problem and the batched kernels: block `bid` of
 // `nblk` working for problem p.
+// prox-f preparation of the z_2 block of a chain node k (one child): zbar =
+// z - alpha L* eta on (y, tau, s), then the projection on ker [E^T, -I, -I]
+// (the m = 1 case of the closed form in lstar_body), by one lane.
+template <typename S>
+__device__ __forceinline__ void prep_z2_chain(const KP<S>& p, int k, const S* __restrict__ eta,
+                                              const S* __restrict__ z, S* __restrict__ zo) {
+  const S al = p.alpha;
+  const int64_t el = p.enl[k], z2 = p.zz2[k];
+  const int c = p.ch_begin[k];
+  const int64_t er = p.enr[c], es = __ldg(&p.desc[c].es);
+  const int nxu = p.nx + p.nu;
+  const S sb = eta[el + 3];
+  const S tl = S(0.5) * (eta[er + nxu] + eta[er + nxu + 1]);
+  const S sl = (c < p.nl) ? eta[es] : S(0.5) * (eta[es] + eta[es + 1]);
+  const S a = p.av[k];
+  const S y3 = z[z2 + 2] - al * (eta[el + 2] - sb);
+  const S y1 = z[z2] - al * (eta[el] - p.prob[c] * sb);
+  const S y2 = z[z2 + 1] - al * eta[el + 1];
+  const S ta = z[z2 + 3] - al * tl;
+  const S sv = z[z2 + 4] - al * sl;
+  const S mw = a * y1 - y2 + y3 - ta - sv;
+  const S lam = (mw - mw * p.s2inv[2 * (int64_t)k + 1]) * p.s2inv[2 * (int64_t)k];
+  zo[z2] = y1 - a * lam;
+  zo[z2 + 1] = y2 + lam;
+  zo[z2 + 2] = y3 - lam;
+  zo[z2 + 3] = ta + lam;
+  zo[z2 + 4] = sv + lam;
+  if (k == 0) zo[0] = (z[0] - al * sb) - al;   // prox of alpha * s^0 (a tree that is one chain)
+}
+
 template <typename S, int MODE, int J>
 __device__ __forceinline__ void lstar_body(const KP<S>& p, int bid, int nblk, const S* __restrict__ eta,
                                            const S* __restrict__ z, S* __restrict__ zo) {
@@ -37,6 +67,7 @@ __device__ __forceinline__ void lstar_body(const KP<S>& p, int bid, int nblk, co
   const S al = p.alpha;
   auto E = [&](int64_t i) -> S { return eta[i]; };
   auto emit = [&](int64_t zi, S lt) { zo[zi] = lt; };   // LS_APPLY
+  const int kc0 = p.stage_begin[p.chain_stage];          // first node of the chain region
   uint32_t wnext = gw < p.n ? desc_word(p.desc, gw, lane) : 0u;
   for (int k = gw; k < p.n; k += nw) {
     const NodeF D = node_fields(wnext);
@@ -80,7 +111,9 @@ __device__ __forceinline__ void lstar_body(const KP<S>& p, int bid, int nblk, co
           }
         }
       }
-      // ---- z_2 block
+      // ---- z_2 block (chain nodes of the prox-f preparation: one lane per
+      // node after this loop)
+      if (MODE == LS_PREP && k >= kc0) continue;
       const int64_t el = D.enl, z2 = D.zz2;
       const S sb = E(el + 2 * m + 1);
       // child j's tau and s rows of L* w
@@ -170,6 +203,9 @@ __device__ __forceinline__ void lstar_body(const KP<S>& p, int bid, int nblk, co
       }
     }
   }
+  if (MODE == LS_PREP)
+    for (int64_t base = (int64_t)kc0 + 32 * (int64_t)gw; base < p.nl; base += 32 * (int64_t)nw)
+      if (base + lane < p.nl) prep_z2_chain<S>(p, (int)(base + lane), eta, z, zo);
 }
 
 
@@ -419,6 +455,47 @@ __device__ __forceinline__ void primal_stat(NodeAcc<S>& a, S inv_alpha, S rz, S 
   if (DR) a.s[ST_RD] += rz * dv;
 }
 
+// The s - b'y row and the y rows of a chain node k (one child, b = (p, 0, 1))
+// with their residual statistics, by one lane (the m = 1 case of the warp
+// code in dual_fused_body).
+template <typename S, bool DR>
+__device__ __forceinline__ void dual_y_chain(const KP<S>& p, int k, const S* __restrict__ z,
+                                             const S* __restrict__ zp, const S* __restrict__ eta,
+                                             S* __restrict__ out, const S* __restrict__ dz,
+                                             const S* __restrict__ deta, NodeAcc<S>& nacc) {
+  const S al = p.alpha, ial = p.inv_alpha;
+  const int64_t el = p.enl[k], z2 = p.zz2[k], zsk = p.zs[k];
+  const S pr = p.prob[p.ch_begin[k]];
+  S yz[3], yzp[3], yd[3], ye[3], yde[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    yz[e] = z[z2 + e];
+    yzp[e] = zp[z2 + e];
+    yd[e] = DR ? dz[z2 + e] : S(0);
+    ye[e] = eta[el + e];
+    yde[e] = DR ? deta[el + e] : S(0);
+  }
+  const S sk = z[zsk], skp = zp[zsk], skd = DR ? dz[zsk] : S(0);
+  const S esb = eta[el + 3], desb = DR ? deta[el + 3] : S(0);
+  const S Lz = sk - (pr * yz[0] + yz[2]), Lzp = skp - (pr * yzp[0] + yzp[2]);
+  const S Ld = DR ? skd - (pr * yd[0] + yd[2]) : S(0);
+  const S w = dual_w<S, DM_DUAL>(al, esb, Lz, Lzp);
+  const S o = vmin(w, S(0));
+  const S re_sb = esb - o;
+  out[el + 3] = o;
+  dual_stat<S, true, DR>(nacc, ial, esb, o, Lz - Lzp, desb, Ld);
+  primal_stat<S, DR>(nacc, ial, sk - skp, skd, re_sb);
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const S yw = dual_w<S, DM_DUAL>(al, ye[e], yz[e], yzp[e]);
+    const S yo = e < 2 ? vmin(yw, S(0)) : S(0);
+    out[el + e] = yo;
+    dual_stat<S, true, DR>(nacc, ial, ye[e], yo, yz[e] - yzp[e], yde[e], yd[e]);
+    const S bl = e == 0 ? pr : (e == 1 ? S(0) : S(1));
+    primal_stat<S, DR>(nacc, ial, yz[e] - yzp[e], yd[e], (ye[e] - yo) - bl * re_sb);
+  }
+}
+
 template <typename S, bool DIR, int J>
 __device__ __forceinline__ void dual_fused_body(const KP<S>& p, int bid, int nblk, const S* __restrict__ z,
                                                 const S* __restrict__ zp, const S* __restrict__ eta,
@@ -437,11 +514,13 @@ __device__ __forceinline__ void dual_fused_body(const KP<S>& p, int bid, int nbl
   acc.zero();
   NodeAcc<S> nacc;
   nacc.zero();
+  const int kc0 = p.stage_begin[p.chain_stage];   // chain nodes: y rows one lane per node, below
   uint32_t wnext = gw < p.nl ? desc_word(p.desc, gw, lane) : 0u;
   for (int k = gw; k < p.nl; k += nw) {
     const NodeF D = node_fields(wnext);
     if (k + nw < p.nl) wnext = desc_word(p.desc, k + nw, lane);
     const int m = D.m, c0 = D.c0;
+    const bool warp_y = k < kc0;
     const int64_t el = D.enl, ea = el + 2 * m + 2, z2 = D.zz2;
     // ---- loads issued up front with the node's own rows (one memory round
     // trip per node on chains): the first child's nonroot rows and tau, the
@@ -459,18 +538,26 @@ __device__ __forceinline__ void dual_fused_body(const KP<S>& p, int bid, int nbl
     }
     const S ptz = z[z2 + 2 * m + 1], ptzp = zp[z2 + 2 * m + 1], ptdz = DR ? dz[z2 + 2 * m + 1] : S(0);
     S yz0 = 0, yzp0 = 0, yd0 = 0, ye0 = 0, yde0 = 0, pr0 = 0;
-    if (lane < 2 * m + 1) {
-      yz0 = z[z2 + lane];
-      yzp0 = zp[z2 + lane];
-      if (DR) yd0 = dz[z2 + lane];
-      ye0 = eta[el + lane];
-      if (DR) yde0 = deta[el + lane];
-      if (lane < m) pr0 = p.prob[c0 + lane];
-    }
+    S sk = 0, skp = 0, skd = 0, y3 = 0, y3p = 0, y3d = 0, esb = 0, desb = 0;
     const int64_t ie_sb = el + 2 * m + 1;
-    const S sk = z[D.zs], skp = zp[D.zs], skd = DR ? dz[D.zs] : S(0);
-    const S y3 = z[z2 + 2 * m], y3p = zp[z2 + 2 * m], y3d = DR ? dz[z2 + 2 * m] : S(0);
-    const S esb = eta[ie_sb], desb = DR ? deta[ie_sb] : S(0);
+    if (warp_y) {
+      if (lane < 2 * m + 1) {
+        yz0 = z[z2 + lane];
+        yzp0 = zp[z2 + lane];
+        if (DR) yd0 = dz[z2 + lane];
+        ye0 = eta[el + lane];
+        if (DR) yde0 = deta[el + lane];
+        if (lane < m) pr0 = p.prob[c0 + lane];
+      }
+      sk = z[D.zs];
+      skp = zp[D.zs];
+      if (DR) skd = dz[D.zs];
+      y3 = z[z2 + 2 * m];
+      y3p = zp[z2 + 2 * m];
+      if (DR) y3d = dz[z2 + 2 * m];
+      esb = eta[ie_sb];
+      if (DR) desb = deta[ie_sb];
+    }
     // ---- own (x, u) and its box rows.  Per entry the differences r_z = z - z+
     // (the residual, also L r_z of every row of L that reads it, scaled) and
     // q_z = z+ - r_z = 2 z+ - z (the point L is applied to in the dual update)
@@ -648,7 +735,7 @@ __device__ __forceinline__ void dual_fused_body(const KP<S>& p, int bid, int nbl
     for (int j = 0; j < J; ++j)
       if (lane + 32 * j < nxu) primal_stat<S, DR>(nacc, ial, rzv[j], adz[j], lt[j]);
     // ---- the s - b'y row of k (b = (p^children, 0, 1)), then the y rows
-    {
+    if (warp_y) {
       S bs = pr0 * yz0, bsp = pr0 * yzp0, bsd = DR ? pr0 * yd0 : S(0);
       for (int jj = lane + 32; jj < m; jj += 32) {  // nodes with more than 32 children
         const S pj = p.prob[c0 + jj];
@@ -680,6 +767,10 @@ __device__ __forceinline__ void dual_fused_body(const KP<S>& p, int bid, int nbl
       for (int e = lane + 32; e < 2 * m + 1; e += 32)
         yrow(e, z[z2 + e], zp[z2 + e], DR ? dz[z2 + e] : S(0), eta[el + e], DR ? deta[el + e] : S(0));
     }
+    nacc.node_done(acc);
+  }
+  for (int64_t base = (int64_t)kc0 + 32 * (int64_t)gw; base < p.nl; base += 32 * (int64_t)nw) {
+    if (base + lane < p.nl) dual_y_chain<S, DR>(p, (int)(base + lane), z, zp, eta, out, dz, deta, nacc);
     nacc.node_done(acc);
   }
   nacc.flush(acc);

@@ -87,7 +87,15 @@ int launch_fwd_chain_grp(const KP<S>& p, S* zo, cudaStream_t st);
 // the staged variant fits too few warps per SM (tma_chain_fits).
 // SPOCK_RICCATI_KERNELS forces one family everywhere (the tests cover each).
 enum ChainFamily { CF_AUTO = -1, CF_GRP = 0, CF_TMA = 1, CF_DIRECT = 2 };
-constexpr int kStagedMaxNodes = 2048;  // FP64 stages with more nodes use the direct kernels
+// FP64 stages with at least this many nodes use the direct kernels (many
+// resident warps keep the FP64 pipe busy); SPOCK_STAGED_MAX_NODES overrides.
+inline int staged_max_nodes() {
+  static int v = [] {
+    const char* e = getenv("SPOCK_STAGED_MAX_NODES");
+    return e ? atoi(e) : 2048;
+  }();
+  return v;
+}
 static int chain_family() {
   const char* e = getenv("SPOCK_RICCATI_KERNELS");
   if (!e || !e[0]) return CF_AUTO;
@@ -127,7 +135,7 @@ int riccati_passes_sl(const KP<S>& p, const std::vector<int32_t>& stage_begin,
   // every stage in FP32 (measured); in FP64 a stage with many nodes runs
   // better on the direct warp-per-node kernels, which keep far more warps
   // resident (FP64 needs one per SM sub-partition).
-  auto staged = [&](int cnt) { return tma_stage && (sizeof(S) == 4 || cnt < kStagedMaxNodes); };
+  auto staged = [&](int cnt) { return tma_stage && (sizeof(S) == 4 || cnt < staged_max_nodes()); };
   for (int t = cs - 1; t >= 0; --t) {
     const int cnt = stage_begin[t + 1] - stage_begin[t];
     if (staged(cnt)) {
