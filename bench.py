@@ -280,6 +280,8 @@ def run_ours(args, rank, world, local_rank):
         if (rank == 0 and args.mpc_realisations > 0) else None
     small = section("small tree", lambda: small_workload(args, spock, workloads, dev)) if rank == 0 else None
     batch = section("batch", lambda: batch_workload(args, spock, workloads, dev, seed=rank)) if args.batch > 0 else None
+    family = section("family batch", lambda: family_workload(args, spock, workloads, dev, seed=rank)) \
+        if args.families > 0 else None
     grad = section("gradient", lambda: grad_workload(args, spock, workloads, dev)) \
         if (rank == 0 and args.grad_instances > 0) else None
 
@@ -327,6 +329,8 @@ def run_ours(args, rank, world, local_rank):
             line["closed_loop_mpc"] = mpc_res
         if batch:
             line["batch"] = batch
+        if family:
+            line["family_batch"] = family
         if grad:
             line["gradient"] = grad
         if cpu:
@@ -559,6 +563,45 @@ def batch_workload(args, spock, workloads, dev, seed=0):
     return out
 
 
+def family_workload(args, spock, workloads, dev, seed=0):
+    """Batched family form: 64 families of 8 instances that share tree and
+    data and differ in x0 (the members are spock_problem_clone's of the
+    family's problem, so a launch reads a family's factors from HBM once and
+    from L2 for the other members).  Families drawn as the batched workload;
+    x0 ~ N(0, 1) per member.  Same measurement as the independent batch:
+    args.batch_iter SPOCK iterations per instance from a cold start."""
+    import torch
+    ds = workloads.batch_instances(seed=seed + 17, count=args.families)
+    rng = np.random.default_rng(seed + 5)
+    bases = [spock.Problem(d) for d in ds]
+    members, x0s = [], []
+    for P, d in zip(bases, ds):
+        fam = [P] + [P.clone() for _ in range(args.family_size - 1)]
+        for m in fam:
+            members.append(m)
+            x0s.append(torch.tensor(np.clip(rng.standard_normal(d["nx"]), -5, 5), dtype=torch.float64, device=dev))
+    b = spock.spock_batch_create([m.handle for m in members])
+    zs = [torch.zeros(m.n_z, dtype=torch.float64, device=dev) for m in members]
+    es = [torch.zeros(m.n_eta, dtype=torch.float64, device=dev) for m in members]
+    out = {"families": len(bases), "members": args.family_size, "instances": len(members),
+           "nodes_total": int(sum(len(d["anc"]) for d in ds)) * args.family_size,
+           "iterations_per_instance": args.batch_iter}
+    for prec, nm in ((spock.SPOCK_FP32, "fp32"), (spock.SPOCK_FP64, "fp64")):
+        st = spock.spock_default_settings(precision=prec, max_iter=args.batch_iter, memory=args.memory, fp64_tail=0)
+        spock.spock_batch_solve_dev(b, x0s, st, zs, es, 0)   # warm-up: autotune + capture
+        torch.cuda.synchronize()
+        infos = spock.spock_batch_solve_dev(b, x0s, st, zs, es, 0)
+        torch.cuda.synchronize()
+        nT = sum(i.n_T for i in infos)
+        out[nm] = {"value": round(nT / infos[0].solve_ms * 1e3, 1), "unit": "instance CP iters/s",
+                   "device_ms": round(infos[0].solve_ms, 2), "n_T_total": nT}
+    spock.spock_free(b)
+    for m in members:
+        m.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def grad_workload(args, spock, workloads, dev):
     """Gradients of the optimal cost (envelope theorem at the converged pair)
     on 64 instances of the tree with branching 3 for 4 stages, N = 10
@@ -781,6 +824,8 @@ def main():
                     help="disturbance sequences of the closed-loop MPC measurement (0 skips it; the paper uses 15)")
     ap.add_argument("--batch", type=int, default=512, help="instances of the batched measurement (0 skips it)")
     ap.add_argument("--batch-iter", type=int, default=50)
+    ap.add_argument("--families", type=int, default=64, help="families of the family-form batch (0 skips it)")
+    ap.add_argument("--family-size", type=int, default=8, help="instances per family (x0 differs)")
     ap.add_argument("--batch-tol-iter", type=int, default=10000,
                     help="iteration cap of the batched time-to-1e-6 solve (0 skips it)")
     ap.add_argument("--batch-only", action="store_true",

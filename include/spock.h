@@ -192,6 +192,19 @@ int spock_problem_create(const spock_tree* tree, int32_t nx, int32_t nu,
                          const double* umin, const double* umax,
                          int32_t flags, spock_problem** out);
 
+/*
+ * spock_problem_clone -- a problem with the same tree, data and offline
+ * factors as `base`, sharing base's device copies of them (read-only), with
+ * its own iterate, scratch and workspace buffers.  The paper has no
+ * counterpart: it serves batches of instances that differ only in x0 (the
+ * batched "family" form): spock_batch_create accepts the clones as distinct
+ * instances, and each launch then reads a family's factors from HBM once and
+ * from L2 for the other members.  A clone of a clone shares the original.
+ * Freeing the base while clones exist defers its deletion to the last clone.
+ * Errors: INVALID_ARG, CUDA, OOM.
+ */
+int spock_problem_clone(const spock_problem* base, spock_problem** out);
+
 /* Sizes of z and eta, ||L|| (closed form, remark after the definition of L)
    and the seconds spent in Algorithm 1. */
 int spock_problem_info(const spock_problem* p, int64_t* n_z, int64_t* n_eta,

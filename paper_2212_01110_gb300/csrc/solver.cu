@@ -2387,12 +2387,64 @@ int spock_batch_solve(spock_batch* batch, const double* const* x0, const spock_s
   });
 }
 
+int spock_problem_clone(const spock_problem* base, spock_problem** out) {
+  return guarded([&]() -> int {
+    Problem* B = const_cast<Problem*>(reinterpret_cast<const Problem*>(base));
+    if (!B || B->tag != TAG_PROBLEM || !out) return fail(SPOCK_ERR_INVALID_ARG, "not a problem handle");
+    while (B->base) B = B->base;   // clones of clones share the original
+    CUDA_TRY(cudaSetDevice(B->device));
+    auto* C = new Problem();
+    try {
+      C->device = B->device;
+      C->tree = B->tree;
+      C->off = B->off;
+      C->nx = B->nx;
+      C->nu = B->nu;
+      C->normL = B->normL;
+      C->idx = B->idx;      // read-only index arrays, shared
+      C->f64 = B->f64;      // data and factors, shared
+      C->f32 = B->f32;
+      const Tree& t = C->tree;
+      auto scratch = [&](auto& f, auto zero) {
+        using S = decltype(zero);
+        f.xbar = dalloc<S>(*C, (size_t)t.n * f.xs);
+        f.ubar = dalloc<S>(*C, (size_t)t.n_nonleaf * f.us);
+        f.q = dalloc<S>(*C, (size_t)t.n * f.xs);
+        f.d = dalloc<S>(*C, (size_t)t.n_nonleaf * f.us);
+        f.x0 = dalloc<S>(*C, (size_t)C->nx);
+      };
+      scratch(C->f64, 0.0);
+      scratch(C->f32, 0.0f);
+      C->err = upload(*C, std::vector<int32_t>(1, 0));
+      CUDA_TRY(cudaDeviceSynchronize());
+    } catch (...) {
+      delete C;
+      throw;
+    }
+    C->base = B;
+    B->n_clones++;
+    *out = reinterpret_cast<spock_problem*>(C);
+    return SPOCK_OK;
+  });
+}
+
 void spock_free(void* handle) {
   if (!handle) return;
   const int32_t tag = *reinterpret_cast<const int32_t*>(handle);
-  if (tag == TAG_TREE) delete reinterpret_cast<Tree*>(handle);
-  else if (tag == TAG_PROBLEM) delete reinterpret_cast<Problem*>(handle);
-  else if (tag == TAG_BATCH) delete reinterpret_cast<Batch*>(handle);
+  if (tag == TAG_TREE) {
+    delete reinterpret_cast<Tree*>(handle);
+  } else if (tag == TAG_PROBLEM) {
+    Problem* P = reinterpret_cast<Problem*>(handle);
+    if (P->n_clones > 0) {   // clones still use its device data: delete it with the last one
+      P->free_pending = true;
+      return;
+    }
+    Problem* B = P->base;
+    delete P;
+    if (B && --B->n_clones == 0 && B->free_pending) delete B;
+  } else if (tag == TAG_BATCH) {
+    delete reinterpret_cast<Batch*>(handle);
+  }
 }
 
 const char* spock_last_error(void) { return g_last_error.c_str(); }

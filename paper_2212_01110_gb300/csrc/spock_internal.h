@@ -110,6 +110,11 @@ struct Problem {
   // solver workspace, allocated on first use per precision
   struct Workspace* ws64 = nullptr;
   struct Workspace* ws32 = nullptr;
+  // clones (spock_problem_clone) share this problem's data, factors and
+  // index arrays; a base freed while clones exist is deleted with its last clone
+  struct Problem* base = nullptr;
+  int32_t n_clones = 0;
+  bool free_pending = false;
   ~Problem();
 };
 

@@ -72,6 +72,7 @@ _sig = {
     "spock_tree_info": ([_P, _I32, _I32, _I32], C.c_int),
     "spock_problem_create": ([_P, C.c_int32, C.c_int32] + [_D] * 10 + [C.c_int32, C.POINTER(_P)], C.c_int),
     "spock_problem_info": ([_P, _I64, _I64, _D, _D], C.c_int),
+    "spock_problem_clone": ([_P, C.POINTER(_P)], C.c_int),
     "spock_solve": ([_P, _D, C.POINTER(Settings), _D, _D, C.c_int32, C.POINTER(Info)], C.c_int),
     "spock_solve_dev": ([_P, _P, C.POINTER(Settings), _P, _P, C.c_int32, C.POINTER(Info), _P], C.c_int),
     "spock_cp_step": ([_P, _D, C.c_int32, C.c_double, C.c_int32, _D, _D, _D], C.c_int),
@@ -165,6 +166,14 @@ def spock_problem_create(tree, d):
     arrs = [_dptr(d[k]) for k in ("A", "B", "Q", "R", "QN", "a", "xmin", "xmax", "umin", "umax")]
     h = _P()
     _check(_lib.spock_problem_create(tree, nx, nu, *[p for _, p in arrs], 0, C.byref(h)))
+    return h
+
+
+def spock_problem_clone(problem):
+    """A problem sharing the data and factors of `problem` (device memory),
+    with its own iterate and scratch buffers."""
+    h = _P()
+    _check(_lib.spock_problem_clone(problem, C.byref(h)))
     return h
 
 
@@ -359,6 +368,11 @@ class Problem:
     def n_v(self):
         return self.n_z + self.n_eta
 
+    def clone(self):
+        """A problem sharing this one's data and factors on the device, with its
+        own iterate and scratch buffers (spock_problem_clone)."""
+        return _Clone(self)
+
     def close(self):
         if getattr(self, "handle", None):
             spock_free(self.handle)
@@ -366,6 +380,31 @@ class Problem:
         if getattr(self, "tree", None):
             spock_free(self.tree)
             self.tree = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _Clone:
+    """Owner of a spock_problem_clone handle; same attributes as Problem."""
+
+    def __init__(self, base):
+        self.handle = spock_problem_clone(base.handle)
+        self.tree = None
+        self.nx, self.nu, self.n_nodes = base.nx, base.nu, base.n_nodes
+        self.n_z, self.n_eta, self.norm_L, self.factor_seconds = spock_problem_info(self.handle)
+
+    @property
+    def n_v(self):
+        return self.n_z + self.n_eta
+
+    def close(self):
+        if getattr(self, "handle", None):
+            spock_free(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:

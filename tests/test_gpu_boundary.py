@@ -121,3 +121,45 @@ def test_fp64_fma_rate_is_plausible():
     assert 0.1 < v < 100.0
     with pytest.raises(spock.SpockError):
         spock.spock_fp64_fma_rate(0)
+
+
+def test_problem_clones_share_data_and_solve_alike():
+    """spock_problem_clone: a clone solves exactly as its base; a batch of
+    clones (one family, different x0) equals the batch of independent
+    problems built from the same data; the base may be freed first."""
+    import torch
+    from paper_2212_01110_gb300 import spock
+    dev = torch.device("cuda:0")
+    d = W.random_tree(4, N=6, max_branch=3, nx=5, nu=2, chain_after=2)
+    base = spock.Problem(d)
+    clones = [base.clone() for _ in range(3)]
+    rng = np.random.default_rng(9)
+    x0s = [torch.tensor(np.clip(d["x0"] + 0.3 * rng.standard_normal(d["nx"]), -5, 5), dtype=torch.float64,
+                        device=dev) for _ in range(3)]
+    s = spock.spock_default_settings(max_iter=60, eps_abs=1e-14, eps_rel=1e-14)
+    # a clone against its base, same x0
+    z1, e1 = torch.zeros(base.n_z, dtype=torch.float64, device=dev), torch.zeros(base.n_eta, dtype=torch.float64,
+                                                                                 device=dev)
+    z2, e2 = torch.zeros_like(z1), torch.zeros_like(e1)
+    spock.spock_solve_dev(base.handle, x0s[0], s, z1, e1, 0)
+    spock.spock_solve_dev(clones[0].handle, x0s[0], s, z2, e2, 0)
+    assert torch.equal(z1, z2) and torch.equal(e1, e2)
+    # batch of clones vs batch of independent problems with the same data
+    indep = [spock.Problem(d) for _ in range(3)]
+    outs = []
+    for probs in (clones, indep):
+        b = spock.spock_batch_create([p.handle for p in probs])
+        zs = [torch.zeros(base.n_z, dtype=torch.float64, device=dev) for _ in probs]
+        es = [torch.zeros(base.n_eta, dtype=torch.float64, device=dev) for _ in probs]
+        spock.spock_batch_solve_dev(b, x0s, s, zs, es, 0)
+        spock.spock_free(b)
+        outs.append([torch.cat([z, e]).cpu().numpy() for z, e in zip(zs, es)])
+    for a, b_ in zip(*outs):
+        assert np.array_equal(a, b_)
+    # freeing the base first keeps the clones usable
+    base.close()
+    z3, e3 = torch.zeros_like(z1), torch.zeros_like(e1)
+    spock.spock_solve_dev(clones[1].handle, x0s[0], s, z3, e3, 0)
+    assert torch.equal(z3, z1)
+    for c in clones:
+        c.close()
