@@ -603,39 +603,50 @@ def family_workload(args, spock, workloads, dev, seed=0):
 
 
 def grad_workload(args, spock, workloads, dev):
-    """Gradients of the optimal cost (envelope theorem at the converged pair)
-    on 64 instances of the tree with branching 3 for 4 stages, N = 10
-    (607 nodes), nx = 20, nu = 8, data as the large tree with uniform child
-    probabilities (the workload does not state them): one batched FP64 solve
-    (tolerance 1e-6, at most args.grad_iter iterations per instance), then
-    spock_grad_dev per instance in FP64 and FP32 (CUDA events), compared with
-    the solve time per instance.  Finite-difference check on instance 0 of
-    the same workload: central differences with h = 1e-6 along random
-    directions of x0 and of diag Q, from solves to xi <= 1e-12."""
+    """Gradients of the optimal cost on 64 instances of the tree with
+    branching 3 for 4 stages, N = 10 (607 nodes), nx = 20, nu = 8, data as
+    the large tree with uniform child probabilities and dynamics of spectral
+    radius 0.5 (the workload states neither; with 0.95 the method does not
+    reach 1e-6 on this tree within 20,000 iterations).  One batched FP64
+    solve (tolerance 1e-6, at most args.grad_iter iterations per instance),
+    then per instance the envelope gradient (spock_grad_dev, FP64 and FP32)
+    and the adjoint of the CP fixed point (spock_adjoint_dev, FP64, on a few
+    instances), timed with CUDA events against the solve time per instance.
+    Finite-difference check on instance 0: central differences with h = 1e-6
+    along random directions of x0, diag Q, diag R, A and B, from solves to
+    xi <= 1e-12, against both gradients."""
     import torch
     cnt = args.grad_instances
-    ds = [workloads.large_tree(seed=s, branching_stages=4, branch=3, N=10, nx=20, nu=8, probs="uniform")
+    ds = [workloads.large_tree(seed=s, branching_stages=4, branch=3, N=10, nx=20, nu=8, probs="uniform", rho=0.5)
           for s in range(cnt)]
     probs = [spock.Problem(d) for d in ds]
     b = spock.spock_batch_create([p.handle for p in probs])
     x0s = [torch.tensor(d["x0"], dtype=torch.float64, device=dev) for d in ds]
     zs = [torch.zeros(p.n_z, dtype=torch.float64, device=dev) for p in probs]
     es = [torch.zeros(p.n_eta, dtype=torch.float64, device=dev) for p in probs]
+    warm = spock.spock_default_settings(precision=spock.SPOCK_FP64, memory=5, max_iter=50)
+    spock.spock_batch_solve_dev(b, x0s, warm, zs, es, 0)
+    for z, e in zip(zs, es):
+        z.zero_()
+        e.zero_()
     st = spock.spock_default_settings(precision=spock.SPOCK_FP64, memory=5, max_iter=args.grad_iter)
-    spock.spock_batch_solve_dev(b, x0s, st, zs, es, 0)
     torch.cuda.synchronize()
     infos = spock.spock_batch_solve_dev(b, x0s, st, zs, es, 0)
     torch.cuda.synchronize()
     batch_ms = infos[0].solve_ms
+    its = [i.iterations for i in infos]
     out = {"instances": cnt, "nodes": len(ds[0]["anc"]), "n_z": probs[0].n_z, "n_eta": probs[0].n_eta,
+           "dynamics": "A = 0.5 x Haar-orthogonal, B ~ N(0, 1/nx), uniform child probabilities",
            "solve": {"tol": 1e-6, "max_iter": args.grad_iter, "batch_ms": round(batch_ms, 2),
                      "ms_per_instance": round(batch_ms / cnt, 3),
                      "converged": sum(1 for i in infos if i.status == 0),
+                     "iterations_median_max": [int(np.median(its)), int(max(its))],
                      "median_xi": float(np.median([i.xi for i in infos])),
                      "mode": "persistent (one launch, one block per instance)" if infos[0].n_launches == 1
                              else "work-list kernels, %d launches" % infos[0].n_launches}}
+    n, nx, nu = len(ds[0]["anc"]), ds[0]["nx"], ds[0]["nu"]
 
-    def grads(p, n, nx, nu):
+    def grads():
         return [torch.zeros(nx, dtype=torch.float64, device=dev),
                 torch.zeros(n, nx, nx, dtype=torch.float64, device=dev),
                 torch.zeros(n, nx, nu, dtype=torch.float64, device=dev),
@@ -643,8 +654,9 @@ def grad_workload(args, spock, workloads, dev):
                 torch.zeros(n, nu, dtype=torch.float64, device=dev),
                 torch.zeros(n, nx, dtype=torch.float64, device=dev)]
 
-    g = grads(None, len(ds[0]["anc"]), ds[0]["nx"], ds[0]["nu"])
+    g = grads()
     cur = torch.cuda.current_stream()
+    per_inst = batch_ms / cnt
     for prec, nm in ((spock.SPOCK_FP64, "fp64"), (spock.SPOCK_FP32, "fp32")):
         for i in range(min(3, cnt)):   # warm-up
             spock.spock_grad_dev(probs[i].handle, zs[i], es[i], prec, *g)
@@ -657,7 +669,21 @@ def grad_workload(args, spock, workloads, dev):
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1) / cnt
         out[f"grad_ms_{nm}"] = round(ms, 4)
-        out[f"grad_over_solve_{nm}"] = round(ms / (batch_ms / cnt), 5)
+        out[f"grad_over_solve_{nm}"] = round(ms / per_inst, 5)
+    # adjoint of the fixed point (phi = s^0) on the first instances
+    na = min(4, cnt)
+    adj = []
+    for i in range(na):
+        ga = grads()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, it, res = spock.spock_adjoint_dev(probs[i].handle, zs[i], es[i], None, 20000, 1e-10, *ga)
+        torch.cuda.synchronize()
+        adj.append((time.perf_counter() - t0) * 1e3)
+        adj.append(it)
+    out["adjoint_fp64"] = {"instances": na, "ms_median": round(float(np.median(adj[0::2])), 3),
+                           "iterations_median": int(np.median(adj[1::2])), "tol": 1e-10,
+                           "over_solve": round(float(np.median(adj[0::2])) / per_inst, 4)}
     spock.spock_free(b)
     for p in probs:
         p.close()
@@ -665,7 +691,7 @@ def grad_workload(args, spock, workloads, dev):
     d = ds[0]
     P = spock.Problem(d)
     tight = spock.spock_default_settings(precision=spock.SPOCK_FP64, eps_abs=1e-12, eps_rel=1e-12, memory=5,
-                                         max_iter=50000)
+                                         max_iter=args.grad_fd_iter)
 
     def solve(PP, x0):
         z = torch.zeros(PP.n_z, dtype=torch.float64, device=dev)
@@ -674,37 +700,51 @@ def grad_workload(args, spock, workloads, dev):
         return z, e, inf
 
     z, e, inf0 = solve(P, d["x0"])
-    g = grads(None, len(d["anc"]), d["nx"], d["nu"])
-    spock.spock_grad_dev(P.handle, z, e, spock.SPOCK_FP64, *g)
+    ge = grads()
+    spock.spock_grad_dev(P.handle, z, e, spock.SPOCK_FP64, *ge)
+    ga = grads()
+    rc, ait, ares = spock.spock_adjoint_dev(P.handle, z, e, None, 200000, 1e-12, *ga)
+    ge = [t.cpu().numpy() for t in ge]
+    ga = [t.cpu().numpy() for t in ga]
+    out["adjoint_vs_envelope"] = {"max_rel_diff": max(float(np.max(np.abs(a - b_)) / max(np.max(np.abs(b_)), 1e-300))
+                                                      for a, b_ in zip(ga, ge)),
+                                  "adjoint_iterations": ait, "adjoint_residual": ares}
     rng = np.random.default_rng(7)
     h = 1e-6
-    dirv = rng.standard_normal(d["nx"])
+    checks = {}
+    conv = [inf0.status == 0]
+    dirv = rng.standard_normal(nx)
     dirv /= np.linalg.norm(dirv)
     zp_, _, infp = solve(P, d["x0"] + h * dirv)
     zm_, _, infm = solve(P, d["x0"] - h * dirv)
-    fd = (float(zp_[0].item()) - float(zm_[0].item())) / (2 * h)
-    an = float(g[0].cpu().numpy() @ dirv)
-    out["fd_check_x0"] = {"tree": "instance 0 of the workload (607 nodes)", "analytic": an, "central_fd": fd,
-                          "rel_err": abs(an - fd) / max(abs(fd), 1e-12), "h": h, "solve_tol": 1e-12,
-                          "iterations": [inf0.iterations, infp.iterations, infm.iterations],
-                          "converged": all(i.status == 0 for i in (inf0, infp, infm))}
-    # diag Q along a random direction over all nonroot nodes (relative step h per entry)
-    dq = rng.standard_normal(d["Q"].shape)
-    dq[0] = 0.0
-    an_q = float(np.sum(g[3].cpu().numpy() * dq * d["Q"]))
-    vals = []
-    for sgn in (1.0, -1.0):
-        dd = dict(d)
-        dd["Q"] = d["Q"] * (1.0 + sgn * h * dq)
-        PP = spock.Problem(dd)
-        zz, _, inf_ = solve(PP, d["x0"])
-        vals.append((float(zz[0].item()), inf_.status == 0))
-        PP.close()
-    fd_q = (vals[0][0] - vals[1][0]) / (2 * h)
-    out["fd_check_Q"] = {"analytic": an_q, "central_fd": fd_q, "rel_err": abs(an_q - fd_q) / max(abs(fd_q), 1e-12),
-                         "h": h, "direction": "Q <- Q (1 + h dQ), dQ ~ N(0, 1) per entry",
-                         "converged": all(v[1] for v in vals)}
+    conv += [infp.status == 0, infm.status == 0]
+    checks["x0"] = ((float(zp_[0].item()) - float(zm_[0].item())) / (2 * h), float(ge[0] @ dirv),
+                    float(ga[0] @ dirv))
     P.close()
+    # data directions: Q, R relative per entry; A, B absolute; all nonroot nodes
+    for key, gi, rel in (("Q", 3, True), ("R", 4, True), ("A", 1, False), ("B", 2, False)):
+        dq = rng.standard_normal(d[key].shape)
+        dq[0] = 0.0
+        scale = d[key] if rel else 1.0
+        an_e = float(np.sum(ge[gi] * dq * scale))
+        an_a = float(np.sum(ga[gi] * dq * scale))
+        vals = []
+        for sgn in (1.0, -1.0):
+            dd = dict(d)
+            dd[key] = d[key] + sgn * h * dq * scale
+            PP = spock.Problem(dd)
+            zz, _, inf_ = solve(PP, d["x0"])
+            vals.append(float(zz[0].item()))
+            conv.append(inf_.status == 0)
+            PP.close()
+        checks[key] = ((vals[0] - vals[1]) / (2 * h), an_e, an_a)
+    out["fd_check"] = {
+        "tree": "instance 0 of the workload (607 nodes)", "h": h, "solve_tol": 1e-12,
+        "directions": "x0: unit N(0, 1); Q, R: X <- X (1 + h dX); A, B: X <- X + h dX; dX ~ N(0, 1) per entry",
+        "converged": all(conv),
+        **{k: {"central_fd": fd, "envelope": ae, "adjoint": aa,
+               "rel_err_envelope": abs(ae - fd) / max(abs(fd), 1e-12),
+               "rel_err_adjoint": abs(aa - fd) / max(abs(fd), 1e-12)} for k, (fd, ae, aa) in checks.items()}}
     torch.cuda.empty_cache()
     return out
 
@@ -832,8 +872,10 @@ def main():
                     help="run only the batched measurement and print it (profiling aid, not a bench line)")
     ap.add_argument("--grad-instances", type=int, default=64,
                     help="instances of the gradient measurement (0 skips it)")
-    ap.add_argument("--grad-iter", type=int, default=2000,
+    ap.add_argument("--grad-iter", type=int, default=20000,
                     help="iteration cap per instance of the gradient workload's solve")
+    ap.add_argument("--grad-fd-iter", type=int, default=60000,
+                    help="iteration cap of the 1e-12 solves of the finite-difference check")
     ap.add_argument("--horizon", type=int, default=20,
                     help="horizon N of the tree (20 = the 62,805-node tree; shorter chains for profiling)")
     ap.add_argument("--branching-stages", type=int, default=6,

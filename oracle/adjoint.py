@@ -114,6 +114,7 @@ class Linearisation:
     def __init__(self, cp: CP, z, eta):
         self.cp = cp
         P = cp.P
+        P.require_box_diag("Linearisation")
         self.P = P
         self.z = np.asarray(z, float)
         self.eta = np.asarray(eta, float)

@@ -50,8 +50,11 @@ def proj_S3(w, P: Problem):
         ey = lay.e_y[i]
         out[ey[:2 * m]] = np.maximum(w[ey[:2 * m]], 0.0)     # (K^i)*: R^{2m}_+ x R
         out[lay.e_sb[i]] = max(w[lay.e_sb[i]], 0.0)          # R_+
-        out[lay.e_x[i]] = np.clip(w[lay.e_x[i]], P.xmin[i], P.xmax[i])   # C^i
-        out[lay.e_u[i]] = np.clip(w[lay.e_u[i]], P.umin[i], P.umax[i])
+        if P.general:                                        # C^i = [cmin, cmax]
+            out[lay.e_c[i]] = np.clip(w[lay.e_c[i]], P.cmin[i], P.cmax[i])
+        else:                                                # C^i = box on (x, u)
+            out[lay.e_x[i]] = np.clip(w[lay.e_x[i]], P.xmin[i], P.xmax[i])
+            out[lay.e_u[i]] = np.clip(w[lay.e_u[i]], P.umin[i], P.umax[i])
     shift_nr = np.zeros(P.nx + P.nu + 2)
     shift_nr[-2:] = (0.5, -0.5)
     for c in t.nonroot:
@@ -60,7 +63,10 @@ def proj_S3(w, P: Problem):
     shift_lf = np.zeros(P.nx + 2)
     shift_lf[-2:] = (0.5, -0.5)
     for j in t.leaves:
-        out[lay.e_lx[j]] = np.clip(w[lay.e_lx[j]], P.xmin[j], P.xmax[j])  # C^j_N
+        if P.general:                                        # C_N^j
+            out[lay.e_lc[j]] = np.clip(w[lay.e_lc[j]], P.cNmin[j], P.cNmax[j])
+        else:
+            out[lay.e_lx[j]] = np.clip(w[lay.e_lx[j]], P.xmin[j], P.xmax[j])
         idx = np.concatenate([lay.e_qn[j], lay.e_ls[j]])
         out[idx] = proj_translated_soc(w[idx], shift_lf)
     return out

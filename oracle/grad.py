@@ -35,6 +35,7 @@ from .cp import CP
 
 def envelope_gradient(cp: CP, z, eta):
     P = cp.P
+    P.require_box_diag("envelope_gradient")
     t, lay, nx, nu = P.tree, P.lay, P.nx, P.nu
     w = cp.Lt @ eta
     S = cp.S1

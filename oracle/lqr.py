@@ -7,7 +7,7 @@ recursion (dynamic programming, textbook):
   P^j = Q_N^j at leaves; for nonleaf i with children c (conditional p^c):
   H = sum p^c A^cT P^c B^c,  S = sum p^c (R^c + B^cT P^c B^c),
   P^i = sum p^c (Q^c + A^cT P^c A^c) - H S^-1 H^T,  u^i = -S^-1 H^T x^i,
-  optimal cost x^0T P^0 x^0.
+  optimal cost x^0T P^0 x^0.  Q, R, Q_N enter as matrices (diagonal or dense).
 """
 from __future__ import annotations
 
@@ -20,7 +20,7 @@ def tree_lqr(P, x0):
     K = [None] * t.n
     for i in sorted(range(t.n), key=lambda k: -t.stage[k]):
         if not t.children[i]:
-            Pm[i] = np.diag(P.QN[i])
+            Pm[i] = P.QNmat(i)
             continue
         nx, nu = P.nx, P.nu
         H = np.zeros((nx, nu))
@@ -30,8 +30,8 @@ def tree_lqr(P, x0):
             p = t.prob[c]
             A, B, Pc = P.A[c], P.B[c], Pm[c]
             H += p * A.T @ Pc @ B
-            S += p * (np.diag(P.R[c]) + B.T @ Pc @ B)
-            G += p * (np.diag(P.Q[c]) + A.T @ Pc @ A)
+            S += p * (P.Rmat(c) + B.T @ Pc @ B)
+            G += p * (P.Qmat(c) + A.T @ Pc @ A)
         K[i] = -np.linalg.solve(S, H.T)
         Pm[i] = G - H @ np.linalg.solve(S, H.T)
     # forward simulation of the optimal policy

@@ -5,10 +5,20 @@ z   = (s^0, z_1, z_2), z_1 = (x^i for every node, u^i for every nonleaf node),
       z_2 = (y^i, tau^[i], s^[i]) for every nonleaf node i, children of i in
       increasing id.  y^i has 2 m_i + 1 entries for AV@R over m_i children
       (E = [aI, -I, 1]^T, Sec. "Conic representation of risk measures").
-eta = ((y^i, s^i - b^iT y^i, x^i, u^i) for nonleaf i,
+eta = ((y^i, s^i - b^iT y^i, Gamma_x^i x^i + Gamma_u^i u^i) for nonleaf i,
        (Q^i^1/2 x^anc(i), R^i^1/2 u^anc(i), tau^i/2, tau^i/2) for nonroot i,
-       (x^j, Q_N^j^1/2 x^j, s^j/2, s^j/2) for leaf j)
-with the box constraints Gamma = I of Eq. (constraints).
+       (Gamma_N^j x^j, Q_N^j^1/2 x^j, s^j/2, s^j/2) for leaf j)
+(definition of L).  Two forms of the data:
+  * box form: Gamma = I (the constraint rows are x^i, u^i and x^j) with C^i,
+    C_N^j boxes, diagonal Q, R, Q_N given by their diagonals;
+  * general form (Eq. (constraints) with polyhedral C): constraint matrices
+    Gamma_x^i (nc x nx), Gamma_u^i (nc x nu), Gamma_N^j (ncN x nx) with C^i,
+    C_N^j boxes [cmin, cmax] of nc / ncN rows, and/or dense symmetric
+    positive definite Q, R, Q_N.  The square roots in L are the upper
+    Cholesky factors F (F^T F = Q): any factor with F^T F = Q gives the same
+    cost x'Qx = ||F x||^2, so the choice is a reading of the paper's
+    notation Q^1/2; the library documents the same factor.
+With Gamma = I and diagonal costs both forms give the same L.
 
 The index maps below are an interface: the CUDA library documents the same
 ordering for its z and eta buffers.
@@ -42,9 +52,17 @@ class Layout:
     e_lx: dict             # leaf j -> (nx,)      x^j (terminal box)
     e_qn: dict             # leaf j -> (nx,)      Q_N^1/2 x^j
     e_ls: dict             # leaf j -> (2,)       s^j/2, s^j/2
+    e_c: dict              # nonleaf i -> (nc,)   Gamma_x x^i + Gamma_u u^i
+    e_lc: dict             # leaf j -> (ncN,)     Gamma_N x^j
 
 
-def build_layout(tree: Tree, nx: int, nu: int) -> Layout:
+def build_layout(tree: Tree, nx: int, nu: int, nc: int | None = None, ncN: int | None = None) -> Layout:
+    """Index maps of z and eta.  ``nc`` / ``ncN`` (constraint rows per nonleaf
+    / leaf node) default to the box form's nx + nu / nx; in the box form the
+    constraint rows are also split into e_x, e_u (nonleaf) and e_lx (leaf)."""
+    box = nc is None and ncN is None
+    nc = nx + nu if nc is None else int(nc)
+    ncN = nx if ncN is None else int(ncN)
     n = tree.n
     pos = 0
     s0 = pos
@@ -68,17 +86,18 @@ def build_layout(tree: Tree, nx: int, nu: int) -> Layout:
         pos += m
     n_z = pos
     pos = 0
-    e_y, e_sb, e_x, e_u = {}, {}, {}, {}
+    e_y, e_sb, e_x, e_u, e_c = {}, {}, {}, {}, {}
     for i in tree.nonleaf:
         m = len(tree.children[i])
         e_y[i] = np.arange(pos, pos + 2 * m + 1)
         pos += 2 * m + 1
         e_sb[i] = pos
         pos += 1
-        e_x[i] = np.arange(pos, pos + nx)
-        pos += nx
-        e_u[i] = np.arange(pos, pos + nu)
-        pos += nu
+        e_c[i] = np.arange(pos, pos + nc)
+        if box:
+            e_x[i] = e_c[i][:nx]
+            e_u[i] = e_c[i][nx:]
+        pos += nc
     e_qx, e_ru, e_t = {}, {}, {}
     for c in tree.nonroot:
         e_qx[c] = np.arange(pos, pos + nx)
@@ -87,24 +106,30 @@ def build_layout(tree: Tree, nx: int, nu: int) -> Layout:
         pos += nu
         e_t[c] = np.arange(pos, pos + 2)
         pos += 2
-    e_lx, e_qn, e_ls = {}, {}, {}
+    e_lx, e_qn, e_ls, e_lc = {}, {}, {}, {}
     for j in tree.leaves:
-        e_lx[j] = np.arange(pos, pos + nx)
-        pos += nx
+        e_lc[j] = np.arange(pos, pos + ncN)
+        if box:
+            e_lx[j] = e_lc[j]
+        pos += ncN
         e_qn[j] = np.arange(pos, pos + nx)
         pos += nx
         e_ls[j] = np.arange(pos, pos + 2)
         pos += 2
     return Layout(n_z, pos, s0, x, u, y, tau, s, e_y, e_sb, e_x, e_u,
-                  e_qx, e_ru, e_t, e_lx, e_qn, e_ls)
+                  e_qx, e_ru, e_t, e_lx, e_qn, e_ls, e_c, e_lc)
 
 
 class Problem:
-    """A RAOCP with diagonal quadratic costs and box constraints.
+    """A RAOCP with quadratic costs and polyhedral constraints.
 
     Arrays follow the workload dict convention: per-node A, B of the edge
-    into the node, diagonal Q, R (edge into the node), Q_N (leaves), AV@R
-    parameter a (nonleaf), box bounds on x (all nodes) and u (nonleaf).
+    into the node, Q, R (edge into the node), Q_N (leaves), AV@R parameter a
+    (nonleaf).  Q, R, Q_N are diagonals ([n][nx]) or, when given as [n][nx][nx]
+    arrays, dense symmetric positive definite matrices (``dense_cost``).
+    Constraints: box bounds xmin/xmax (all nodes) and umin/umax (nonleaf), or,
+    when the dict has "Gx", the general form: Gx [n][nc][nx], Gu [n][nc][nu],
+    cmin/cmax [n][nc] (nonleaf), GN [n][ncN][nx], cNmin/cNmax [n][ncN] (leaves).
     """
 
     def __init__(self, d):
@@ -114,15 +139,71 @@ class Problem:
         n, nx, nu = self.tree.n, self.nx, self.nu
         self.A = np.asarray(d["A"], float).reshape(n, nx, nx)
         self.B = np.asarray(d["B"], float).reshape(n, nx, nu)
-        self.Q = np.asarray(d["Q"], float).reshape(n, nx)
-        self.R = np.asarray(d["R"], float).reshape(n, nu)
-        self.QN = np.asarray(d["QN"], float).reshape(n, nx)
+        self.dense_cost = np.asarray(d["Q"]).ndim == 3
+        if self.dense_cost:
+            self.Q = np.asarray(d["Q"], float).reshape(n, nx, nx)
+            self.R = np.asarray(d["R"], float).reshape(n, nu, nu)
+            self.QN = np.asarray(d["QN"], float).reshape(n, nx, nx)
+        else:
+            self.Q = np.asarray(d["Q"], float).reshape(n, nx)
+            self.R = np.asarray(d["R"], float).reshape(n, nu)
+            self.QN = np.asarray(d["QN"], float).reshape(n, nx)
         self.a = np.asarray(d["a"], float).reshape(n)
-        self.xmin = np.asarray(d["xmin"], float).reshape(n, nx)
-        self.xmax = np.asarray(d["xmax"], float).reshape(n, nx)
-        self.umin = np.asarray(d["umin"], float).reshape(n, nu)
-        self.umax = np.asarray(d["umax"], float).reshape(n, nu)
-        self.lay = build_layout(self.tree, nx, nu)
+        self.general = "Gx" in d
+        if self.general:
+            self.Gx = np.asarray(d["Gx"], float)
+            self.nc = self.Gx.shape[1]
+            self.Gx = self.Gx.reshape(n, self.nc, nx)
+            self.Gu = np.asarray(d["Gu"], float).reshape(n, self.nc, nu)
+            self.cmin = np.asarray(d["cmin"], float).reshape(n, self.nc)
+            self.cmax = np.asarray(d["cmax"], float).reshape(n, self.nc)
+            self.GN = np.asarray(d["GN"], float)
+            self.ncN = self.GN.shape[1]
+            self.GN = self.GN.reshape(n, self.ncN, nx)
+            self.cNmin = np.asarray(d["cNmin"], float).reshape(n, self.ncN)
+            self.cNmax = np.asarray(d["cNmax"], float).reshape(n, self.ncN)
+            self.lay = build_layout(self.tree, nx, nu, self.nc, self.ncN)
+        else:
+            self.xmin = np.asarray(d["xmin"], float).reshape(n, nx)
+            self.xmax = np.asarray(d["xmax"], float).reshape(n, nx)
+            self.umin = np.asarray(d["umin"], float).reshape(n, nu)
+            self.umax = np.asarray(d["umax"], float).reshape(n, nu)
+            self.nc, self.ncN = nx + nu, nx
+            self.lay = build_layout(self.tree, nx, nu)
+
+    # -- cost matrices and their square roots (definition of L) ---------------
+    def _mat(self, M, i):
+        return M[i] if self.dense_cost else np.diag(M[i])
+
+    def Qmat(self, i):
+        return self._mat(self.Q, i)
+
+    def Rmat(self, i):
+        return self._mat(self.R, i)
+
+    def QNmat(self, i):
+        return self._mat(self.QN, i)
+
+    def _half(self, M, i):
+        """F with F^T F = M^i: sqrt of the diagonal, or the upper Cholesky
+        factor (numpy's lower factor, transposed) of a dense matrix."""
+        if self.dense_cost:
+            return np.linalg.cholesky(M[i]).T
+        return np.diag(np.sqrt(M[i]))
+
+    def Qhalf(self, i):
+        return self._half(self.Q, i)
+
+    def Rhalf(self, i):
+        return self._half(self.R, i)
+
+    def QNhalf(self, i):
+        return self._half(self.QN, i)
+
+    def require_box_diag(self, what):
+        """Parts of the oracle written for the box form with diagonal costs."""
+        if self.general or self.dense_cost:
+            raise NotImplementedError(what + ": box constraints and diagonal costs only")
 
     def b(self, i):
         """b^i = (p^ch(i), 0_m, 1) for AV@R (Sec. "Conic representation of

@@ -70,6 +70,8 @@ class RiccatiCPU:
     Algorithm 1 runs at construction with ``threads`` OpenMP threads."""
 
     def __init__(self, d, threads=1):
+        if "Gx" in d or np.asarray(d["Q"]).ndim == 3:
+            raise NotImplementedError("RiccatiCPU: box constraints and diagonal costs only")
         lib = _load()
         self._keep = {k: np.ascontiguousarray(d[k], dtype=np.float64)
                       for k in ("prob", "A", "B", "Q", "R", "QN", "a", "xmin", "xmax", "umin", "umax")}

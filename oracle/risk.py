@@ -99,10 +99,10 @@ def nested_value(P, x, u, avar=avar_sort):
     W = np.zeros(t.n)
     for i in sorted(range(t.n), key=lambda k: -t.stage[k]):
         if not t.children[i]:
-            W[i] = float(x[i] @ (P.QN[i] * x[i]))
+            W[i] = float(x[i] @ P.QNmat(i) @ x[i])
         else:
             ch = t.children[i]
-            Z = np.array([x[i] @ (P.Q[c] * x[i]) + u[i] @ (P.R[c] * u[i]) + W[c] for c in ch])
+            Z = np.array([x[i] @ P.Qmat(c) @ x[i] + u[i] @ P.Rmat(c) @ u[i] + W[c] for c in ch])
             W[i] = avar(Z, t.prob[ch], P.a[i])
     return float(W[0]), W
 

@@ -16,6 +16,14 @@ Every generator returns a plain dict of numpy arrays in *user* node order
     xmin, xmax float64[n,nx]; umin, umax float64[n,nu]   box constraints
     x0      float64[nx]     initial state
 
+General form (polyhedral constraints, dense costs; ``general_*`` below):
+    Q, R, QN  float64[n,nx,nx] / [n,nu,nu] / [n,nx,nx]  dense SPD matrices
+    Gx, Gu    float64[n,nc,nx], [n,nc,nu]   constraint matrices of nonleaf nodes
+    cmin, cmax float64[n,nc]                bounds of Gx x + Gu u (nonleaf)
+    GN        float64[n,ncN,nx]             terminal constraint matrices (leaves)
+    cNmin, cNmax float64[n,ncN]             bounds of GN x (leaves)
+(no xmin/xmax/umin/umax).
+
 The tree shapes, distributions and sizes follow the workloads described for
 SPOCK (scenario trees with stage-wise branching, Sec. "Scenario trees"; the
 data-center system of Eq. (dynamics-example)).  Random draws use
@@ -140,11 +148,11 @@ def small_binary(seed=0, N=3, nx=3, nu=2, a=0.5):
 
 
 def large_tree(seed=0, branching_stages=6, branch=4, N=20, nx=50, nu=20,
-               xlim=5.0, ulim=1.0, probs="dirichlet"):
+               xlim=5.0, ulim=1.0, probs="dirichlet", rho=0.95):
     """Branching ``branch`` for the first ``branching_stages`` stages, then one
     child per node, horizon N (defaults: 62,805 nodes, 58,709 nonleaf, 4,096
-    scenarios, about 4.3 M state/input variables).  A = 0.95 U with U
-    Haar-orthogonal (spectral radius 0.95), B ~ N(0, 1/nx), Q = diag U(0.5, 2),
+    scenarios, about 4.3 M state/input variables).  A = rho U with U
+    Haar-orthogonal (spectral radius rho, default 0.95), B ~ N(0, 1/nx), Q = diag U(0.5, 2),
     R = 0.1 I, Q_N = I, AV@R parameter U(0.1, 0.9) per nonleaf node,
     Dirichlet(1) child probabilities (``probs="uniform"``: 1/branch; the draws
     of the other data do not change), |x| <= xlim, |u| <= ulim,
@@ -156,7 +164,7 @@ def large_tree(seed=0, branching_stages=6, branch=4, N=20, nx=50, nu=20,
     prob = _conditional_probs(rng, anc, "dirichlet")
     if probs == "uniform":
         prob = _conditional_probs(None, anc, "uniform")
-    A = 0.95 * _haar_orthogonal(rng, n, nx)
+    A = float(rho) * _haar_orthogonal(rng, n, nx)
     B = rng.standard_normal((n, nx, nu)) / np.sqrt(nx)
     A[0] = 0.0
     B[0] = 0.0
@@ -302,4 +310,100 @@ def batch_instances(seed=0, count=512, max_scenarios=64, probs="uniform"):
         stages = min(stages, N)
         out.append(large_tree(seed=1000 * seed + i, branching_stages=stages, branch=b, N=N, nx=nx, nu=nu,
                               probs=probs))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# general form: polyhedral constraints and dense cost matrices
+# ----------------------------------------------------------------------------
+
+def _scaled_orthogonal(rng, count, n):
+    """count matrices U diag(s), U Haar-orthogonal, s ~ U(0.5, 2): random
+    well-conditioned coordinate changes."""
+    return _haar_orthogonal(rng, count, n) * rng.uniform(0.5, 2.0, size=(count, 1, n))
+
+
+def general_transform(d, seed=0):
+    """The same problem as the box-form instance ``d`` in new coordinates
+    x'^i = T^i x^i, u'^i = S^i u^i with per-node random T^i, S^i (scaled
+    orthogonal).  Returns (d', T, S): dynamics A'^c = T^c A^c T^p^-1,
+    B'^c = T^c B^c S^p^-1 (p the ancestor), dense costs Q'^c = T^p^-T Q^c T^p^-1,
+    R'^c = S^p^-T R^c S^p^-1, Q_N'^j = T^j^-T Q_N^j T^j^-1, constraint rows
+    Gx = [T^i^-1; 0], Gu = [0; S^i^-1] with the box bounds of d, GN = T^j^-1,
+    x0' = T^0 x0.  Its solution is (T^i x^i, S^i u^i) and its optimal value
+    that of d."""
+    rng = np.random.default_rng(seed)
+    anc = np.asarray(d["anc"])
+    n, nx, nu = len(anc), int(d["nx"]), int(d["nu"])
+    T = _scaled_orthogonal(rng, n, nx)
+    S = _scaled_orthogonal(rng, n, nu)
+    Ti, Si = np.linalg.inv(T), np.linalg.inv(S)
+    A = np.zeros((n, nx, nx))
+    B = np.zeros((n, nx, nu))
+    Q = np.zeros((n, nx, nx))
+    R = np.zeros((n, nu, nu))
+    QN = np.zeros((n, nx, nx))
+    for c in range(n):
+        QN[c] = Ti[c].T @ np.diag(d["QN"][c]) @ Ti[c]
+        if c == 0:
+            Q[c], R[c] = np.eye(nx), np.eye(nu)
+            continue
+        p = int(anc[c])
+        A[c] = T[c] @ d["A"][c] @ Ti[p]
+        B[c] = T[c] @ d["B"][c] @ Si[p]
+        Q[c] = Ti[p].T @ np.diag(d["Q"][c]) @ Ti[p]
+        R[c] = Si[p].T @ np.diag(d["R"][c]) @ Si[p]
+    Q = 0.5 * (Q + Q.transpose(0, 2, 1))
+    R = 0.5 * (R + R.transpose(0, 2, 1))
+    QN = 0.5 * (QN + QN.transpose(0, 2, 1))
+    Gx = np.zeros((n, nx + nu, nx))
+    Gu = np.zeros((n, nx + nu, nu))
+    Gx[:, :nx, :] = Ti
+    Gu[:, nx:, :] = Si
+    cmin = np.concatenate([d["xmin"], d["umin"]], axis=1)
+    cmax = np.concatenate([d["xmax"], d["umax"]], axis=1)
+    out = dict(anc=d["anc"], prob=d["prob"], nx=nx, nu=nu, A=A, B=B, Q=Q, R=R, QN=QN, a=d["a"],
+               Gx=Gx, Gu=Gu, cmin=cmin, cmax=cmax, GN=Ti.copy(), cNmin=d["xmin"].copy(),
+               cNmax=d["xmax"].copy(), x0=T[0] @ d["x0"])
+    return out, T, S
+
+
+def general_random(d, seed=0, extra_rows=4, extra_leaf_rows=2, bound=3.0, dense=True):
+    """General-form data on the tree and dynamics of ``d``: dense SPD costs
+    Q^i = D (0.5 I + M M^T / nx) D with M ~ N(0, 1), D the square root of the
+    diagonal of d's Q^i (R, Q_N alike), and constraint rows: the box rows of d
+    (Gamma = I) followed by ``extra_rows`` coupled rows g^T (x, u) in
+    [-bound, bound], g ~ N(0, 1/(nx + nu)) (leaves: ``extra_leaf_rows`` rows
+    on x).  With ``dense=False`` the costs stay diagonal."""
+    rng = np.random.default_rng(seed)
+    n, nx, nu = len(d["anc"]), int(d["nx"]), int(d["nu"])
+
+    def spd(diag, dim):
+        M = rng.standard_normal((n, dim, dim))
+        core = 0.5 * np.eye(dim)[None] + M @ M.transpose(0, 2, 1) / dim
+        Dh = np.sqrt(np.asarray(diag))
+        out = Dh[:, :, None] * core * Dh[:, None, :]
+        return 0.5 * (out + out.transpose(0, 2, 1))
+
+    out = dict(anc=d["anc"], prob=d["prob"], nx=nx, nu=nu, A=d["A"], B=d["B"], a=d["a"], x0=d["x0"])
+    if dense:
+        out["Q"], out["R"], out["QN"] = spd(d["Q"], nx), spd(d["R"], nu), spd(d["QN"], nx)
+    else:
+        out["Q"], out["R"], out["QN"] = d["Q"], d["R"], d["QN"]
+    nc, ncN = nx + nu + extra_rows, nx + extra_leaf_rows
+    Gx = np.zeros((n, nc, nx))
+    Gu = np.zeros((n, nc, nu))
+    Gx[:, :nx, :] = np.eye(nx)
+    Gu[:, nx:nx + nu, :] = np.eye(nu)
+    g = rng.standard_normal((n, extra_rows, nx + nu)) / np.sqrt(nx + nu)
+    Gx[:, nx + nu:, :] = g[:, :, :nx]
+    Gu[:, nx + nu:, :] = g[:, :, nx:]
+    cmin = np.concatenate([d["xmin"], d["umin"], np.full((n, extra_rows), -bound)], axis=1)
+    cmax = np.concatenate([d["xmax"], d["umax"], np.full((n, extra_rows), bound)], axis=1)
+    GN = np.zeros((n, ncN, nx))
+    GN[:, :nx, :] = np.eye(nx)
+    GN[:, nx:, :] = rng.standard_normal((n, extra_leaf_rows, nx)) / np.sqrt(nx)
+    cNmin = np.concatenate([d["xmin"], np.full((n, extra_leaf_rows), -bound)], axis=1)
+    cNmax = np.concatenate([d["xmax"], np.full((n, extra_leaf_rows), bound)], axis=1)
+    out.update(Gx=Gx, Gu=Gu, cmin=cmin, cmax=cmax, GN=GN, cNmin=cNmin, cNmax=cNmax)
     return out
