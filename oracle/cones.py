@@ -9,7 +9,8 @@ Readings taken where the paper is silent or garbled:
   * Eq. (prox:g) prints eta - proj_S3(eta / alpha); the extended Moreau
     decomposition for g = indicator of S3 gives
     prox_{alpha g*}(eta) = eta - alpha proj_S3(eta / alpha), used here.
-  * (K^i)* for K^i = R^{2m}_+ x {0} is R^{2m}_+ x R.
+  * (K^i)* for K^i = R^{2m}_+ x {0} is R^{2m}_+ x R; for a general conic
+    risk measure K^i = R^kp_+ x {0}^(ny - kp) and (K^i)* = R^kp_+ x R^(ny - kp).
 
 Pins (tests/test_oracle_cones.py): Moreau decomposition and orthogonality
 for the SOC, a brute-force grid search for SOC dims 2-3, the optimality
@@ -46,9 +47,9 @@ def proj_S3(w, P: Problem):
     t, lay = P.tree, P.lay
     out = np.array(w, dtype=float, copy=True)
     for i in t.nonleaf:
-        m = len(t.children[i])
         ey = lay.e_y[i]
-        out[ey[:2 * m]] = np.maximum(w[ey[:2 * m]], 0.0)     # (K^i)*: R^{2m}_+ x R
+        kp = P.kp(i)
+        out[ey[:kp]] = np.maximum(w[ey[:kp]], 0.0)           # (K^i)* = R^kp_+ x R^(ny - kp)
         out[lay.e_sb[i]] = max(w[lay.e_sb[i]], 0.0)          # R_+
         if P.general:                                        # C^i = [cmin, cmax]
             out[lay.e_c[i]] = np.clip(w[lay.e_c[i]], P.cmin[i], P.cmax[i])
@@ -78,10 +79,14 @@ def prox_gconj(eta, alpha, P: Problem):
 
 
 def s2_matrix(P: Problem, i):
-    """The matrix [E^iT, -I, -I] whose kernel is S2^i (F^i is empty for
-    AV@R), acting on (y^i, tau^[i], s^[i])."""
+    """The matrix [[E^iT, -I, -I], [F^iT, 0, 0]] whose kernel is S2^i (F^i
+    has no columns for AV@R), acting on (y^i, tau^[i], s^[i])."""
     m = len(P.tree.children[i])
-    return np.hstack([P.E(i).T, -np.eye(m), -np.eye(m)])
+    top = np.hstack([P.E(i).T, -np.eye(m), -np.eye(m)])
+    F = P.F(i)
+    if F.shape[1] == 0:
+        return top
+    return np.vstack([top, np.hstack([F.T, np.zeros((F.shape[1], 2 * m))])])
 
 
 def z2_block(P: Problem, i):

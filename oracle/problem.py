@@ -56,11 +56,14 @@ class Layout:
     e_lc: dict             # leaf j -> (ncN,)     Gamma_N x^j
 
 
-def build_layout(tree: Tree, nx: int, nu: int, nc: int | None = None, ncN: int | None = None) -> Layout:
+def build_layout(tree: Tree, nx: int, nu: int, nc: int | None = None, ncN: int | None = None,
+                 ny: dict | None = None) -> Layout:
     """Index maps of z and eta.  ``nc`` / ``ncN`` (constraint rows per nonleaf
     / leaf node) default to the box form's nx + nu / nx; in the box form the
-    constraint rows are also split into e_x, e_u (nonleaf) and e_lx (leaf)."""
+    constraint rows are also split into e_x, e_u (nonleaf) and e_lx (leaf).
+    ``ny`` (nonleaf node -> rows of y^i) defaults to AV@R's 2 m + 1."""
     box = nc is None and ncN is None
+    nyof = (lambda i: 2 * len(tree.children[i]) + 1) if ny is None else (lambda i: int(ny[i]))
     nc = nx + nu if nc is None else int(nc)
     ncN = nx if ncN is None else int(ncN)
     n = tree.n
@@ -76,8 +79,8 @@ def build_layout(tree: Tree, nx: int, nu: int, nc: int | None = None, ncN: int |
     y, tau, s = {}, {}, {0: s0}
     for i in tree.nonleaf:
         m = len(tree.children[i])
-        y[i] = np.arange(pos, pos + 2 * m + 1)
-        pos += 2 * m + 1
+        y[i] = np.arange(pos, pos + nyof(i))
+        pos += nyof(i)
         for k, c in enumerate(tree.children[i]):
             tau[c] = pos + k
         pos += m
@@ -88,9 +91,8 @@ def build_layout(tree: Tree, nx: int, nu: int, nc: int | None = None, ncN: int |
     pos = 0
     e_y, e_sb, e_x, e_u, e_c = {}, {}, {}, {}, {}
     for i in tree.nonleaf:
-        m = len(tree.children[i])
-        e_y[i] = np.arange(pos, pos + 2 * m + 1)
-        pos += 2 * m + 1
+        e_y[i] = np.arange(pos, pos + nyof(i))
+        pos += nyof(i)
         e_sb[i] = pos
         pos += 1
         e_c[i] = np.arange(pos, pos + nc)
@@ -149,6 +151,20 @@ class Problem:
             self.R = np.asarray(d["R"], float).reshape(n, nu)
             self.QN = np.asarray(d["QN"], float).reshape(n, nx)
         self.a = np.asarray(d["a"], float).reshape(n)
+        # coherent risk measures in conic form (b, E, F, K) per nonleaf node,
+        # K = R^kp_+ x {0}^(ny - kp) (Sec. "Conic representation of risk
+        # measures"); absent: AV@R with parameter a
+        self.general_risk = d.get("risk") is not None
+        self.risk = {}
+        if self.general_risk:
+            for i in self.tree.nonleaf:
+                r = d["risk"][i]
+                m = len(self.tree.children[i])
+                b = np.asarray(r["b"], float).reshape(-1)
+                E = np.asarray(r["E"], float).reshape(b.size, m)
+                F = np.asarray(r.get("F", np.zeros((b.size, 0))), float).reshape(b.size, -1)
+                self.risk[i] = (b, E, F, int(r["kp"]))
+        ny = {i: self.risk[i][0].size for i in self.tree.nonleaf} if self.general_risk else None
         self.general = "Gx" in d
         if self.general:
             self.Gx = np.asarray(d["Gx"], float)
@@ -162,14 +178,14 @@ class Problem:
             self.GN = self.GN.reshape(n, self.ncN, nx)
             self.cNmin = np.asarray(d["cNmin"], float).reshape(n, self.ncN)
             self.cNmax = np.asarray(d["cNmax"], float).reshape(n, self.ncN)
-            self.lay = build_layout(self.tree, nx, nu, self.nc, self.ncN)
+            self.lay = build_layout(self.tree, nx, nu, self.nc, self.ncN, ny=ny)
         else:
             self.xmin = np.asarray(d["xmin"], float).reshape(n, nx)
             self.xmax = np.asarray(d["xmax"], float).reshape(n, nx)
             self.umin = np.asarray(d["umin"], float).reshape(n, nu)
             self.umax = np.asarray(d["umax"], float).reshape(n, nu)
             self.nc, self.ncN = nx + nu, nx
-            self.lay = build_layout(self.tree, nx, nu)
+            self.lay = build_layout(self.tree, nx, nu, ny=ny)
 
     # -- cost matrices and their square roots (definition of L) ---------------
     def _mat(self, M, i):
@@ -201,18 +217,37 @@ class Problem:
         return self._half(self.QN, i)
 
     def require_box_diag(self, what):
-        """Parts of the oracle written for the box form with diagonal costs."""
-        if self.general or self.dense_cost:
-            raise NotImplementedError(what + ": box constraints and diagonal costs only")
+        """Parts of the oracle written for the box form with diagonal costs
+        and AV@R."""
+        if self.general or self.dense_cost or self.general_risk:
+            raise NotImplementedError(what + ": box constraints, diagonal costs and AV@R only")
 
     def b(self, i):
-        """b^i = (p^ch(i), 0_m, 1) for AV@R (Sec. "Conic representation of
-        risk measures"), with conditional child probabilities."""
+        """b^i of the conic representation (Sec. "Conic representation of
+        risk measures"); AV@R: (p^ch(i), 0_m, 1) with conditional child
+        probabilities."""
+        if self.general_risk:
+            return self.risk[i][0]
         ch = self.tree.children[i]
         m = len(ch)
         return np.concatenate([self.tree.prob[ch], np.zeros(m), [1.0]])
 
     def E(self, i):
-        """E^i = [a I, -I, 1]^T, shape (2m+1, m)."""
+        """E^i; AV@R: [a I, -I, 1]^T, shape (2m+1, m)."""
+        if self.general_risk:
+            return self.risk[i][1]
         m = len(self.tree.children[i])
         return np.vstack([self.a[i] * np.eye(m), -np.eye(m), np.ones((1, m))])
+
+    def F(self, i):
+        """F^i (ny x n_nu); AV@R: no columns."""
+        if self.general_risk:
+            return self.risk[i][2]
+        return np.zeros((2 * len(self.tree.children[i]) + 1, 0))
+
+    def kp(self, i):
+        """Rows of y^i in the orthant part of K^i (the rest: the zero cone);
+        (K^i)* = R^kp_+ x R^(ny - kp).  AV@R: 2 m."""
+        if self.general_risk:
+            return self.risk[i][3]
+        return 2 * len(self.tree.children[i])

@@ -88,13 +88,28 @@ def avar_bruteforce(Z, pi, a):
     return best
 
 
-def nested_value(P, x, u, avar=avar_sort):
+def conic_lp(Z, b, E, F, kp):
+    """rho[Z] of the conic representation, Eq. (dual_risk):
+    min { y^T b : E^T y = Z, F^T y = 0, y in K* }, K* = R^kp_+ x R^(ny - kp)
+    (scipy linprog, a library primitive)."""
+    Z = np.asarray(Z, float)
+    ny = b.size
+    A_eq = E.T if F.shape[1] == 0 else np.vstack([E.T, F.T])
+    b_eq = Z if F.shape[1] == 0 else np.concatenate([Z, np.zeros(F.shape[1])])
+    bounds = [(0, None)] * kp + [(None, None)] * (ny - kp)
+    res = linprog(b, A_eq=A_eq, b_eq=b_eq, bounds=bounds, method="highs")
+    assert res.status == 0, res.message
+    return float(res.fun)
+
+
+def nested_value(P, x, u, avar=avar_sort, risk=None):
     """Nested risk-averse cost of Eq. (original-problem) of a given
     trajectory, by backward recursion over the tree:
       W^j = x^jT Q_N^j x^j at leaves,
-      W^i = AV@R_{a^i}[ (x^iT Q^c x^i + u^iT R^c u^i + W^c)_{c in ch(i)} ]
-    with the conditional probabilities of the children.  x: [n, nx],
-    u: dict or [n, nu] (nonleaf rows used)."""
+      W^i = rho^i[ (x^iT Q^c x^i + u^iT R^c u^i + W^c)_{c in ch(i)} ]
+    with rho^i = AV@R_{a^i} over the conditional probabilities of the
+    children, or risk(i, Z) when given.  x: [n, nx], u: dict or [n, nu]
+    (nonleaf rows used)."""
     t = P.tree
     W = np.zeros(t.n)
     for i in sorted(range(t.n), key=lambda k: -t.stage[k]):
@@ -103,7 +118,7 @@ def nested_value(P, x, u, avar=avar_sort):
         else:
             ch = t.children[i]
             Z = np.array([x[i] @ P.Qmat(c) @ x[i] + u[i] @ P.Rmat(c) @ u[i] + W[c] for c in ch])
-            W[i] = avar(Z, t.prob[ch], P.a[i])
+            W[i] = risk(i, Z) if risk is not None else avar(Z, t.prob[ch], P.a[i])
     return float(W[0]), W
 
 

@@ -407,3 +407,58 @@ def general_random(d, seed=0, extra_rows=4, extra_leaf_rows=2, bound=3.0, dense=
     cNmax = np.concatenate([d["xmax"], np.full((n, extra_leaf_rows), bound)], axis=1)
     out.update(Gx=Gx, Gu=Gu, cmin=cmin, cmax=cmax, GN=GN, cNmin=cNmin, cNmax=cNmax)
     return out
+
+
+# ----------------------------------------------------------------------------
+# coherent risk measures in conic form (b, E, F, K), K = R^kp_+ x {0}^(ny-kp)
+# ----------------------------------------------------------------------------
+
+def risk_measures(d, kind="mean_avar", lam=0.5, radius=0.3):
+    """The instance ``d`` with a conic risk measure at every nonleaf node
+    (key "risk": per node None or dict(b, E, F, kp)), children's conditional
+    probabilities pi = d["prob"], AV@R parameter a = d["a"]:
+      "avar":      AV@R_a written in the general form, b = (pi, 0, 1),
+                   E = [a I, -I, 1]^T, kp = 2m;
+      "mean_avar": lam E^pi + (1 - lam) AV@R_a, ambiguity set
+                   {mu : sum mu = 1, lam pi <= mu <= lam pi + (1 - lam) pi / a}:
+                   b = (pi (lam + (1 - lam) / a), -lam pi, 1), E = [I, -I, 1]^T,
+                   kp = 2m (needs a > 0);
+      "tv":        worst case over the total-variation ball
+                   {mu in simplex : ||mu - pi||_1 <= radius}, with nu >= |mu - pi|:
+                   rows (pi - mu + nu, -pi + mu + nu, radius - 1'nu, mu >= 0 | 1 - 1'mu = 0),
+                   n_nu = m, kp = 3m + 1, ny = 3m + 2."""
+    anc = np.asarray(d["anc"])
+    n = len(anc)
+    kids = [[] for _ in range(n)]
+    for c in range(1, n):
+        kids[int(anc[c])].append(c)
+    risk = [None] * n
+    for i in range(n):
+        ch = kids[i]
+        m = len(ch)
+        if m == 0:
+            continue
+        pi = np.asarray(d["prob"], float)[ch]
+        a = float(d["a"][i])
+        I, one = np.eye(m), np.ones((1, m))
+        if kind == "avar":
+            b = np.concatenate([pi, np.zeros(m), [1.0]])
+            E = np.vstack([a * I, -I, one])
+            risk[i] = dict(b=b, E=E, F=np.zeros((2 * m + 1, 0)), kp=2 * m)
+        elif kind == "mean_avar":
+            if a <= 0:
+                raise ValueError("mean_avar needs a > 0")
+            b = np.concatenate([pi * (lam + (1.0 - lam) / a), -lam * pi, [1.0]])
+            E = np.vstack([I, -I, one])
+            risk[i] = dict(b=b, E=E, F=np.zeros((2 * m + 1, 0)), kp=2 * m)
+        elif kind == "tv":
+            Z = np.zeros((m, m))
+            b = np.concatenate([pi, -pi, [radius], np.zeros(m), [1.0]])
+            E = np.vstack([I, -I, np.zeros((1, m)), -I, one])
+            F = np.vstack([-I, -I, one, Z, np.zeros((1, m))])
+            risk[i] = dict(b=b, E=E, F=F, kp=3 * m + 1)
+        else:
+            raise ValueError(kind)
+    out = dict(d)
+    out["risk"] = risk
+    return out
