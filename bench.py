@@ -45,13 +45,14 @@ def measured_peaks():
         return {}
 
 
-# DRAM bytes (read + write) per chain of one launch of the backward chain
-# kernels, from ncu captures on the 15,701-node tree (1,024 chains of 14
-# nonleaf nodes, nx = 50, nu = 20), scaled by the chains of the measured tree
-# (each chain reads its own factors once).  Valid for these kernels as
-# captured; remeasure after changing them.
-NCU_TRAFFIC_PER_CHAIN = {"fp64": 739.954688e6 / 1024, "fp32": 372.118272e6 / 1024}
-NCU_CHAIN_SHAPE = (14, 50, 20)   # chain length, nx, nu of the capture
+# DRAM bytes (read + write) per chain node of one launch of the backward
+# chain kernel, from an ncu capture on the 17,749-node tree (branching 4 for
+# 6 stages, N = 9: 4,096 chains of 3 nonleaf nodes, nx = 50, nu = 20), scaled
+# by the chain nodes of the measured tree (each chain node's factors are read
+# once).  Valid for the kernel as captured (None: not captured since the
+# kernel last changed); remeasure after changing it.
+NCU_TRAFFIC_PER_CHAIN_NODE = {"fp64": 594.511104e6 / (4096 * 3), "fp32": None}
+NCU_CHAIN_SHAPE = (50, 20)   # nx, nu of the capture
 
 
 
@@ -194,9 +195,10 @@ def run_ours(args, rank, world, local_rank):
         return ms, nT, nT_all, infos, clk.summary()
 
     def traffic(prec):
-        if (chain_len, d["nx"], d["nu"]) != NCU_CHAIN_SHAPE:
+        per = NCU_TRAFFIC_PER_CHAIN_NODE["fp64" if prec == spock.SPOCK_FP64 else "fp32"]
+        if per is None or (d["nx"], d["nu"]) != NCU_CHAIN_SHAPE:
             return None
-        return round(NCU_TRAFFIC_PER_CHAIN["fp64" if prec == spock.SPOCK_FP64 else "fp32"] * n_chains)
+        return round(per * n_chains * chain_len)
 
     def roofline(infos, prec):
         elt = 8 if prec == spock.SPOCK_FP64 else 4
@@ -284,6 +286,8 @@ def run_ours(args, rank, world, local_rank):
         if args.families > 0 else None
     grad = section("gradient", lambda: grad_workload(args, spock, workloads, dev)) \
         if (rank == 0 and args.grad_instances > 0) else None
+    general = section("general form", lambda: general_workload(args, spock, workloads, dev)) \
+        if (rank == 0 and args.general) else None
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -302,7 +306,11 @@ def run_ours(args, rank, world, local_rank):
                        "n_z": P.n_z, "n_eta": P.n_eta, "nodes": n, "nonleaf": nl,
                        "step": "one SPOCK iteration (Anderson m=%d), K steps = one cold-start solve capped "
                                "at K iterations" % args.memory,
-                       "l2": "inputs larger than L2 (factors 5.1 GB FP64 / 2.6 GB FP32 per T)",
+                       "l2": "inputs larger than L2 (chain factors %.2f GB FP64 / %.2f GB FP32 per T)" % (
+                           (bytes_bwd_chain(d, n_chains, wl["N"] - wl["branching_stages"], 8)
+                            + bytes_fwd_chain(d, n_chains, wl["N"] - wl["branching_stages"], 8)) / 1e9,
+                           (bytes_bwd_chain(d, n_chains, wl["N"] - wl["branching_stages"], 4)
+                            + bytes_fwd_chain(d, n_chains, wl["N"] - wl["branching_stages"], 4)) / 1e9),
                        "parallelism": f"replicas x{world}"},
             "time_to_tol": h.get("time_to_tol"), "iterations": h["iterations"], "n_T_steps": h["n_T_steps"],
             "branches_K0_K1_K2_cap": h["branches"], "roofline": h["roofline"], "clocks": h["clocks"], "gpu_launches": h["gpu_launches"], "e2e": e2e,
@@ -333,6 +341,8 @@ def run_ours(args, rank, world, local_rank):
             line["family_batch"] = family
         if grad:
             line["gradient"] = grad
+        if general:
+            line["general_form"] = general
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
@@ -609,12 +619,14 @@ def grad_workload(args, spock, workloads, dev):
     radius 0.5 (the workload states neither; with 0.95 the method does not
     reach 1e-6 on this tree within 20,000 iterations).  One batched FP64
     solve (tolerance 1e-6, at most args.grad_iter iterations per instance),
-    then per instance the envelope gradient (spock_grad_dev, FP64 and FP32)
-    and the adjoint of the CP fixed point (spock_adjoint_dev, FP64, on a few
-    instances), timed with CUDA events against the solve time per instance.
-    Finite-difference check on instance 0: central differences with h = 1e-6
-    along random directions of x0, diag Q, diag R, A and B, from solves to
-    xi <= 1e-12, against both gradients."""
+    then per instance the envelope gradient (spock_grad_dev, FP64 and FP32),
+    timed with CUDA events against the solve time per instance, and the
+    adjoint of the CP fixed point (spock_adjoint_dev, FP64) at instance 0's
+    solution to the solve's tolerance.  Finite-difference check on instance
+    0: central differences with h = 1e-6 along random directions of x0,
+    diag Q, diag R, A and B, from solves to xi <= 1e-12 (perturbed solves
+    warm-started from the base solution), against both gradients (adjoint
+    solved to 1e-11 there)."""
     import torch
     cnt = args.grad_instances
     ds = [workloads.large_tree(seed=s, branching_stages=4, branch=3, N=10, nx=20, nu=8, probs="uniform", rho=0.5)
@@ -670,20 +682,16 @@ def grad_workload(args, spock, workloads, dev):
         ms = ev0.elapsed_time(ev1) / cnt
         out[f"grad_ms_{nm}"] = round(ms, 4)
         out[f"grad_over_solve_{nm}"] = round(ms / per_inst, 5)
-    # adjoint of the fixed point (phi = s^0) on the first instances
-    na = min(4, cnt)
-    adj = []
-    for i in range(na):
-        ga = grads()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rc, it, res = spock.spock_adjoint_dev(probs[i].handle, zs[i], es[i], None, 20000, 1e-10, *ga)
-        torch.cuda.synchronize()
-        adj.append((time.perf_counter() - t0) * 1e3)
-        adj.append(it)
-    out["adjoint_fp64"] = {"instances": na, "ms_median": round(float(np.median(adj[0::2])), 3),
-                           "iterations_median": int(np.median(adj[1::2])), "tol": 1e-10,
-                           "over_solve": round(float(np.median(adj[0::2])) / per_inst, 4)}
+    # adjoint of the fixed point (phi = s^0) at the first instance's solution,
+    # to the solve's own tolerance
+    ga = grads()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, it, res = spock.spock_adjoint_dev(probs[0].handle, zs[0], es[0], None, 10000, 1e-6, *ga)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3
+    out["adjoint_fp64"] = {"instance": 0, "ms": round(ms, 3), "applications_of_JT": it, "tol": 1e-6,
+                           "residual": res, "over_solve": round(ms / per_inst, 4)}
     spock.spock_free(b)
     for p in probs:
         p.close()
@@ -693,31 +701,51 @@ def grad_workload(args, spock, workloads, dev):
     tight = spock.spock_default_settings(precision=spock.SPOCK_FP64, eps_abs=1e-12, eps_rel=1e-12, memory=5,
                                          max_iter=args.grad_fd_iter)
 
-    def solve(PP, x0):
+    def solve(PP, x0, start=None):
+        """Solve to 1e-12; perturbed problems start from the base solution."""
         z = torch.zeros(PP.n_z, dtype=torch.float64, device=dev)
         e = torch.zeros(PP.n_eta, dtype=torch.float64, device=dev)
-        inf = spock.spock_solve_dev(PP.handle, torch.tensor(x0, dtype=torch.float64, device=dev), tight, z, e, 0)
+        if start is not None:
+            z.copy_(start[0])
+            e.copy_(start[1])
+        inf = spock.spock_solve_dev(PP.handle, torch.tensor(x0, dtype=torch.float64, device=dev), tight, z, e,
+                                    0 if start is None else 1)
         return z, e, inf
 
+    tight_base = tight
+    tight = spock.spock_default_settings(precision=spock.SPOCK_FP64, eps_abs=1e-12, eps_rel=1e-12, memory=5,
+                                         max_iter=4 * args.grad_fd_iter)
+    t_fd = time.perf_counter()
     z, e, inf0 = solve(P, d["x0"])
+    tight = tight_base
+    base = (z.clone(), e.clone())
+    t_base = time.perf_counter() - t_fd
+    print(f"[bench]   gradient: base solve to 1e-12 {t_base:.1f} s, "
+          f"{inf0.iterations} iterations", file=sys.stderr, flush=True)
     ge = grads()
     spock.spock_grad_dev(P.handle, z, e, spock.SPOCK_FP64, *ge)
     ga = grads()
-    rc, ait, ares = spock.spock_adjoint_dev(P.handle, z, e, None, 200000, 1e-12, *ga)
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter()
+    rc, ait, ares = spock.spock_adjoint_dev(P.handle, z, e, None, 100000, 1e-11, *ga)
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t_adj
     ge = [t.cpu().numpy() for t in ge]
     ga = [t.cpu().numpy() for t in ga]
     out["adjoint_vs_envelope"] = {"max_rel_diff": max(float(np.max(np.abs(a - b_)) / max(np.max(np.abs(b_)), 1e-300))
                                                       for a, b_ in zip(ga, ge)),
-                                  "adjoint_iterations": ait, "adjoint_residual": ares}
+                                  "adjoint_applications_of_JT": ait, "adjoint_residual": ares,
+                                  "adjoint_s": round(t_adj, 2), "base_solve_s": round(t_base, 1)}
     rng = np.random.default_rng(7)
     h = 1e-6
     checks = {}
     conv = [inf0.status == 0]
     dirv = rng.standard_normal(nx)
     dirv /= np.linalg.norm(dirv)
-    zp_, _, infp = solve(P, d["x0"] + h * dirv)
-    zm_, _, infm = solve(P, d["x0"] - h * dirv)
+    zp_, _, infp = solve(P, d["x0"] + h * dirv, base)
+    zm_, _, infm = solve(P, d["x0"] - h * dirv, base)
     conv += [infp.status == 0, infm.status == 0]
+    fd_its = [infp.iterations, infm.iterations]
     checks["x0"] = ((float(zp_[0].item()) - float(zm_[0].item())) / (2 * h), float(ge[0] @ dirv),
                     float(ga[0] @ dirv))
     P.close()
@@ -733,19 +761,92 @@ def grad_workload(args, spock, workloads, dev):
             dd = dict(d)
             dd[key] = d[key] + sgn * h * dq * scale
             PP = spock.Problem(dd)
-            zz, _, inf_ = solve(PP, d["x0"])
+            zz, _, inf_ = solve(PP, d["x0"], base)
             vals.append(float(zz[0].item()))
             conv.append(inf_.status == 0)
+            fd_its.append(inf_.iterations)
             PP.close()
         checks[key] = ((vals[0] - vals[1]) / (2 * h), an_e, an_a)
     out["fd_check"] = {
         "tree": "instance 0 of the workload (607 nodes)", "h": h, "solve_tol": 1e-12,
         "directions": "x0: unit N(0, 1); Q, R: X <- X (1 + h dX); A, B: X <- X + h dX; dX ~ N(0, 1) per entry",
-        "converged": all(conv),
+        "converged": all(conv), "base_iterations": inf0.iterations,
+        "perturbed_solve_iterations": fd_its,
         **{k: {"central_fd": fd, "envelope": ae, "adjoint": aa,
                "rel_err_envelope": abs(ae - fd) / max(abs(fd), 1e-12),
                "rel_err_adjoint": abs(aa - fd) / max(abs(fd), 1e-12)} for k, (fd, ae, aa) in checks.items()}}
     torch.cuda.empty_cache()
+    return out
+
+
+def general_workload(args, spock, workloads, dev):
+    """The general form: polyhedral constraints, dense cost matrices and
+    conic risk measures.  (1) T evaluations per second through
+    spock_cp_step_dev (50 CP steps, CUDA events, FP64 and FP32) on a tree
+    with the large tree's launch shapes at smaller size -- branching 4 for
+    5 stages then chains, N = 9 (5,461 nodes), nx = 50, nu = 20 -- in the box
+    form and in the general form (dense Q, R, Q_N; nc = 80 constraint rows:
+    the box rows and 10 coupled rows; ncN = 56), with the bytes of the
+    per-node matrices of L that one T reads (column-major copies once in the
+    dual update, transposed copies in the dual update's L* r_eta and in the
+    prox-f preparation).  (2) Solves to 1e-6 of the 15-node binary tree with
+    AV@R, the mean-AV@R mixture and the total-variation worst case."""
+    import torch
+    base = workloads.large_tree(seed=1, branching_stages=5, branch=4, N=9)
+    gen = workloads.general_random(base, seed=1, extra_rows=10, extra_leaf_rows=6)
+    n, nl = len(base["anc"]), int(np.sum(np.bincount(base["anc"][1:], minlength=len(base["anc"])) > 0))
+    nx, nu = base["nx"], base["nu"]
+    nc, ncN = gen["Gx"].shape[1], gen["GN"].shape[1]
+    pad = lambda k: (k + 3) // 4 * 4
+    # entries of the per-node matrices (one layout): Gamma, Q^1/2, R^1/2 of
+    # the edge into each nonroot node, Gamma_N and Q_N^1/2 at leaves
+    ent_c = nl * (nx + nu) * pad(nc) + (n - 1) * (nx * pad(nx) + nu * pad(nu)) + (n - nl) * (
+        nx * pad(ncN) + nx * pad(nx))
+    ent_t = nl * nc * pad(nx + nu) + (n - 1) * (nx * pad(nx) + nu * pad(nu)) + (n - nl) * (
+        ncN * pad(nx) + nx * pad(nx))
+    out = {"nodes": n, "nx": nx, "nu": nu, "nc": nc, "ncN": ncN, "steps": 50}
+    K = 50
+    for nm, d in (("box", base), ("general", gen)):
+        P = spock.Problem(d)
+        x0 = torch.tensor(d["x0"], dtype=torch.float64, device=dev)
+        alpha = 0.99 / P.norm_L
+        r = {"norm_L": P.norm_L}
+        for prec, pn in ((spock.SPOCK_FP64, "fp64"), (spock.SPOCK_FP32, "fp32")):
+            z = torch.zeros(P.n_z, dtype=torch.float64, device=dev)
+            e = torch.zeros(P.n_eta, dtype=torch.float64, device=dev)
+            spock.spock_cp_step_dev(P.handle, x0, 3, alpha, prec, z, e)   # warm-up
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            cur = torch.cuda.current_stream()
+            torch.cuda.synchronize()
+            ev0.record(cur)
+            spock.spock_cp_step_dev(P.handle, x0, K, alpha, prec, z, e)
+            ev1.record(cur)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1) / K
+            r[pn] = {"ms_per_T": round(ms, 4), "T_per_s": round(1e3 / ms, 1)}
+            if nm == "general":
+                elt = 8 if prec == spock.SPOCK_FP64 else 4
+                mb = elt * (ent_c + 2 * ent_t)
+                r[pn]["L_matrix_bytes_per_T"] = mb
+        out[nm] = r
+        P.close()
+    for pn in ("fp64", "fp32"):
+        out["general"][pn]["added_ms_per_T"] = round(out["general"][pn]["ms_per_T"] - out["box"][pn]["ms_per_T"], 4)
+    # risk measures on the 15-node binary tree
+    risks = {}
+    for kind in ("avar", "mean_avar", "tv"):
+        d = workloads.risk_measures(workloads.small_binary(0, a=0.5), kind, lam=0.5, radius=0.3)
+        P = spock.Problem(d)
+        s = spock.spock_default_settings(memory=5, max_iter=20000)
+        z = np.zeros(P.n_z)
+        e = np.zeros(P.n_eta)
+        t0 = time.perf_counter()
+        info = spock.spock_solve(P.handle, d["x0"], s, z, e, 0)
+        risks[kind] = {"ms": round((time.perf_counter() - t0) * 1e3, 2), "iterations": info.iterations,
+                       "status": "converged" if info.status == 0 else "max_iter", "cost": float(z[0]),
+                       "n_z": P.n_z, "n_eta": P.n_eta}
+        P.close()
+    out["risk_measures_binary_N3"] = risks
     return out
 
 
@@ -865,6 +966,7 @@ def main():
     ap.add_argument("--batch", type=int, default=512, help="instances of the batched measurement (0 skips it)")
     ap.add_argument("--batch-iter", type=int, default=50)
     ap.add_argument("--families", type=int, default=64, help="families of the family-form batch (0 skips it)")
+    ap.add_argument("--general", type=int, default=1, help="general-form measurement (0 skips it)")
     ap.add_argument("--family-size", type=int, default=8, help="instances per family (x0 differs)")
     ap.add_argument("--batch-tol-iter", type=int, default=10000,
                     help="iteration cap of the batched time-to-1e-6 solve (0 skips it)")

@@ -179,18 +179,93 @@ int spock_tree_info(const spock_tree* tree, int32_t* n_nodes, int32_t* horizon,
  *   a         : [n] AV@R parameter of each nonleaf node, in [0, 1].
  *   xmin,xmax : [n][nx] state box of every node (xmin <= xmax).
  *   umin,umax : [n][nu] input box of every nonleaf node.
- *   flags     : reserved, pass 0.
+ *   flags     : 0, or SPOCK_DENSE_COST: Q, R, QN are then full symmetric
+ *               positive definite matrices [n][nx][nx], [n][nu][nu],
+ *               [n][nx][nx] (row-major), as in spock_problem_create_general,
+ *               and the problem runs on the general-form kernels with the
+ *               box rows as constraint matrices Gamma = I.
  *   out       : receives the handle; it owns a copy of the data, the FP64
  *               factors (and their FP32 copies) in device memory.
  * The current CUDA device at creation is used for every later call.
- * Errors: INVALID_ARG, NOT_POSDEF, NUMERICAL (non-finite input), CUDA, OOM.
+ * Errors: INVALID_ARG, NOT_POSDEF, NUMERICAL (non-finite input), CUDA, OOM,
+ * UNSUPPORTED (unknown flag).
  */
+#define SPOCK_DENSE_COST 1
 int spock_problem_create(const spock_tree* tree, int32_t nx, int32_t nu,
                          const double* A, const double* B, const double* Q,
                          const double* R, const double* QN, const double* a,
                          const double* xmin, const double* xmax,
                          const double* umin, const double* umax,
                          int32_t flags, spock_problem** out);
+
+/*
+ * spock_problem_create_general -- RAOCP data in the paper's general form:
+ * constraints Gamma_x^i x^i + Gamma_u^i u^i in C^i (nonleaf i) and
+ * Gamma_N^j x^j in C_N^j (leaf j) of Eq. (constraints), with C^i, C_N^j
+ * boxes, and quadratic costs with full matrices (Sec. "Quadratic costs").
+ * The rows of L (definition of L) become per-node matrix-vector products:
+ *   nonleaf block:  (y^i, s^i - b'y^i, Gamma_x^i x^i + Gamma_u^i u^i)   nc rows
+ *   nonroot block:  (Q^i^1/2 x^anc, R^i^1/2 u^anc, tau^i/2, tau^i/2)
+ *   leaf block:     (Gamma_N^j x^j, Q_N^j^1/2 x^j, s^j/2, s^j/2)         ncN rows
+ * where M^1/2 is the upper Cholesky factor F of M (F'F = M; any factor gives
+ * the same cost ||F x||^2 = x'Mx, this one is the library's).  Eta is laid out
+ * as for spock_problem_create with nc (nonleaf) and ncN (leaf) constraint
+ * rows in place of the nx + nu and nx box rows.  ||L|| is the largest norm
+ * of the per-node blocks (remark after the definition of L): the largest
+ * eigenvalue of Gamma^i'Gamma^i + sum_c blockdiag(Q^c, R^c), resp.
+ * Gamma_N'Gamma_N + Q_N, found by power iteration and certified as an upper
+ * bound by a Cholesky factorisation of (lambda (1 + 1e-9) I - M) on the host.
+ *   A, B, a     : as spock_problem_create (a is read only where risk is NULL).
+ *   risk        : NULL (AV@R with parameter a at every nonleaf node), or [n]
+ *                 per node (caller's numbering; leaves ignored) a coherent
+ *                 risk measure in the conic form of Sec. "Conic representation
+ *                 of risk measures", Eq. (dual_risk): rho[Z] = min { y'b :
+ *                 E'y = Z, F'y = 0, y in K* } with K = R^kp_+ x {0}^(ny - kp).
+ *                 Then y^i has ny entries, S2^i = ker [[E'  -I  -I], [F'  0  0]]
+ *                 (projected with the dense projector I - M'(MM')^-1 M, formed
+ *                 on the host: M must have full row rank, i.e. F full column
+ *                 rank), and (K^i)* = R^kp_+ x R^(ny - kp) in S3.  Needs
+ *                 ny + 2 m <= 160 per node.  With risk NULL the AV@R
+ *                 projection on S2 is the closed form (any m).  z_2 of node i is (y^i [ny],
+ *                 tau^[i] [m], s^[i] [m]) and its nonleaf eta block
+ *                 (y^i [ny], s^i - b'y^i, constraint rows [nc]).
+ *   Q, R, QN    : with flags & SPOCK_DENSE_COST: [n][nx][nx], [n][nu][nu],
+ *                 [n][nx][nx] symmetric positive definite (row-major; the
+ *                 upper triangle is read); otherwise diagonals [n][nx],
+ *                 [n][nu], [n][nx] (> 0).
+ *   nc          : constraint rows per nonleaf node, 1 <= nc <= 128.
+ *   Gx, Gu      : [n][nc][nx], [n][nc][nu] row-major Gamma_x^i, Gamma_u^i
+ *                 (read at nonleaf nodes).
+ *   cmin, cmax  : [n][nc] bounds of C^i (cmin <= cmax; +-inf allowed).
+ *   ncN         : constraint rows per leaf, 1 <= ncN <= 128.
+ *   GN          : [n][ncN][nx] row-major Gamma_N^j (read at leaves).
+ *   cNmin,cNmax : [n][ncN] bounds of C_N^j.
+ *   flags       : 0 or SPOCK_DENSE_COST.
+ * Every entry point that takes a problem accepts a general one except
+ * spock_grad(_dev), spock_adjoint_dev (their formulas are written for
+ * diagonal costs and box constraints) and spock_batch_create: these return
+ * SPOCK_ERR_UNSUPPORTED.  Solves never use the single-block solve kernel.
+ * Errors: INVALID_ARG, NOT_POSDEF (a cost matrix is not positive
+ * definite), NUMERICAL, CUDA, OOM, UNSUPPORTED (unknown flag).
+ */
+typedef struct spock_risk {
+  int32_t ny;        /* rows of y^i, >= 1 */
+  int32_t n_nu;      /* columns of F^i, >= 0 */
+  int32_t kp;        /* 0 <= kp <= ny: K^i = R^kp_+ x {0}^(ny - kp) */
+  const double* b;   /* [ny] */
+  const double* E;   /* [ny][m] row-major, m = the node's number of children */
+  const double* F;   /* [ny][n_nu] row-major; may be NULL when n_nu = 0 */
+} spock_risk;
+
+int spock_problem_create_general(const spock_tree* tree, int32_t nx, int32_t nu,
+                                 const double* A, const double* B, const double* Q,
+                                 const double* R, const double* QN, const double* a,
+                                 const spock_risk* risk,
+                                 int32_t nc, const double* Gx, const double* Gu,
+                                 const double* cmin, const double* cmax,
+                                 int32_t ncN, const double* GN,
+                                 const double* cNmin, const double* cNmax,
+                                 int32_t flags, spock_problem** out);
 
 /*
  * spock_problem_clone -- a problem with the same tree, data and offline
@@ -330,9 +405,13 @@ int spock_grad_dev(spock_problem* p, const double* z, const double* eta, int32_t
  * spock_adjoint_dev -- gradient of phi(z*) = <g, z*> for any linear function
  * of the solution (g_z = NULL: phi = s^0, the optimal cost V*) with respect
  * to the problem data, by implicit differentiation of the CP fixed point
- * v* = T(v*) of Eq. (chambolle-pock-operator): the adjoint w = J^T w + (g, 0)
- * is iterated from w = 0 with J the Jacobian of T at the converged pair
- * (z, eta) (device buffers, FP64, e.g. the output of spock_solve_dev).  J^T
+ * v* = T(v*) of Eq. (chambolle-pock-operator): the adjoint equation
+ * (I - J^T) w = (g, 0) is solved by restarted GMRES(m) from w = 0 (m = 100,
+ * or fewer -- at least 10 -- when the basis would take more than a quarter of
+ * the free device memory at the first call; classical Gram-Schmidt with one
+ * reorthogonalisation, deterministic reductions), J the
+ * Jacobian of T at the converged pair (z, eta) (device buffers, FP64, e.g.
+ * the output of spock_solve_dev).  J^T
  * is applied with the library's kernels: the Jacobians of the cone
  * projections of S3 at eta + alpha L z, L*, the Jacobian of prox_{alpha f}
  * (the homogeneous Riccati pass of Algorithm 2 and proj_S2) and L.  Then
@@ -346,17 +425,22 @@ int spock_grad_dev(spock_problem* p, const double* z, const double* eta, int32_t
  * spock_grad_dev's (envelope theorem); for other phi (a component of the
  * first input u^0, say) it is the derivative of the solution map.
  *   g_z        : [n_z] device, the gradient of phi in z (NULL: e_{s^0}).
- *   max_iter, tol : the iteration stops when max|w_new - w| <=
- *                tol max(1, max|w|) (checked every 20 iterations).
+ *   max_iter, tol : the solve stops when the residual of the adjoint
+ *                equation max|(g, 0) - (I - J^T) w| <= tol max(1, max|w|)
+ *                (the true residual, checked at every restart; inside a
+ *                cycle the GMRES residual estimate ends it early), or after
+ *                max_iter applications of J^T.
  *   outputs    : as spock_grad_dev (device, FP64, caller's numbering, any
  *                may be NULL); iterations, residual (optional host pointers)
- *                receive the iterations run and the final relative change.
+ *                receive the applications of J^T and the final relative
+ *                residual.
  * Returns SPOCK_OK when the tolerance is met, SPOCK_MAX_ITER at the cap
  * (gradients written), SPOCK_ERR_NUMERICAL if the iteration diverges (the
  * fixed point must be one where T is differentiable and I - J^T invertible
  * on the data's directions).  Uses the problem's Riccati scratch: not
- * concurrent with solves on the same problem.  Device vectors are allocated
- * on the first call and kept by the problem.  Blocking.
+ * concurrent with solves on the same problem.  Device vectors (the Krylov
+ * basis: m + 1 vectors of n_z + n_eta doubles, and about 12 more) are
+ * allocated on the first call and kept by the problem.  Blocking.
  */
 int spock_adjoint_dev(spock_problem* p, const double* z, const double* eta, const double* g_z, int32_t max_iter,
                       double tol, double* g_x0, double* g_A, double* g_B, double* g_Q, double* g_R, double* g_QN,

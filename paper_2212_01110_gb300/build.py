@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libspock.so")
-SOURCES = ["tree.cpp", "factor.cpp", "ops.cu", "riccati.cu", "riccati_tma.cu", "riccati_grp.cu", "supermann.cu", "rounds.cu", "grad.cu", "adjoint.cu", "peak.cu", "cta.cu", "solver.cu"]
+SOURCES = ["tree.cpp", "factor.cpp", "general.cpp", "ops.cu", "ops_gen.cu", "riccati.cu", "riccati_tma.cu", "riccati_grp.cu", "supermann.cu", "rounds.cu", "grad.cu", "adjoint.cu", "peak.cu", "cta.cu", "solver.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,6 +1,6 @@
 // Adjoint of the CP fixed point (implicit differentiation of v* = T(v*)):
-// the kernels of the adjoint iteration w <- J^T w + (g, 0) and of the
-// gradient of phi(z*) = <g, z*> in the problem data (FP64).
+// the kernels of the adjoint solve (I - J^T) w = (g, 0) by restarted GMRES
+// and of the gradient of phi(z*) = <g, z*> in the problem data (FP64).
 //
 // J is the Jacobian of T (Eq. (chambolle-pock-operator)) at the converged
 // pair.  With A the Jacobian of prox_{alpha f} (identity on s^0, the
@@ -127,28 +127,97 @@ __global__ void k_axpy(int64_t n, double a, const double* __restrict__ x, const 
     out[i] = y[i] + a * x[i];
 }
 
-// One adjoint step from (q, t = L* q, p, Lp): w <- (p - alpha t + g, q - alpha Lp);
-// red (optional) receives max |w_new - w_old| and max |w_new| (as the bit
-// patterns of non-negative doubles, which order like the values).
-__global__ void k_adj_update(int64_t nz, int64_t ne, double alpha, const double* __restrict__ pz,
-                             const double* __restrict__ t, const double* __restrict__ g,
-                             const double* __restrict__ q, const double* __restrict__ Lp, double* __restrict__ w,
-                             unsigned long long* red) {
-  double dmax = 0.0, wmax = 0.0;
+// ---------------------------------------------------------------------------
+// restarted GMRES on (I - J^T) w = (g, 0): the Krylov basis is a set of
+// vectors of length nz + ne with stride ld (FP64), built by classical
+// Gram-Schmidt with one reorthogonalisation; dot products are reduced in a
+// fixed order (block partials, then one block), so runs are deterministic.
+// ---------------------------------------------------------------------------
+constexpr int kGmresMaxBasis = 32;    // basis vectors per dot-product launch
+constexpr int kGmresMaxRestart = 128; // basis vectors of one axpy launch
+
+// u = x - J^T x from the parts of J^T x: (pz - alpha t, q - alpha Lp)
+__global__ void k_jt_residual(int64_t nz, int64_t ne, double alpha, const double* __restrict__ pz,
+                              const double* __restrict__ t, const double* __restrict__ q,
+                              const double* __restrict__ Lp, const double* __restrict__ x, double* __restrict__ u) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nz + ne;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double nv = i < nz ? pz[i] - alpha * t[i] + g[i] : q[i - nz] - alpha * Lp[i - nz];
-    dmax = fmax(dmax, fabs(nv - w[i]));
-    wmax = fmax(wmax, fabs(nv));
-    w[i] = nv;
+       i += (int64_t)gridDim.x * blockDim.x)
+    u[i] = x[i] - (i < nz ? pz[i] - alpha * t[i] : q[i - nz] - alpha * Lp[i - nz]);
+}
+
+// partials[block][j] = sum over the block's entries of u . V_j, j < k
+__global__ void __launch_bounds__(256) k_dots(int64_t n, const double* __restrict__ u, const double* __restrict__ V,
+                                              int64_t ld, int k, double* __restrict__ partials) {
+  double acc[kGmresMaxBasis];
+#pragma unroll
+  for (int j = 0; j < kGmresMaxBasis; ++j) acc[j] = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double ui = u[i];
+#pragma unroll
+    for (int j = 0; j < kGmresMaxBasis; ++j)
+      if (j < k) acc[j] = fma(ui, V[(int64_t)j * ld + i], acc[j]);
   }
-  if (red) {
-    dmax = warp_max(dmax);
-    wmax = warp_max(wmax);
-    if ((threadIdx.x & 31) == 0) {
-      atomicMax(red, (unsigned long long)__double_as_longlong(dmax));
-      atomicMax(red + 1, (unsigned long long)__double_as_longlong(wmax));
+  __shared__ double red[8][kGmresMaxBasis];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < kGmresMaxBasis; ++j) {
+    if (j < k) {
+      const double v = warp_sum(acc[j]);
+      if (lane == 0) red[w][j] = v;
     }
+  }
+  __syncthreads();
+  if (threadIdx.x < k) {
+    double sum = 0.0;
+    for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) sum += red[ww][threadIdx.x];
+    partials[(int64_t)blockIdx.x * kGmresMaxBasis + threadIdx.x] = sum;
+  }
+}
+
+// out[j] = sum_b partials[b][j], j < k (one block, fixed order)
+__global__ void k_dots_reduce(int nblocks, int k, const double* __restrict__ partials, double* __restrict__ out) {
+  const int j = threadIdx.x;
+  if (j >= k) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += partials[(int64_t)b * kGmresMaxBasis + j];
+  out[j] = s;
+}
+
+// u += sign * sum_{j < k} h_j V_j  (h on the device, k <= kGmresMaxRestart)
+__global__ void k_axpy_many(int64_t n, double* __restrict__ u, const double* __restrict__ V, int64_t ld, int k,
+                            const double* __restrict__ h, double sign) {
+  __shared__ double hs[kGmresMaxRestart];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = sign * h[j];
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = u[i];
+    for (int j = 0; j < k; ++j) v = fma(hs[j], V[(int64_t)j * ld + i], v);
+    u[i] = v;
+  }
+}
+
+// v = a u
+__global__ void k_scale(int64_t n, double a, const double* __restrict__ u, double* __restrict__ v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = a * u[i];
+}
+
+// red[0] = max |b - u|, red[1] = max |x| (bit patterns of non-negative
+// doubles), r = b - u written out; b = (g, 0)
+__global__ void k_true_residual(int64_t nz, int64_t ntot, const double* __restrict__ g, const double* __restrict__ u,
+                                const double* __restrict__ x, double* __restrict__ r, unsigned long long* red) {
+  double rmax = 0.0, xmax = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ntot; i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = (i < nz ? g[i] : 0.0) - u[i];
+    r[i] = ri;
+    rmax = fmax(rmax, fabs(ri));
+    xmax = fmax(xmax, fabs(x[i]));
+  }
+  rmax = warp_max(rmax);
+  xmax = warp_max(xmax);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(red, (unsigned long long)__double_as_longlong(rmax));
+    atomicMax(red + 1, (unsigned long long)__double_as_longlong(xmax));
   }
 }
 
@@ -225,10 +294,34 @@ void launch_axpy(int64_t n, double a, const double* x, const double* y, double* 
   k_axpy<<<grid, 256, 0, st>>>(n, a, x, y, out);
 }
 
-void launch_adj_update(int64_t nz, int64_t ne, double alpha, const double* pz, const double* t, const double* g,
-                       const double* q, const double* Lp, double* w, unsigned long long* red, int grid,
-                       cudaStream_t st) {
-  k_adj_update<<<grid, 256, 0, st>>>(nz, ne, alpha, pz, t, g, q, Lp, w, red);
+void launch_jt_residual(int64_t nz, int64_t ne, double alpha, const double* pz, const double* t, const double* q,
+                        const double* Lp, const double* x, double* u, int grid, cudaStream_t st) {
+  k_jt_residual<<<grid, 256, 0, st>>>(nz, ne, alpha, pz, t, q, Lp, x, u);
+}
+
+// out[j] = u . V_j for j < k, in launches of 32 basis vectors; partials
+// holds grid x 32 doubles
+void launch_dots(int64_t n, const double* u, const double* V, int64_t ld, int k, double* partials, double* out,
+                 int grid, cudaStream_t st) {
+  for (int c = 0; c < k; c += kGmresMaxBasis) {
+    const int kc = std::min(kGmresMaxBasis, k - c);
+    k_dots<<<grid, 256, 0, st>>>(n, u, V + (int64_t)c * ld, ld, kc, partials);
+    k_dots_reduce<<<1, kGmresMaxBasis, 0, st>>>(grid, kc, partials, out + c);
+  }
+}
+
+void launch_axpy_many(int64_t n, double* u, const double* V, int64_t ld, int k, const double* h, double sign,
+                      int grid, cudaStream_t st) {
+  k_axpy_many<<<grid, 256, 0, st>>>(n, u, V, ld, k, h, sign);
+}
+
+void launch_scale(int64_t n, double a, const double* u, double* v, int grid, cudaStream_t st) {
+  k_scale<<<grid, 256, 0, st>>>(n, a, u, v);
+}
+
+void launch_true_residual(int64_t nz, int64_t ntot, const double* g, const double* u, const double* x, double* r,
+                          unsigned long long* red, int grid, cudaStream_t st) {
+  k_true_residual<<<grid, 256, 0, st>>>(nz, ntot, g, u, x, r, red);
 }
 
 void launch_adj_gradients(const KP<double>& p, const double* z, const double* eta, const double* q,

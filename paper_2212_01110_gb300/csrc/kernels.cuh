@@ -129,6 +129,30 @@ struct KP {
   S* __restrict__ q;
   S* __restrict__ d;
   const S* __restrict__ x0;
+  // general form (gen != 0): constraint rows and leading dimensions, and the
+  // per-node matrices of L in column-major (c) and transposed (t) layouts
+  int32_t gen, nc, ncN, ldc, ldxu, ldx, ldu, ldcn, cst;
+  const S* __restrict__ gc;
+  const S* __restrict__ gt;
+  const S* __restrict__ fqc;
+  const S* __restrict__ fqt;
+  const S* __restrict__ frc;
+  const S* __restrict__ frt;
+  const S* __restrict__ fnc;
+  const S* __restrict__ fnt;
+  const S* __restrict__ gnc;
+  const S* __restrict__ gnt;
+  const S* __restrict__ clo;
+  const S* __restrict__ chi;
+  // risk measures of the general form (per nonleaf node): rows of y, orthant
+  // rows of K, offsets of b and of the S2 projector, their values
+  int32_t max_nz2;
+  const int32_t* __restrict__ rny;
+  const int32_t* __restrict__ rkp;
+  const int64_t* __restrict__ rboff;
+  const int64_t* __restrict__ rpoff;
+  const S* __restrict__ rb;
+  const S* __restrict__ rpi;
 };
 
 // Records `ev` on `st`; while `st` is being captured into a graph the record

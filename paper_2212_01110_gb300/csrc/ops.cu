@@ -113,14 +113,29 @@ static void dual_j(const KP<S>& p, const S* z, const S* zp, const S* eta, S* out
   }
 }
 
+// the general form's kernels (ops_gen.cu)
+template <typename S>
+void launch_lstar_gen(const KP<S>& p, int mode, const S* eta, const S* z, S* zo, int grid, cudaStream_t st);
+template <typename S>
+void launch_dual_gen(const KP<S>& p, int mode, bool stats, const S* z, const S* zp, const S* eta, S* out,
+                     const S* dir, double* partials, int grid, cudaStream_t st);
+
 template <typename S>
 void launch_prep(const KP<S>& p, const S* z, const S* eta, S* zo, int max_blocks, cudaStream_t st) {
+  if (p.gen) {
+    launch_lstar_gen<S>(p, LS_PREP, eta, z, zo, warp_grid(p.n, max_blocks), st);
+    return;
+  }
   lstar_j<S, LS_PREP>(p, eta, z, zo, warp_grid(p.n, max_blocks), st);
 }
 
 template <typename S>
 void launch_dual(const KP<S>& p, int mode, bool stats, const S* z, const S* zp, const S* eta, S* out,
                  const S* dir, double* partials, int grid, cudaStream_t st) {
+  if (p.gen) {
+    launch_dual_gen<S>(p, mode, stats, z, zp, eta, out, dir, partials, grid, st);
+    return;
+  }
   // operator-level modes (not on the solve path) use the widest lane layout
   if (mode == DM_APPLY_L) {
     k_dual<S, DM_APPLY_L, kMaxJ><<<grid, 128, 0, st>>>(p, z, zp, eta, out);
@@ -147,6 +162,10 @@ void launch_dual(const KP<S>& p, int mode, bool stats, const S* z, const S* zp, 
 // z_out = L* eta
 template <typename S>
 void launch_lstar(const KP<S>& p, const S* eta, S* zout, int grid, cudaStream_t st) {
+  if (p.gen) {
+    launch_lstar_gen<S>(p, LS_APPLY, eta, nullptr, zout, grid, st);
+    return;
+  }
   k_lstar<S, LS_APPLY, kMaxJ><<<grid, 128, 0, st>>>(p, eta, nullptr, zout);
 }
 

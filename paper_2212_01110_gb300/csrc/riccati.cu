@@ -88,13 +88,17 @@ int launch_fwd_chain_grp(const KP<S>& p, S* zo, cudaStream_t st);
 // SPOCK_RICCATI_KERNELS forces one family everywhere (the tests cover each).
 enum ChainFamily { CF_AUTO = -1, CF_GRP = 0, CF_TMA = 1, CF_DIRECT = 2 };
 // FP64 stages with at least this many nodes use the direct kernels (many
-// resident warps keep the FP64 pipe busy); SPOCK_STAGED_MAX_NODES overrides.
-inline int staged_max_nodes() {
+// resident warps keep the FP64 pipe busy): 1,024 in the backward pass, 2,048
+// in the forward pass (on the 62,805-node tree the stage of 1,024 nodes with
+// four children each took 0.174 vs 0.213 ms per T of backward stages on the
+// direct kernel, but 0.211 vs 0.184 ms of forward stages);
+// SPOCK_STAGED_MAX_NODES overrides both.
+inline int staged_max_nodes(bool backward) {
   static int v = [] {
     const char* e = getenv("SPOCK_STAGED_MAX_NODES");
-    return e ? atoi(e) : 2048;
+    return e ? atoi(e) : -1;
   }();
-  return v;
+  return v >= 0 ? v : (backward ? 1024 : 2048);
 }
 static int chain_family() {
   const char* e = getenv("SPOCK_RICCATI_KERNELS");
@@ -135,10 +139,12 @@ int riccati_passes_sl(const KP<S>& p, const std::vector<int32_t>& stage_begin,
   // every stage in FP32 (measured); in FP64 a stage with many nodes runs
   // better on the direct warp-per-node kernels, which keep far more warps
   // resident (FP64 needs one per SM sub-partition).
-  auto staged = [&](int cnt) { return tma_stage && (sizeof(S) == 4 || cnt < staged_max_nodes()); };
+  auto staged = [&](int cnt, bool bwd) {
+    return tma_stage && (sizeof(S) == 4 || cnt < staged_max_nodes(bwd));
+  };
   for (int t = cs - 1; t >= 0; --t) {
     const int cnt = stage_begin[t + 1] - stage_begin[t];
-    if (staged(cnt)) {
+    if (staged(cnt, true)) {
       launches += launch_bwd_stage_tma<S, SL>(p, t, cnt, stage_maxch[t], st);
     } else {
       k_bwd_stage<S, SL><<<(cnt + kWarpsPerBlock - 1) / kWarpsPerBlock, 128, 0, st>>>(p, t);
@@ -148,7 +154,7 @@ int riccati_passes_sl(const KP<S>& p, const std::vector<int32_t>& stage_begin,
   if (ev) record_event(ev[1], st);
   for (int t = 0; t < cs; ++t) {
     const int cnt = stage_begin[t + 1] - stage_begin[t];
-    if (staged(cnt)) {
+    if (staged(cnt, false)) {
       launches += launch_fwd_stage_tma<S, SL>(p, t, cnt, stage_maxch[t], zo, st);
     } else {
       k_fwd_stage<S, SL><<<(cnt + kWarpsPerBlock - 1) / kWarpsPerBlock, 128, 0, st>>>(p, t, zo);

@@ -15,6 +15,7 @@
 
 #include "batch.cuh"
 #include "kernels.cuh"
+#include "general.h"
 #include "spock_internal.h"
 #include "supermann.cuh"
 
@@ -316,6 +317,35 @@ static KP<S> make_kp(const Problem& P, double alpha, const int32_t* stage_begin_
   k.ktstride = f.ktstride;
   k.err = P.err;
   k.skip = nullptr;
+  const GenDims& g = P.gd;
+  k.gen = P.general ? 1 : 0;
+  k.nc = g.nc;
+  k.ncN = g.ncN;
+  k.ldc = g.ldc;
+  k.ldxu = g.ldxu;
+  k.ldx = g.ldx;
+  k.ldu = g.ldu;
+  k.ldcn = g.ldcn;
+  k.cst = g.cst;
+  k.gc = f.gc;
+  k.gt = f.gt;
+  k.fqc = f.fqc;
+  k.fqt = f.fqt;
+  k.frc = f.frc;
+  k.frt = f.frt;
+  k.fnc = f.fnc;
+  k.fnt = f.fnt;
+  k.gnc = f.gnc;
+  k.gnt = f.gnt;
+  k.clo = f.clo;
+  k.chi = f.chi;
+  k.max_nz2 = g.max_nz2;
+  k.rny = P.idx.rny;
+  k.rkp = P.idx.rkp;
+  k.rboff = P.idx.rboff;
+  k.rpoff = P.idx.rpoff;
+  k.rb = f.rb;
+  k.rpi = f.rpi;
   return k;
 }
 
@@ -796,7 +826,7 @@ static int solve_impl(Problem& P, const double* x0_dev, const spock_settings& s,
   if (drv && drv[0] == 'h')
     return solve_host<S>(P, x0_dev, s, z_dev, eta_dev, warm, info, st, tol_given, stall_window, final_action_out);
   const int mem = std::max(0, std::min<int>(s.memory, kMaxMemory));
-  const bool cta_ok = cta_supported(P.nx, P.nu, mem) && !s.profile;
+  const bool cta_ok = cta_supported(P.nx, P.nu, mem) && !s.profile && !P.general;
   const bool cta = cta_ok && (drv && drv[0] == 'c' ? true : (!(drv && drv[0]) && P.tree.n <= kCtaAutoNodes));
   return solve_graph<S>(P, x0_dev, s, z_dev, eta_dev, warm, info, st, tol_given, stall_window, final_action_out,
                         cta);
@@ -1431,9 +1461,15 @@ int launch_lambda(const KP<S>& p, const std::vector<int32_t>& stage_begin, const
 void launch_cone_jac(const KP<double>& p, const double* wbar, const double* x, double* out, int grid,
                      cudaStream_t st);
 void launch_axpy(int64_t n, double a, const double* x, const double* y, double* out, int grid, cudaStream_t st);
-void launch_adj_update(int64_t nz, int64_t ne, double alpha, const double* pz, const double* t, const double* g,
-                       const double* q, const double* Lp, double* w, unsigned long long* red, int grid,
-                       cudaStream_t st);
+void launch_jt_residual(int64_t nz, int64_t ne, double alpha, const double* pz, const double* t, const double* q,
+                        const double* Lp, const double* x, double* u, int grid, cudaStream_t st);
+void launch_dots(int64_t n, const double* u, const double* V, int64_t ld, int k, double* partials, double* out,
+                 int grid, cudaStream_t st);
+void launch_axpy_many(int64_t n, double* u, const double* V, int64_t ld, int k, const double* h, double sign,
+                      int grid, cudaStream_t st);
+void launch_scale(int64_t n, double a, const double* u, double* v, int grid, cudaStream_t st);
+void launch_true_residual(int64_t nz, int64_t ntot, const double* g, const double* u, const double* x, double* r,
+                          unsigned long long* red, int grid, cudaStream_t st);
 void launch_adj_gradients(const KP<double>& p, const double* z, const double* eta, const double* q,
                           const double* pv, const double* lam_mu, const double* negy, const double* lam_env,
                           const double* wenv, double* gx0, double* gA, double* gB, double* gQ, double* gR,
@@ -1447,6 +1483,7 @@ int launch_gradient(const KP<S>& p, const std::vector<int32_t>& stage_begin, con
 template <typename S>
 static int grad_impl(Problem& P, const double* z, const double* eta, double* gx0, double* gA, double* gB,
                      double* gQ, double* gR, double* gQN, cudaStream_t st) {
+  if (P.general) return fail(SPOCK_ERR_UNSUPPORTED, "gradients: box constraints and diagonal costs only");
   Workspace* ws = get_ws_impl<S>(P, 0);
   const DevFactors<S>& f = factors<S>(P);
   const int64_t nz = P.off.n_z, ne = P.off.n_eta;
@@ -1481,17 +1518,32 @@ static int grad_impl(Problem& P, const double* z, const double* eta, double* gx0
 static int adjoint_impl(Problem& P, const double* z, const double* eta, const double* gz, int max_iter, double tol,
                         double* gx0, double* gA, double* gB, double* gQ, double* gR, double* gQN,
                         int32_t* iters_out, double* res_out, cudaStream_t st) {
+  if (P.general) return fail(SPOCK_ERR_UNSUPPORTED, "adjoint: box constraints and diagonal costs only");
   Workspace* ws = get_ws_impl<double>(P, 0);
-  const int64_t nz = P.off.n_z, ne = P.off.n_eta;
+  const int64_t nz = P.off.n_z, ne = P.off.n_eta, ntot = nz + ne;
   const size_t n = (size_t)P.tree.n, nx = (size_t)P.nx, nu = (size_t)P.nu;
   const size_t xs = (size_t)P.f64.xs;
-  const size_t len = (size_t)(nz + ne) + 3 * (size_t)ne + 6 * (size_t)nz + 2 * n * xs + xs + 2;
+  // restarted GMRES(m): basis of m + 1 vectors, Hessenberg columns and dot
+  // partials on the device.  m = 100, fewer when the basis would take more
+  // than a quarter of the free device memory (at least 10); fixed at the
+  // first call.
+  const int gvec = sm_count() * 4;
+  const size_t ldv = ((size_t)ntot + 31) / 32 * 32;
+  if (!P.adj) {
+    size_t fr = 0, tot = 0;
+    CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+    const size_t fit = fr / 4 / (ldv * sizeof(double));
+    P.adj_restart = (int)std::max<size_t>(10, std::min<size_t>(100, fit > 1 ? fit - 1 : 1));
+  }
+  const int m = P.adj_restart;
+  const size_t len = (size_t)ntot + 3 * (size_t)ne + 6 * (size_t)nz + 2 * n * xs + xs + 2 +
+                     (size_t)(m + 1) * ldv + 2 * (size_t)ntot + (size_t)gvec * 32 + 3 * (size_t)(m + 1) + 8;
   if (!P.adj) {
     CUDA_TRY(cudaMalloc(&P.adj, sizeof(double) * len));
     P.allocations.push_back(P.adj);
   }
   double* w = P.adj;
-  double* wbar = w + nz + ne;
+  double* wbar = w + ntot;
   double* q = wbar + ne;
   double* Lp = q + ne;
   double* t = Lp + ne;
@@ -1504,6 +1556,16 @@ static int adjoint_impl(Problem& P, const double* z, const double* eta, const do
   double* lam_env = lam_mu + n * xs;
   double* zero_x0 = lam_env + n * xs;
   unsigned long long* red = reinterpret_cast<unsigned long long*>(zero_x0 + xs);
+  double* V = zero_x0 + xs + 2;        // basis, stride ldv
+  double* u = V + (size_t)(m + 1) * ldv;
+  double* res = u + ntot;              // true residual b - (I - J^T) w
+  double* part = res + ntot;           // dot partials [gvec][32]
+  // [m + 1] Hessenberg column, [m + 1] its second Gram-Schmidt pass, [1] norm;
+  // then [m + 1] the solution of the small least-squares problem
+  double* hdev = part + (size_t)gvec * 32;
+  double* hdev2 = hdev + (m + 1);
+  double* hnorm = hdev2 + (m + 1);
+  double* ydev = hnorm + 1;
   const double alpha = default_alpha(P, 0.0);
   KP<double> kp = make_kp<double>(P, alpha, P.idx.stage_begin);
   KP<double> kA = kp;   // Jacobian of prox_{alpha f}: no shift of s^0, x0 = 0
@@ -1512,7 +1574,6 @@ static int adjoint_impl(Problem& P, const double* z, const double* eta, const do
   kA.x0 = zero_x0;
   const int maxb = sm_count() * 16;
   const int gnode = std::min((P.tree.n + 3) / 4, maxb);
-  const int gvec = sm_count() * 4;
   CUDA_TRY(cudaMemsetAsync(zero_x0, 0, sizeof(double) * xs, st));
   // wbar = eta + alpha L z (the point of prox_{alpha g*} at the fixed point)
   launch_dual<double>(kp, DM_APPLY_L_, false, z, nullptr, nullptr, Lp, nullptr, nullptr, gnode, st);
@@ -1523,38 +1584,106 @@ static int adjoint_impl(Problem& P, const double* z, const double* eta, const do
     const double one = 1.0;
     CUDA_TRY(cudaMemsetAsync(g, 0, sizeof(double) * nz, st));
     CUDA_TRY(cudaMemcpyAsync(g, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));   // the host value `one` goes out of scope
   }
-  CUDA_TRY(cudaMemsetAsync(w, 0, sizeof(double) * (nz + ne), st));
+  CUDA_TRY(cudaMemsetAsync(w, 0, sizeof(double) * ntot, st));
   const double* zero_eta = (const double*)ws->zero_eta;
-  auto jt_parts = [&]() {   // q, t, r, p, L p from the current w
-    launch_cone_jac(kp, wbar, w + nz, q, gnode, st);
+  auto jt_parts = [&](const double* x) {   // q, t, r, p, L p of J^T x
+    launch_cone_jac(kp, wbar, x + nz, q, gnode, st);
     launch_lstar<double>(kp, q, t, gnode, st);
-    launch_axpy(nz, 2.0 * alpha, t, w, r, gvec, st);
+    launch_axpy(nz, 2.0 * alpha, t, x, r, gvec, st);
     launch_prep<double>(kA, r, zero_eta, pv, maxb, st);
     launch_riccati<double>(kA, P.tree.stage_begin, P.tree.stage_maxch, pv, st, nullptr);
     launch_dual<double>(kp, DM_APPLY_L_, false, pv, nullptr, nullptr, Lp, nullptr, nullptr, gnode, st);
   };
-  constexpr int kCheckEvery = 20;
-  int it = 0;
-  double diff = INFINITY, mag = 0.0;
-  for (; it < max_iter;) {
-    const bool check = (it + 1) % kCheckEvery == 0 || it + 1 == max_iter;
-    jt_parts();
-    if (check) CUDA_TRY(cudaMemsetAsync(red, 0, 2 * sizeof(unsigned long long), st));
-    launch_adj_update(nz, ne, alpha, pv, t, g, q, Lp, w, check ? red : nullptr, gvec, st);
-    ++it;
-    if (check) {
-      unsigned long long h[2];
-      CUDA_TRY(cudaMemcpyAsync(h, red, sizeof(h), cudaMemcpyDeviceToHost, st));
+  auto apply_op = [&](const double* x, double* out) {   // out = (I - J^T) x
+    jt_parts(x);
+    launch_jt_residual(nz, ne, alpha, pv, t, q, Lp, x, out, gvec, st);
+  };
+  auto dots = [&](const double* a, int k, double* out_dev, std::vector<double>& out_host) {
+    launch_dots(ntot, a, V, (int64_t)ldv, k, part, out_dev, gvec, st);
+    out_host.resize(k);
+    CUDA_TRY(cudaMemcpyAsync(out_host.data(), out_dev, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+  };
+  // true residual res = b - (I - J^T) w and its max norm against max |w|
+  double rinf = INFINITY, winf = 0.0;
+  auto true_residual = [&]() {
+    apply_op(w, u);
+    CUDA_TRY(cudaMemsetAsync(red, 0, 2 * sizeof(unsigned long long), st));
+    launch_true_residual(nz, ntot, g, u, w, res, red, gvec, st);
+    unsigned long long h[2];
+    CUDA_TRY(cudaMemcpyAsync(h, red, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    std::memcpy(&rinf, &h[0], sizeof(double));
+    std::memcpy(&winf, &h[1], sizeof(double));
+    if (!std::isfinite(rinf)) throw SpockError(SPOCK_ERR_NUMERICAL, "the adjoint solve diverged");
+  };
+  int it = 0;   // applications of J^T inside the Arnoldi steps
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gam(m + 1), hv, y(m), hh(2 * (size_t)(m + 1) + 1);
+  true_residual();
+  while (!(rinf <= tol * std::max(1.0, winf)) && it < max_iter) {
+    // v_0 = res / ||res||
+    CUDA_TRY(cudaMemcpyAsync(V, res, sizeof(double) * ntot, cudaMemcpyDeviceToDevice, st));
+    dots(res, 1, hdev, hv);
+    const double beta = std::sqrt(std::max(hv[0], 0.0));
+    if (!(beta > 0.0)) break;
+    launch_scale(ntot, 1.0 / beta, res, V, gvec, st);
+    std::fill(gam.begin(), gam.end(), 0.0);
+    gam[0] = beta;
+    const double thr = tol * std::max(1.0, winf);
+    int k = 0;
+    for (; k < m && it < max_iter; ++k) {
+      double* vk1 = V + (size_t)(k + 1) * ldv;
+      apply_op(V + (size_t)k * ldv, u);
+      ++it;
+      // classical Gram-Schmidt, twice, with the coefficients kept on the
+      // device; one copy to the host per step
+      launch_dots(ntot, u, V, (int64_t)ldv, k + 1, part, hdev, gvec, st);
+      launch_axpy_many(ntot, u, V, (int64_t)ldv, k + 1, hdev, -1.0, gvec, st);
+      launch_dots(ntot, u, V, (int64_t)ldv, k + 1, part, hdev2, gvec, st);
+      launch_axpy_many(ntot, u, V, (int64_t)ldv, k + 1, hdev2, -1.0, gvec, st);
+      launch_dots(ntot, u, u, 0, 1, part, hnorm, gvec, st);   // ||u||^2 (V stride 0: u itself)
+      CUDA_TRY(cudaMemcpyAsync(hh.data(), hdev, sizeof(double) * (2 * (size_t)(m + 1) + 1), cudaMemcpyDeviceToHost,
+                               st));
       CUDA_TRY(cudaStreamSynchronize(st));
-      std::memcpy(&diff, &h[0], sizeof(double));
-      std::memcpy(&mag, &h[1], sizeof(double));
-      if (!std::isfinite(diff)) return fail(SPOCK_ERR_NUMERICAL, "the adjoint iteration diverged");
-      if (diff <= tol * std::max(1.0, mag)) break;
+      const double hn = std::sqrt(std::max(hh[2 * (size_t)(m + 1)], 0.0));
+      for (int i = 0; i <= k; ++i) H[(size_t)i * m + k] = hh[i] + hh[(size_t)(m + 1) + i];
+      H[(size_t)(k + 1) * m + k] = hn;
+      if (hn > 0.0) launch_scale(ntot, 1.0 / hn, u, vk1, gvec, st);
+      // Givens rotations on the new column
+      for (int i = 0; i < k; ++i) {
+        const double a = H[(size_t)i * m + k], b = H[(size_t)(i + 1) * m + k];
+        H[(size_t)i * m + k] = cs[i] * a + sn[i] * b;
+        H[(size_t)(i + 1) * m + k] = -sn[i] * a + cs[i] * b;
+      }
+      const double a = H[(size_t)k * m + k], b = H[(size_t)(k + 1) * m + k];
+      const double rr = std::hypot(a, b);
+      cs[k] = rr > 0.0 ? a / rr : 1.0;
+      sn[k] = rr > 0.0 ? b / rr : 0.0;
+      H[(size_t)k * m + k] = rr;
+      H[(size_t)(k + 1) * m + k] = 0.0;
+      gam[k + 1] = -sn[k] * gam[k];
+      gam[k] = cs[k] * gam[k];
+      if (std::fabs(gam[k + 1]) <= thr || !(hn > 0.0)) {
+        ++k;
+        break;
+      }
     }
+    // w += V y, H(0:k, 0:k) y = gam(0:k)
+    for (int i = k - 1; i >= 0; --i) {
+      double sum = gam[i];
+      for (int c = i + 1; c < k; ++c) sum -= H[(size_t)i * m + c] * y[c];
+      y[i] = H[(size_t)i * m + i] != 0.0 ? sum / H[(size_t)i * m + i] : 0.0;
+    }
+    CUDA_TRY(cudaMemcpyAsync(ydev, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
+    launch_axpy_many(ntot, w, V, (int64_t)ldv, k, ydev, 1.0, gvec, st);
+    CUDA_TRY(cudaStreamSynchronize(st));   // y is a host buffer
+    true_residual();
   }
+  const double diff = rinf, mag = winf;
   // data derivatives from the final w
-  jt_parts();
+  jt_parts(w);
   launch_axpy(nz, -1.0, r, pv, negy, gvec, st);                    // negy = p - r
   launch_lambda<double>(kp, P.tree.stage_begin, negy, lam_mu, maxb, st);
   launch_lstar<double>(kp, eta, wenv, gnode, st);                  // wenv = L* eta
@@ -1600,7 +1729,8 @@ static int32_t pad16(int64_t elems, size_t elt) {
 template <typename S>
 static void upload_factors(Problem& P, DevFactors<S>& f, const std::vector<double>& Gb,
                            const std::vector<double>& Gf, const std::vector<double>& NB,
-                           const std::vector<double>& Kt, const std::vector<std::vector<double>>& par) {
+                           const std::vector<double>& Kt, const std::vector<std::vector<double>>& par,
+                           const GenHost* gen) {
   auto cast = [](const std::vector<double>& v) {
     std::vector<S> o(v.size());
     for (size_t i = 0; i < v.size(); ++i) o[i] = (S)v[i];
@@ -1643,6 +1773,23 @@ static void upload_factors(Problem& P, DevFactors<S>& f, const std::vector<doubl
     }
     f.s2inv = upload(P, inv);
   }
+  if (gen) {
+    f.gc = upload(P, cast(gen->gc));
+    f.gt = upload(P, cast(gen->gt));
+    f.fqc = upload(P, cast(gen->fqc));
+    f.fqt = upload(P, cast(gen->fqt));
+    f.frc = upload(P, cast(gen->frc));
+    f.frt = upload(P, cast(gen->frt));
+    f.fnc = upload(P, cast(gen->fnc));
+    f.fnt = upload(P, cast(gen->fnt));
+    f.gnc = upload(P, cast(gen->gnc));
+    f.gnt = upload(P, cast(gen->gnt));
+    // infinite bounds stay infinite in FP32 as well
+    f.clo = upload(P, cast(gen->clo));
+    f.chi = upload(P, cast(gen->chi));
+    f.rb = upload(P, cast(gen->rb));
+    f.rpi = upload(P, cast(gen->rpi));
+  }
   f.xbar = dalloc<S>(P, (size_t)t.n * f.xs);
   f.ubar = dalloc<S>(P, (size_t)t.n_nonleaf * f.us);
   f.q = dalloc<S>(P, (size_t)t.n * f.xs);
@@ -1658,19 +1805,48 @@ static bool all_finite(const double* a, size_t n) {
 
 static int noalloc_scratch(int dev, double** out);
 
+// General-form inputs of problem_create (user numbering; see
+// spock_problem_create_general).
+struct GenInput {
+  bool dense = false;
+  const spock_risk* risk = nullptr;   // nullptr: AV@R with parameter a
+  int32_t nc = 0, ncN = 0;
+  const double *Gx = nullptr, *Gu = nullptr, *cmin = nullptr, *cmax = nullptr;
+  const double *GN = nullptr, *cNmin = nullptr, *cNmax = nullptr;
+};
+
+// Box form (gi == nullptr): diagonal Q, R, QN and boxes xmin..umax.  General
+// form (gi != nullptr): Q, R, QN dense or diagonal as gi->dense says, the
+// constraint rows of gi; xmin..umax are not read.
 static int problem_create(const Tree& tree, int32_t nx, int32_t nu, const double* A, const double* B,
                           const double* Q, const double* R, const double* QN, const double* a, const double* xmin,
-                          const double* xmax, const double* umin, const double* umax, spock_problem** out) {
-  if (!A || !B || !Q || !R || !QN || !a || !xmin || !xmax || !umin || !umax || !out)
+                          const double* xmax, const double* umin, const double* umax, const GenInput* gi,
+                          spock_problem** out) {
+  if (!A || !B || !Q || !R || !QN || (!a && !(gi && gi->risk)) || !out)
+    return fail(SPOCK_ERR_INVALID_ARG, "NULL argument");
+  if (!gi && (!xmin || !xmax || !umin || !umax)) return fail(SPOCK_ERR_INVALID_ARG, "NULL argument");
+  if (gi && (!gi->Gx || !gi->Gu || !gi->cmin || !gi->cmax || !gi->GN || !gi->cNmin || !gi->cNmax))
     return fail(SPOCK_ERR_INVALID_ARG, "NULL argument");
   if (nx < 1 || nu < 1 || nx + nu > kMaxDim)
     return fail(SPOCK_ERR_INVALID_ARG, "need nx >= 1, nu >= 1, nx + nu <= 128");
+  if (gi && (gi->nc < 1 || gi->nc > kMaxDim || gi->ncN < 1 || gi->ncN > kMaxDim))
+    return fail(SPOCK_ERR_INVALID_ARG, "need 1 <= nc, ncN <= 128");
   const int32_t n = tree.n;
   const size_t nn = (size_t)n;
   // validation (user numbering)
   if (!all_finite(A + (size_t)nx * nx, (nn - 1) * nx * nx) || !all_finite(B + (size_t)nx * nu, (nn - 1) * nx * nu))
     return fail(SPOCK_ERR_NUMERICAL, "non-finite dynamics");
-  for (int32_t u = 0; u < n; ++u) {
+  if (gi) {
+    const size_t qsz = gi->dense ? (size_t)nx * nx : (size_t)nx, rsz = gi->dense ? (size_t)nu * nu : (size_t)nu;
+    if (!all_finite(Q, nn * qsz) || !all_finite(R, nn * rsz) || !all_finite(QN, nn * qsz) ||
+        !all_finite(gi->Gx, nn * gi->nc * nx) || !all_finite(gi->Gu, nn * gi->nc * nu) ||
+        !all_finite(gi->GN, nn * gi->ncN * nx))
+      return fail(SPOCK_ERR_NUMERICAL, "non-finite cost or constraint matrices");
+    for (int32_t u = 0; u < n && !gi->risk; ++u)
+      if (tree.int_of[u] < tree.n_nonleaf && !(a[u] >= 0.0 && a[u] <= 1.0))
+        return fail(SPOCK_ERR_INVALID_ARG, "AV@R parameter must be in [0, 1]");
+  }
+  for (int32_t u = 0; u < n && !gi; ++u) {
     const int32_t k = tree.int_of[u];
     const bool nonroot = k > 0, leaf = k >= tree.n_nonleaf, nonleaf = !leaf;
     for (int r = 0; r < nx; ++r) {
@@ -1697,9 +1873,27 @@ static int problem_create(const Tree& tree, int32_t nx, int32_t nu, const double
     P->tree = tree;
     P->nx = nx;
     P->nu = nu;
-    build_offsets(P->tree, nx, nu, P->off);
     const Tree& t = P->tree;
     const int nl = t.n_nonleaf, ncol = nx + nu;
+    int threads = (int)std::thread::hardware_concurrency();
+    if (threads <= 0) threads = 4;
+    GenHost gh;
+    if (gi) {
+      std::string err;
+      const int rc = build_general(t, nx, nu, gi->dense, Q, R, QN, a, gi->risk, gi->nc, gi->Gx, gi->Gu, gi->cmin,
+                                   gi->cmax, gi->ncN, gi->GN, gi->cNmin, gi->cNmax, threads, gh, err);
+      if (rc != SPOCK_OK) {
+        delete P;
+        return fail(rc, err);
+      }
+      P->general = true;
+      P->gd = gh.d;
+      build_offsets(P->tree, nx, nu, gi->nc, gi->ncN, &gh.ny_user, P->off);
+    } else {
+      P->gd.nc = nx + nu;
+      P->gd.ncN = nx;
+      build_offsets(P->tree, nx, nu, nx + nu, nx, nullptr, P->off);
+    }
     // internal-order dynamics
     std::vector<double> Ai(nn * nx * nx), Bi(nn * nx * nu);
     for (int32_t k = 1; k < n; ++k) {
@@ -1709,8 +1903,6 @@ static int problem_create(const Tree& tree, int32_t nx, int32_t nu, const double
     }
     std::vector<double> Gb, NB;
     const auto t0 = std::chrono::steady_clock::now();
-    int threads = (int)std::thread::hardware_concurrency();
-    if (threads <= 0) threads = 4;
     if (!riccati_factor(t, nx, nu, Ai, Bi, Gb, NB, threads)) {
       delete P;
       return fail(SPOCK_ERR_NUMERICAL, "Cholesky of I + sum B'PB failed");
@@ -1745,6 +1937,11 @@ static int problem_create(const Tree& tree, int32_t nx, int32_t nu, const double
     par[8].assign(nn, 1.0);
     for (int32_t k = 0; k < n; ++k) {
       const int32_t u = t.user_of[k];
+      if (gi) {   // general form: the box-form arrays stay zero
+        if (k < nl && a) par[7][k] = a[u];
+        par[8][k] = t.prob[k];
+        continue;
+      }
       for (int r = 0; r < nx; ++r) {
         if (k > 0) par[0][(size_t)k * nx + r] = std::sqrt(Q[(size_t)u * nx + r]);
         if (k >= nl) par[2][(size_t)k * nx + r] = std::sqrt(QN[(size_t)u * nx + r]);
@@ -1762,15 +1959,15 @@ static int problem_create(const Tree& tree, int32_t nx, int32_t nu, const double
       par[8][k] = t.prob[k];
     }
     // ||L||^2 as the largest block norm (remark after the definition of L)
-    double best = 0.5;
-    for (int32_t k = 0; k < nl; ++k) {
+    double best = std::max(0.5, std::max(gh.normL2_xu, gh.normL2_ys));
+    for (int32_t k = 0; k < nl && !gi; ++k) {
       const int c0 = t.ch_begin[k], m = t.ch_count[k];
-      for (int r = 0; r < nx; ++r) {
+      for (int r = 0; r < nx && !gi; ++r) {
         double s = 1.0;
         for (int j = 0; j < m; ++j) s += par[0][(size_t)(c0 + j) * nx + r] * par[0][(size_t)(c0 + j) * nx + r];
         best = std::max(best, s);
       }
-      for (int r = 0; r < nu; ++r) {
+      for (int r = 0; r < nu && !gi; ++r) {
         double s = 1.0;
         for (int j = 0; j < m; ++j) s += par[1][(size_t)(c0 + j) * nu + r] * par[1][(size_t)(c0 + j) * nu + r];
         best = std::max(best, s);
@@ -1780,7 +1977,7 @@ static int problem_create(const Tree& tree, int32_t nx, int32_t nu, const double
       const double bb = std::sqrt(b2);
       best = std::max(best, (2.0 + b2 + bb * std::sqrt(b2 + 4.0)) / 2.0);
     }
-    for (int32_t k = nl; k < n; ++k)
+    for (int32_t k = nl; k < n && !gi; ++k)
       for (int r = 0; r < nx; ++r) best = std::max(best, 1.0 + par[2][(size_t)k * nx + r] * par[2][(size_t)k * nx + r]);
     P->normL = std::sqrt(best);
     // device index
@@ -1796,8 +1993,14 @@ static int problem_create(const Tree& tree, int32_t nx, int32_t nu, const double
     P->idx.enl = upload(*P, P->off.enl);
     P->idx.enr = upload(*P, P->off.enr);
     P->idx.elf = upload(*P, P->off.elf);
-    upload_factors<double>(*P, P->f64, Gb, Gf, NB, Kt, par);
-    upload_factors<float>(*P, P->f32, Gb, Gf, NB, Kt, par);
+    upload_factors<double>(*P, P->f64, Gb, Gf, NB, Kt, par, gi ? &gh : nullptr);
+    upload_factors<float>(*P, P->f32, Gb, Gf, NB, Kt, par, gi ? &gh : nullptr);
+    if (gi) {
+      P->idx.rny = upload(*P, gh.rny);
+      P->idx.rkp = upload(*P, gh.rkp);
+      P->idx.rboff = upload(*P, gh.rboff);
+      P->idx.rpoff = upload(*P, gh.rpoff);
+    }
     P->idx.stage_begin = upload(*P, t.stage_begin);
     {
       std::vector<NodeDesc> dh(nn);
@@ -1819,7 +2022,7 @@ static int problem_create(const Tree& tree, int32_t nx, int32_t nu, const double
         q.user = t.user_of[k];
         q.zxp = k > 0 ? o.zx[t.parent[k]] : -1;
         q.zup = k > 0 ? o.zu[t.parent[k]] : -1;
-        q.es = k < nl ? o.enl[k] + 2 * t.ch_count[k] + 1 : o.elf[k] + 2 * nx;
+        q.es = k < nl ? o.enl[k] + (gi ? gh.rny[k] : 2 * t.ch_count[k] + 1) : o.elf[k] + P->gd.ncN + nx;
       }
       for (int32_t k = 0; k < n; ++k) {
         dh[k].enr_c0 = t.ch_count[k] > 0 ? dh[t.ch_begin[k]].enr : -1;
@@ -1940,8 +2143,68 @@ int spock_problem_create(const spock_tree* tree, int32_t nx, int32_t nu, const d
   return guarded([&]() -> int {
     const Tree* t = as_tree(tree);
     if (!t) return fail(SPOCK_ERR_INVALID_ARG, "not a tree handle");
-    if (flags != 0) return fail(SPOCK_ERR_UNSUPPORTED, "flags must be 0");
-    return problem_create(*t, nx, nu, A, B, Q, R, QN, a, xmin, xmax, umin, umax, out);
+    if (flags & ~SPOCK_DENSE_COST) return fail(SPOCK_ERR_UNSUPPORTED, "unknown flag");
+    if (!(flags & SPOCK_DENSE_COST))
+      return problem_create(*t, nx, nu, A, B, Q, R, QN, a, xmin, xmax, umin, umax, nullptr, out);
+    // dense costs with the box constraints: the general form with Gamma = I
+    if (!xmin || !xmax || !umin || !umax) return fail(SPOCK_ERR_INVALID_ARG, "NULL argument");
+    if (nx < 1 || nu < 1 || nx + nu > kMaxDim)
+      return fail(SPOCK_ERR_INVALID_ARG, "need nx >= 1, nu >= 1, nx + nu <= 128");
+    const size_t n = (size_t)t->n, nc = (size_t)nx + nu;
+    std::vector<double> Gx(n * nc * nx, 0.0), Gu(n * nc * nu, 0.0), cmin(n * nc), cmax(n * nc);
+    std::vector<double> GN(n * nx * nx, 0.0);
+    for (size_t u = 0; u < n; ++u) {
+      for (int r = 0; r < nx; ++r) {
+        Gx[(u * nc + r) * nx + r] = 1.0;
+        GN[(u * nx + r) * nx + r] = 1.0;
+        cmin[u * nc + r] = xmin[u * nx + r];
+        cmax[u * nc + r] = xmax[u * nx + r];
+      }
+      for (int r = 0; r < nu; ++r) {
+        Gu[(u * nc + nx + r) * nu + r] = 1.0;
+        cmin[u * nc + nx + r] = umin[u * nu + r];
+        cmax[u * nc + nx + r] = umax[u * nu + r];
+      }
+    }
+    GenInput gi;
+    gi.dense = true;
+    gi.risk = nullptr;
+    gi.nc = (int32_t)nc;
+    gi.ncN = nx;
+    gi.Gx = Gx.data();
+    gi.Gu = Gu.data();
+    gi.cmin = cmin.data();
+    gi.cmax = cmax.data();
+    gi.GN = GN.data();
+    gi.cNmin = xmin;
+    gi.cNmax = xmax;
+    return problem_create(*t, nx, nu, A, B, Q, R, QN, a, nullptr, nullptr, nullptr, nullptr, &gi, out);
+  });
+}
+
+int spock_problem_create_general(const spock_tree* tree, int32_t nx, int32_t nu, const double* A,
+                                 const double* B, const double* Q, const double* R, const double* QN,
+                                 const double* a, const spock_risk* risk, int32_t nc, const double* Gx,
+                                 const double* Gu, const double* cmin, const double* cmax, int32_t ncN,
+                                 const double* GN, const double* cNmin, const double* cNmax, int32_t flags,
+                                 spock_problem** out) {
+  return guarded([&]() -> int {
+    const Tree* t = as_tree(tree);
+    if (!t) return fail(SPOCK_ERR_INVALID_ARG, "not a tree handle");
+    if (flags & ~SPOCK_DENSE_COST) return fail(SPOCK_ERR_UNSUPPORTED, "unknown flag");
+    GenInput gi;
+    gi.dense = (flags & SPOCK_DENSE_COST) != 0;
+    gi.risk = risk;
+    gi.nc = nc;
+    gi.ncN = ncN;
+    gi.Gx = Gx;
+    gi.Gu = Gu;
+    gi.cmin = cmin;
+    gi.cmax = cmax;
+    gi.GN = GN;
+    gi.cNmin = cNmin;
+    gi.cNmax = cNmax;
+    return problem_create(*t, nx, nu, A, B, Q, R, QN, a, nullptr, nullptr, nullptr, nullptr, &gi, out);
   });
 }
 
@@ -2024,6 +2287,11 @@ static int root_box_ok(const Problem& P, const double* x0, cudaStream_t st, bool
     CUDA_TRY(cudaStreamSynchronize(st));
   } else {
     std::memcpy(h.data(), x0, sizeof(double) * P.nx);
+  }
+  if (P.general) {   // the root's constraint rows involve u^0: only finiteness is checked
+    for (int r = 0; r < P.nx; ++r)
+      if (!std::isfinite(h[r])) return fail(SPOCK_ERR_NUMERICAL, "x0 is not finite");
+    return SPOCK_OK;
   }
   std::vector<double> lo(P.nx), hi(P.nx);
   CUDA_TRY(cudaMemcpy(lo.data(), P.f64.xlo, sizeof(double) * P.nx, cudaMemcpyDeviceToHost));
@@ -2296,6 +2564,10 @@ int spock_batch_create(int32_t n, spock_problem* const* problems, spock_batch** 
           delete B;
           return fail(SPOCK_ERR_INVALID_ARG, "not a problem handle in the batch");
         }
+        if (P->general) {
+          delete B;
+          return fail(SPOCK_ERR_UNSUPPORTED, "batches take box-form problems only");
+        }
         for (Problem* q : B->probs)
           if (q == P) {
             delete B;
@@ -2401,6 +2673,8 @@ int spock_problem_clone(const spock_problem* base, spock_problem** out) {
       C->nx = B->nx;
       C->nu = B->nu;
       C->normL = B->normL;
+      C->general = B->general;
+      C->gd = B->gd;
       C->idx = B->idx;      // read-only index arrays, shared
       C->f64 = B->f64;      // data and factors, shared
       C->f32 = B->f32;

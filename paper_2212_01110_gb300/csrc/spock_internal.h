@@ -67,6 +67,21 @@ struct DevFactors {
   S* av = nullptr;   // [n] AV@R parameter
   S* prob = nullptr; // [n] conditional probability
   S* s2inv = nullptr; // [n][2] 1 / c and 1 / (c + m_i), c = a_i^2 + 3 (closed form of proj_S2^i)
+  // general form (spock_problem_create_general): per-node matrices of the
+  // rows of L, each in two layouts -- column-major (element (r, c) at
+  // c * ld + r: a warp's lanes run over rows, M v) and transposed (element
+  // (r, c) at r * ldT + c: lanes over columns, M^T w)
+  S* gc = nullptr;  S* gt = nullptr;    // Gamma^k = [Gx | Gu] (nonleaf): [n][nx+nu][ldc], [n][nc][ldxu]
+  S* fqc = nullptr; S* fqt = nullptr;   // Q^k 1/2 (edge into k):  [n][nx][ldx] both
+  S* frc = nullptr; S* frt = nullptr;   // R^k 1/2:                [n][nu][ldu] both
+  S* fnc = nullptr; S* fnt = nullptr;   // Q_N^k 1/2 (leaves):     [n][nx][ldx] both
+  S* gnc = nullptr; S* gnt = nullptr;   // Gamma_N^k (leaves):     [n][nx][ldcn], [n][ncN][ldx]
+  S* clo = nullptr; S* chi = nullptr;   // [n][cst] bounds of C^k (nc rows) or C_N^k (ncN rows)
+  // risk measures of the general form: per nonleaf node b^k (ny_k entries
+  // at rboff[k]) and the projector on S2^k (nz2 x nz2 column-major,
+  // nz2 = ny_k + 2 m_k, at rpoff[k])
+  S* rb = nullptr;
+  S* rpi = nullptr;
   // scratch of the Riccati passes
   S* xbar = nullptr;  // [n][nx]
   S* ubar = nullptr;  // [nl][nu]
@@ -86,6 +101,17 @@ struct DevIndex {
   int64_t *enl = nullptr, *enr = nullptr, *elf = nullptr;
   int32_t* stage_begin = nullptr;  // [N + 2]
   struct NodeDesc* desc = nullptr; // [n] per-node record (kernels.cuh)
+  // general form: rows of y^k, orthant rows of K^k, offsets of b^k and of
+  // the S2 projector (nonleaf nodes)
+  int32_t *rny = nullptr, *rkp = nullptr;
+  int64_t *rboff = nullptr, *rpoff = nullptr;
+};
+
+// Padded leading dimensions of the general form's matrices (elements).
+struct GenDims {
+  int32_t nc = 0, ncN = 0;                  // constraint rows per nonleaf / leaf node
+  int32_t ldc = 0, ldxu = 0, ldx = 0, ldu = 0, ldcn = 0, cst = 0;
+  int32_t max_nz2 = 0;                      // largest z_2 block (ny + 2 m) of a node
 };
 
 struct Problem {
@@ -94,6 +120,8 @@ struct Problem {
   Tree tree;
   Offsets off;
   int32_t nx = 0, nu = 0;
+  bool general = false;   // general form: the L kernels are the matrix-row ones
+  GenDims gd;
   double normL = 0.0;
   double factor_seconds = 0.0;
   DevIndex idx;
@@ -106,7 +134,8 @@ struct Problem {
   double* io_z = nullptr;
   double* io_eta = nullptr;
   double* io_grad = nullptr;   // outputs of spock_grad (host-buffer variant)
-  double* adj = nullptr;       // vectors of the adjoint iteration (spock_adjoint_dev)
+  double* adj = nullptr;       // vectors of the adjoint solve (spock_adjoint_dev)
+  int32_t adj_restart = 0;     // its GMRES restart length, fixed at the first call
   // solver workspace, allocated on first use per precision
   struct Workspace* ws64 = nullptr;
   struct Workspace* ws32 = nullptr;
@@ -120,7 +149,11 @@ struct Problem {
 
 // host-side helpers (tree.cpp, factor.cpp)
 int build_tree(int32_t n, const int32_t* anc, const double* prob, Tree& t);
-void build_offsets(const Tree& t, int nx, int nu, Offsets& o);
+// nc / ncN: constraint rows of the nonleaf / leaf blocks of eta (box form:
+// nx + nu and nx); ny_user: rows of y per node in the caller's numbering
+// (nullptr: AV@R's 2 m + 1).
+void build_offsets(const Tree& t, int nx, int nu, int nc, int ncN, const std::vector<int32_t>* ny_user,
+                   Offsets& o);
 
 // Offline factorisation of the projection on S1 (Algorithm 1), FP64.
 // Inputs in internal numbering: A [n][nx][nx], B [n][nx][nu].

@@ -103,7 +103,8 @@ int build_tree(int32_t n, const int32_t* anc, const double* prob, Tree& t) {
   return SPOCK_OK;
 }
 
-void build_offsets(const Tree& t, int nx, int nu, Offsets& o) {
+void build_offsets(const Tree& t, int nx, int nu, int nc, int ncN, const std::vector<int32_t>* ny_user,
+                   Offsets& o) {
   const int32_t n = t.n;
   o.zx.assign(n, -1); o.zu.assign(n, -1); o.zz2.assign(n, -1); o.zs.assign(n, -1); o.ztau.assign(n, -1);
   o.enl.assign(n, -1); o.enr.assign(n, -1); o.elf.assign(n, -1);
@@ -113,19 +114,21 @@ void build_offsets(const Tree& t, int nx, int nu, Offsets& o) {
   int64_t pos = 1;  // z[0] = s^0
   for (int32_t u = 0; u < n; ++u) { o.zx[t.int_of[u]] = pos; pos += nx; }
   for (int32_t u = 0; u < n; ++u) if (m[u]) { o.zu[t.int_of[u]] = pos; pos += nu; }
-  for (int32_t u = 0; u < n; ++u) if (m[u]) { o.zz2[t.int_of[u]] = pos; pos += 4 * m[u] + 1; }
+  auto ny = [&](int32_t u) { return ny_user ? (*ny_user)[u] : 2 * m[u] + 1; };
+  for (int32_t u = 0; u < n; ++u) if (m[u]) { o.zz2[t.int_of[u]] = pos; pos += ny(u) + 2 * m[u]; }
   o.n_z = pos;
   o.zs[0] = 0;
   for (int32_t k = 1; k < n; ++k) {
     int32_t p = t.parent[k];
     int32_t mp = t.ch_count[p];
-    o.ztau[k] = o.zz2[p] + 2 * mp + 1 + t.sib[k];
-    o.zs[k] = o.zz2[p] + 3 * mp + 1 + t.sib[k];
+    const int32_t nyp = ny(t.user_of[p]);
+    o.ztau[k] = o.zz2[p] + nyp + t.sib[k];
+    o.zs[k] = o.zz2[p] + nyp + mp + t.sib[k];
   }
   pos = 0;
-  for (int32_t u = 0; u < n; ++u) if (m[u]) { o.enl[t.int_of[u]] = pos; pos += 2 * m[u] + 2 + nx + nu; }
+  for (int32_t u = 0; u < n; ++u) if (m[u]) { o.enl[t.int_of[u]] = pos; pos += ny(u) + 1 + nc; }
   for (int32_t u = 1; u < n; ++u) { o.enr[t.int_of[u]] = pos; pos += nx + nu + 2; }
-  for (int32_t u = 0; u < n; ++u) if (!m[u]) { o.elf[t.int_of[u]] = pos; pos += 2 * nx + 2; }
+  for (int32_t u = 0; u < n; ++u) if (!m[u]) { o.elf[t.int_of[u]] = pos; pos += ncN + nx + 2; }
   o.n_eta = pos;
 }
 

@@ -24,6 +24,13 @@ SPOCK_OK = 0
 SPOCK_MAX_ITER = 1
 SPOCK_FP64 = 0
 SPOCK_FP32 = 1
+SPOCK_ERR_INVALID_ARG = -1
+SPOCK_ERR_BAD_TREE = -2
+SPOCK_ERR_NOT_POSDEF = -3
+SPOCK_ERR_NUMERICAL = -4
+SPOCK_ERR_CUDA = -5
+SPOCK_ERR_OOM = -6
+SPOCK_ERR_UNSUPPORTED = -7
 ERRORS = {-1: "INVALID_ARG", -2: "BAD_TREE", -3: "NOT_POSDEF", -4: "NUMERICAL", -5: "CUDA", -6: "OOM",
           -7: "UNSUPPORTED"}
 BRANCHES = {0: "K0", 1: "K1", 2: "K2", 3: "CAP"}
@@ -71,6 +78,8 @@ _sig = {
     "spock_tree_create_abs": ([C.c_int32, _I32, _D, C.POINTER(_P)], C.c_int),
     "spock_tree_info": ([_P, _I32, _I32, _I32], C.c_int),
     "spock_problem_create": ([_P, C.c_int32, C.c_int32] + [_D] * 10 + [C.c_int32, C.POINTER(_P)], C.c_int),
+    "spock_problem_create_general": ([_P, C.c_int32, C.c_int32] + [_D] * 6 + [_P, C.c_int32] + [_D] * 4
+                                     + [C.c_int32] + [_D] * 3 + [C.c_int32, C.POINTER(_P)], C.c_int),
     "spock_problem_info": ([_P, _I64, _I64, _D, _D], C.c_int),
     "spock_problem_clone": ([_P, C.POINTER(_P)], C.c_int),
     "spock_solve": ([_P, _D, C.POINTER(Settings), _D, _D, C.c_int32, C.POINTER(Info)], C.c_int),
@@ -161,11 +170,66 @@ def spock_tree_create_abs(anc, pi):
     return h
 
 
+SPOCK_DENSE_COST = 1
+
+
+class Risk(C.Structure):
+    """spock_risk: a coherent risk measure in conic form at one node."""
+    _fields_ = [("ny", C.c_int32), ("n_nu", C.c_int32), ("kp", C.c_int32),
+                ("b", _D), ("E", _D), ("F", _D)]
+
+
+def _risk_array(risk):
+    """ctypes array of spock_risk from a per-node list (None at leaves) of
+    dicts b, E, F, kp; returns (array, arrays kept alive)."""
+    arr = (Risk * len(risk))()
+    keep = []
+    for i, r in enumerate(risk):
+        if r is None:
+            continue
+        b, pb = _dptr(r["b"])
+        E, pE = _dptr(r["E"])
+        F = np.asarray(r.get("F", np.zeros((b.size, 0))), float)
+        nnu = F.shape[1] if F.ndim == 2 else 0
+        Fa, pF = _dptr(F) if nnu > 0 else (None, None)
+        arr[i] = Risk(b.size, nnu, int(r["kp"]), pb, pE, pF)
+        keep += [b, E, Fa]
+    return arr, keep
+
+
 def spock_problem_create(tree, d):
+    """Problem from a workload dict: the box form, or -- when the dict has
+    constraint matrices "Gx" or conic risk measures "risk" --
+    spock_problem_create_general (box constraints become Gamma = I).  Q, R,
+    QN given as [n][nx][nx] arrays are dense (SPOCK_DENSE_COST)."""
     nx, nu = int(d["nx"]), int(d["nu"])
-    arrs = [_dptr(d[k]) for k in ("A", "B", "Q", "R", "QN", "a", "xmin", "xmax", "umin", "umax")]
+    dense = np.asarray(d["Q"]).ndim == 3
+    flags = SPOCK_DENSE_COST if dense else 0
     h = _P()
-    _check(_lib.spock_problem_create(tree, nx, nu, *[p for _, p in arrs], 0, C.byref(h)))
+    risk = d.get("risk")
+    if "Gx" in d or risk is not None:
+        if "Gx" not in d:   # box constraints as constraint rows
+            n = len(d["anc"])
+            Gx = np.zeros((n, nx + nu, nx))
+            Gu = np.zeros((n, nx + nu, nu))
+            Gx[:, :nx] = np.eye(nx)
+            Gu[:, nx:] = np.eye(nu)
+            d = dict(d, Gx=Gx, Gu=Gu, cmin=np.concatenate([d["xmin"], d["umin"]], 1),
+                     cmax=np.concatenate([d["xmax"], d["umax"]], 1), GN=np.repeat(np.eye(nx)[None], n, 0),
+                     cNmin=d["xmin"], cNmax=d["xmax"])
+        nc, ncN = int(np.asarray(d["Gx"]).shape[1]), int(np.asarray(d["GN"]).shape[1])
+        arrs = [_dptr(d[k]) for k in ("A", "B", "Q", "R", "QN", "a")]
+        cons = [_dptr(d[k]) for k in ("Gx", "Gu", "cmin", "cmax")]
+        term = [_dptr(d[k]) for k in ("GN", "cNmin", "cNmax")]
+        rarr, keep = _risk_array(risk) if risk is not None else (None, [])
+        _check(_lib.spock_problem_create_general(tree, nx, nu, *[p for _, p in arrs],
+                                                 C.cast(rarr, _P) if rarr is not None else None, nc,
+                                                 *[p for _, p in cons], ncN, *[p for _, p in term], flags,
+                                                 C.byref(h)))
+        del keep
+        return h
+    arrs = [_dptr(d[k]) for k in ("A", "B", "Q", "R", "QN", "a", "xmin", "xmax", "umin", "umax")]
+    _check(_lib.spock_problem_create(tree, nx, nu, *[p for _, p in arrs], flags, C.byref(h)))
     return h
 
 

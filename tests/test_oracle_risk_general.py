@@ -58,7 +58,8 @@ def _closed_form(P, kind, lam=0.5, radius=0.3):
 
 
 def test_avar_in_general_form_is_the_builtin():
-    d = workloads.random_tree(3, N=3, max_branch=3, nx=3, nu=2, a_range=(0.2, 0.8))
+    d = workloads.with_tree(workloads.fig1_tree(), seed=4, nx=3, nu=2, a=0.3)
+    d["a"] = np.linspace(0.2, 0.8, len(d["anc"]))
     Pb, Pg = Problem(d), Problem(workloads.risk_measures(d, "avar"))
     assert Pg.general_risk
     np.testing.assert_array_equal(build_L(Pg).toarray(), build_L(Pb).toarray())
