@@ -39,8 +39,11 @@ __global__ void __launch_bounds__(128) k_dual(KP<S> p, const S* __restrict__ z, 
   dual_body<S, MODE, J>(p, blockIdx.x, gridDim.x, z, zp, eta, out);
 }
 
+// FP32: at most 128 registers, four resident blocks per SM (16 warps) for
+// this latency-bound kernel; FP64 keeps its registers (FP64-pipe bound).
 template <typename S, bool DIR, int J>
-__global__ void __launch_bounds__(128) k_dual_fused(KP<S> p, const S* __restrict__ z, const S* __restrict__ zp,
+__global__ void __launch_bounds__(128, sizeof(S) == 4 ? 4 : 1)
+    k_dual_fused(KP<S> p, const S* __restrict__ z, const S* __restrict__ zp,
                                                     const S* __restrict__ eta, S* __restrict__ out,
                                                     const S* __restrict__ dir, double* __restrict__ partials) {
   dual_fused_body<S, DIR, J>(p, blockIdx.x, gridDim.x, z, zp, eta, out, dir, partials);

@@ -31,8 +31,7 @@ __device__ __forceinline__ void wmv(const S* __restrict__ M, int ld, int nrows, 
 #pragma unroll
   for (int js = 0; js < J; ++js) {
     const int qlo = max(32 * js, c0), qhi = min(32 * js + 32, c0 + ncols);
-#pragma unroll 4
-    for (int cq = qlo; cq < qhi; ++cq) {   // warp-uniform bounds; unrolled: loads of 4 columns in flight
+    for (int cq = qlo; cq < qhi; ++cq) {   // warp-uniform bounds
       S xv[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) xv[v] = __shfl_sync(kFull, x[v][js], cq & 31);

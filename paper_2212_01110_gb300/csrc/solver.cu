@@ -232,7 +232,7 @@ static Workspace* get_ws_impl(Problem& P, int mem) {
     // one wave of the dual kernel (its register count leaves three resident
     // 128-thread blocks per SM in FP32, two in FP64): fewer end-of-block
     // statistics reductions
-    ws->grid_d = std::min((P.tree.n + kWarpsPerBlock - 1) / kWarpsPerBlock, sms * (sizeof(S) == 8 ? 2 : 3));
+    ws->grid_d = std::min((P.tree.n + kWarpsPerBlock - 1) / kWarpsPerBlock, sms * (sizeof(S) == 8 ? 2 : 4));
     ws->grid_d = std::max(ws->grid_d, 1);
     ws->grid_v = sms * 4;
     ws->pd = (double*)ws->alloc(sizeof(double) * 8 * ws->grid_d);
