@@ -46,12 +46,13 @@ def measured_peaks():
 
 
 # DRAM bytes (read + write) per chain node of one launch of the backward
-# chain kernel, from an ncu capture on the 17,749-node tree (branching 4 for
-# 6 stages, N = 9: 4,096 chains of 3 nonleaf nodes, nx = 50, nu = 20), scaled
-# by the chain nodes of the measured tree (each chain node's factors are read
-# once).  Valid for the kernel as captured (None: not captured since the
-# kernel last changed); remeasure after changing it.
-NCU_TRAFFIC_PER_CHAIN_NODE = {"fp64": 594.511104e6 / (4096 * 3), "fp32": None}
+# chain kernel (k_bwd_chain<double> / k_bwd_chain_tma<float>), from ncu
+# captures on the 17,749-node tree (branching 4 for 6 stages, N = 9: 4,096
+# chains of 3 nonleaf nodes, nx = 50, nu = 20), scaled by the chain nodes of
+# the measured tree (each chain node's factors are read once).  Valid for the
+# kernels as captured (None: not captured since the kernel last changed);
+# remeasure after changing them.
+NCU_TRAFFIC_PER_CHAIN_NODE = {"fp64": 594.511104e6 / (4096 * 3), "fp32": 296.087040e6 / (4096 * 3)}
 NCU_CHAIN_SHAPE = (50, 20)   # nx, nu of the capture
 
 
@@ -746,6 +747,7 @@ def grad_workload(args, spock, workloads, dev):
     zm_, _, infm = solve(P, d["x0"] - h * dirv, base)
     conv += [infp.status == 0, infm.status == 0]
     fd_its = [infp.iterations, infm.iterations]
+    fd_xi = [infp.xi, infm.xi]
     checks["x0"] = ((float(zp_[0].item()) - float(zm_[0].item())) / (2 * h), float(ge[0] @ dirv),
                     float(ga[0] @ dirv))
     P.close()
@@ -765,13 +767,14 @@ def grad_workload(args, spock, workloads, dev):
             vals.append(float(zz[0].item()))
             conv.append(inf_.status == 0)
             fd_its.append(inf_.iterations)
+            fd_xi.append(inf_.xi)
             PP.close()
         checks[key] = ((vals[0] - vals[1]) / (2 * h), an_e, an_a)
     out["fd_check"] = {
         "tree": "instance 0 of the workload (607 nodes)", "h": h, "solve_tol": 1e-12,
         "directions": "x0: unit N(0, 1); Q, R: X <- X (1 + h dX); A, B: X <- X + h dX; dX ~ N(0, 1) per entry",
-        "converged": all(conv), "base_iterations": inf0.iterations,
-        "perturbed_solve_iterations": fd_its,
+        "converged": all(conv), "base_iterations": inf0.iterations, "base_xi": inf0.xi,
+        "perturbed_solve_iterations": fd_its, "perturbed_xi_max": max(fd_xi),
         **{k: {"central_fd": fd, "envelope": ae, "adjoint": aa,
                "rel_err_envelope": abs(ae - fd) / max(abs(fd), 1e-12),
                "rel_err_adjoint": abs(aa - fd) / max(abs(fd), 1e-12)} for k, (fd, ae, aa) in checks.items()}}
@@ -976,7 +979,7 @@ def main():
                     help="instances of the gradient measurement (0 skips it)")
     ap.add_argument("--grad-iter", type=int, default=20000,
                     help="iteration cap per instance of the gradient workload's solve")
-    ap.add_argument("--grad-fd-iter", type=int, default=60000,
+    ap.add_argument("--grad-fd-iter", type=int, default=30000,
                     help="iteration cap of the 1e-12 solves of the finite-difference check")
     ap.add_argument("--horizon", type=int, default=20,
                     help="horizon N of the tree (20 = the 62,805-node tree; shorter chains for profiling)")

@@ -14,8 +14,13 @@
 // column's entry is broadcast with a shuffle and every lane accumulates the
 // rows it owns, reading the matrix column-major (lanes over rows: coalesced).
 // The adjoint rows use the transposed copy of each matrix the same way.
-// Everything else -- the y / s rows of the risk constraints, the cone
-// projections and the statistics -- is as in the box form.
+// Risk measures are in the conic form of Sec. "Conic representation of risk
+// measures": per nonleaf node k, y^k has ny_k rows, the row s^k - b^kT y^k
+// reads all of them, (K^k)* = R^kp_+ x R^(ny - kp) in S3, and the projection
+// on S2^k is the node's dense projector applied by the same warp
+// matrix-vector product (AV@R without a given risk measure: the closed form).
+// The cone projections of the cost epigraphs and the statistics are as in
+// the box form.
 #include "kernels.cuh"
 #include "ops_body.cuh"
 #include "spock_internal.h"

@@ -229,10 +229,11 @@ static Workspace* get_ws_impl(Problem& P, int mem) {
     ws->zero_eta = ws->alloc(sizeof(double) * (size_t)P.off.n_eta);
     CUDA_TRY(cudaMemset(ws->zero_eta, 0, sizeof(double) * (size_t)P.off.n_eta));
     const int sms = sm_count();
-    // one wave of the dual kernel (its register count leaves three resident
-    // 128-thread blocks per SM in FP32, two in FP64): fewer end-of-block
-    // statistics reductions
-    ws->grid_d = std::min((P.tree.n + kWarpsPerBlock - 1) / kWarpsPerBlock, sms * (sizeof(S) == 8 ? 2 : 4));
+    // one wave of the fused dual kernel (fewer end-of-block statistics
+    // reductions): the box form's FP64 kernel holds 238 registers (two
+    // resident 128-thread blocks per SM), the others at most 128 (four)
+    const int per_sm = (sizeof(S) == 8 && !P.general) ? 2 : 4;
+    ws->grid_d = std::min((P.tree.n + kWarpsPerBlock - 1) / kWarpsPerBlock, sms * per_sm);
     ws->grid_d = std::max(ws->grid_d, 1);
     ws->grid_v = sms * 4;
     ws->pd = (double*)ws->alloc(sizeof(double) * 8 * ws->grid_d);
