@@ -715,7 +715,7 @@ def grad_workload(args, spock, workloads, dev):
 
     tight_base = tight
     tight = spock.spock_default_settings(precision=spock.SPOCK_FP64, eps_abs=1e-12, eps_rel=1e-12, memory=5,
-                                         max_iter=4 * args.grad_fd_iter)
+                                         max_iter=args.grad_base_iter)
     t_fd = time.perf_counter()
     z, e, inf0 = solve(P, d["x0"])
     tight = tight_base
@@ -979,6 +979,8 @@ def main():
                     help="instances of the gradient measurement (0 skips it)")
     ap.add_argument("--grad-iter", type=int, default=20000,
                     help="iteration cap per instance of the gradient workload's solve")
+    ap.add_argument("--grad-base-iter", type=int, default=250000,
+                    help="iteration cap of the finite-difference check's base solve to 1e-12")
     ap.add_argument("--grad-fd-iter", type=int, default=30000,
                     help="iteration cap of the 1e-12 solves of the finite-difference check")
     ap.add_argument("--horizon", type=int, default=20,

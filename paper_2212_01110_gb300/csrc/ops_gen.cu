@@ -29,28 +29,43 @@ namespace spock {
 
 // y[v][j] += sum_q M(e - r0, q) x[v][c0 + q] for the entries e = lane + 32 j
 // in [r0, r0 + nrows), v < NV; M (nrows x ncols) column-major with leading
-// dimension ld.  All lanes of the warp call it (the shuffles).
+// dimension ld.  All lanes of the warp call it (the shuffles).  The next
+// column's entries are loaded while the current column is applied (one
+// column of lookahead: two loads per lane slot in flight).
 template <typename S, int J, int NV, int NA>
 __device__ __forceinline__ void wmv(const S* __restrict__ M, int ld, int nrows, int r0, int ncols, int c0,
                                     const S (&x)[NA][J], S (&y)[NA][J], int lane) {
+  if (ncols <= 0) return;
+  bool live[J];
 #pragma unroll
-  for (int js = 0; js < J; ++js) {
-    const int qlo = max(32 * js, c0), qhi = min(32 * js + 32, c0 + ncols);
-    for (int cq = qlo; cq < qhi; ++cq) {   // warp-uniform bounds
-      S xv[NV];
+  for (int j = 0; j < J; ++j) {
+    const int r = lane + 32 * j - r0;
+    live[j] = r >= 0 && r < nrows;
+  }
+  auto load = [&](int q, S (&m)[J]) {
+    const S* col = M + (int64_t)q * ld - r0;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) xv[v] = __shfl_sync(kFull, x[v][js], cq & 31);
-      const S* col = M + (int64_t)(cq - c0) * ld;
+    for (int j = 0; j < J; ++j) m[j] = live[j] ? __ldg(col + lane + 32 * j) : S(0);
+  };
+  S cur[J], nxt[J];
+  load(0, cur);
+  for (int q = 0; q < ncols; ++q) {   // warp-uniform bounds
+    if (q + 1 < ncols) load(q + 1, nxt);
+    const int cq = c0 + q;
+    S xv[NV];
 #pragma unroll
-      for (int j = 0; j < J; ++j) {
-        const int r = lane + 32 * j - r0;
-        if (r >= 0 && r < nrows) {
-          const S mv = __ldg(col + r);
+    for (int js = 0; js < J; ++js) {
+      if (js == (cq >> 5)) {
 #pragma unroll
-          for (int v = 0; v < NV; ++v) y[v][j] = fma(mv, xv[v], y[v][j]);
-        }
+        for (int v = 0; v < NV; ++v) xv[v] = __shfl_sync(kFull, x[v][js], cq & 31);
       }
     }
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) y[v][j] = fma(cur[j], xv[v], y[v][j]);
+#pragma unroll
+    for (int j = 0; j < J; ++j) cur[j] = nxt[j];
   }
 }
 
