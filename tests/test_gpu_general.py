@@ -277,3 +277,51 @@ def test_invalid_general_inputs():
     with pytest.raises(spock.SpockError) as ei:
         spock.Problem(bad)
     assert ei.value.code == spock.SPOCK_ERR_INVALID_ARG
+
+
+def test_general_kernels_at_launch_scale_equal_the_box_kernels():
+    """The 17,749-node tree (branching 4 for 6 stages, then 4,096 chains;
+    nx = 50, nu = 20) written twice: in the box form and in the general form
+    with Gamma = I and the diagonal costs as dense matrices.  The two define
+    the same L, so one evaluation of T (FP64) and one CP step through the
+    solve path's kernels with statistics (FP64 and FP32) agree element by
+    element: the general kernels at the benchmark's launch shapes (many
+    blocks per SM, every node of a stage in flight) against the box-form
+    kernels, which are parity-tested against the oracle and riccati_cpu."""
+    import torch
+    from paper_2212_01110_gb300 import spock, workloads as W
+    d = W.large_tree(seed=0, branching_stages=6, N=9)
+    n, nx, nu = len(d["anc"]), d["nx"], d["nu"]
+    g = dict(d)
+    g["Q"] = np.zeros((n, nx, nx))
+    g["R"] = np.zeros((n, nu, nu))
+    g["QN"] = np.zeros((n, nx, nx))
+    idx_x, idx_u = np.arange(nx), np.arange(nu)
+    g["Q"][:, idx_x, idx_x] = d["Q"]
+    g["R"][:, idx_u, idx_u] = d["R"]
+    g["QN"][:, idx_x, idx_x] = d["QN"]
+    Pb, Pg = spock.Problem(d), spock.Problem(g)   # Q dense: SPOCK_DENSE_COST, boxes as Gamma = I
+    assert (Pb.n_z, Pb.n_eta) == (Pg.n_z, Pg.n_eta)
+    assert Pb.norm_L * (1 - 1e-12) <= Pg.norm_L <= Pb.norm_L * (1 + 1e-6)
+    dev = torch.device("cuda:0")
+    x0 = torch.tensor(d["x0"], dtype=torch.float64, device=dev)
+    alpha = 0.99 / Pg.norm_L
+    rng = np.random.default_rng(5)
+    z0 = torch.tensor(rng.standard_normal(Pb.n_z), dtype=torch.float64, device=dev)
+    e0 = torch.tensor(rng.standard_normal(Pb.n_eta), dtype=torch.float64, device=dev)
+    outs = []
+    for P in (Pb, Pg):
+        zo, eo = torch.empty_like(z0), torch.empty_like(e0)
+        spock.spock_T_dev(P.handle, x0, alpha, z0, e0, zo, eo)
+        outs.append(torch.cat([zo, eo]).cpu().numpy())
+    assert rel_err(outs[1], outs[0]) < 1e-12
+    for prec, tol in ((spock.SPOCK_FP64, 1e-12), (spock.SPOCK_FP32, 2e-6)):
+        res = []
+        for P in (Pb, Pg):
+            z, e = z0.clone(), e0.clone()
+            xi = spock.spock_cp_step_dev(P.handle, x0, 1, alpha, prec, z, e)
+            res.append((torch.cat([z, e]).cpu().numpy(), xi))
+        assert rel_err(res[1][0], res[0][0]) < tol
+        assert abs(res[1][1] - res[0][1]) <= 1e3 * tol * max(1.0, res[0][1])
+    Pb.close()
+    Pg.close()
