@@ -97,7 +97,7 @@ typedef struct spock_settings {
                            taken when FP32 stagnates                       (1)    */
   int32_t stall_window; /* FP32 stagnation: no halving of xi in this many
                            iterations while xi <= 30 x tolerance hands over
-                           to FP64 (0 = never)                              (500)  */
+                           to FP64 (0 = never)                             (2000)  */
 } spock_settings;
 
 /* Outcome of a solve. */

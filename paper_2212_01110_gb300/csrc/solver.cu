@@ -2085,7 +2085,7 @@ int spock_default_settings(spock_settings* s) {
   s->trace = nullptr;
   s->profile = 0;
   s->fp64_tail = 1;
-  s->stall_window = 500;
+  s->stall_window = 2000;   // near the tolerance the FP32 iteration can take ~500 iterations to halve xi
   return SPOCK_OK;
 }
 
