@@ -146,41 +146,47 @@ __global__ void k_jt_residual(int64_t nz, int64_t ne, double alpha, const double
 }
 
 // partials[block][j] = sum over the block's entries of u . V_j, j < k
+// (k <= kGmresMaxRestart), in chunks of 32 basis vectors held in registers
 __global__ void __launch_bounds__(256) k_dots(int64_t n, const double* __restrict__ u, const double* __restrict__ V,
                                               int64_t ld, int k, double* __restrict__ partials) {
-  double acc[kGmresMaxBasis];
-#pragma unroll
-  for (int j = 0; j < kGmresMaxBasis; ++j) acc[j] = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double ui = u[i];
-#pragma unroll
-    for (int j = 0; j < kGmresMaxBasis; ++j)
-      if (j < k) acc[j] = fma(ui, V[(int64_t)j * ld + i], acc[j]);
-  }
   __shared__ double red[8][kGmresMaxBasis];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int c0 = 0; c0 < k; c0 += kGmresMaxBasis) {
+    const int kc = min(kGmresMaxBasis, k - c0);
+    const double* Vc = V + (int64_t)c0 * ld;
+    double acc[kGmresMaxBasis];
 #pragma unroll
-  for (int j = 0; j < kGmresMaxBasis; ++j) {
-    if (j < k) {
-      const double v = warp_sum(acc[j]);
-      if (lane == 0) red[w][j] = v;
+    for (int j = 0; j < kGmresMaxBasis; ++j) acc[j] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+      const double ui = u[i];
+#pragma unroll
+      for (int j = 0; j < kGmresMaxBasis; ++j)
+        if (j < kc) acc[j] = fma(ui, Vc[(int64_t)j * ld + i], acc[j]);
     }
-  }
-  __syncthreads();
-  if (threadIdx.x < k) {
-    double sum = 0.0;
-    for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) sum += red[ww][threadIdx.x];
-    partials[(int64_t)blockIdx.x * kGmresMaxBasis + threadIdx.x] = sum;
+#pragma unroll
+    for (int j = 0; j < kGmresMaxBasis; ++j) {
+      if (j < kc) {
+        const double v = warp_sum(acc[j]);
+        if (lane == 0) red[w][j] = v;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < kc) {
+      double sum = 0.0;
+      for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) sum += red[ww][threadIdx.x];
+      partials[(int64_t)blockIdx.x * kGmresMaxRestart + c0 + threadIdx.x] = sum;
+    }
+    __syncthreads();
   }
 }
 
 // out[j] = sum_b partials[b][j], j < k (one block, fixed order)
 __global__ void k_dots_reduce(int nblocks, int k, const double* __restrict__ partials, double* __restrict__ out) {
-  const int j = threadIdx.x;
-  if (j >= k) return;
-  double s = 0.0;
-  for (int b = 0; b < nblocks; ++b) s += partials[(int64_t)b * kGmresMaxBasis + j];
-  out[j] = s;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partials[(int64_t)b * kGmresMaxRestart + j];
+    out[j] = s;
+  }
 }
 
 // u += sign * sum_{j < k} h_j V_j  (h on the device, k <= kGmresMaxRestart)
@@ -299,15 +305,12 @@ void launch_jt_residual(int64_t nz, int64_t ne, double alpha, const double* pz, 
   k_jt_residual<<<grid, 256, 0, st>>>(nz, ne, alpha, pz, t, q, Lp, x, u);
 }
 
-// out[j] = u . V_j for j < k, in launches of 32 basis vectors; partials
-// holds grid x 32 doubles
+// out[j] = u . V_j for j < k (k <= 128) in two launches; partials holds
+// grid x 128 doubles
 void launch_dots(int64_t n, const double* u, const double* V, int64_t ld, int k, double* partials, double* out,
                  int grid, cudaStream_t st) {
-  for (int c = 0; c < k; c += kGmresMaxBasis) {
-    const int kc = std::min(kGmresMaxBasis, k - c);
-    k_dots<<<grid, 256, 0, st>>>(n, u, V + (int64_t)c * ld, ld, kc, partials);
-    k_dots_reduce<<<1, kGmresMaxBasis, 0, st>>>(grid, kc, partials, out + c);
-  }
+  k_dots<<<grid, 256, 0, st>>>(n, u, V, ld, k, partials);
+  k_dots_reduce<<<1, kGmresMaxRestart, 0, st>>>(grid, k, partials, out);
 }
 
 void launch_axpy_many(int64_t n, double* u, const double* V, int64_t ld, int k, const double* h, double sign,

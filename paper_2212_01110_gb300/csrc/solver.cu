@@ -1538,7 +1538,7 @@ static int adjoint_impl(Problem& P, const double* z, const double* eta, const do
   }
   const int m = P.adj_restart;
   const size_t len = (size_t)ntot + 3 * (size_t)ne + 6 * (size_t)nz + 2 * n * xs + xs + 2 +
-                     (size_t)(m + 1) * ldv + 2 * (size_t)ntot + (size_t)gvec * 32 + 3 * (size_t)(m + 1) + 8;
+                     (size_t)(m + 1) * ldv + 2 * (size_t)ntot + (size_t)gvec * 128 + 3 * (size_t)(m + 1) + 8;
   if (!P.adj) {
     CUDA_TRY(cudaMalloc(&P.adj, sizeof(double) * len));
     P.allocations.push_back(P.adj);
@@ -1560,10 +1560,10 @@ static int adjoint_impl(Problem& P, const double* z, const double* eta, const do
   double* V = zero_x0 + xs + 2;        // basis, stride ldv
   double* u = V + (size_t)(m + 1) * ldv;
   double* res = u + ntot;              // true residual b - (I - J^T) w
-  double* part = res + ntot;           // dot partials [gvec][32]
+  double* part = res + ntot;           // dot partials [gvec][128]
   // [m + 1] Hessenberg column, [m + 1] its second Gram-Schmidt pass, [1] norm;
   // then [m + 1] the solution of the small least-squares problem
-  double* hdev = part + (size_t)gvec * 32;
+  double* hdev = part + (size_t)gvec * 128;
   double* hdev2 = hdev + (m + 1);
   double* hnorm = hdev2 + (m + 1);
   double* ydev = hnorm + 1;
