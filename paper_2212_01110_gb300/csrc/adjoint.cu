@@ -146,9 +146,12 @@ __global__ void k_jt_residual(int64_t nz, int64_t ne, double alpha, const double
 }
 
 // partials[block][j] = sum over the block's entries of u . V_j, j < k
-// (k <= kGmresMaxRestart), in chunks of 32 basis vectors held in registers
+// (k <= kGmresMaxRestart), in chunks of 32 basis vectors held in registers.
+// With kdev, k is *kdev + k (the basis size of a captured Arnoldi step).
 __global__ void __launch_bounds__(256) k_dots(int64_t n, const double* __restrict__ u, const double* __restrict__ V,
-                                              int64_t ld, int k, double* __restrict__ partials) {
+                                              int64_t ld, int k, const int* __restrict__ kdev,
+                                              double* __restrict__ partials) {
+  if (kdev) k += *kdev;
   __shared__ double red[8][kGmresMaxBasis];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int c0 = 0; c0 < k; c0 += kGmresMaxBasis) {
@@ -181,7 +184,9 @@ __global__ void __launch_bounds__(256) k_dots(int64_t n, const double* __restric
 }
 
 // out[j] = sum_b partials[b][j], j < k (one block, fixed order)
-__global__ void k_dots_reduce(int nblocks, int k, const double* __restrict__ partials, double* __restrict__ out) {
+__global__ void k_dots_reduce(int nblocks, int k, const int* __restrict__ kdev, const double* __restrict__ partials,
+                              double* __restrict__ out) {
+  if (kdev) k += *kdev;
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     double s = 0.0;
     for (int b = 0; b < nblocks; ++b) s += partials[(int64_t)b * kGmresMaxRestart + j];
@@ -189,9 +194,11 @@ __global__ void k_dots_reduce(int nblocks, int k, const double* __restrict__ par
   }
 }
 
-// u += sign * sum_{j < k} h_j V_j  (h on the device, k <= kGmresMaxRestart)
+// u += sign * sum_{j < k} h_j V_j  (h on the device, k <= kGmresMaxRestart;
+// with kdev, k is *kdev + k)
 __global__ void k_axpy_many(int64_t n, double* __restrict__ u, const double* __restrict__ V, int64_t ld, int k,
-                            const double* __restrict__ h, double sign) {
+                            const int* __restrict__ kdev, const double* __restrict__ h, double sign) {
+  if (kdev) k += *kdev;
   __shared__ double hs[kGmresMaxRestart];
   for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = sign * h[j];
   __syncthreads();
@@ -207,6 +214,23 @@ __global__ void k_scale(int64_t n, double a, const double* __restrict__ u, doubl
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     v[i] = a * u[i];
 }
+
+// The next basis vector of a captured Arnoldi step: V_{k+1} = vin = u / ||u||
+// with k = *kdev and ||u||^2 = *norm2 (0 when the norm vanishes)
+__global__ void k_next_basis(int64_t n, const double* __restrict__ u, const double* __restrict__ norm2,
+                             const int* __restrict__ kdev, double* __restrict__ V, int64_t ld,
+                             double* __restrict__ vin) {
+  const double nn = *norm2;
+  const double a = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+  double* vk1 = V + (int64_t)(*kdev + 1) * ld;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = a * u[i];
+    vk1[i] = v;
+    vin[i] = v;
+  }
+}
+
+__global__ void k_inc(int* kdev) { *kdev += 1; }
 
 // red[0] = max |b - u|, red[1] = max |x| (bit patterns of non-negative
 // doubles), r = b - u written out; b = (g, 0)
@@ -305,17 +329,23 @@ void launch_jt_residual(int64_t nz, int64_t ne, double alpha, const double* pz, 
   k_jt_residual<<<grid, 256, 0, st>>>(nz, ne, alpha, pz, t, q, Lp, x, u);
 }
 
-// out[j] = u . V_j for j < k (k <= 128) in two launches; partials holds
-// grid x 128 doubles
-void launch_dots(int64_t n, const double* u, const double* V, int64_t ld, int k, double* partials, double* out,
-                 int grid, cudaStream_t st) {
-  k_dots<<<grid, 256, 0, st>>>(n, u, V, ld, k, partials);
-  k_dots_reduce<<<1, kGmresMaxRestart, 0, st>>>(grid, k, partials, out);
+// out[j] = u . V_j for j < k (k <= 128; plus *kdev when kdev is given) in
+// two launches; partials holds grid x 128 doubles
+void launch_dots(int64_t n, const double* u, const double* V, int64_t ld, int k, const int* kdev, double* partials,
+                 double* out, int grid, cudaStream_t st) {
+  k_dots<<<grid, 256, 0, st>>>(n, u, V, ld, k, kdev, partials);
+  k_dots_reduce<<<1, kGmresMaxRestart, 0, st>>>(grid, k, kdev, partials, out);
 }
 
-void launch_axpy_many(int64_t n, double* u, const double* V, int64_t ld, int k, const double* h, double sign,
-                      int grid, cudaStream_t st) {
-  k_axpy_many<<<grid, 256, 0, st>>>(n, u, V, ld, k, h, sign);
+void launch_axpy_many(int64_t n, double* u, const double* V, int64_t ld, int k, const int* kdev, const double* h,
+                      double sign, int grid, cudaStream_t st) {
+  k_axpy_many<<<grid, 256, 0, st>>>(n, u, V, ld, k, kdev, h, sign);
+}
+
+void launch_next_basis(int64_t n, const double* u, const double* norm2, int* kdev, double* V, int64_t ld,
+                       double* vin, int grid, cudaStream_t st) {
+  k_next_basis<<<grid, 256, 0, st>>>(n, u, norm2, kdev, V, ld, vin);
+  k_inc<<<1, 1, 0, st>>>(kdev);
 }
 
 void launch_scale(int64_t n, double a, const double* u, double* v, int grid, cudaStream_t st) {

@@ -190,6 +190,7 @@ Problem::~Problem() {
   delete ws64;
   delete ws32;
   for (void* p : allocations) cudaFree(p);
+  if (adj_pinned) cudaFreeHost(adj_pinned);
 }
 
 static int sm_count() {
@@ -1464,10 +1465,12 @@ void launch_cone_jac(const KP<double>& p, const double* wbar, const double* x, d
 void launch_axpy(int64_t n, double a, const double* x, const double* y, double* out, int grid, cudaStream_t st);
 void launch_jt_residual(int64_t nz, int64_t ne, double alpha, const double* pz, const double* t, const double* q,
                         const double* Lp, const double* x, double* u, int grid, cudaStream_t st);
-void launch_dots(int64_t n, const double* u, const double* V, int64_t ld, int k, double* partials, double* out,
-                 int grid, cudaStream_t st);
-void launch_axpy_many(int64_t n, double* u, const double* V, int64_t ld, int k, const double* h, double sign,
-                      int grid, cudaStream_t st);
+void launch_dots(int64_t n, const double* u, const double* V, int64_t ld, int k, const int* kdev, double* partials,
+                 double* out, int grid, cudaStream_t st);
+void launch_axpy_many(int64_t n, double* u, const double* V, int64_t ld, int k, const int* kdev, const double* h,
+                      double sign, int grid, cudaStream_t st);
+void launch_next_basis(int64_t n, const double* u, const double* norm2, int* kdev, double* V, int64_t ld,
+                       double* vin, int grid, cudaStream_t st);
 void launch_scale(int64_t n, double a, const double* u, double* v, int grid, cudaStream_t st);
 void launch_true_residual(int64_t nz, int64_t ntot, const double* g, const double* u, const double* x, double* r,
                           unsigned long long* red, int grid, cudaStream_t st);
@@ -1521,6 +1524,11 @@ static int adjoint_impl(Problem& P, const double* z, const double* eta, const do
                         int32_t* iters_out, double* res_out, cudaStream_t st) {
   if (P.general) return fail(SPOCK_ERR_UNSUPPORTED, "adjoint: box constraints and diagonal costs only");
   Workspace* ws = get_ws_impl<double>(P, 0);
+  // the inputs were produced on the caller's stream; the solve runs on the
+  // workspace's own stream (a CUDA graph cannot be captured on the legacy
+  // default stream) and is synchronised before returning
+  CUDA_TRY(cudaStreamSynchronize(st));
+  st = ws->stream;
   const int64_t nz = P.off.n_z, ne = P.off.n_eta, ntot = nz + ne;
   const size_t n = (size_t)P.tree.n, nx = (size_t)P.nx, nu = (size_t)P.nu;
   const size_t xs = (size_t)P.f64.xs;
@@ -1538,11 +1546,13 @@ static int adjoint_impl(Problem& P, const double* z, const double* eta, const do
   }
   const int m = P.adj_restart;
   const size_t len = (size_t)ntot + 3 * (size_t)ne + 6 * (size_t)nz + 2 * n * xs + xs + 2 +
-                     (size_t)(m + 1) * ldv + 2 * (size_t)ntot + (size_t)gvec * 128 + 3 * (size_t)(m + 1) + 8;
+                     (size_t)(m + 1) * ldv + 3 * (size_t)ntot + (size_t)gvec * 128 + 3 * (size_t)(m + 1) + 8;
   if (!P.adj) {
     CUDA_TRY(cudaMalloc(&P.adj, sizeof(double) * len));
     P.allocations.push_back(P.adj);
   }
+  const size_t nh = 2 * (size_t)(m + 1) + 1;   // Hessenberg column, second pass, norm
+  if (!P.adj_pinned) CUDA_TRY(cudaMallocHost(&P.adj_pinned, sizeof(double) * nh));
   double* w = P.adj;
   double* wbar = w + ntot;
   double* q = wbar + ne;
@@ -1567,6 +1577,8 @@ static int adjoint_impl(Problem& P, const double* z, const double* eta, const do
   double* hdev2 = hdev + (m + 1);
   double* hnorm = hdev2 + (m + 1);
   double* ydev = hnorm + 1;
+  double* vin = ydev + (m + 1) + 1;    // the current basis vector (input of the captured step)
+  int* kdev = reinterpret_cast<int*>(ydev + (m + 1));   // basis index of the captured step
   const double alpha = default_alpha(P, 0.0);
   KP<double> kp = make_kp<double>(P, alpha, P.idx.stage_begin);
   KP<double> kA = kp;   // Jacobian of prox_{alpha f}: no shift of s^0, x0 = 0
@@ -1602,7 +1614,7 @@ static int adjoint_impl(Problem& P, const double* z, const double* eta, const do
     launch_jt_residual(nz, ne, alpha, pv, t, q, Lp, x, out, gvec, st);
   };
   auto dots = [&](const double* a, int k, double* out_dev, std::vector<double>& out_host) {
-    launch_dots(ntot, a, V, (int64_t)ldv, k, part, out_dev, gvec, st);
+    launch_dots(ntot, a, V, (int64_t)ldv, k, nullptr, part, out_dev, gvec, st);
     out_host.resize(k);
     CUDA_TRY(cudaMemcpyAsync(out_host.data(), out_dev, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
@@ -1621,7 +1633,34 @@ static int adjoint_impl(Problem& P, const double* z, const double* eta, const do
     if (!std::isfinite(rinf)) throw SpockError(SPOCK_ERR_NUMERICAL, "the adjoint solve diverged");
   };
   int it = 0;   // applications of J^T inside the Arnoldi steps
-  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gam(m + 1), hv, y(m), hh(2 * (size_t)(m + 1) + 1);
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gam(m + 1), hv, y(m);
+  const double* hh = P.adj_pinned;
+  // one Arnoldi step, captured once and replayed: u = (I - J^T) vin; two
+  // classical Gram-Schmidt passes against V_0 .. V_k (k = *kdev); ||u||^2;
+  // the coefficients copied to pinned host memory; V_{k+1} = vin = u / ||u||
+  cudaGraphExec_t step = nullptr;
+  {
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    apply_op(vin, u);
+    launch_dots(ntot, u, V, (int64_t)ldv, 1, kdev, part, hdev, gvec, st);
+    launch_axpy_many(ntot, u, V, (int64_t)ldv, 1, kdev, hdev, -1.0, gvec, st);
+    launch_dots(ntot, u, V, (int64_t)ldv, 1, kdev, part, hdev2, gvec, st);
+    launch_axpy_many(ntot, u, V, (int64_t)ldv, 1, kdev, hdev2, -1.0, gvec, st);
+    launch_dots(ntot, u, u, 0, 1, nullptr, part, hnorm, gvec, st);   // ||u||^2 (V stride 0: u itself)
+    cudaMemcpyAsync(P.adj_pinned, hdev, sizeof(double) * nh, cudaMemcpyDeviceToHost, st);
+    launch_next_basis(ntot, u, hnorm, kdev, V, (int64_t)ldv, vin, gvec, st);
+    CUDA_TRY(cudaStreamEndCapture(st, &g));
+    const cudaError_t e = cudaGraphInstantiate(&step, g, 0);
+    cudaGraphDestroy(g);
+    CUDA_TRY(e);
+  }
+  struct StepGuard {
+    cudaGraphExec_t& s;
+    ~StepGuard() {
+      if (s) cudaGraphExecDestroy(s);
+    }
+  } step_guard{step};
   true_residual();
   while (!(rinf <= tol * std::max(1.0, winf)) && it < max_iter) {
     // v_0 = res / ||res||
@@ -1630,28 +1669,19 @@ static int adjoint_impl(Problem& P, const double* z, const double* eta, const do
     const double beta = std::sqrt(std::max(hv[0], 0.0));
     if (!(beta > 0.0)) break;
     launch_scale(ntot, 1.0 / beta, res, V, gvec, st);
+    CUDA_TRY(cudaMemcpyAsync(vin, V, sizeof(double) * ntot, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaMemsetAsync(kdev, 0, sizeof(int), st));
     std::fill(gam.begin(), gam.end(), 0.0);
     gam[0] = beta;
     const double thr = tol * std::max(1.0, winf);
     int k = 0;
     for (; k < m && it < max_iter; ++k) {
-      double* vk1 = V + (size_t)(k + 1) * ldv;
-      apply_op(V + (size_t)k * ldv, u);
-      ++it;
-      // classical Gram-Schmidt, twice, with the coefficients kept on the
-      // device; one copy to the host per step
-      launch_dots(ntot, u, V, (int64_t)ldv, k + 1, part, hdev, gvec, st);
-      launch_axpy_many(ntot, u, V, (int64_t)ldv, k + 1, hdev, -1.0, gvec, st);
-      launch_dots(ntot, u, V, (int64_t)ldv, k + 1, part, hdev2, gvec, st);
-      launch_axpy_many(ntot, u, V, (int64_t)ldv, k + 1, hdev2, -1.0, gvec, st);
-      launch_dots(ntot, u, u, 0, 1, part, hnorm, gvec, st);   // ||u||^2 (V stride 0: u itself)
-      CUDA_TRY(cudaMemcpyAsync(hh.data(), hdev, sizeof(double) * (2 * (size_t)(m + 1) + 1), cudaMemcpyDeviceToHost,
-                               st));
+      CUDA_TRY(cudaGraphLaunch(step, st));
       CUDA_TRY(cudaStreamSynchronize(st));
+      ++it;
       const double hn = std::sqrt(std::max(hh[2 * (size_t)(m + 1)], 0.0));
       for (int i = 0; i <= k; ++i) H[(size_t)i * m + k] = hh[i] + hh[(size_t)(m + 1) + i];
       H[(size_t)(k + 1) * m + k] = hn;
-      if (hn > 0.0) launch_scale(ntot, 1.0 / hn, u, vk1, gvec, st);
       // Givens rotations on the new column
       for (int i = 0; i < k; ++i) {
         const double a = H[(size_t)i * m + k], b = H[(size_t)(i + 1) * m + k];
@@ -1678,7 +1708,7 @@ static int adjoint_impl(Problem& P, const double* z, const double* eta, const do
       y[i] = H[(size_t)i * m + i] != 0.0 ? sum / H[(size_t)i * m + i] : 0.0;
     }
     CUDA_TRY(cudaMemcpyAsync(ydev, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
-    launch_axpy_many(ntot, w, V, (int64_t)ldv, k, ydev, 1.0, gvec, st);
+    launch_axpy_many(ntot, w, V, (int64_t)ldv, k, nullptr, ydev, 1.0, gvec, st);
     CUDA_TRY(cudaStreamSynchronize(st));   // y is a host buffer
     true_residual();
   }

@@ -136,6 +136,7 @@ struct Problem {
   double* io_grad = nullptr;   // outputs of spock_grad (host-buffer variant)
   double* adj = nullptr;       // vectors of the adjoint solve (spock_adjoint_dev)
   int32_t adj_restart = 0;     // its GMRES restart length, fixed at the first call
+  double* adj_pinned = nullptr;  // pinned host copy of a GMRES step's coefficients
   // solver workspace, allocated on first use per precision
   struct Workspace* ws64 = nullptr;
   struct Workspace* ws32 = nullptr;
