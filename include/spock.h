@@ -440,7 +440,9 @@ int spock_grad_dev(spock_problem* p, const double* z, const double* eta, int32_t
  * on the data's directions).  Uses the problem's Riccati scratch: not
  * concurrent with solves on the same problem.  Device vectors (the Krylov
  * basis: m + 1 vectors of n_z + n_eta doubles, and about 12 more) are
- * allocated on the first call and kept by the problem.  Blocking.
+ * allocated on the first call and kept by the problem.  Runs on the
+ * problem's own stream after synchronising `stream` (one Arnoldi step is
+ * captured into a CUDA graph and replayed).  Blocking.
  */
 int spock_adjoint_dev(spock_problem* p, const double* z, const double* eta, const double* g_z, int32_t max_iter,
                       double tol, double* g_x0, double* g_A, double* g_B, double* g_Q, double* g_R, double* g_QN,
