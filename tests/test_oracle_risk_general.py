@@ -115,3 +115,39 @@ def test_tv_radius_zero_is_the_expectation():
     assert res.status == "converged"
     V, x, u = tree_lqr(P, d["x0"])
     assert abs(res.v[0] - V) <= 1e-7 * max(1.0, abs(V))
+
+
+def test_norm_with_risk_measures_matches_power_iteration():
+    """||L|| from the column-group blocks, with the (y, s) blocks of general
+    b vectors (total variation: ny = 3m + 2), against a power iteration."""
+    from oracle.linop import norm_L_blocks, norm_L_power
+    d = workloads.risk_measures(workloads.general_random(workloads.small_binary(3), seed=4), "tv", radius=0.4)
+    P = Problem(d)
+    ref = norm_L_power(build_L(P), iters=20000)
+    assert abs(norm_L_blocks(P) - ref) <= 1e-7 * ref
+
+
+def test_expectation_as_a_conic_risk_measure_is_tree_lqr():
+    """The expectation written as a conic risk measure with ambiguity set
+    {pi}: b = (pi, -pi), E = [I; -I], K = R^2m_+ (mu <= pi and mu >= pi), no F.
+    With loose constraints the solve is the tree LQR."""
+    base = workloads.small_binary(2, a=0.5)
+    n = len(base["anc"])
+    big = 1e6
+    base = dict(base)
+    base["xmin"], base["xmax"] = -big * np.ones((n, base["nx"])), big * np.ones((n, base["nx"]))
+    base["umin"], base["umax"] = -big * np.ones((n, base["nu"])), big * np.ones((n, base["nu"]))
+    kids = [[c for c in range(1, n) if base["anc"][c] == i] for i in range(n)]
+    risk = [None] * n
+    for i in range(n):
+        if kids[i]:
+            pi = np.asarray(base["prob"])[kids[i]]
+            m = len(pi)
+            risk[i] = dict(b=np.concatenate([pi, -pi]), E=np.vstack([np.eye(m), -np.eye(m)]),
+                           F=np.zeros((2 * m, 0)), kp=2 * m)
+    d = dict(base, risk=risk)
+    P = Problem(d)
+    res = spock(CP(P), d["x0"], s=TIGHT)
+    assert res.status == "converged"
+    V, _, _ = tree_lqr(Problem(dict(base, a=np.ones(n))), d["x0"])
+    assert abs(res.v[0] - V) <= 1e-7 * max(1.0, abs(V))
