@@ -38,3 +38,28 @@ def test_chain_launch_bytes():
     assert bench.bytes_bwd_chain(d, 4096, 14, 4) == 1375600640
     assert bench.flops_bwd_chain(d, 4096, 14) == 676659200.0
     assert bench.bytes_fwd_chain(d, 4096, 14, 4) == 1053655040
+
+
+def test_clock_summary_parses_nvidia_smi_rows(tmp_path):
+    """The clocks record of the timed region: median SM clock under load, the
+    maximum clock, and every throttle reason seen Active in any sample (rows
+    as nvidia-smi --format=csv,noheader,nounits writes them; a malformed row
+    is skipped)."""
+    rows = [
+        "0, 2070, 2070, 812.40, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.10, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2040, 2070, 1201.00, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070",
+    ]
+    path = tmp_path / "clocks.csv"
+    path.write_text("\n".join(rows) + "\n")
+    c = bench.Clocks(0)
+    c.path = str(path)
+    s = c.summary()
+    assert s["sm_mhz"] == 2040.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    rows[0] = rows[0].replace("Not Active, Not Active, Not Active, Not Active",
+                              "Active, Not Active, Active, Not Active")
+    path.write_text("\n".join(rows) + "\n")
+    assert c.summary()["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
+    assert bench.Clocks(0).summary()["reasons"] == ["unavailable"]
