@@ -106,7 +106,7 @@ bool riccati_factor(const Tree& t, int nx, int nu, const std::vector<double>& A,
     std::vector<char> okv(nth, 1);
     auto work = [&](int tid) {
       std::vector<double> Pt(nu * nx), Rt(nu * nu), SA(nu * nx), K(nu * nx), Ab(nx * nx),
-          PA(nx * nx), W(nx * nu), Rinv(nu * nu), tmp(nx * nx);
+          PA(nx * nx), W(nx * nu), Rinv(nu * nu), PB(nx * nu);
       for (int32_t k = b0 + tid; k < b1; k += nth) {
         const int32_t c0 = t.ch_begin[k], m = t.ch_count[k];
         std::fill(Rt.begin(), Rt.end(), 0.0);
@@ -159,8 +159,8 @@ bool riccati_factor(const Tree& t, int nx, int nu, const std::vector<double>& A,
           gemm(nx, nx, nx, Pc, Ab.data(), PA.data());
           gemm_tn_acc(nx, nx, nx, Ab.data(), PA.data(), Pi);
           // W += Abar^T (P B)
-          gemm(nx, nx, nu, Pc, Bc, tmp.data());
-          gemm_tn_acc(nx, nx, nu, Ab.data(), tmp.data(), W.data());
+          gemm(nx, nx, nu, Pc, Bc, PB.data());
+          gemm_tn_acc(nx, nx, nu, Ab.data(), PB.data(), W.data());
           // store [Abar | B] rows
           double* g = &Gb[(size_t)(c - 1) * gsz];
           for (int r = 0; r < nx; ++r) {

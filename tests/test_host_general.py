@@ -132,8 +132,9 @@ def _run(driver, d, tmp_path):
     return json.loads(r.stdout)
 
 
-def test_matrices_factors_and_norm(driver, tmp_path):
-    d = W.general_random(W.random_tree(3, N=3, max_branch=3, nx=5, nu=3), seed=1, extra_rows=3, extra_leaf_rows=2)
+@pytest.mark.parametrize("nx,nu", [(5, 3), (2, 5)])
+def test_matrices_factors_and_norm(driver, tmp_path, nx, nu):
+    d = W.general_random(W.random_tree(3, N=3, max_branch=3, nx=nx, nu=nu), seed=1, extra_rows=3, extra_leaf_rows=2)
     out = _run(driver, d, tmp_path)
     assert out["rc"] == 0
     P = Problem(d)

@@ -27,6 +27,7 @@ CASES = {
     "wide_50_20": lambda: W.large_tree(0, branching_stages=2, branch=3, N=5, nx=50, nu=20),
     "datacenter": lambda: W.datacenter(N=4, nx=6),
     "root_17_2": lambda: W.with_tree(W.tree_from_branching([17, 2])[0], seed=10, nx=4, nu=2, a=0.3),
+    "nu_gt_nx": lambda: W.random_tree(9, N=3, max_branch=4, nx=2, nu=5),
 }
 
 
