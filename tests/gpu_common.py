@@ -60,4 +60,8 @@ def cases():
         # per SM for the direct kernels, several chains per block in the
         # persistent loops of the staged kernels
         "chains_1024_50_20": W.large_tree(3, branching_stages=5, branch=4, N=8, nx=50, nu=20),
+        # more inputs than states: nu > nx, and nu > 32 with chains below two
+        # branching stages (the input-indexed loops and slots of every kernel)
+        "nu_gt_nx": W.random_tree(9, N=3, max_branch=4, nx=2, nu=5),
+        "wide_20_50": W.large_tree(1, branching_stages=2, branch=3, N=5, nx=20, nu=50),
     }
