@@ -64,4 +64,8 @@ def cases():
         # branching stages (the input-indexed loops and slots of every kernel)
         "nu_gt_nx": W.random_tree(9, N=3, max_branch=4, nx=2, nu=5),
         "wide_20_50": W.large_tree(1, branching_stages=2, branch=3, N=5, nx=20, nu=50),
+        # horizon 1: a root and one leaf (a chain of one step), a root and
+        # five leaves (one branching stage, no chain region)
+        "two_nodes": W.with_tree(W.tree_from_branching([1])[0], seed=11, nx=3, nu=2),
+        "N1_star": W.with_tree(W.tree_from_branching([5])[0], seed=12, nx=3, nu=2),
     }

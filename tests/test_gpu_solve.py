@@ -65,7 +65,7 @@ def test_spock_fixed_k_replayed(pair):
     assert same >= K - 2, (free.trace, tr)
 
 
-@pytest.mark.parametrize("name", ["binary_N3", "fig1", "ragged", "chains"])
+@pytest.mark.parametrize("name", ["binary_N3", "fig1", "ragged", "chains", "two_nodes", "N1_star"])
 def test_spock_converged(name):
     from paper_2212_01110_gb300 import spock
     pair = Pair(CASES[name])

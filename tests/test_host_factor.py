@@ -148,6 +148,8 @@ CASES = {
     "chains": lambda: W.random_tree(7, N=6, max_branch=3, nx=3, nu=2, chain_after=2),
     "wide_nu_gt_nx": lambda: W.random_tree(9, N=3, max_branch=4, nx=2, nu=5),
     "branch4_stage3": lambda: W.large_tree(seed=3, branching_stages=3, branch=4, N=4, nx=6, nu=3),
+    "two_nodes": lambda: W.with_tree(W.tree_from_branching([1])[0], seed=11, nx=3, nu=2),
+    "N1_star": lambda: W.with_tree(W.tree_from_branching([5])[0], seed=12, nx=3, nu=2),
 }
 
 
