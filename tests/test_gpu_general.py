@@ -44,6 +44,10 @@ def general_cases():
                                        extra_rows=14, extra_leaf_rows=3),
         "poly_root_40": W.general_random(W.with_tree(W.tree_from_branching([40, 1])[0], seed=9, nx=3, nu=2),
                                          seed=6),
+        # more inputs than states (R^1/2 blocks larger than Q^1/2; nu > 32)
+        "poly_nu_gt_nx": W.general_random(W.random_tree(9, N=3, max_branch=4, nx=2, nu=5), seed=7),
+        "poly_wide_20_50": W.general_random(W.large_tree(1, branching_stages=2, branch=3, N=5, nx=20, nu=50),
+                                            seed=8, extra_rows=6, extra_leaf_rows=4),
         # conic risk measures (b, E, F, K): total variation (n_nu = m, zero-cone
         # row), mean-AV@R, AV@R in general form on a 30-child root
         # (z_2 block of 121 entries: four lane slots)
