@@ -28,7 +28,8 @@ CASES = cases()
 TOL_FP32_T = {1: 2e-6, 25: 5e-6}
 
 
-@pytest.fixture(scope="module", params=["chains", "wide_50_20", "root_40", "datacenter_N6", "chains_1024_50_20"])
+@pytest.fixture(scope="module", params=["chains", "wide_50_20", "root_40", "datacenter_N6", "chains_1024_50_20",
+                                        "wide_20_50"])
 def pair(request):
     return Pair(CASES[request.param])
 
