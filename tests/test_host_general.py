@@ -22,6 +22,7 @@ from oracle.problem import Problem
 from paper_2212_01110_gb300 import workloads as W
 
 HERE = os.path.dirname(os.path.abspath(__file__))
+SANITIZE = ["-fsanitize=address,undefined", "-fno-sanitize-recover=all", "-fno-omit-frame-pointer", "-g"]
 CSRC = os.path.join(HERE, "..", "paper_2212_01110_gb300", "csrc")
 INC = os.path.join(HERE, "..", "include")
 
@@ -98,7 +99,11 @@ def driver(tmp_path_factory):
     exe = d / "driver"
     cmd = [gxx, "-std=c++17", "-O1", "-I", CSRC, "-I", INC, "-I", cuda_inc, str(src),
            os.path.join(CSRC, "general.cpp"), os.path.join(CSRC, "tree.cpp"), "-o", str(exe), "-lpthread"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
+    # address and undefined-behaviour sanitizers where the toolchain has them:
+    # an out-of-bounds write in the host code fails the run
+    r = subprocess.run(cmd[:1] + SANITIZE + cmd[1:], capture_output=True, text=True)
+    if r.returncode != 0:
+        r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     return str(exe)
 
