@@ -66,3 +66,91 @@ def test_riccati_projection_is_a_projection_on_a_larger_tree():
     p1 = rc.prox_f(z, 0.0)
     assert _rel(p1, cp.prox_f(z, d["x0"]) + np.eye(1, cp.n_z, 0)[0] * cp.alpha) < TOL
     assert _rel(rc.prox_f(p1, 0.0), p1) < TOL
+
+
+SAN_DRIVER = r"""
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+extern "C" {
+void* rc_create(int32_t, const int32_t*, const double*, int32_t, int32_t, const double*, const double*,
+                const double*, const double*, const double*, const double*, const double*, const double*,
+                const double*, const double*, int32_t);
+void rc_sizes(void*, int64_t*, int64_t*);
+void rc_T(void*, const double*, double, const double*, const double*, double*, double*);
+void rc_free(void*);
+}
+static std::vector<double> rd(FILE* f, size_t n) { std::vector<double> v(n); for (auto& x : v) if (fscanf(f, "%lf", &x) != 1) exit(3); return v; }
+int main(int argc, char** argv) {
+  FILE* f = fopen(argv[1], "r");
+  int n, nx, nu, th;
+  if (fscanf(f, "%d %d %d %d", &n, &nx, &nu, &th) != 4) return 2;
+  std::vector<int32_t> anc(n);
+  for (auto& a : anc) if (fscanf(f, "%d", &a) != 1) return 3;
+  auto prob = rd(f, n), A = rd(f, (size_t)n * nx * nx), B = rd(f, (size_t)n * nx * nu), Q = rd(f, (size_t)n * nx),
+       R = rd(f, (size_t)n * nu), QN = rd(f, (size_t)n * nx), a = rd(f, n), xmin = rd(f, (size_t)n * nx),
+       xmax = rd(f, (size_t)n * nx), umin = rd(f, (size_t)n * nu), umax = rd(f, (size_t)n * nu), x0 = rd(f, nx),
+       al = rd(f, 1);
+  void* h = rc_create(n, anc.data(), prob.data(), nx, nu, A.data(), B.data(), Q.data(), R.data(), QN.data(), a.data(),
+                      xmin.data(), xmax.data(), umin.data(), umax.data(), th);
+  int64_t nz = 0, ne = 0;
+  rc_sizes(h, &nz, &ne);
+  auto z = rd(f, nz), e = rd(f, ne);
+  std::vector<double> zo(nz), eo(ne);
+  rc_T(h, x0.data(), al[0], z.data(), e.data(), zo.data(), eo.data());
+  for (auto v : zo) printf("%.17g\n", v);
+  for (auto v : eo) printf("%.17g\n", v);
+  rc_free(h);
+  return 0;
+}
+"""
+
+
+def test_sanitized_build_gives_the_same_T(tmp_path):
+    """The C++ operator built with the address and undefined-behaviour
+    sanitizers runs T without a finding (an out-of-bounds access fails the
+    run) on shapes that stress its indexing -- horizon 1, nu > nx, a node
+    with 17 children, chains -- with three threads, and gives the library
+    build's T to 1e-13."""
+    import os
+    import shutil
+    import subprocess
+    from oracle import riccati_cpu
+    gxx = shutil.which("g++")
+    if not gxx:
+        pytest.skip("g++ not available")
+    src = tmp_path / "drv.cpp"
+    src.write_text(SAN_DRIVER)
+    exe = tmp_path / "drv"
+    cmd = [gxx, "-std=c++17", "-O1", "-g", "-fopenmp", "-fsanitize=address,undefined", "-fno-sanitize-recover=all",
+           "-fno-omit-frame-pointer", str(src), riccati_cpu.SRC, "-o", str(exe)]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.skip("sanitizer build unavailable: " + r.stderr[-200:])
+    cases = {
+        "two_nodes": W.with_tree(W.tree_from_branching([1])[0], seed=11, nx=3, nu=2),
+        "N1_star": W.with_tree(W.tree_from_branching([5])[0], seed=12, nx=3, nu=2),
+        "nu_gt_nx": W.random_tree(9, N=3, max_branch=4, nx=2, nu=5),
+        "root_17_2": CASES["root_17_2"](),
+        "chains": CASES["chains"](),
+    }
+    env = dict(os.environ, ASAN_OPTIONS="detect_leaks=1", OMP_NUM_THREADS="3")
+    for name, d in cases.items():
+        cp = CP(Problem(d))
+        rng = np.random.default_rng(5)
+        z = rng.standard_normal(cp.n_z)
+        e = rng.standard_normal(cp.n_eta)
+        parts = [f"{len(d['anc'])} {d['nx']} {d['nu']} 3", " ".join(map(str, np.asarray(d["anc"], int)))]
+        for k in ("prob", "A", "B", "Q", "R", "QN", "a", "xmin", "xmax", "umin", "umax", "x0"):
+            parts.append(" ".join(repr(float(v)) for v in np.asarray(d[k], float).ravel()))
+        parts += [repr(float(cp.alpha)), " ".join(repr(float(v)) for v in z), " ".join(repr(float(v)) for v in e)]
+        inp = tmp_path / f"{name}.txt"
+        inp.write_text("\n".join(parts) + "\n")
+        r = subprocess.run([str(exe), str(inp)], capture_output=True, text=True, env=env)
+        assert r.returncode == 0, (name, r.stderr[-2000:])
+        got = np.array([float(v) for v in r.stdout.split()])
+        rc = RiccatiCPU(d, threads=3)
+        zo, eo = rc.T(z, e, cp.alpha)
+        rc.close()
+        assert _rel(got, np.concatenate([zo, eo])) < 1e-13, name
