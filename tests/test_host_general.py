@@ -186,8 +186,20 @@ def test_matrices_factors_and_norm(driver, tmp_path, nx, nu):
     assert lam * (1 - 1e-12) <= out["normL2_xu"] <= lam * (1 + 1e-6)
 
 
-def test_risk_projectors_and_offsets(driver, tmp_path):
-    d = W.risk_measures(W.general_random(W.with_tree(W.fig1_tree(), seed=2, nx=3, nu=2), seed=3), "tv", radius=0.3)
+RISK_CASES = {
+    "tv_fig1": lambda: W.risk_measures(W.general_random(W.with_tree(W.fig1_tree(), seed=2, nx=3, nu=2), seed=3),
+                                       "tv", radius=0.3),
+    # z_2 block of 121 entries at the root (AV@R in conic form, 30 children)
+    "avar_root_30": lambda: W.risk_measures(
+        W.general_random(W.with_tree(W.tree_from_branching([30, 1])[0], seed=9, nx=3, nu=2), seed=4), "avar"),
+    "mean_avar_nu_gt_nx": lambda: W.risk_measures(
+        W.general_random(W.random_tree(9, N=3, max_branch=4, nx=2, nu=5), seed=5), "mean_avar"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(RISK_CASES))
+def test_risk_projectors_and_offsets(driver, tmp_path, name):
+    d = RISK_CASES[name]()
     out = _run(driver, d, tmp_path)
     assert out["rc"] == 0
     P = Problem(d)
