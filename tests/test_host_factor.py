@@ -192,3 +192,26 @@ def test_threaded_factorisation_is_bitwise_the_serial_one(driver, tmp_path):
     one = _factor(driver, d, 1, tmp_path)
     four = _factor(driver, d, 4, tmp_path)
     assert one["Gb"] == four["Gb"] and one["NB"] == four["NB"]
+
+
+@pytest.mark.parametrize("anc,prob", [
+    ([0, 0, 0], [1.0, 0.5, 0.5]),            # root's ancestor is not -1
+    ([-1, 3, 0], [1.0, 0.5, 0.5]),           # ancestor out of range
+    ([-1, -2, 0], [1.0, 0.5, 0.5]),          # negative ancestor below the root
+    ([-1, 2, 1], [1.0, 1.0, 1.0]),           # cycle not reachable from the root
+    ([-1, 0, 0, 1], [1.0, 0.5, 0.5, 1.0]),   # leaves at different stages
+    ([-1, 0, 0], [1.0, 0.5, 0.4]),           # child probabilities do not sum to 1
+    ([-1, 0, 0], [1.0, 1.5, -0.5]),          # a negative probability
+    ([-1, 0, 0], [1.0, float("nan"), 0.5]),  # NaN probability
+])
+def test_invalid_trees_are_rejected_cleanly(driver, tmp_path, anc, prob):
+    """build_tree turns every malformed ancestor array or probability
+    vector into an error return, with no out-of-bounds access on the way
+    (the driver runs under the sanitizers)."""
+    n, nx, nu = len(anc), 1, 1
+    parts = [f"{n} {nx} {nu} 1", " ".join(map(str, anc)), " ".join(repr(float(p)) for p in prob),
+             " ".join(["0.5"] * (n * nx * nx)), " ".join(["1.0"] * (n * nx * nu))]
+    inp = tmp_path / "bad.txt"
+    inp.write_text("\n".join(parts) + "\n")
+    r = subprocess.run([driver, str(inp)], capture_output=True, text=True)
+    assert r.returncode == 5 and "tree error" in r.stdout, (r.returncode, r.stdout, r.stderr[-1500:])
