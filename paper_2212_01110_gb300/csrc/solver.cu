@@ -2631,6 +2631,7 @@ int spock_batch_solve_dev(spock_batch* batch, const double* const* x0_dev, const
     if (settings) s = *settings;
     if (s.memory < 0 || s.memory > kMaxMemory) return fail(SPOCK_ERR_INVALID_ARG, "memory must be in 0..16");
     if (!(s.eps_abs > 0) || !(s.eps_rel >= 0)) return fail(SPOCK_ERR_INVALID_ARG, "tolerances must be positive");
+    if (s.max_iter < 0 || s.max_backtracks < 0) return fail(SPOCK_ERR_INVALID_ARG, "negative cap");
     for (size_t i = 0; i < B->probs.size(); ++i) {
       if (!x0_dev[i] || !z_dev[i] || !eta_dev[i]) return fail(SPOCK_ERR_INVALID_ARG, "NULL instance buffer");
       if (s.alpha > 0 && s.alpha * B->probs[i]->normL >= 1.0)
