@@ -10,8 +10,11 @@ not involved.
 Prints, for the 85-node member (branching 4 for 2 stages, N = 6, nx = 10,
 nu = 4): xi of vanilla CP every 1,000 iterations up to 20,000; SPOCK with
 Anderson memory 3 and 10 up to 20,000 iterations; and the variants with the
-boxes removed, with a = 1, and with uniform child probabilities; finally the
-components of the residual that remain largest after 8,000 CP iterations.
+boxes removed, with a = 1, and with uniform child probabilities; the
+components of the residual that remain largest after 8,000 CP iterations;
+finally SPOCK (memory 5) to 1e-6 on a 31-node member (branching 3 for 2
+stages, N = 4, nx = 10, nu = 4) with the Dirichlet child probabilities and
+with uniform ones.
 """
 from __future__ import annotations
 
@@ -25,9 +28,12 @@ from oracle.problem import Problem
 from oracle.spock import Settings, spock
 
 
-def member(variant=""):
+def member(variant="", small=False):
     from paper_2212_01110_gb300 import workloads as W
-    d = W.large_tree(seed=0, branching_stages=2, N=6, nx=10, nu=4)
+    if small:
+        d = W.large_tree(seed=0, branching_stages=2, branch=3, N=4, nx=10, nu=4)
+    else:
+        d = W.large_tree(seed=0, branching_stages=2, N=6, nx=10, nu=4)
     if "nobox" in variant:
         for k in ("xmin", "umin"):
             d[k][:] = -1e3
@@ -88,6 +94,11 @@ def main(quick=False):
         print(f"SPOCK m={m}: status {r.status}, {r.k} iterations, {r.n_T} evaluations of T, "
               f"branches {dict(Counter(t[0] for t in r.trace))}, xi every {len(h) // 10}: "
               + ", ".join(f"{h[k]:.1e}" for k in range(0, len(h), max(1, len(h) // 10))), flush=True)
+    for variant in ("", "uniform"):
+        d = member(variant, small=True)
+        r = spock(CP(Problem(d)), d["x0"], s=Settings(memory=5, max_iter=iters))
+        print(f"SPOCK m=5 on the 31-node member, {variant or 'Dirichlet'} probabilities: status {r.status}, "
+              f"{r.k} iterations, branches {dict(Counter(t[0] for t in r.trace))}", flush=True)
 
 
 if __name__ == "__main__":
