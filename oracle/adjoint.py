@@ -42,7 +42,7 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from .cones import proj_soc, s2_matrix, z2_block
+from .cones import s2_matrix, z2_block
 from .cp import CP
 
 

@@ -13,7 +13,6 @@ tolerance on the GPU.  Marshalling only: every step runs in libspock.
 """
 from __future__ import annotations
 
-import numpy as np
 import torch
 
 from . import spock

@@ -2,7 +2,6 @@
 import json
 import os
 
-import numpy as np
 import pytest
 
 from oracle.tree import Tree, TreeError
