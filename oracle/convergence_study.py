@@ -15,6 +15,11 @@ components of the residual that remain largest after 8,000 CP iterations;
 finally SPOCK (memory 5) to 1e-6 on a 31-node member (branching 3 for 2
 stages, N = 4, nx = 10, nu = 4) with the Dirichlet child probabilities and
 with uniform ones.
+
+    python -m oracle.convergence_study --batch   # about 15 minutes
+
+instead runs SPOCK (memory 3, at most 10,000 iterations) on the six smallest
+and the median-size instance of the batched workload (512 instances, seed 0).
 """
 from __future__ import annotations
 
@@ -101,5 +106,22 @@ def main(quick=False):
               f"{r.k} iterations, branches {dict(Counter(t[0] for t in r.trace))}", flush=True)
 
 
+def batch_members():
+    from paper_2212_01110_gb300 import workloads as W
+    ds = W.batch_instances(seed=0, count=512)
+    order = sorted(range(len(ds)), key=lambda i: len(ds[i]["anc"]) * (ds[i]["nx"] + ds[i]["nu"]))
+    for i in order[:6] + [order[len(order) // 2]]:
+        d = ds[i]
+        cp = CP(Problem(d))
+        r = spock(cp, d["x0"], s=Settings(max_iter=10000))
+        h = r.xi_hist
+        print(f"instance {i}: {len(d['anc'])} nodes, nx {d['nx']}, nu {d['nu']}, ||L|| {cp.normL:.2f}: "
+              f"{r.status} after {r.k} iterations, branches {dict(Counter(t[0] for t in r.trace))}, xi "
+              + ", ".join(f"{h[k]:.1e}" for k in range(0, len(h), max(1, len(h) // 8))), flush=True)
+
+
 if __name__ == "__main__":
-    main(quick="--quick" in sys.argv)
+    if "--batch" in sys.argv:
+        batch_members()
+    else:
+        main(quick="--quick" in sys.argv)
