@@ -92,3 +92,40 @@ def test_fig1_tree_accepted(lib):
     assert lib.spock_tree_info(t, C.byref(n), C.byref(N), C.byref(nl)) == 0
     assert (n.value, N.value, nl.value) == (9, g["N"], len(g["nonleaf"]))
     spock.spock_free(t)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures (settings, info, risk measure) have
+    the header's field order, offsets and sizes: a C program compiled
+    against include/spock.h prints offsetof / sizeof for every field the
+    binding declares (a field missing from the header fails to compile)."""
+    import json
+    import shutil
+    import subprocess
+    from paper_2212_01110_gb300 import spock
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = {"spock_settings": spock.Settings, "spock_info": spock.Info, "spock_risk": spock.Risk}
+    cname = {"lambda_": "lambda"}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "spock.h"', "int main(void) {", 'printf("{");']
+    first = True
+    for sname, cls in structs.items():
+        for fname, _ in cls._fields_:
+            c = cname.get(fname, fname)
+            sep = "" if first else ","
+            first = False
+            lines.append(f'printf("{sep}\\"{sname}.{fname}\\": %zu", offsetof({sname}, {c}));')
+        lines.append(f'printf(",\\"{sname}.sizeof\\": %zu", sizeof({sname}));')
+    lines += ['printf("}\\n");', "return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = json.loads(subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout)
+    for sname, cls in structs.items():
+        for fname, _ in cls._fields_:
+            assert got[f"{sname}.{fname}"] == getattr(cls, fname).offset, (sname, fname)
+        assert got[f"{sname}.sizeof"] == C.sizeof(cls), sname
