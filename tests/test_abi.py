@@ -129,3 +129,44 @@ def test_struct_layouts_match_the_header(tmp_path):
         for fname, _ in cls._fields_:
             assert got[f"{sname}.{fname}"] == getattr(cls, fname).offset, (sname, fname)
         assert got[f"{sname}.sizeof"] == C.sizeof(cls), sname
+
+
+def _header_prototypes():
+    src = open(os.path.join(ROOT, "include", "spock.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"^\s*(int|void|const char\*)\s+(spock_\w+)\s*\(([^;]*?)\)\s*;", src, flags=re.M | re.S):
+        args = [a.strip() for a in m.group(3).replace("\n", " ").split(",") if a.strip() and a.strip() != "void"]
+        out[m.group(2)] = (m.group(1), args)
+    return out
+
+
+def _c_kind(arg):
+    if "*" in arg:
+        return "ptr"
+    typ = " ".join(arg.split()[:-1]).replace("const ", "")
+    return {"int32_t": "i32", "int": "i32", "int64_t": "i64", "double": "f64"}[typ]
+
+
+def _py_kind(t):
+    if t in (C.c_int32, C.c_int):
+        return "i32"
+    if t is C.c_int64:
+        return "i64"
+    if t is C.c_double:
+        return "f64"
+    return "ptr"
+
+
+def test_binding_signatures_match_the_header():
+    """Every function's argument count and the kind of each argument (32-bit
+    integer, 64-bit integer, double or pointer) and its return type agree
+    between include/spock.h and the binding's ctypes declarations."""
+    from paper_2212_01110_gb300 import spock
+    protos = _header_prototypes()
+    assert set(protos) == set(spock._sig)
+    for name, (ret, args) in protos.items():
+        pargs, pres = spock._sig[name]
+        assert [_c_kind(a) for a in args] == [_py_kind(t) for t in pargs], name
+        want = {"int": C.c_int, "void": None, "const char*": C.c_char_p}[ret]
+        assert pres is want, name
