@@ -170,3 +170,26 @@ def test_binding_signatures_match_the_header():
         assert [_c_kind(a) for a in args] == [_py_kind(t) for t in pargs], name
         want = {"int": C.c_int, "void": None, "const char*": C.c_char_p}[ret]
         assert pres is want, name
+
+
+def test_risk_marshalling():
+    """spock_risk entries built by the binding carry each node's sizes and
+    point at row-major copies of b, E and F that stay alive with the array
+    (leaves: zeroed entries)."""
+    from paper_2212_01110_gb300 import spock, workloads
+    d = workloads.risk_measures(workloads.small_binary(1, a=0.5), "tv", radius=0.3)
+    arr, keep = spock._risk_array(d["risk"])
+    assert len(arr) == len(d["risk"])
+    for i, r in enumerate(d["risk"]):
+        e = arr[i]
+        if r is None:
+            assert e.ny == 0 and not e.b
+            continue
+        b, E = np.asarray(r["b"], float), np.asarray(r["E"], float)
+        F = np.asarray(r.get("F", np.zeros((b.size, 0))), float)
+        assert (e.ny, e.n_nu, e.kp) == (b.size, F.shape[1] if F.ndim == 2 else 0, int(r["kp"]))
+        np.testing.assert_array_equal(np.ctypeslib.as_array(e.b, (b.size,)), b)
+        np.testing.assert_array_equal(np.ctypeslib.as_array(e.E, (E.size,)), E.ravel())
+        if e.n_nu:
+            np.testing.assert_array_equal(np.ctypeslib.as_array(e.F, (F.size,)), F.ravel())
+    assert keep
