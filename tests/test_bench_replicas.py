@@ -65,3 +65,33 @@ def test_cpu_baseline_leg_runs_on_the_host():
     out = bench.cpu_baseline(d, seconds=0.2, threads=2)
     assert out["kind"] == "oracle" and out["value"] > 0 and out["cores"] == 2
     assert out["one_thread"]["value"] > 0 and out["nproc"] == cores
+
+
+def test_reference_arm_line():
+    """bench.py --impl reference prints one JSON line with the contract's
+    keys (the oracle's C++ operator on the host cores, on the benchmark's
+    own tree); under a multi-rank launch only rank 0 prints."""
+    import json
+    import subprocess
+    root = os.path.dirname(HERE)
+    env = dict(os.environ, OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
+                       cwd=root, capture_output=True, text=True, env=env, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 1
+    assert line["higher_is_better"] is True and line["vs_baseline"] is None
+    assert "workload" in line["config"]
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    r1 = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
+                        cwd=root, capture_output=True, text=True, timeout=120,
+                        env=dict(env, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1"))
+    assert r1.returncode == 0 and not r1.stdout.strip()
