@@ -69,6 +69,7 @@ int main(int argc, char** argv) {
   GenHost g; std::string err;
   int rc = build_general(t, nx, nu, dense != 0, Q.data(), R.data(), QN.data(), a.data(), hasrisk ? risk.data() : nullptr,
                          nc, Gx.data(), Gu.data(), cmin.data(), cmax.data(), ncN, GN.data(), cNmin.data(), cNmax.data(), 2, g, err);
+  if (rc != SPOCK_OK) { printf("{\"rc\": %d}\n", rc); return 0; }   // as the library: nothing else is built
   Offsets o;
   build_offsets(t, nx, nu, nc, ncN, &g.ny_user, o);
   printf("{\"rc\": %d,\n", rc);
@@ -230,3 +231,43 @@ def test_risk_projectors_and_offsets(driver, tmp_path, name):
     # (y, s) block norm: [[I, 0], [-b^T, 1]]
     ys = max((2 + b @ b + np.sqrt((b @ b) * (b @ b + 4))) / 2 for b, _, _, _ in P.risk.values())
     assert abs(out["normL2_ys"] - ys) <= 1e-12 * ys
+
+
+def _bad_risk(kind):
+    d = W.risk_measures(W.general_random(W.with_tree(W.fig1_tree(), seed=2, nx=3, nu=2), seed=3), "tv", radius=0.3)
+    risk = [None if r is None else dict(r) for r in d["risk"]]
+    i = next(k for k, r in enumerate(risk) if r is not None)
+    r = risk[i]
+    if kind == "kp_above_ny":
+        r["kp"] = len(r["b"]) + 1
+    elif kind == "rank_deficient_F":
+        F = np.asarray(r["F"], float)
+        r["F"] = np.hstack([F, F[:, :1]])           # a repeated column
+    elif kind == "nan_b":
+        r["b"] = np.asarray(r["b"], float).copy()
+        r["b"][0] = np.nan
+    return dict(d, risk=risk)
+
+
+@pytest.mark.parametrize("kind,code", [("kp_above_ny", -1), ("rank_deficient_F", -1), ("nan_b", -4),
+                                       ("too_large_z2", -1), ("indefinite_Q", -3), ("crossed_bounds", -1)])
+def test_invalid_inputs_are_rejected_cleanly(driver, tmp_path, kind, code):
+    """build_general returns the documented error for malformed risk
+    measures, an S2 block above 160 entries, an indefinite cost matrix and
+    crossed constraint bounds, with no out-of-bounds access on the way (the
+    driver runs under the sanitizers)."""
+    if kind in ("kp_above_ny", "rank_deficient_F", "nan_b"):
+        d = _bad_risk(kind)
+    elif kind == "too_large_z2":   # AV@R in conic form at a 60-child root: 121 + 120 entries
+        d = W.risk_measures(W.general_random(W.with_tree(W.tree_from_branching([60, 1])[0], seed=9, nx=3, nu=2),
+                                             seed=4), "avar")
+    elif kind == "indefinite_Q":
+        d = W.general_random(W.random_tree(3, N=3, max_branch=3, nx=4, nu=3), seed=1)
+        d["Q"] = np.array(d["Q"], float)
+        d["Q"][1] = -np.eye(4)
+    else:
+        d = W.general_random(W.random_tree(3, N=3, max_branch=3, nx=4, nu=3), seed=1)
+        d["cmin"] = np.array(d["cmin"], float)
+        d["cmin"][0, 0] = d["cmax"][0, 0] + 1.0
+    out = _run(driver, d, tmp_path)
+    assert out["rc"] == code
