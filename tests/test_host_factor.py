@@ -215,3 +215,25 @@ def test_invalid_trees_are_rejected_cleanly(driver, tmp_path, anc, prob):
     inp.write_text("\n".join(parts) + "\n")
     r = subprocess.run([driver, str(inp)], capture_output=True, text=True)
     assert r.returncode == 5 and "tree error" in r.stdout, (r.returncode, r.stdout, r.stderr[-1500:])
+
+
+def test_threaded_factorisation_has_no_data_race(tmp_path):
+    """The factorisation with four host threads per stage, built with the
+    thread sanitizer: no data race is reported."""
+    gxx = shutil.which("g++")
+    cuda_inc = next((p for p in ("/usr/local/cuda/include", "/usr/include") if
+                     os.path.exists(os.path.join(p, "cuda_runtime.h"))), None)
+    if not gxx or cuda_inc is None:
+        pytest.skip("g++ or cuda_runtime.h not available")
+    src = tmp_path / "driver.cpp"
+    src.write_text(DRIVER)
+    exe = tmp_path / "driver_tsan"
+    r = subprocess.run([gxx, "-std=c++17", "-O1", "-g", "-fsanitize=thread", "-I", CSRC, "-I", INC, "-I", cuda_inc,
+                        str(src), os.path.join(CSRC, "factor.cpp"), os.path.join(CSRC, "tree.cpp"), "-o", str(exe),
+                        "-lpthread"], capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.skip("thread sanitizer unavailable: " + r.stderr[-200:])
+    d = CASES["branch4_stage3"]()
+    out = _factor(str(exe), d, 4, tmp_path)   # fails on a sanitizer report (non-zero exit)
+    ref = _factor(str(exe), d, 1, tmp_path)
+    assert out["Gb"] == ref["Gb"] and out["NB"] == ref["NB"]
