@@ -37,7 +37,7 @@ from oracle.problem import Problem
 from oracle.spock import Settings, spock
 
 TOL = 1e-3
-PAPER = {3: 105, 6: 128}
+TABLE1 = {3: 105, 6: 128}   # iterations printed in Table 1
 
 
 def printed(N):
@@ -70,7 +70,7 @@ def main(sweep=False):
             for m in (3, 10):
                 nL, res = iterations(prob, m)
                 print(f"N = {N:2d}  {name:22s} ||L|| = {nL:.3f}  memory {m:2d}: {res.k:4d} iterations "
-                      f"({res.n_T} T, {res.status}), s0 = {res.v[0]:.6f}   [paper: {PAPER[N]}]", flush=True)
+                      f"({res.n_T} T, {res.status}), s0 = {res.v[0]:.6f}   [Table 1: {TABLE1[N]}]", flush=True)
     if sweep:
         d = printed(3)
         cp = CP(Problem(d))
