@@ -193,3 +193,37 @@ def test_risk_marshalling():
         if e.n_nu:
             np.testing.assert_array_equal(np.ctypeslib.as_array(e.F, (F.size,)), F.ravel())
     assert keep
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """A copy of the binding next to no built library raises ImportError on
+    import: there is no CPU fallback."""
+    import importlib.util
+    import shutil
+    pkg = tmp_path / "pkg"
+    pkg.mkdir()
+    shutil.copy(os.path.join(ROOT, "paper_2212_01110_gb300", "spock.py"), pkg / "spock.py")
+    spec = importlib.util.spec_from_file_location("spock_copy", pkg / "spock.py")
+    mod = importlib.util.module_from_spec(spec)
+    with pytest.raises(ImportError):
+        spec.loader.exec_module(mod)
+
+
+def test_status_codes_match_the_header():
+    from paper_2212_01110_gb300 import spock
+    src = open(os.path.join(ROOT, "include", "spock.h")).read()
+    for name, val in re.findall(r"\b(SPOCK_(?:OK|MAX_ITER|ERR_\w+|FP64|FP32))\s*=\s*(-?\d+)", src):
+        assert getattr(spock, name) == int(val), name
+    assert re.search(r"#define SPOCK_DENSE_COST (\d+)", src).group(1) == str(spock.SPOCK_DENSE_COST)
+
+
+def test_product_path_does_not_use_the_oracle():
+    """No module of the package imports, loads or runs anything under
+    oracle/ (the oracle is test infrastructure)."""
+    pkg = os.path.join(ROOT, "paper_2212_01110_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle\b", src, flags=re.M), f
+                assert "riccati_cpu" not in src and "oracle/" not in src, f
