@@ -227,3 +227,19 @@ def test_product_path_does_not_use_the_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle\b", src, flags=re.M), f
                 assert "riccati_cpu" not in src and "oracle/" not in src, f
+
+
+def test_oracle_uses_only_the_input_generators():
+    """The oracle imports nothing of the package but the seeded input
+    generators (workloads.py), which themselves hold no arithmetic of the
+    method: they import numpy only."""
+    odir = os.path.join(ROOT, "oracle")
+    for f in os.listdir(odir):
+        if f.endswith((".py", ".cpp")):
+            src = open(os.path.join(odir, f)).read()
+            for mod in re.findall(r"paper_2212_01110_gb300(?:\.(\w+)|\s+import\s+(\w+))", src):
+                assert "workloads" in mod, (f, mod)
+            assert "libspock" not in src and "csrc" not in src, f
+    wl = open(os.path.join(ROOT, "paper_2212_01110_gb300", "workloads.py")).read()
+    imports = set(re.findall(r"^\s*(?:from\s+(\S+)\s+import|import\s+(\S+))", wl, flags=re.M))
+    assert {m for pair in imports for m in pair if m} <= {"__future__", "numpy"}
