@@ -114,10 +114,9 @@ def test_datacenter_system():
         np.testing.assert_allclose(np.diag(Ac, 1), 0.01)
         np.testing.assert_allclose(np.diag(Ac, -1), 0.01)
         assert np.count_nonzero(np.triu(Ac, 2)) == 0 and np.count_nonzero(np.tril(Ac, -2)) == 0
-        if w == 1:
-            np.testing.assert_allclose(np.diag(Ac), 1.0)   # w = 1: the identity's diagonal
-        else:
-            assert np.all(np.diff(np.diag(Ac)) > 0)     # grows with j for w > 1
+        # A_jj(w) = 1 + (w - 1)/d (1 + (j - 1)/nx), d = 2 disturbance values
+        j = np.arange(1, 5)
+        np.testing.assert_allclose(np.diag(Ac), 1.0 + (w - 1) / 2.0 * (1.0 + (j - 1) / 4.0), rtol=0, atol=1e-15)
     np.testing.assert_array_equal(np.asarray(d["B"])[1], np.eye(4))
     assert np.all(d["Q"] == 1.0) and np.all(d["QN"] == 1.0) and np.all(d["R"] == 10.0)
     assert np.all(d["xmax"] == 1.0) and np.all(d["umax"] == 1.5)
