@@ -7,6 +7,7 @@ not involved.
 
     python -m oracle.table1_study            # a few minutes on one core
     python -m oracle.table1_study --sweep    # plus the SuperMann parameter sweep
+    python -m oracle.table1_study --fig1     # the Fig. 1 setting instead (about a minute)
 
 Prints, for horizons N = 3 and 6:
   * the problem as printed (R = 10 I): ||L||, and the iterations with
@@ -24,6 +25,11 @@ and with --sweep the best of 108 SuperMann parameter combinations (memory
 3/5/10, lambda 1/1.5/1.9, sigma 0.1/1e-2/1e-4, c0 = c1 = c2 0.99/0.9,
 beta 0.5/0.8) on the printed problem at N = 3.  The paper reports 105 (N = 3)
 and 128 (N = 6) iterations without printing its SuperMann parameters.
+
+With --fig1: the setting of Fig. 1 (N = 7, nx = nu = 5, tolerance 1e-5),
+printed and in scaled inputs, vanilla CP iterations and SPOCK iterations /
+evaluations of T to the tolerance (Fig. 1 plots xi against calls of L: 3,159
+for CP and 571 for SPOCK, with no statement of how calls are counted).
 """
 from __future__ import annotations
 
@@ -88,5 +94,29 @@ def main(sweep=False):
             print("  ", row)
 
 
+def fig1():
+    from paper_2212_01110_gb300 import workloads as W
+    d = W.datacenter(N=7, nx=5)
+    tol = 1e-5
+    for name, prob in (("printed (R = 10 I)", d), ("scaled inputs (R = I)", scaled_inputs(d))):
+        cp = CP(Problem(prob))
+        v = np.zeros(cp.n_z + cp.n_eta)
+        xi0 = None
+        k = 0
+        for k in range(1, 20001):   # vanilla CP: v <- T(v) until xi <= max(tol, tol xi0)
+            Tv = cp.T(v, prob["x0"])
+            xi = cp.stats(v, Tv)["xi"]
+            xi0 = xi if xi0 is None else xi0
+            if xi <= max(tol, tol * xi0):
+                break
+            v = Tv
+        r = spock(cp, prob["x0"], s=Settings(eps_abs=tol, eps_rel=tol, max_iter=20000))
+        print(f"Fig. 1 setting, {name:22s} ||L|| = {cp.normL:.3f}: vanilla CP {k} evaluations of T; "
+              f"SPOCK {r.k} iterations, {r.n_T} evaluations of T ({r.status})", flush=True)
+
+
 if __name__ == "__main__":
-    main(sweep="--sweep" in sys.argv)
+    if "--fig1" in sys.argv:
+        fig1()
+    else:
+        main(sweep="--sweep" in sys.argv)
