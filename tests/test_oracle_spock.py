@@ -127,3 +127,25 @@ def test_forced_replay_reproduces():
     r2 = spock(cp, d["x0"], s=s, forced=r1.trace)
     assert r1.trace == r2.trace
     np.testing.assert_array_equal(r1.v, r2.v)
+
+
+@pytest.mark.parametrize("x0v,ub", [(0.1, 1.5), (0.5, 0.6)])
+def test_scaled_inputs_are_the_same_problem(x0v, ub):
+    """The change of input u' = sqrt(10) u used by the Table 1 study (R = I,
+    B / sqrt(10), input box times sqrt(10)) leaves the problem unchanged: the
+    same optimal value, and the same inputs after scaling back."""
+    from oracle.risk import trajectory
+    from oracle.table1_study import scaled_inputs
+    d = workloads.datacenter(N=2, nx=3)
+    d["x0"] = np.full(3, x0v)
+    d["umin"][:] = -ub
+    d["umax"][:] = ub
+    res = []
+    for prob in (d, scaled_inputs(d)):
+        P = Problem(prob)
+        r = spock(CP(P), prob["x0"], s=Settings(eps_abs=1e-10, eps_rel=1e-10, max_iter=30000))
+        assert r.status == "converged"
+        res.append((r.v[0], trajectory(P, r.v[:P.lay.n_z])[1]))
+    (v1, u1), (v2, u2) = res
+    assert abs(v1 - v2) <= 1e-8 * max(1.0, abs(v1))
+    np.testing.assert_allclose(u2 / np.sqrt(10.0), u1, atol=1e-6)
